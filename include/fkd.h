@@ -1,0 +1,253 @@
+/*
+ * fkd.h -- C ABI of the GB300 masked keypoint detector for video.
+ *
+ * Method: Baroffio, Cesana, Redondi, Tagliasacchi, "Fast keypoint detection
+ * in video sequences" (arXiv 1503.06959). For every frame I_n the library
+ *   1. builds the scale-space pyramid of octaves c_i and intra-octaves d_i
+ *      (Sec. 2; Sec. 3.1 reuses it for the mask),
+ *   2. builds the detection mask M'_n on an N_r x N_c grid of bins, either by
+ *      the intensity difference test (Eq. 2, Sec. 3.1) or by keypoint
+ *      binning of D_{n-1} (Eqs. 3-4, Sec. 3.2), with the first frame of a
+ *      stream fully active,
+ *   3. runs the segment test (16-pixel radius-3 Bresenham ring, 9 contiguous
+ *      pixels brighter than I_p + t or darker than I_p - t), the corner score
+ *      and 3x3 non-maximum suppression on every layer, at pixels whose bin is
+ *      active (Sec. 2),
+ *   4. returns D_n = new detections in active bins united with the keypoints
+ *      of D_{n-1} in inactive bins (Eq. 1), sorted by (layer, y, x).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: FKD_OK (0) or a negative FKD_E_* code. Nothing throws
+ *     across the ABI. fkd_last_error() returns a message for the calling
+ *     thread's last failure.
+ *   - Frames are 8-bit grayscale, row-major, W x H pixels, with a row pitch
+ *     in bytes (pitch >= W).
+ *   - "on_device" arguments say whether a pointer is CUDA device memory (1)
+ *     or host memory (0). Host buffers are copied on the stream's CUDA
+ *     stream; pinned host memory makes those copies asynchronous.
+ *   - Each fkd_stream is bound to one CUDA stream (given at creation; NULL
+ *     is the legacy default stream) and is not thread-safe: one host thread
+ *     drives one fkd_stream at a time. Different fkd_streams are independent.
+ *   - The library owns all device state of a stream (pyramid, masks, the
+ *     kept keypoint set D_{n-1}, scratch) and frees it in
+ *     fkd_destroy_stream. The caller owns every buffer it passes in.
+ */
+#ifndef FKD_H
+#define FKD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FKD_VERSION 1u
+
+/* status codes */
+#define FKD_OK 0
+#define FKD_E_ARG (-1)      /* invalid argument or parameter                 */
+#define FKD_E_CAPACITY (-2) /* output larger than the buffer given / K_max   */
+#define FKD_E_BUDGET (-3)   /* admission refused: memory budget exhausted    */
+#define FKD_E_CUDA (-4)     /* a CUDA call failed (message has the details)  */
+#define FKD_E_TIMEOUT (-5)  /* a bounded device wait ran out                 */
+#define FKD_E_STATE (-6)    /* call out of order (e.g. no frame pushed yet)  */
+
+/* mask modes (Sec. 3: "two efficient algorithms" plus plain detection) */
+#define FKD_MASK_FULL 0 /* every bin active: the plain per-frame detector      */
+#define FKD_MASK_ID 1   /* intensity difference detection mask, Eq. 2         */
+#define FKD_MASK_KB 2   /* keypoint binning detection mask, Eqs. 3-4          */
+
+/*
+ * Parameters, named as the paper names them.
+ *   N_r, N_c    bin grid rows and columns (Sec. 3.2); a bin covers
+ *               S_x = W/N_c by S_y = H/N_r pixels. 1 <= N_c <= W,
+ *               1 <= N_r <= H, N_r*N_c <= 4096.
+ *   T_I         intensity-difference threshold (Eq. 2). A bin is active when
+ *               the mean of |L_n - L_{n-1}| over its pixels of the mask layer
+ *               exceeds T_I (evaluated exactly as sum > T_I * count). >= 0.
+ *   T_H         keypoint-binning threshold (Eq. 4): a bin is active when it
+ *               held at least T_H keypoints of D_{n-1}. >= 0.
+ *   O           octaves (Sec. 2), 1..6.
+ *   intra       1: add the intra-octave layers d_i (scale 1.5 * 2^i);
+ *               0: octaves only.
+ *   t           segment-test threshold (Sec. 2), 1..255.
+ *   n           contiguous ring pixels the test asks for; must be 9.
+ *   mask_mode   FKD_MASK_FULL / FKD_MASK_ID / FKD_MASK_KB.
+ *   mask_layer  layer the intensity difference is taken on (layer index as
+ *               in fkd_layer_info); -1 selects the coarsest octave c_{O-1},
+ *               the paper's choice in its experiments (Sec. 4).
+ *   K_max       capacity of the kept keypoint set of one frame (>= 1).
+ *   T_max       most frames one fkd_push_frames call may carry (>= 1); it
+ *               sizes the per-batch scratch.
+ */
+typedef struct {
+  uint32_t version; /* FKD_VERSION */
+  int32_t N_r, N_c;
+  int32_t T_I;
+  int32_t T_H;
+  int32_t O;
+  int32_t intra;
+  int32_t t;
+  int32_t n;
+  int32_t mask_mode;
+  int32_t mask_layer;
+  int32_t K_max;
+  int32_t T_max;
+} fkd_params;
+
+/*
+ * One keypoint, 8 bytes. x, y are layer-pixel coordinates; the image
+ * position is (floor(x*S/2), floor(y*S/2)) and the scale sigma = S/2, with S
+ * the layer's scale code from fkd_layer_info (feature tuple of Sec. 3).
+ * score is the largest threshold for which the segment test still fires
+ * (>= t). flags bit 0 (FKD_KP_PROPAGATED) marks a keypoint carried over from
+ * D_{n-1} because its bin was inactive (Eq. 1).
+ */
+typedef struct {
+  uint16_t x, y;
+  uint8_t layer, score;
+  uint16_t flags;
+} fkd_keypoint;
+#define FKD_KP_PROPAGATED 1u
+
+typedef struct fkd_stream fkd_stream;
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* fkd_last_error(void);
+
+/* Fill *p with defaults: 8 x 8 bins, T_I 4, T_H 1, O 1, intra 0, t 20, n 9,
+ * FKD_MASK_ID on layer 0, K_max 65536, T_max 1. */
+int fkd_params_default(fkd_params* p);
+
+/*
+ * Create a stream for W x H frames (1..16384 each). cuda_stream is a
+ * cudaStream_t (NULL: legacy default stream). On success *out owns the
+ * device state; release it with fkd_destroy_stream.
+ * Errors: FKD_E_ARG (bad parameters or sizes), FKD_E_CUDA (allocation).
+ */
+int fkd_create_stream(const fkd_params* p, int W, int H, void* cuda_stream, fkd_stream** out);
+
+/* Synchronise the stream and free everything it owns. NULL is a no-op. */
+int fkd_destroy_stream(fkd_stream* s);
+
+/* Number of pyramid layers (O, or 2*O with intra-octaves). */
+int fkd_num_layers(const fkd_stream* s, int* L);
+
+/*
+ * Geometry of layer `layer` (0 .. L-1, ordered by scale: c_0, d_0, c_1, d_1,
+ * ... with intra-octaves, c_0, c_1, ... without). w, h: layer size; S: scale
+ * code 2*sigma (2, 3, 4, 6, 8, 12, ...). c_{i+1} is c_i halved (floor);
+ * d_0 has 2*floor(W/3) x 2*floor(H/3) pixels; d_{i+1} is d_i halved.
+ * Any output pointer may be NULL. Errors: FKD_E_ARG.
+ */
+int fkd_layer_info(const fkd_stream* s, int layer, int* w, int* h, int* S);
+
+/*
+ * Process the next frame of the stream (steps 1-4 above), asynchronously on
+ * the stream's CUDA stream. The result D_n replaces D_{n-1} and is read with
+ * fkd_get_keypoints.
+ *   frame, pitch: the W x H frame.
+ *   on_device = 0: host memory, copied to device memory the stream owns. From
+ *     pageable memory the copy completes before the call returns and the
+ *     buffer may be reused at once; from pinned (page-locked) memory the copy
+ *     is asynchronous and the buffer must stay unmodified until the next
+ *     fkd_get_keypoints, fkd_get_mask or fkd_synchronize on this stream.
+ *   on_device = 1: device memory read in place. It must stay valid and
+ *     unmodified until the NEXT fkd_push_frame / fkd_push_frames call on this
+ *     stream has completed, because that call compares against it (Eq. 2).
+ * Errors: FKD_E_ARG, FKD_E_CUDA.
+ */
+int fkd_push_frame(fkd_stream* s, const uint8_t* frame, size_t pitch, int on_device);
+
+/*
+ * Wait for the last pushed frame and copy D_n, sorted by (layer, y, x), to
+ * host memory `out` (room for `cap` records). *n_out receives |D_n| even
+ * when it does not fit. Errors: FKD_E_STATE (no frame pushed yet),
+ * FKD_E_CAPACITY (|D_n| > cap, or |D_n| > K_max: the set was truncated to
+ * K_max on the device; nothing is copied in either case), FKD_E_CUDA.
+ */
+int fkd_get_keypoints(fkd_stream* s, fkd_keypoint* out, size_t cap, size_t* n_out);
+
+/* Wait for the last pushed frame and copy its mask M'_n (N_r*N_c bytes, row
+ * major, 1 = active bin) to host memory `out`. Errors: FKD_E_STATE, FKD_E_CUDA. */
+int fkd_get_mask(fkd_stream* s, uint8_t* out);
+
+/*
+ * Process T consecutive frames of the stream in one batched launch sequence
+ * (1 <= T <= T_max). Output is bit-identical to T fkd_push_frame calls.
+ *   frames: frame k at frames + k*frame_stride, rows `pitch` bytes apart;
+ *     on_device as for fkd_push_frame (device frames must additionally stay
+ *     valid until this call has completed; the last one as for
+ *     fkd_push_frame).
+ *   out, cap, offsets: D_{n0+k} for every k, concatenated; offsets[k] is the
+ *     index of its first record and offsets[T] the total (T+1 entries).
+ *   masks: NULL, or T*N_r*N_c bytes receiving M'_{n0+k}.
+ *   out_on_device: 1 if out, offsets and masks are device memory. The call
+ *     is then asynchronous on the stream's CUDA stream; records past `cap`
+ *     are dropped, offsets still give the full counts, and the overflow is
+ *     reported as FKD_E_CAPACITY by the next fkd_synchronize. 0: host
+ *     memory; the call waits and returns FKD_E_CAPACITY itself (outputs
+ *     filled up to cap).
+ * With FKD_MASK_KB each frame's mask depends on the previous frame's
+ * keypoints, so the batch runs frame after frame inside the call.
+ * Errors: FKD_E_ARG, FKD_E_CAPACITY, FKD_E_CUDA.
+ */
+int fkd_push_frames(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t frame_stride, int T,
+                    int on_device, fkd_keypoint* out, size_t cap, uint32_t* offsets, uint8_t* masks,
+                    int out_on_device);
+
+/* Wait for all work of the stream; report a deferred FKD_E_CAPACITY from an
+ * asynchronous fkd_push_frames (and clear it). */
+int fkd_synchronize(fkd_stream* s);
+
+/* Frames processed so far (the index n of the next frame). */
+int fkd_frame_count(const fkd_stream* s, int64_t* n);
+
+/*
+ * Device pointers of the last frame's result, for callers that keep working
+ * on the GPU: *records (K_max entries, the first *count_dev valid), *count_dev
+ * (one uint32 on the device). Valid until the next push on this stream.
+ */
+int fkd_device_keypoints(fkd_stream* s, const fkd_keypoint** records, const uint32_t** count_dev);
+
+/*
+ * Forget the stream's history: the next frame is treated as the first one
+ * (all bins active, nothing carried over), as after a scene cut. Waits for
+ * the stream's pending work. Errors: FKD_E_ARG.
+ */
+int fkd_reset_stream(fkd_stream* s);
+
+/*
+ * Per-stage timing of the launch sequence, for profiling. While enabled,
+ * every batch records CUDA events around each of its kernels on the stream's
+ * CUDA stream. fkd_profile_read waits for the stream, adds the elapsed times
+ * of all batches since the last read (reset != 0 clears them afterwards).
+ * Stages: FKD_STAGE_PYRAMID (pyramid + per-bin change sums), _MASK (mask and
+ * source frames), _WORKLIST (active-tile compaction), _DETECT (segment test,
+ * score, suppression), _COUNT and _EMIT (assembly of D_n).
+ * tile_pixels counts the layer pixels inside the detection tiles processed
+ * (each is one input byte the detection kernel must read), tiles the tiles.
+ */
+#define FKD_STAGE_PYRAMID 0
+#define FKD_STAGE_MASK 1
+#define FKD_STAGE_WORKLIST 2
+#define FKD_STAGE_DETECT 3
+#define FKD_STAGE_COUNT 4
+#define FKD_STAGE_EMIT 5
+#define FKD_NUM_STAGES 6
+typedef struct {
+  double ms[FKD_NUM_STAGES];       /* summed kernel time per stage            */
+  uint64_t launches[FKD_NUM_STAGES];
+  uint64_t batches;                /* launch sequences recorded              */
+  uint64_t frames;                 /* frames those sequences processed       */
+  uint64_t tiles;                  /* detection tiles processed              */
+  uint64_t tile_pixels;            /* layer pixels in those tiles            */
+} fkd_profile;
+int fkd_profile_enable(fkd_stream* s, int on);
+int fkd_profile_read(fkd_stream* s, fkd_profile* out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FKD_H */

@@ -1,0 +1,615 @@
+// fkd_api.cu -- the C ABI of include/fkd.h: stream state, geometry tables
+// and the launch sequence of one batch (pyramid -> mask -> active tiles ->
+// detection -> assembly).
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fkd_internal.cuh"
+
+using namespace fkd;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(FKD_E_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                              \
+  } while (0)
+
+long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct fkd_stream {
+  fkd_params p{};
+  Geometry g{};
+  cudaStream_t st = nullptr;
+  std::vector<void*> allocs;
+
+  uint16_t* colblk = nullptr;
+  uint16_t* rowblk = nullptr;
+  int* xstart = nullptr;
+  uint32_t* npix = nullptr;
+  DetTile* tiles = nullptr;
+
+  Scratch s{};
+  uint32_t* state_bits[2] = {nullptr, nullptr};
+  uint8_t* state_score[2] = {nullptr, nullptr};
+  uint32_t* state_cnt[2] = {nullptr, nullptr};
+  int state_cur = 0;
+
+  uint8_t* staging[2] = {nullptr, nullptr};
+  int staging_next = 0;
+  long long staging_pitch = 0;
+
+  fkd_keypoint* rec = nullptr;     // result of the last fkd_push_frame (K_max records)
+  uint32_t* rec_offsets = nullptr; // [2]
+  fkd_keypoint* host_out = nullptr;  // device staging for host-output batches
+  long long host_out_cap = 0;
+  uint32_t* host_offsets = nullptr;  // [T_max + 1]
+  uint8_t* last_mask = nullptr;      // device pointer to the last frame's mask
+
+  const uint8_t* prev = nullptr;
+  int prev_pitch = 0;
+  long long frame = 0;
+  int detect_grid = 0;
+  bool have_frame_result = false;
+
+  // profiling: events around each stage of each batch, read back lazily
+  bool profiling = false;
+  struct Pending {
+    cudaEvent_t ev[FKD_NUM_STAGES + 1];
+    int frames;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  fkd_profile prof{};
+  unsigned long long tile_stats_seen[2] = {0, 0};
+
+  cudaEvent_t take_event() {
+    if (!event_pool.empty()) {
+      cudaEvent_t e = event_pool.back();
+      event_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+
+  template <class T>
+  int alloc(T** p, size_t count) {
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return fail(FKD_E_CUDA, "cudaMalloc(%zu) failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    allocs.push_back(d);
+    *p = static_cast<T*>(d);
+    return FKD_OK;
+  }
+  void release() {
+    for (void* d : allocs) cudaFree(d);
+    allocs.clear();
+    for (auto& pd : pending)
+      for (cudaEvent_t e : pd.ev) cudaEventDestroy(e);
+    pending.clear();
+    for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
+    event_pool.clear();
+  }
+};
+
+namespace {
+
+int validate(const fkd_params* p, int W, int H) {
+  if (!p) return fail(FKD_E_ARG, "params is NULL");
+  if (p->version != FKD_VERSION) return fail(FKD_E_ARG, "params.version %u != %u", p->version, FKD_VERSION);
+  if (W < 1 || H < 1 || W > 16384 || H > 16384) return fail(FKD_E_ARG, "frame size %dx%d outside 1..16384", W, H);
+  if (p->N_r < 1 || p->N_c < 1 || p->N_c > W || p->N_r > H || p->N_r * p->N_c > kMaxBins)
+    return fail(FKD_E_ARG, "bin grid %dx%d invalid for %dx%d frames", p->N_r, p->N_c, W, H);
+  if (p->O < 1 || p->O > 6) return fail(FKD_E_ARG, "O=%d outside 1..6", p->O);
+  if (p->intra != 0 && p->intra != 1) return fail(FKD_E_ARG, "intra must be 0 or 1");
+  if (p->t < 1 || p->t > 255) return fail(FKD_E_ARG, "t=%d outside 1..255", p->t);
+  if (p->n != 9) return fail(FKD_E_ARG, "arc length n=%d: only 9 is supported", p->n);
+  if (p->T_I < 0 || p->T_H < 0) return fail(FKD_E_ARG, "thresholds must be >= 0");
+  if (p->mask_mode < FKD_MASK_FULL || p->mask_mode > FKD_MASK_KB) return fail(FKD_E_ARG, "bad mask_mode");
+  const int L = p->intra ? 2 * p->O : p->O;
+  if (p->mask_layer < -1 || p->mask_layer >= L) return fail(FKD_E_ARG, "mask_layer %d outside -1..%d", p->mask_layer, L - 1);
+  if (p->K_max < 1) return fail(FKD_E_ARG, "K_max must be >= 1");
+  if (p->T_max < 1 || p->T_max > 65535) return fail(FKD_E_ARG, "T_max outside 1..65535");
+  return FKD_OK;
+}
+
+// Layer sizes: c_0 = W x H; c_{i+1} = floor(c_i / 2); d_0 = 2 floor(W/3) x
+// 2 floor(H/3); d_{i+1} = floor(d_i / 2). Scale code S = 2 * sigma.
+void layer_dims(int W, int H, int intra, int l, int* w, int* h, int* S) {
+  const int i = intra ? l / 2 : l;
+  const bool d = intra && (l & 1);
+  int ww = d ? (W / 3) * 2 : W, hh = d ? (H / 3) * 2 : H;
+  ww >>= i;
+  hh >>= i;
+  *w = ww;
+  *h = hh;
+  *S = (d ? 3 : 2) << i;
+}
+
+int build_geometry(fkd_stream* s, int W, int H) {
+  const fkd_params& p = s->p;
+  Geometry& g = s->g;
+  g.W = W;
+  g.H = H;
+  g.O = p.O;
+  g.intra = p.intra;
+  g.L = p.intra ? 2 * p.O : p.O;
+  g.N_r = p.N_r;
+  g.N_c = p.N_c;
+  g.NB = p.N_r * p.N_c;
+  g.mask_layer = p.mask_layer == -1 ? (p.O - 1) * (p.intra ? 2 : 1) : p.mask_layer;
+
+  std::vector<uint16_t> colblk, rowblk;
+  std::vector<int> xstart;
+  std::vector<DetTile> tiles;
+  long long pyr = 0, score = 0, bits = 0;
+  for (int l = 0; l < g.L; ++l) {
+    LayerGeom& lg = g.layer[l];
+    layer_dims(W, H, p.intra, l, &lg.w, &lg.h, &lg.S);
+    lg.pitch = (int)round_up(std::max(lg.w, 1), 16);
+    if (l == 0) {
+      lg.pyr_off = -1;
+    } else {
+      lg.pyr_off = pyr;
+      pyr += round_up((long long)lg.pitch * lg.h, 256);
+    }
+    lg.score_off = score;
+    score += round_up((long long)lg.pitch * lg.h, 256);
+    lg.wpr = (lg.w + 31) / 32;
+    lg.bit_off = bits;
+    bits += (long long)lg.wpr * lg.h;
+    // bins of the layer's pixels: image position X = floor(x*S/2), bin column
+    // floor(X / (W/N_c)) = floor(X*N_c/W) (Eq. 3), rows likewise
+    lg.col_off = (int)colblk.size();
+    for (int x = 0; x < lg.w; ++x) colblk.push_back((uint16_t)(((long long)x * lg.S / 2) * p.N_c / W));
+    lg.row_off = (int)rowblk.size();
+    for (int y = 0; y < lg.h; ++y) rowblk.push_back((uint16_t)(((long long)y * lg.S / 2) * p.N_r / H));
+    lg.xs_off = (int)xstart.size();
+    for (int c = 0; c <= p.N_c; ++c) {
+      int x = 0;
+      while (x < lg.w && colblk[lg.col_off + x] < c) ++x;
+      xstart.push_back(x);
+    }
+    lg.tile_off = (int)tiles.size();
+    if (lg.w > 0 && lg.h > 0) {
+      for (int ty = 0; ty * kDetTH < lg.h; ++ty)
+        for (int tx = 0; tx * kDetTW < lg.w; ++tx) {
+          DetTile t{};
+          t.layer = (uint16_t)l;
+          t.tx = (uint16_t)tx;
+          t.ty = (uint16_t)ty;
+          const int x1 = std::min((tx + 1) * kDetTW, lg.w) - 1, y1 = std::min((ty + 1) * kDetTH, lg.h) - 1;
+          t.cb0 = colblk[lg.col_off + tx * kDetTW];
+          t.cb1 = colblk[lg.col_off + x1];
+          t.rb0 = rowblk[lg.row_off + ty * kDetTH];
+          t.rb1 = rowblk[lg.row_off + y1];
+          tiles.push_back(t);
+        }
+    }
+  }
+  g.pyr_bytes = std::max(pyr, 256LL);
+  g.score_bytes = score;
+  g.bit_words = bits;
+  g.n_tiles = (int)tiles.size();
+  g.n_chunks = (int)((bits + kAsmChunkWords - 1) / kAsmChunkWords);
+  g.pyr_tiles_x = (W + kPyrTile - 1) / kPyrTile;
+  g.pyr_tiles_y = (H + kPyrTile - 1) / kPyrTile;
+
+  // pixels of the mask layer in each bin
+  std::vector<uint32_t> npix(g.NB, 0);
+  const LayerGeom& ml = g.layer[g.mask_layer];
+  for (int y = 0; y < ml.h; ++y)
+    for (int x = 0; x < ml.w; ++x) npix[rowblk[ml.row_off + y] * p.N_c + colblk[ml.col_off + x]] += 1;
+
+  int rc;
+  if ((rc = s->alloc(&s->colblk, colblk.size())) || (rc = s->alloc(&s->rowblk, rowblk.size())) ||
+      (rc = s->alloc(&s->xstart, xstart.size())) || (rc = s->alloc(&s->npix, npix.size())) ||
+      (rc = s->alloc(&s->tiles, tiles.size())))
+    return rc;
+  CK(cudaMemcpy(s->colblk, colblk.data(), colblk.size() * 2, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->rowblk, rowblk.data(), rowblk.size() * 2, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->xstart, xstart.data(), xstart.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->npix, npix.data(), npix.size() * 4, cudaMemcpyHostToDevice));
+  if (!tiles.empty())
+    CK(cudaMemcpy(s->tiles, tiles.data(), tiles.size() * sizeof(DetTile), cudaMemcpyHostToDevice));
+  return FKD_OK;
+}
+
+int allocate_state(fkd_stream* s) {
+  const Geometry& g = s->g;
+  const long long T = s->p.T_max;
+  Scratch& sc = s->s;
+  int rc;
+  if ((rc = s->alloc(&sc.pyr, (size_t)(T * g.pyr_bytes))) ||
+      (rc = s->alloc(&sc.bsum, (size_t)(T * g.NB))) || (rc = s->alloc(&sc.mask, (size_t)(T * g.NB))) ||
+      (rc = s->alloc(&sc.src, (size_t)(T * g.NB))) ||
+      (rc = s->alloc(&sc.work, (size_t)(T * std::max(g.n_tiles, 1)))) ||
+      (rc = s->alloc(&sc.work_count, 1)) ||
+      (rc = s->alloc(&sc.det_bits, (size_t)(T * std::max(g.bit_words, 1LL)))) ||
+      (rc = s->alloc(&sc.det_score, (size_t)(T * g.score_bytes))) ||
+      (rc = s->alloc(&sc.chunk_counts, (size_t)(T * std::max(g.n_chunks, 1)))) ||
+      (rc = s->alloc(&sc.frame_totals, (size_t)T)) || (rc = s->alloc(&sc.out_base, 2)) ||
+      (rc = s->alloc(&sc.overflow, 1)) || (rc = s->alloc(&sc.tile_stats, 2)))
+    return rc;
+  CK(cudaMemset(sc.tile_stats, 0, 16));
+  for (int i = 0; i < 2; ++i) {
+    if ((rc = s->alloc(&s->state_bits[i], (size_t)std::max(g.bit_words, 1LL))) ||
+        (rc = s->alloc(&s->state_score[i], (size_t)g.score_bytes)) ||
+        (rc = s->alloc(&s->state_cnt[i], (size_t)g.NB)))
+      return rc;
+    CK(cudaMemset(s->state_bits[i], 0, (size_t)std::max(g.bit_words, 1LL) * 4));
+    CK(cudaMemset(s->state_cnt[i], 0, (size_t)g.NB * 4));
+  }
+  CK(cudaMemset(sc.bsum, 0, (size_t)(T * g.NB) * 8));
+  CK(cudaMemset(sc.overflow, 0, 4));
+  CK(cudaMemset(sc.out_base, 0, 16));
+  if ((rc = s->alloc(&s->rec, (size_t)s->p.K_max)) || (rc = s->alloc(&s->rec_offsets, 2)) ||
+      (rc = s->alloc(&s->host_offsets, (size_t)(T + 1))))
+    return rc;
+  CK(cudaMemset(s->rec_offsets, 0, 8));
+  return FKD_OK;
+}
+
+// One batch of T frames already in device memory (T == 1 for keypoint
+// binning, whose mask needs the previous frame's keypoints).
+int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride, int T,
+              fkd_keypoint* out, long long cap, uint32_t* offsets, int base_slot, bool reset_base) {
+  Batch b{};
+  b.T = T;
+  b.first_frame = s->frame;
+  b.frames = frames;
+  b.frame_stride = stride;
+  b.pitch = pitch;
+  b.prev = s->prev;
+  b.prev_pitch = s->prev_pitch;
+  b.c0_vec = 0;
+  Params pr{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode};
+  Tables tb{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles};
+  State stt{};
+  stt.bits_in = s->state_bits[s->state_cur];
+  stt.score_in = s->state_score[s->state_cur];
+  stt.cnt_in = s->state_cnt[s->state_cur];
+  stt.bits_out = s->state_bits[s->state_cur ^ 1];
+  stt.score_out = s->state_score[s->state_cur ^ 1];
+  stt.cnt_out = s->state_cnt[s->state_cur ^ 1];
+  Output o{out, cap, offsets, base_slot};
+
+  fkd_stream::Pending pd{};
+  const bool prof = s->profiling;
+  auto mark = [&](int i) {
+    if (prof) {
+      pd.ev[i] = s->take_event();
+      cudaEventRecord(pd.ev[i], s->st);
+    }
+  };
+  mark(0);
+  launch_pyramid(s->g, tb, b, s->s, pr, s->st);
+  mark(1);
+  launch_mask(s->g, tb, b, s->s, pr, stt, s->st, reset_base ? base_slot : -1);
+  mark(2);
+  launch_worklist(s->g, tb, b, s->s, s->st);
+  mark(3);
+  launch_detect(s->g, tb, b, s->s, pr, s->detect_grid, s->st);
+  mark(4);
+  launch_count(s->g, tb, b, s->s, stt, s->st);
+  mark(5);
+  launch_emit(s->g, tb, b, s->s, stt, o, s->st);
+  mark(6);
+  CK(cudaGetLastError());
+  if (prof) {
+    pd.frames = T;
+    s->pending.push_back(pd);
+  }
+
+  s->state_cur ^= 1;
+  s->prev = frames + (long long)(T - 1) * stride;
+  s->prev_pitch = pitch;
+  s->frame += T;
+  s->last_mask = s->s.mask + (long long)(T - 1) * s->g.NB;
+  return FKD_OK;
+}
+
+bool is_pinned(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fkd_last_error(void) { return g_err.c_str(); }
+
+int fkd_params_default(fkd_params* p) {
+  if (!p) return fail(FKD_E_ARG, "params is NULL");
+  std::memset(p, 0, sizeof *p);
+  p->version = FKD_VERSION;
+  p->N_r = 8;
+  p->N_c = 8;
+  p->T_I = 4;
+  p->T_H = 1;
+  p->O = 1;
+  p->intra = 0;
+  p->t = 20;
+  p->n = 9;
+  p->mask_mode = FKD_MASK_ID;
+  p->mask_layer = 0;
+  p->K_max = 65536;
+  p->T_max = 1;
+  return FKD_OK;
+}
+
+int fkd_create_stream(const fkd_params* p, int W, int H, void* cuda_stream, fkd_stream** out) {
+  if (!out) return fail(FKD_E_ARG, "out is NULL");
+  *out = nullptr;
+  int rc = validate(p, W, H);
+  if (rc) return rc;
+  fkd_stream* s = new (std::nothrow) fkd_stream();
+  if (!s) return fail(FKD_E_ARG, "out of host memory");
+  s->p = *p;
+  s->st = static_cast<cudaStream_t>(cuda_stream);
+  if ((rc = build_geometry(s, W, H)) || (rc = allocate_state(s))) {
+    s->release();
+    delete s;
+    return rc;
+  }
+  s->staging_pitch = round_up(W, 16);
+  s->detect_grid = detect_grid_size();
+  *out = s;
+  return FKD_OK;
+}
+
+int fkd_destroy_stream(fkd_stream* s) {
+  if (!s) return FKD_OK;
+  cudaStreamSynchronize(s->st);
+  s->release();
+  delete s;
+  return FKD_OK;
+}
+
+int fkd_num_layers(const fkd_stream* s, int* L) {
+  if (!s || !L) return fail(FKD_E_ARG, "NULL argument");
+  *L = s->g.L;
+  return FKD_OK;
+}
+
+int fkd_layer_info(const fkd_stream* s, int layer, int* w, int* h, int* S) {
+  if (!s) return fail(FKD_E_ARG, "stream is NULL");
+  if (layer < 0 || layer >= s->g.L) return fail(FKD_E_ARG, "layer %d outside 0..%d", layer, s->g.L - 1);
+  if (w) *w = s->g.layer[layer].w;
+  if (h) *h = s->g.layer[layer].h;
+  if (S) *S = s->g.layer[layer].S;
+  return FKD_OK;
+}
+
+int fkd_push_frames(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t frame_stride, int T,
+                    int on_device, fkd_keypoint* out, size_t cap, uint32_t* offsets, uint8_t* masks,
+                    int out_on_device) {
+  if (!s || !frames || !offsets || (!out && cap > 0)) return fail(FKD_E_ARG, "NULL argument");
+  const Geometry& g = s->g;
+  if (T < 1 || T > s->p.T_max) return fail(FKD_E_ARG, "T=%d outside 1..T_max=%d", T, s->p.T_max);
+  if (pitch < (size_t)g.W || pitch > (1u << 30)) return fail(FKD_E_ARG, "pitch %zu < W=%d", pitch, g.W);
+  if (T > 1 && frame_stride < pitch * (size_t)g.H) return fail(FKD_E_ARG, "frame_stride too small");
+  if (cap > 0xffffffffull) return fail(FKD_E_ARG, "cap must fit in 32 bits");
+
+  // 1. frames to device memory
+  const uint8_t* dframes = frames;
+  int dpitch = (int)pitch;
+  long long dstride = (long long)frame_stride;
+  if (!on_device) {
+    uint8_t*& buf = s->staging[s->staging_next];
+    if (!buf) {
+      int rc = s->alloc(&buf, (size_t)(s->staging_pitch * g.H * s->p.T_max));
+      if (rc) return rc;
+    }
+    for (int k = 0; k < T; ++k)
+      CK(cudaMemcpy2DAsync(buf + (long long)k * s->staging_pitch * g.H, s->staging_pitch,
+                           frames + (size_t)k * frame_stride, pitch, g.W, g.H, cudaMemcpyHostToDevice,
+                           s->st));
+    dframes = buf;
+    dpitch = (int)s->staging_pitch;
+    dstride = s->staging_pitch * g.H;
+    s->staging_next ^= 1;
+  }
+
+  // 2. where the records go
+  fkd_keypoint* drec = out;
+  uint32_t* doff = offsets;
+  if (!out_on_device) {
+    if ((long long)cap > s->host_out_cap) {
+      if (s->host_out) {
+        CK(cudaStreamSynchronize(s->st));
+        cudaFree(s->host_out);
+        s->allocs.erase(std::find(s->allocs.begin(), s->allocs.end(), (void*)s->host_out));
+        s->host_out = nullptr;
+        s->host_out_cap = 0;
+      }
+      fkd_keypoint* nb = nullptr;
+      int rc = s->alloc(&nb, cap);
+      if (rc) return rc;
+      s->host_out = nb;
+      s->host_out_cap = (long long)cap;
+    }
+    drec = s->host_out;
+    doff = s->host_offsets;
+  }
+
+  // 3. the batch (frame by frame for keypoint binning)
+  const bool serial = s->p.mask_mode == FKD_MASK_KB;
+  int slot = 0;
+  for (int k0 = 0; k0 < T;) {
+    const int n = serial ? 1 : T;
+    int rc = run_batch(s, dframes + (long long)k0 * dstride, dpitch, dstride, n, drec, (long long)cap,
+                       doff + k0, slot, k0 == 0);
+    if (rc) return rc;
+    if (masks) {
+      CK(cudaMemcpyAsync(masks + (size_t)k0 * g.NB, s->s.mask, (size_t)n * g.NB,
+                         out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->st));
+    }
+    slot ^= 1;
+    k0 += n;
+  }
+  s->have_frame_result = false;
+
+  if (out_on_device) return FKD_OK;
+  CK(cudaMemcpyAsync(offsets, doff, (size_t)(T + 1) * 4, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  const long long total = offsets[T];
+  const long long ncopy = std::min<long long>(total, (long long)cap);
+  if (ncopy > 0)
+    CK(cudaMemcpyAsync(out, drec, (size_t)ncopy * sizeof(fkd_keypoint), cudaMemcpyDeviceToHost, s->st));
+  int ov = 0;
+  CK(cudaMemcpyAsync(&ov, s->s.overflow, 4, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemsetAsync(s->s.overflow, 0, 4, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  if (total > (long long)cap || ov)
+    return fail(FKD_E_CAPACITY, "batch produced %lld keypoints, cap %zu", total, cap);
+  return FKD_OK;
+}
+
+int fkd_push_frame(fkd_stream* s, const uint8_t* frame, size_t pitch, int on_device) {
+  if (!s || !frame) return fail(FKD_E_ARG, "NULL argument");
+  const Geometry& g = s->g;
+  if (pitch < (size_t)g.W) return fail(FKD_E_ARG, "pitch %zu < W=%d", pitch, g.W);
+  const uint8_t* dframe = frame;
+  int dpitch = (int)pitch;
+  if (!on_device) {
+    uint8_t*& buf = s->staging[s->staging_next];
+    if (!buf) {
+      int rc = s->alloc(&buf, (size_t)(s->staging_pitch * g.H * s->p.T_max));
+      if (rc) return rc;
+    }
+    CK(cudaMemcpy2DAsync(buf, s->staging_pitch, frame, pitch, g.W, g.H, cudaMemcpyHostToDevice, s->st));
+    if (!is_pinned(frame)) CK(cudaStreamSynchronize(s->st));
+    dframe = buf;
+    dpitch = (int)s->staging_pitch;
+    s->staging_next ^= 1;
+  }
+  int rc = run_batch(s, dframe, dpitch, (long long)dpitch * g.H, 1, s->rec, s->p.K_max, s->rec_offsets,
+                     0, true);
+  if (rc) return rc;
+  s->have_frame_result = true;
+  return FKD_OK;
+}
+
+int fkd_get_keypoints(fkd_stream* s, fkd_keypoint* out, size_t cap, size_t* n_out) {
+  if (!s || !n_out || (!out && cap > 0)) return fail(FKD_E_ARG, "NULL argument");
+  if (!s->have_frame_result) return fail(FKD_E_STATE, "no frame pushed with fkd_push_frame");
+  uint32_t off[2];
+  CK(cudaMemcpyAsync(off, s->rec_offsets, 8, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  const size_t n = off[1] - off[0];
+  *n_out = n;
+  if (n > (size_t)s->p.K_max) {
+    CK(cudaMemset(s->s.overflow, 0, 4));
+    return fail(FKD_E_CAPACITY, "frame has %zu keypoints > K_max %d", n, s->p.K_max);
+  }
+  if (n > cap) return fail(FKD_E_CAPACITY, "frame has %zu keypoints > cap %zu", n, cap);
+  if (n) CK(cudaMemcpy(out, s->rec, n * sizeof(fkd_keypoint), cudaMemcpyDeviceToHost));
+  return FKD_OK;
+}
+
+int fkd_get_mask(fkd_stream* s, uint8_t* out) {
+  if (!s || !out) return fail(FKD_E_ARG, "NULL argument");
+  if (!s->last_mask) return fail(FKD_E_STATE, "no frame pushed yet");
+  CK(cudaMemcpyAsync(out, s->last_mask, (size_t)s->g.NB, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  return FKD_OK;
+}
+
+int fkd_synchronize(fkd_stream* s) {
+  if (!s) return fail(FKD_E_ARG, "stream is NULL");
+  int ov = 0;
+  CK(cudaMemcpyAsync(&ov, s->s.overflow, 4, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaMemsetAsync(s->s.overflow, 0, 4, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  if (ov) return fail(FKD_E_CAPACITY, "an asynchronous batch dropped records past its capacity");
+  return FKD_OK;
+}
+
+int fkd_frame_count(const fkd_stream* s, int64_t* n) {
+  if (!s || !n) return fail(FKD_E_ARG, "NULL argument");
+  *n = s->frame;
+  return FKD_OK;
+}
+
+int fkd_reset_stream(fkd_stream* s) {
+  if (!s) return fail(FKD_E_ARG, "stream is NULL");
+  CK(cudaStreamSynchronize(s->st));
+  s->frame = 0;
+  s->prev = nullptr;
+  s->prev_pitch = 0;
+  s->have_frame_result = false;
+  s->last_mask = nullptr;
+  return FKD_OK;
+}
+
+int fkd_profile_enable(fkd_stream* s, int on) {
+  if (!s) return fail(FKD_E_ARG, "stream is NULL");
+  s->profiling = on != 0;
+  return FKD_OK;
+}
+
+int fkd_profile_read(fkd_stream* s, fkd_profile* out, int reset) {
+  if (!s || !out) return fail(FKD_E_ARG, "NULL argument");
+  CK(cudaStreamSynchronize(s->st));
+  for (auto& pd : s->pending) {
+    for (int i = 0; i < FKD_NUM_STAGES; ++i) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, pd.ev[i], pd.ev[i + 1]));
+      s->prof.ms[i] += ms;
+      s->prof.launches[i] += 1;
+    }
+    s->prof.batches += 1;
+    s->prof.frames += (uint64_t)pd.frames;
+    for (cudaEvent_t e : pd.ev) s->event_pool.push_back(e);
+  }
+  s->pending.clear();
+  unsigned long long ts[2];
+  CK(cudaMemcpy(ts, s->s.tile_stats, 16, cudaMemcpyDeviceToHost));
+  s->prof.tiles += ts[0] - s->tile_stats_seen[0];
+  s->prof.tile_pixels += ts[1] - s->tile_stats_seen[1];
+  s->tile_stats_seen[0] = ts[0];
+  s->tile_stats_seen[1] = ts[1];
+  *out = s->prof;
+  if (reset) s->prof = fkd_profile{};
+  return FKD_OK;
+}
+
+int fkd_device_keypoints(fkd_stream* s, const fkd_keypoint** records, const uint32_t** count_dev) {
+  if (!s || !records || !count_dev) return fail(FKD_E_ARG, "NULL argument");
+  if (!s->have_frame_result) return fail(FKD_E_STATE, "no frame pushed with fkd_push_frame");
+  *records = s->rec;
+  *count_dev = s->rec_offsets + 1;
+  return FKD_OK;
+}
+
+}  // extern "C"

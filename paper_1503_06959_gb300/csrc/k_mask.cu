@@ -1,0 +1,107 @@
+// k_mask.cu -- detection mask M'_n per bin, the source frame of each bin's
+// keypoints across a batch, and the compacted list of active detection tiles.
+#include "fkd_internal.cuh"
+
+namespace fkd {
+namespace {
+
+// One warp per bin, walking the batch's frames 32 at a time.
+//   mask:  first frame of the stream or FKD_MASK_FULL -> 1; FKD_MASK_ID ->
+//          sum |L_n - L_{n-1}| > T_I * (pixels of the bin) (Eq. 2 read as
+//          "detect where the content changed"); FKD_MASK_KB -> keypoints of
+//          D_{n-1} in the bin >= T_H (Eqs. 3-4, batches of one frame).
+//   src:   Eq. 1 applied frame after frame means a bin of frame k shows the
+//          detections of the last frame m <= k in which the bin was active;
+//          src = m, or -1 when no such frame is in the batch (the kept set).
+//          Per bin this is a running "last set index", done with a ballot
+//          and a count of leading zeros per 32 frames.
+__global__ void k_mask(Geometry g, Tables tb, Batch b, Scratch s, Params p, State st,
+                       int reset_base_slot) {
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nthreads = gridDim.x * blockDim.x;
+  for (int k = gtid; k < b.T; k += nthreads) s.frame_totals[k] = 0;
+  if (gtid == 0) {
+    *s.work_count = 0;
+    if (reset_base_slot >= 0) s.out_base[reset_base_slot] = 0;
+  }
+  const int bin = gtid >> 5, lane = threadIdx.x & 31;
+  if (bin >= g.NB) return;
+  int carry = -1;
+  for (int k0 = 0; k0 < b.T; k0 += 32) {
+    const int k = k0 + lane;
+    int m = 0;
+    if (k < b.T) {
+      const long long n = b.first_frame + k;
+      if (n == 0 || p.mask_mode == FKD_MASK_FULL) {
+        m = 1;
+      } else if (p.mask_mode == FKD_MASK_ID) {
+        unsigned long long* sum = s.bsum + (long long)k * g.NB + bin;
+        m = *sum > (unsigned long long)p.T_I * tb.npix[bin];
+        *sum = 0;  // ready for the next batch
+      } else {
+        m = st.cnt_in[bin] >= (uint32_t)p.T_H;
+      }
+      s.mask[(long long)k * g.NB + bin] = (uint8_t)m;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, m);
+    const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const unsigned mine = bal & upto;
+    const int src = mine ? k0 + 31 - __clz(mine) : carry;
+    if (k < b.T) s.src[(long long)k * g.NB + bin] = src;
+    if (bal) carry = k0 + 31 - __clz(bal);
+  }
+  if (lane == 0) st.cnt_out[bin] = 0;
+}
+
+// One thread per (frame, tile): a tile is active when any bin its pixels map
+// to is active. Active items are compacted with a warp ballot, a popcount and
+// one atomic per warp.
+__global__ void k_worklist(Geometry g, Tables tb, Batch b, Scratch s) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)b.T * g.n_tiles;
+  bool act = false;
+  uint32_t area = 0;
+  if (i < total) {
+    const int k = (int)(i / g.n_tiles), tile = (int)(i % g.n_tiles);
+    const DetTile t = tb.tiles[tile];
+    const uint8_t* m = s.mask + (long long)k * g.NB;
+    for (int r = t.rb0; r <= t.rb1 && !act; ++r)
+      for (int c = t.cb0; c <= t.cb1; ++c)
+        if (m[r * g.N_c + c]) { act = true; break; }
+    if (act) {
+      const LayerGeom& lg = g.layer[t.layer];
+      area = (uint32_t)(min(kDetTW, lg.w - t.tx * kDetTW) * min(kDetTH, lg.h - t.ty * kDetTH));
+    }
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, act);
+  if (bal == 0) return;
+  area = __reduce_add_sync(0xffffffffu, area);
+  const int lane = threadIdx.x & 31, leader = __ffs(bal) - 1;
+  uint32_t base = 0;
+  if (lane == leader) {
+    base = atomicAdd(s.work_count, (uint32_t)__popc(bal));
+    atomicAdd(&s.tile_stats[0], (unsigned long long)__popc(bal));
+    atomicAdd(&s.tile_stats[1], (unsigned long long)area);
+  }
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (act) s.work[base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
+}
+
+}  // namespace
+
+void launch_mask(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
+                 const Params& p, const State& state, cudaStream_t st, int reset_base_slot) {
+  const int threads = 256;
+  const int blocks = (g.NB * 32 + threads - 1) / threads;
+  k_mask<<<blocks, threads, 0, st>>>(g, tb, b, s, p, state, reset_base_slot);
+}
+
+void launch_worklist(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
+                     cudaStream_t st) {
+  const int threads = 256;
+  const long long total = (long long)b.T * g.n_tiles;
+  const int blocks = (int)((total + threads - 1) / threads);
+  k_worklist<<<blocks, threads, 0, st>>>(g, tb, b, s);
+}
+
+}  // namespace fkd

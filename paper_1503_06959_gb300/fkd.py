@@ -1,0 +1,245 @@
+"""ctypes binding of the C ABI in ``include/fkd.h`` (names kept).
+
+Argument marshalling only: every step of the detector runs in ``libfkd.so``.
+Host frames are numpy arrays; device frames and outputs are torch CUDA
+tensors (torch is used only for device memory and streams). There is no
+fallback: if the CUDA library cannot be loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FKD_OK, FKD_E_ARG, FKD_E_CAPACITY, FKD_E_BUDGET, FKD_E_CUDA, FKD_E_TIMEOUT, FKD_E_STATE = (
+    0, -1, -2, -3, -4, -5, -6)
+FKD_MASK_FULL, FKD_MASK_ID, FKD_MASK_KB = 0, 1, 2
+FKD_VERSION = 1
+FKD_KP_PROPAGATED = 1
+
+KEYPOINT_DTYPE = np.dtype(
+    [("x", "<u2"), ("y", "<u2"), ("layer", "u1"), ("score", "u1"), ("flags", "<u2")])
+
+EXPORTS = [
+    "fkd_last_error", "fkd_params_default", "fkd_create_stream", "fkd_destroy_stream",
+    "fkd_num_layers", "fkd_layer_info", "fkd_push_frame", "fkd_get_keypoints", "fkd_get_mask",
+    "fkd_push_frames", "fkd_synchronize", "fkd_frame_count", "fkd_device_keypoints",
+    "fkd_reset_stream", "fkd_profile_enable", "fkd_profile_read",
+]
+STAGES = ["pyramid", "mask", "worklist", "detect", "count", "emit"]
+
+
+class fkd_params(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_uint32)] + [
+        (n, ctypes.c_int32) for n in
+        ("N_r", "N_c", "T_I", "T_H", "O", "intra", "t", "n", "mask_mode", "mask_layer",
+         "K_max", "T_max")]
+
+
+class fkd_profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_uint64 * 6),
+                ("batches", ctypes.c_uint64), ("frames", ctypes.c_uint64),
+                ("tiles", ctypes.c_uint64), ("tile_pixels", ctypes.c_uint64)]
+
+
+class FkdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fkd error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(build: bool = True) -> ctypes.CDLL:
+    """Load libfkd.so (building it first if asked). Raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; run build() first")
+    lib = ctypes.CDLL(path)
+    vp, c_int, c_size = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    P = ctypes.POINTER
+    lib.fkd_last_error.restype = ctypes.c_char_p
+    lib.fkd_params_default.argtypes = [P(fkd_params)]
+    lib.fkd_create_stream.argtypes = [P(fkd_params), c_int, c_int, vp, P(vp)]
+    lib.fkd_destroy_stream.argtypes = [vp]
+    lib.fkd_num_layers.argtypes = [vp, P(c_int)]
+    lib.fkd_layer_info.argtypes = [vp, c_int, P(c_int), P(c_int), P(c_int)]
+    lib.fkd_push_frame.argtypes = [vp, vp, c_size, c_int]
+    lib.fkd_get_keypoints.argtypes = [vp, vp, c_size, P(c_size)]
+    lib.fkd_get_mask.argtypes = [vp, vp]
+    lib.fkd_push_frames.argtypes = [vp, vp, c_size, c_size, c_int, c_int, vp, c_size, vp, vp, c_int]
+    lib.fkd_synchronize.argtypes = [vp]
+    lib.fkd_frame_count.argtypes = [vp, P(ctypes.c_int64)]
+    lib.fkd_device_keypoints.argtypes = [vp, P(vp), P(vp)]
+    lib.fkd_reset_stream.argtypes = [vp]
+    lib.fkd_profile_enable.argtypes = [vp, c_int]
+    lib.fkd_profile_read.argtypes = [vp, P(fkd_profile), c_int]
+    for name in EXPORTS:
+        if name != "fkd_last_error":
+            getattr(lib, name).restype = c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != FKD_OK:
+        raise FkdError(rc, _lib.fkd_last_error().decode())
+
+
+def _is_torch_cuda(a) -> bool:
+    return type(a).__module__.startswith("torch") and getattr(a, "is_cuda", False)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch_cuda(a):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def params_default() -> fkd_params:
+    lib = load()
+    p = fkd_params()
+    _check(lib.fkd_params_default(ctypes.byref(p)))
+    return p
+
+
+class Stream:
+    """One video stream: fkd_create_stream ... fkd_destroy_stream."""
+
+    def __init__(self, W: int, H: int, *, N_r: int = 8, N_c: int = 8, T_I: int = 4, T_H: int = 1,
+                 O: int = 1, intra: int = 0, t: int = 20, n: int = 9,
+                 mask_mode: int = FKD_MASK_ID, mask_layer: int = 0, K_max: int = 65536,
+                 T_max: int = 1, cuda_stream: int | None = None):
+        lib = load()
+        p = params_default()
+        p.N_r, p.N_c, p.T_I, p.T_H, p.O, p.intra, p.t, p.n = N_r, N_c, T_I, T_H, O, intra, t, n
+        p.mask_mode, p.mask_layer, p.K_max, p.T_max = mask_mode, mask_layer, K_max, T_max
+        self.params = p
+        self.W, self.H, self.N_r, self.N_c = W, H, N_r, N_c
+        h = ctypes.c_void_p()
+        _check(lib.fkd_create_stream(ctypes.byref(p), W, H, ctypes.c_void_p(cuda_stream or 0),
+                                     ctypes.byref(h)))
+        self._h = h
+
+    # -- geometry
+    def num_layers(self) -> int:
+        L = ctypes.c_int()
+        _check(_lib.fkd_num_layers(self._h, ctypes.byref(L)))
+        return L.value
+
+    def layer_info(self, layer: int):
+        w, h, S = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib.fkd_layer_info(self._h, layer, ctypes.byref(w), ctypes.byref(h), ctypes.byref(S)))
+        return w.value, h.value, S.value
+
+    # -- one frame at a time
+    def push_frame(self, frame):
+        on_device = 1 if _is_torch_cuda(frame) else 0
+        if not on_device:
+            frame = np.ascontiguousarray(frame, dtype=np.uint8)
+            pitch = frame.strides[0]
+        else:
+            assert frame.dtype.itemsize == 1 and frame.stride(1) == 1
+            pitch = frame.stride(0)
+        assert tuple(frame.shape) == (self.H, self.W)
+        _check(_lib.fkd_push_frame(self._h, _ptr(frame), pitch, on_device))
+
+    def get_keypoints(self, cap: int | None = None) -> np.ndarray:
+        cap = self.params.K_max if cap is None else cap
+        out = np.zeros(cap, KEYPOINT_DTYPE)
+        n = ctypes.c_size_t()
+        _check(_lib.fkd_get_keypoints(self._h, _ptr(out), cap, ctypes.byref(n)))
+        return out[:n.value].copy()
+
+    def get_mask(self) -> np.ndarray:
+        out = np.zeros(self.N_r * self.N_c, np.uint8)
+        _check(_lib.fkd_get_mask(self._h, _ptr(out)))
+        return out.reshape(self.N_r, self.N_c)
+
+    # -- batches
+    def push_frames(self, frames, *, out=None, offsets=None, masks=None, cap: int | None = None,
+                    want_masks: bool = True):
+        """T consecutive frames in one call.
+
+        Host frames (numpy, T x H x W): returns (records, offsets, masks) as numpy.
+        Device frames (torch CUDA uint8, T x H x W): writes into the given
+        device tensors ``out`` (records as int64 / 8-byte rows), ``offsets``
+        (int32, T+1) and ``masks`` (uint8, T x N_r x N_c, optional) and
+        returns immediately (asynchronous)."""
+        T = frames.shape[0]
+        if _is_torch_cuda(frames):
+            assert frames.stride(2) == 1
+            pitch, stride = frames.stride(1), frames.stride(0)
+            on_device = 1
+        else:
+            frames = np.ascontiguousarray(frames, dtype=np.uint8)
+            pitch, stride = frames.strides[1], frames.strides[0]
+            on_device = 0
+        if out is not None and _is_torch_cuda(out):
+            cap = out.numel() * out.element_size() // 8 if cap is None else cap
+            _check(_lib.fkd_push_frames(self._h, _ptr(frames), pitch, stride, T, on_device,
+                                        _ptr(out), cap, _ptr(offsets), _ptr(masks), 1))
+            return out, offsets, masks
+        if out is not None:
+            # caller-owned host buffers (e.g. pinned): out must be KEYPOINT_DTYPE
+            # or 8-byte rows, offsets uint32 (T+1), masks uint8 or None
+            cap = out.nbytes // 8 if cap is None else cap
+            _check(_lib.fkd_push_frames(self._h, _ptr(frames), pitch, stride, T, on_device,
+                                        _ptr(out), cap, _ptr(offsets), _ptr(masks), 0))
+            return out, offsets, masks
+        cap = T * self.params.K_max if cap is None else cap
+        rec = np.zeros(cap, KEYPOINT_DTYPE)
+        off = np.zeros(T + 1, np.uint32)
+        msk = np.zeros((T, self.N_r, self.N_c), np.uint8) if want_masks else None
+        _check(_lib.fkd_push_frames(self._h, _ptr(frames), pitch, stride, T, on_device,
+                                    _ptr(rec), cap, _ptr(off), _ptr(msk), 0))
+        return rec[:off[T]].copy(), off, msk
+
+    def synchronize(self):
+        _check(_lib.fkd_synchronize(self._h))
+
+    def frame_count(self) -> int:
+        n = ctypes.c_int64()
+        _check(_lib.fkd_frame_count(self._h, ctypes.byref(n)))
+        return n.value
+
+    def reset(self):
+        _check(_lib.fkd_reset_stream(self._h))
+
+    def profile_enable(self, on: bool = True):
+        _check(_lib.fkd_profile_enable(self._h, int(on)))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        p = fkd_profile()
+        _check(_lib.fkd_profile_read(self._h, ctypes.byref(p), int(reset)))
+        return {"ms": {STAGES[i]: p.ms[i] for i in range(6)},
+                "launches": {STAGES[i]: int(p.launches[i]) for i in range(6)},
+                "batches": int(p.batches), "frames": int(p.frames), "tiles": int(p.tiles),
+                "tile_pixels": int(p.tile_pixels)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.fkd_destroy_stream(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def split_frames(records: np.ndarray, offsets: np.ndarray):
+    """Per-frame keypoint arrays from a batch's concatenated records."""
+    base = int(offsets[0])
+    return [records[int(offsets[k]) - base:int(offsets[k + 1]) - base]
+            for k in range(len(offsets) - 1)]
