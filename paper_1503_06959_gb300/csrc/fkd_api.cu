@@ -50,6 +50,8 @@ struct fkd_stream {
   int* xstart = nullptr;
   uint32_t* npix = nullptr;
   DetTile* tiles = nullptr;
+  AsmChunk* chunks = nullptr;
+  uint32_t* wbins = nullptr;
 
   Scratch s{};
   uint32_t* state_bits[2] = {nullptr, nullptr};
@@ -166,6 +168,8 @@ int build_geometry(fkd_stream* s, int W, int H) {
   std::vector<uint16_t> colblk, rowblk;
   std::vector<int> xstart;
   std::vector<DetTile> tiles;
+  std::vector<AsmChunk> chunks;
+  std::vector<uint32_t> wbins;
   long long pyr = 0, score = 0, bits = 0;
   for (int l = 0; l < g.L; ++l) {
     LayerGeom& lg = g.layer[l];
@@ -194,6 +198,17 @@ int build_geometry(fkd_stream* s, int W, int H) {
       while (x < lg.w && colblk[lg.col_off + x] < c) ++x;
       xstart.push_back(x);
     }
+    // per bitmap word column: its first and last bin column
+    lg.wb_off = (int)wbins.size();
+    for (int wx = 0; wx < lg.wpr; ++wx) {
+      const int x1 = std::min(32 * wx + 32, lg.w) - 1;
+      wbins.push_back((uint32_t)colblk[lg.col_off + 32 * wx] | ((uint32_t)colblk[lg.col_off + x1] << 16));
+    }
+    // assembly chunks: bands of whole rows, about kAsmChunkWords words each
+    if (lg.wpr > 0) {
+      const int rows = std::max(1, kAsmChunkWords / lg.wpr);
+      for (int y0 = 0; y0 < lg.h; y0 += rows) chunks.push_back(AsmChunk{l, y0, std::min(lg.h, y0 + rows)});
+    }
     lg.tile_off = (int)tiles.size();
     if (lg.w > 0 && lg.h > 0) {
       for (int ty = 0; ty * kDetTH < lg.h; ++ty)
@@ -215,7 +230,7 @@ int build_geometry(fkd_stream* s, int W, int H) {
   g.score_bytes = score;
   g.bit_words = bits;
   g.n_tiles = (int)tiles.size();
-  g.n_chunks = (int)((bits + kAsmChunkWords - 1) / kAsmChunkWords);
+  g.n_chunks = (int)chunks.size();
   g.pyr_tiles_x = (W + kPyrTile - 1) / kPyrTile;
   g.pyr_tiles_y = (H + kPyrTile - 1) / kPyrTile;
 
@@ -228,8 +243,11 @@ int build_geometry(fkd_stream* s, int W, int H) {
   int rc;
   if ((rc = s->alloc(&s->colblk, colblk.size())) || (rc = s->alloc(&s->rowblk, rowblk.size())) ||
       (rc = s->alloc(&s->xstart, xstart.size())) || (rc = s->alloc(&s->npix, npix.size())) ||
-      (rc = s->alloc(&s->tiles, tiles.size())))
+      (rc = s->alloc(&s->tiles, tiles.size())) || (rc = s->alloc(&s->chunks, chunks.size())) ||
+      (rc = s->alloc(&s->wbins, wbins.size())))
     return rc;
+  CK(cudaMemcpy(s->chunks, chunks.data(), chunks.size() * sizeof(AsmChunk), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->wbins, wbins.data(), wbins.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->colblk, colblk.data(), colblk.size() * 2, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->rowblk, rowblk.data(), rowblk.size() * 2, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->xstart, xstart.data(), xstart.size() * 4, cudaMemcpyHostToDevice));
@@ -252,6 +270,7 @@ int allocate_state(fkd_stream* s) {
       (rc = s->alloc(&sc.det_bits, (size_t)(T * std::max(g.bit_words, 1LL)))) ||
       (rc = s->alloc(&sc.det_score, (size_t)(T * g.score_bytes))) ||
       (rc = s->alloc(&sc.chunk_counts, (size_t)(T * std::max(g.n_chunks, 1)))) ||
+      (rc = s->alloc(&sc.merged, (size_t)(T * std::max(g.bit_words, 1LL)))) ||
       (rc = s->alloc(&sc.frame_totals, (size_t)T)) || (rc = s->alloc(&sc.out_base, 2)) ||
       (rc = s->alloc(&sc.overflow, 1)) || (rc = s->alloc(&sc.tile_stats, 2)))
     return rc;
@@ -288,7 +307,7 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   b.prev_pitch = s->prev_pitch;
   b.c0_vec = 0;
   Params pr{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode};
-  Tables tb{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles};
+  Tables tb{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins};
   State stt{};
   stt.bits_in = s->state_bits[s->state_cur];
   stt.score_in = s->state_score[s->state_cur];

@@ -18,17 +18,36 @@ constexpr int kMaxBins = 4096;  // N_r * N_c
 constexpr int kPyrTile = 96;
 constexpr int kPyrThreads = 256;
 
-// Detection kernel tile (output pixels); the input tile adds a 4-pixel halo
-// (3 for the ring, 1 for the suppression neighbours), widened to 16 bytes on
-// each side so that rows load as aligned 16-byte vectors.
-constexpr int kDetTW = 64;
+// Detection tile (output pixels) handled by one warp: one 4-pixel word per
+// lane per row. The staged input adds a 4-pixel halo (3 for the ring, 1 for
+// the suppression neighbours), widened to 16 bytes left and right so that
+// rows load as aligned 16-byte vectors.
+constexpr int kDetTW = 128;
 constexpr int kDetTH = 16;
 constexpr int kDetThreads = 256;
 
-// Assembly: words of the per-frame keypoint bitmap handled by one CTA.
+// Assembly: a chunk is a band of whole rows of one layer of the per-frame
+// keypoint bitmap, about kAsmChunkWords words, handled by one CTA.
 constexpr int kAsmThreads = 256;
 constexpr int kAsmWordsPerThread = 8;
 constexpr int kAsmChunkWords = kAsmThreads * kAsmWordsPerThread;
+
+// Mask kernel: one CTA per bin walks the batch's frames 256 at a time.
+constexpr int kMaskThreads = 256;
+
+// Asynchronous 16-byte global -> shared copy (cp.async, LDGSTS): `bytes` of
+// the 16 are read (0..16) and the rest of the destination is zero-filled.
+// The source must be 16-byte aligned whenever bytes > 0.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 struct LayerGeom {
   int w, h, S;         // size and scale code 2*sigma
@@ -38,6 +57,7 @@ struct LayerGeom {
   int wpr;             // 32-bit words per row of the keypoint bitmap
   long long bit_off;   // word offset of the layer in a frame's bitmap
   int col_off;         // offset of the layer in the colblk table (w entries)
+  int wb_off;          // offset of the layer in the wbins table (wpr entries)
   int row_off;         // offset of the layer in the rowblk table (h entries)
   int xs_off;          // offset of the layer in the xstart table (N_c + 1 entries)
   int tile_off;        // first detection tile of the layer
@@ -56,6 +76,11 @@ struct Geometry {
   int pyr_tiles_x, pyr_tiles_y;
 };
 
+// One assembly chunk: rows y0 .. y1-1 of one layer.
+struct AsmChunk {
+  int layer, y0, y1;
+};
+
 // One detection tile: a kDetTW x kDetTH rectangle of one layer, and the
 // rectangle of bins its pixels map to (inclusive), for the activity test.
 struct DetTile {
@@ -70,6 +95,8 @@ struct Tables {
   const int* xstart;       // per layer, per bin column c: first x with colblk >= c
   const uint32_t* npix;    // per bin: pixels of the mask layer in it
   const DetTile* tiles;    // per detection tile of a frame
+  const AsmChunk* chunks;  // per assembly chunk of a frame
+  const uint32_t* wbins;   // per layer, per bitmap word column: first | last bin column << 16
 };
 
 // Arguments of one batch of T consecutive frames of one stream.
@@ -99,6 +126,7 @@ struct Scratch {
   uint32_t* det_bits;              // [T_max][bit_words]
   uint8_t* det_score;              // [T_max][score_bytes]
   uint32_t* chunk_counts;          // [T_max][n_chunks]
+  uint32_t* merged;                // [T_max][bit_words]: D_n bitmap of every frame of the batch
   uint32_t* frame_totals;          // [T_max]
   unsigned long long* out_base;    // [2]: running output offset (ping-pong)
   int* overflow;                   // [1]

@@ -6,55 +6,20 @@
 // i of frame k, each bin the word's pixels fall in contributes its bits from
 // the frame src(k, bin) -- the last frame up to k in which the bin was active
 // -- or from the kept set D_{n0-1} when the bin was inactive since the batch
-// began. The count pass sums the popcounts per chunk of words; the emit pass
-// turns chunk counts and frame totals into output offsets, scans the words of
-// its chunk, and writes one record per set bit, in order. The last frame of
-// the batch also becomes the new kept set (bitmap, scores, keypoints per bin).
+// began. Work is cut into chunks of whole rows of one layer, so a CTA knows
+// its layer and each row's bin row up front.
+//   k_count: merge each word from its sources, store it, and sum the
+//            popcounts per chunk and per frame;
+//   k_emit:  turn chunk counts and frame totals into output offsets, scan the
+//            chunk's stored words, and write one record per set bit, in order.
+// The last frame of the batch also becomes the new kept set (bitmap, scores,
+// keypoints per bin).
 #include "fkd_internal.cuh"
 
 namespace fkd {
 namespace {
 
-struct WordPos {
-  int l, y, wx;
-};
-
-__device__ __forceinline__ WordPos word_pos(const Geometry& g, long long i) {
-  int l = 0;
-  while (l + 1 < g.L && g.layer[l + 1].bit_off <= i) ++l;
-  const long long r = i - g.layer[l].bit_off;
-  WordPos p;
-  p.l = l;
-  p.y = (int)(r / g.layer[l].wpr);
-  p.wx = (int)(r % g.layer[l].wpr);
-  return p;
-}
-
-// Bits of bitmap word i (position p) of frame k taken from their bins' source
-// frames. prop receives the bits whose source is not frame k (carried over).
-__device__ __forceinline__ uint32_t merged_word(const Geometry& g, const Tables& tb,
-                                                const Scratch& s, const State& st, int k,
-                                                long long i, const WordPos& p, uint32_t* prop) {
-  const LayerGeom& lg = g.layer[p.l];
-  const uint16_t* colblk = tb.colblk + lg.col_off;
-  const int* xstart = tb.xstart + lg.xs_off;
-  const int r = tb.rowblk[lg.row_off + p.y];
-  const int xlo = p.wx * 32, xhi = min(xlo + 32, lg.w);
-  const int c_lo = colblk[xlo], c_hi = colblk[xhi - 1];
-  const int* srcrow = s.src + (long long)k * g.NB + r * g.N_c;
-  uint32_t word = 0, pm = 0;
-  for (int c = c_lo; c <= c_hi; ++c) {
-    const int a = max(xstart[c], xlo) - xlo, e = min(xstart[c + 1], xhi) - xlo;
-    if (e <= a) continue;
-    const uint32_t m = (e - a == 32) ? 0xffffffffu : (((1u << (e - a)) - 1u) << a);
-    const int sf = srcrow[c];
-    const uint32_t bits = sf < 0 ? st.bits_in[i] : s.det_bits[(long long)sf * g.bit_words + i];
-    word |= bits & m;
-    if (sf != k) pm |= m;
-  }
-  *prop = pm & word;
-  return word;
-}
+constexpr int kXsSmem = 1024;  // bin-column starts kept in shared memory when N_c < this
 
 __device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -63,25 +28,65 @@ __device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* red) {
   if (lane == 0) red[wid] = v;
   __syncthreads();
   uint32_t t = 0;
-  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+#pragma unroll
+  for (int q = 0; q < kAsmThreads / 32; ++q) t += red[q];
   return t;
 }
 
 __global__ void __launch_bounds__(kAsmThreads) k_count(Geometry g, Tables tb, Batch b, Scratch s,
                                                        State st) {
+  __shared__ int xs[kXsSmem];
   __shared__ uint32_t red[kAsmThreads / 32];
-  const int k = blockIdx.y, chunk = blockIdx.x;
-  const long long w0 = (long long)chunk * kAsmChunkWords + (long long)threadIdx.x * kAsmWordsPerThread;
+  const int k = blockIdx.y;
+  const AsmChunk ch = tb.chunks[blockIdx.x];
+  const LayerGeom& lg = g.layer[ch.layer];
+  const int wpr = lg.wpr, w = lg.w;
+  const int nwords = (ch.y1 - ch.y0) * wpr;
+  const long long word0 = lg.bit_off + (long long)ch.y0 * wpr;
+  const int* xsg = tb.xstart + lg.xs_off;
+  const bool xs_local = g.N_c < kXsSmem;
+  if (xs_local)
+    for (int q = threadIdx.x; q <= g.N_c; q += kAsmThreads) xs[q] = xsg[q];
+  __syncthreads();
+  const int* xst = xs_local ? xs : xsg;
+
+  const int* src_k = s.src + (long long)k * g.NB;
+  const uint32_t* det0 = s.det_bits + word0;
+  uint32_t* out = s.merged + (long long)k * g.bit_words + word0;
+  int j = threadIdx.x * kAsmWordsPerThread;
+  int y = ch.y0 + j / wpr, wx = j % wpr;
+  const int* srcrow = src_k + (j < nwords ? tb.rowblk[lg.row_off + y] : 0) * g.N_c;
   uint32_t cnt = 0;
-  for (int j = 0; j < kAsmWordsPerThread; ++j) {
-    const long long i = w0 + j;
-    if (i >= g.bit_words) break;
-    uint32_t pm;
-    cnt += __popc(merged_word(g, tb, s, st, k, i, word_pos(g, i), &pm));
+  for (int jj = 0; jj < kAsmWordsPerThread && j < nwords; ++jj, ++j) {
+    const uint32_t wb = tb.wbins[lg.wb_off + wx];
+    const int c_lo = wb & 0xffffu, c_hi = wb >> 16;
+    uint32_t word;
+    if (c_lo == c_hi) {
+      const int sf = srcrow[c_lo];
+      word = sf < 0 ? st.bits_in[word0 + j] : det0[(long long)sf * g.bit_words + j];
+    } else {
+      const int xlo = wx * 32, xhi = min(xlo + 32, w);
+      word = 0;
+      for (int c = c_lo; c <= c_hi; ++c) {
+        const int a = max(xst[c], xlo) - xlo, e = min(xst[c + 1], xhi) - xlo;
+        if (e <= a) continue;
+        const uint32_t m = (e - a == 32) ? 0xffffffffu : (((1u << (e - a)) - 1u) << a);
+        const int sf = srcrow[c];
+        const uint32_t bits = sf < 0 ? st.bits_in[word0 + j] : det0[(long long)sf * g.bit_words + j];
+        word |= bits & m;
+      }
+    }
+    out[j] = word;
+    cnt += __popc(word);
+    if (++wx == wpr) {
+      wx = 0;
+      ++y;
+      if (y < ch.y1) srcrow = src_k + tb.rowblk[lg.row_off + y] * g.N_c;
+    }
   }
   const uint32_t tot = block_sum(cnt, red);
   if (threadIdx.x == 0) {
-    s.chunk_counts[(long long)k * g.n_chunks + chunk] = tot;
+    s.chunk_counts[(long long)k * g.n_chunks + blockIdx.x] = tot;
     if (tot) atomicAdd(&s.frame_totals[k], tot);
   }
 }
@@ -92,14 +97,18 @@ __global__ void __launch_bounds__(kAsmThreads) k_emit(Geometry g, Tables tb, Bat
   __shared__ uint32_t wsum[kAsmThreads / 32];
   const int k = blockIdx.y, chunk = blockIdx.x;
   const bool last = k == b.T - 1;
+  const AsmChunk ch = tb.chunks[chunk];
+  const LayerGeom& lg = g.layer[ch.layer];
+  const int wpr = lg.wpr;
+  const int nwords = (ch.y1 - ch.y0) * wpr;
+  const long long word0 = lg.bit_off + (long long)ch.y0 * wpr;
 
-  // offsets: kept-set base of this call + earlier frames + earlier chunks
+  // offsets: base of this call + earlier frames + earlier chunks of this frame
   uint32_t part = 0;
-  for (int q = threadIdx.x; q < k; q += blockDim.x) part += s.frame_totals[q];
+  for (int q = threadIdx.x; q < k; q += kAsmThreads) part += s.frame_totals[q];
   const uint32_t frame_base = block_sum(part, red);
   part = 0;
-  for (int q = threadIdx.x; q < chunk; q += blockDim.x)
-    part += s.chunk_counts[(long long)k * g.n_chunks + q];
+  for (int q = threadIdx.x; q < chunk; q += kAsmThreads) part += s.chunk_counts[(long long)k * g.n_chunks + q];
   const uint32_t chunk_base = block_sum(part, red);
   const unsigned long long call_base = s.out_base[out.base_slot];
   if (chunk == 0 && threadIdx.x == 0) {
@@ -112,18 +121,16 @@ __global__ void __launch_bounds__(kAsmThreads) k_emit(Geometry g, Tables tb, Bat
   }
 
   // this thread's words (contiguous, so the scan order is the canonical order)
-  const long long w0 = (long long)chunk * kAsmChunkWords + (long long)threadIdx.x * kAsmWordsPerThread;
-  uint32_t words[kAsmWordsPerThread], props[kAsmWordsPerThread];
+  const int j0 = threadIdx.x * kAsmWordsPerThread;
+  const uint32_t* merged = s.merged + (long long)k * g.bit_words + word0;
+  uint32_t words[kAsmWordsPerThread];
   uint32_t cnt = 0;
 #pragma unroll
-  for (int j = 0; j < kAsmWordsPerThread; ++j) {
-    const long long i = w0 + j;
-    words[j] = props[j] = 0;
-    if (i < g.bit_words) {
-      words[j] = merged_word(g, tb, s, st, k, i, word_pos(g, i), &props[j]);
-      if (last) st.bits_out[i] = words[j];
-      cnt += __popc(words[j]);
-    }
+  for (int jj = 0; jj < kAsmWordsPerThread; ++jj) {
+    const int j = j0 + jj;
+    words[jj] = j < nwords ? merged[j] : 0u;
+    cnt += __popc(words[jj]);
+    if (last && j < nwords) st.bits_out[word0 + j] = words[jj];
   }
   // exclusive scan of cnt over the CTA
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -138,39 +145,44 @@ __global__ void __launch_bounds__(kAsmThreads) k_emit(Geometry g, Tables tb, Bat
   uint32_t before = 0;
   for (int q = 0; q < wid; ++q) before += wsum[q];
   unsigned long long idx = call_base + frame_base + chunk_base + before + incl - cnt;
-
   if (cnt == 0) return;
-  for (int j = 0; j < kAsmWordsPerThread; ++j) {
-    uint32_t wv = words[j];
-    if (!wv) continue;
-    const long long i = w0 + j;
-    const WordPos pos = word_pos(g, i);
-    const LayerGeom& lg = g.layer[pos.l];
-    const int r = tb.rowblk[lg.row_off + pos.y];
-    const int* srcrow = s.src + (long long)k * g.NB + r * g.N_c;
-    const long long row_off = lg.score_off + (long long)pos.y * lg.pitch;
-    while (wv) {
-      const int bit = __ffs(wv) - 1;
-      wv &= wv - 1;
-      const int x = pos.wx * 32 + bit;
-      const int c = tb.colblk[lg.col_off + x];
-      const int sf = srcrow[c];
-      const uint8_t score = sf < 0 ? st.score_in[row_off + x]
-                                   : s.det_score[(long long)sf * g.score_bytes + row_off + x];
-      const uint32_t flags = (props[j] >> bit) & 1u;
-      if (idx < (unsigned long long)out.cap) {
-        uint2 rec;
-        rec.x = (uint32_t)x | ((uint32_t)pos.y << 16);
-        rec.y = (uint32_t)pos.l | ((uint32_t)score << 8) | (flags << 16);
-        reinterpret_cast<uint2*>(out.rec)[idx] = rec;
-      } else {
-        *s.overflow = 1;
+
+  const int* src_k = s.src + (long long)k * g.NB;
+  const uint16_t* colblk = tb.colblk + lg.col_off;
+  int y = ch.y0 + j0 / wpr, wx = j0 % wpr;
+  for (int jj = 0; jj < kAsmWordsPerThread; ++jj) {
+    uint32_t wv = words[jj];
+    if (wv) {
+      const int r = tb.rowblk[lg.row_off + y];
+      const int* srcrow = src_k + r * g.N_c;
+      const long long row_off = lg.score_off + (long long)y * lg.pitch;
+      while (wv) {
+        const int bit = __ffs(wv) - 1;
+        wv &= wv - 1;
+        const int x = wx * 32 + bit;
+        const int c = colblk[x];
+        const int sf = srcrow[c];
+        const uint8_t score = sf < 0 ? st.score_in[row_off + x]
+                                     : s.det_score[(long long)sf * g.score_bytes + row_off + x];
+        const uint32_t flags = sf != k ? FKD_KP_PROPAGATED : 0u;
+        if (idx < (unsigned long long)out.cap) {
+          uint2 rec;
+          rec.x = (uint32_t)x | ((uint32_t)y << 16);
+          rec.y = (uint32_t)ch.layer | ((uint32_t)score << 8) | (flags << 16);
+          reinterpret_cast<uint2*>(out.rec)[idx] = rec;
+        } else {
+          *s.overflow = 1;
+        }
+        ++idx;
+        if (last) {
+          st.score_out[row_off + x] = score;
+          atomicAdd(&st.cnt_out[r * g.N_c + c], 1u);
+        }
       }
-      ++idx;
-      if (last) {
-        st.score_out[row_off + x] = score;
-        atomicAdd(&st.cnt_out[r * g.N_c + c], 1u);
-      }
+    }
+    if (++wx == wpr) {
+      wx = 0;
+      ++y;
     }
   }
 }

@@ -1,41 +1,48 @@
 // k_detect.cu -- masked segment test, corner score and 3x3 non-maximum
 // suppression (Sec. 2) over the active detection tiles of a batch.
 //
-// Persistent CTAs walk the compacted list of active (frame, tile) items. Per
-// item the CTA
-//   A. stages the tile plus a 4-pixel halo in shared memory with 16-byte loads;
-//   B. prefilters every pixel whose score the tile needs (the tile and a
-//      1-pixel ring) with packed byte arithmetic, 4 pixels per 32-bit word: a
-//      pixel can only pass the segment test at threshold t if two adjacent
-//      compass points of its ring (12, 3, 6, 9 o'clock) differ from it by more
-//      than t, since every 9-pixel arc of the 16-pixel ring contains two
-//      adjacent ones; candidates are compacted with warp ballots;
-//   C. scores the candidates exactly, two pixels per 32-bit word in 16-bit
-//      lanes: with I_k the ring values, the bright score is
-//      max over arcs of (min over the arc of I_k) - I_p and the dark score
-//      I_p - min over arcs of (max over the arc of I_k); arc minima come from
-//      3-input minima of 3-input minima;
-//   D. keeps a candidate when its score is >= t and strictly above its 8
-//      neighbours' scores (scores below t count as 0, which never changes the
-//      outcome), and writes the tile's keypoint bitmap and scores.
+// Every warp works alone on one 128 x 16 tile of one layer at a time (no
+// block-wide barriers; each warp owns a slice of shared memory), pulling
+// (frame, tile) items from the compacted list of active tiles. Per tile:
+//   A. stage the tile plus a 4-pixel halo (3 for the ring, 1 for the
+//      suppression neighbours), widened to 16 bytes left and right: 24 rows
+//      x 160 bytes, copied with cp.async (zero-filled outside the layer) into
+//      one of two buffers while the warp works on the previous tile;
+//   B. prefilter the 130 x 18 pixels whose score the tile needs, one 32-bit
+//      word (4 pixels) per lane per row, with packed byte arithmetic: a pixel
+//      can pass the segment test at threshold t only if two adjacent compass
+//      points of its ring (12, 3, 6, 9 o'clock) differ from it by more than t,
+//      because every 9-pixel arc of the 16-pixel ring holds two adjacent
+//      compass points; survivors are compacted per row with a warp scan;
+//   C. score the survivors exactly, two per lane in 16-bit lanes: with I_k the
+//      ring values, the bright score is max over arcs of (min over the arc of
+//      I_k) - I_p and the dark one I_p - min over arcs of (max over the arc);
+//      arc extrema are 3-input extrema of 3-input extrema;
+//   D. scan the score map: a pixel of the tile is kept when its score is >= t
+//      and strictly above its 8 neighbours' (scores below t count as 0, which
+//      never changes the outcome); write the tile's bitmap words and scores.
 // Bins are not consulted here: assembly takes each pixel from the frame its
-// bin points to, so the kernel only has to be right on every pixel of every
-// tile it processes.
+// bin points to, so the kernel only has to be right on the tiles it runs.
 #include "fkd_internal.cuh"
 
 namespace fkd {
 namespace {
 
-constexpr int TW = kDetTW, TH = kDetTH;
-constexpr int IN_W = TW + 32;  // smem input row: layer x in [x0-16, x0+TW+16)
-constexpr int IN_H = TH + 8;   // smem input rows: layer y in [y0-4, y0+TH+4)
-constexpr int SC_W = TW + 2;   // scores of x in [x0-1, x0+TW]
-constexpr int SC_H = TH + 2;   // and y in [y0-1, y0+TH]
-constexpr int PW = TW / 4 + 2; // prefilter words per row: x in [x0-4, x0+TW+4)
-constexpr int PWORDS = PW * SC_H;
-constexpr int MAX_CAND = PWORDS * 4;
-static_assert(IN_W <= 256, "candidate entries pack the column in 8 bits");
-static_assert(TW % 32 == 0, "bitmap words are whole inside a tile");
+constexpr int TW = kDetTW, TH = kDetTH;   // 128 x 16 output pixels per warp
+constexpr int IN_W = TW + 32;             // input row: x in [x0-16, x0+TW+16)
+constexpr int IN_H = TH + 8;              // input rows: y in [y0-4, y0+TH+4)
+constexpr int SC_P = TW + 8;              // score row pitch; column = x - x0 + 4
+constexpr int SC_H = TH + 2;              // score rows: y in [y0-1, y0+TH]
+constexpr int WARPS = kDetThreads / 32;
+constexpr int IN_BYTES = IN_W * IN_H;
+constexpr int SC_BYTES = SC_P * SC_H;
+constexpr int DET_WORDS = TH * (TW / 32);
+constexpr int LIST = 512;  // candidate list window per warp (entries)
+// per warp: input (double-buffered), score map, keypoint and pass bitmaps, candidate list
+constexpr int WARP_SMEM = 2 * IN_BYTES + SC_BYTES + 2 * DET_WORDS * 4 + LIST * 2;
+static_assert(TW == 32 * 4, "one 4-pixel word per lane per row");
+static_assert(SC_H * 4 <= 72 && SC_H > 16, "a lane's candidate bits: 16 rows in 64 bits + 2 rows");
+static_assert(IN_BYTES % 16 == 0 && SC_BYTES % 16 == 0, "16-byte aligned slices");
 
 // Per byte: bit 7 set where e >= T1 (T1 in 1..255, the same in every byte).
 __device__ __forceinline__ uint32_t bytes_ge(uint32_t e, uint32_t t1_low7, bool t1_high) {
@@ -47,14 +54,28 @@ __device__ __forceinline__ uint32_t ld32(const uint8_t* p) {
   return *reinterpret_cast<const uint32_t*>(p);
 }
 
-// 16 ring samples of two pixels, packed in 16-bit lanes: ring order starts
-// straight above the pixel and turns clockwise (y grows downwards).
+// Prefilter of the word at input offset o (4 pixels): bit 7 of each byte set
+// where two adjacent compass points differ from the pixel by more than t.
+__device__ __forceinline__ uint32_t prefilter(const uint8_t* in, int o, uint32_t t1_low7,
+                                              bool t1_high) {
+  const uint32_t C = ld32(in + o), Cp = ld32(in + o - 4), Cn = ld32(in + o + 4);
+  const uint32_t N = ld32(in + o - 3 * IN_W), S = ld32(in + o + 3 * IN_W);
+  const uint32_t E = __funnelshift_r(C, Cn, 24);  // bytes x+3 .. x+6
+  const uint32_t Wd = __funnelshift_r(Cp, C, 8);  // bytes x-3 .. x
+  const uint32_t gN = bytes_ge(__vabsdiffu4(N, C), t1_low7, t1_high);
+  const uint32_t gS = bytes_ge(__vabsdiffu4(S, C), t1_low7, t1_high);
+  const uint32_t gE = bytes_ge(__vabsdiffu4(E, C), t1_low7, t1_high);
+  const uint32_t gW = bytes_ge(__vabsdiffu4(Wd, C), t1_low7, t1_high);
+  return (gN | gS) & (gE | gW) & 0x80808080u;
+}
+
+// 16 ring samples, ring order from straight above clockwise (y down).
 #define FKD_RING(X)                                                                     \
   X(0, 0, -3) X(1, 1, -3) X(2, 2, -2) X(3, 3, -1) X(4, 3, 0) X(5, 3, 1) X(6, 2, 2)    \
   X(7, 1, 3) X(8, 0, 3) X(9, -1, 3) X(10, -2, 2) X(11, -3, 1) X(12, -3, 0)            \
   X(13, -3, -1) X(14, -2, -2) X(15, -1, -3)
 
-// Exact scores of two pixels at smem offsets o1, o2 (score in 16-bit lanes).
+// Exact scores of the pixels at input offsets o1, o2, in the two 16-bit lanes.
 __device__ __forceinline__ uint32_t score_pair(const uint8_t* in, int o1, int o2) {
   uint32_t v[16];
 #define FKD_LOAD(k, dx, dy)                                        \
@@ -85,155 +106,255 @@ __device__ __forceinline__ uint32_t score_pair(const uint8_t* in, int o1, int o2
   return __vimax_s16x2_relu(sb, sd);
 }
 
-__global__ void __launch_bounds__(kDetThreads) k_detect(Geometry g, Batch b, Scratch s, Tables tb,
-                                                        Params p) {
-  __shared__ __align__(16) uint8_t in[IN_H * IN_W];
-  __shared__ uint8_t sc[SC_H * SC_W];
-  __shared__ uint16_t cand[MAX_CAND];
-  __shared__ uint32_t detw[TH * (TW / 32)];
-  __shared__ int ncand;
+// Bit 7 of each byte of `keep` gathered into a nibble (byte i -> bit i): the
+// four bits land on distinct positions of the product, so nothing carries.
+__device__ __forceinline__ uint32_t nibble(uint32_t keep) {
+  return (((keep >> 7) & 0x01010101u) * 0x00204081u >> 21) & 0xfu;
+}
 
-  const uint32_t count = *s.work_count;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const uint32_t t1 = (uint32_t)p.t + 1u;  // score >= t  <=>  some arc beyond I_p +- t
+struct Item {
+  int k, l, x0, y0, w, h;
+  const uint8_t* src;
+  int pitch;
+};
+
+__device__ __forceinline__ Item decode(const Geometry& g, const Batch& b, const Scratch& s,
+                                       const Tables& tb, uint32_t item) {
+  const uint32_t wi = s.work[item];
+  const DetTile tile = tb.tiles[wi % (uint32_t)g.n_tiles];
+  Item it;
+  it.k = (int)(wi / (uint32_t)g.n_tiles);
+  it.l = tile.layer;
+  it.w = g.layer[it.l].w;
+  it.h = g.layer[it.l].h;
+  it.x0 = tile.tx * TW;
+  it.y0 = tile.ty * TH;
+  if (it.l == 0) {
+    it.src = b.frames + (long long)it.k * b.frame_stride;
+    it.pitch = b.pitch;
+  } else {
+    it.src = s.pyr + (long long)it.k * g.pyr_bytes + g.layer[it.l].pyr_off;
+    it.pitch = g.layer[it.l].pitch;
+  }
+  return it;
+}
+
+// A. stage input rows y0-4 .. y0+TH+3, columns x0-16 .. x0+TW+15, zeros
+// outside the layer. x0 is a multiple of 128, so each 16-byte chunk is either
+// wholly left of the layer or starts inside it.
+__device__ __forceinline__ void stage(uint8_t* in, const Item& it, int lane) {
+  const bool vec = ((reinterpret_cast<uintptr_t>(it.src) | (uintptr_t)it.pitch) & 15) == 0;
+  for (int q = lane; q < IN_H * (IN_W / 16); q += 32) {
+    const int r = q / (IN_W / 16), c = (q % (IN_W / 16)) * 16;
+    const int gy = it.y0 - 4 + r, gx = it.x0 - 16 + c;
+    uint8_t* d = in + r * IN_W + c;
+    const bool row_ok = gy >= 0 && gy < it.h;
+    if (vec) {
+      const int bytes = (row_ok && gx >= 0) ? max(0, min(16, it.w - gx)) : 0;
+      cp_async16(d, bytes ? it.src + (long long)gy * it.pitch + gx : it.src, bytes);
+    } else {
+      uint32_t wd[4] = {0u, 0u, 0u, 0u};
+      if (row_ok) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (gx + j >= 0 && gx + j < it.w)
+            wd[j >> 2] |= (uint32_t)it.src[(long long)gy * it.pitch + gx + j] << (8 * (j & 3));
+      }
+      *reinterpret_cast<uint4*>(d) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    }
+  }
+}
+
+// Input offset of candidate bit b of a lane's mask (4 bits per score row).
+__device__ __forceinline__ int cand_off(int b, int lane) {
+  return ((b >> 2) + 3) * IN_W + 16 + 4 * lane + (b & 3);
+}
+// Score-map offset of the pixel at input offset o.
+__device__ __forceinline__ int sc_of(int o) { return (o / IN_W - 3) * SC_P + (o % IN_W) - 12; }
+
+__global__ void __launch_bounds__(kDetThreads, 2) k_detect(Geometry g, Batch b, Scratch s,
+                                                           Tables tb, Params p) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint8_t* inbuf = smem + warp * WARP_SMEM;
+  uint8_t* sc = inbuf + 2 * IN_BYTES;
+  uint32_t* detw = reinterpret_cast<uint32_t*>(sc + SC_BYTES);
+  uint32_t* passw = detw + DET_WORDS;
+  uint16_t* list = reinterpret_cast<uint16_t*>(passw + DET_WORDS);
+
+  const uint32_t count_items = *s.work_count;
+  const uint32_t t = (uint32_t)p.t;
+  const uint32_t t1 = t + 1u;  // score >= t  <=>  some arc beyond I_p +- t
   const uint32_t t1_low7 = (t1 & 0x7fu) * 0x01010101u;
   const bool t1_high = t1 >= 128u;
   const bool none = t1 > 255u;
+  const uint32_t stride = gridDim.x * WARPS;
 
-  for (uint32_t item = blockIdx.x; item < count; item += gridDim.x) {
-    const uint32_t wi = s.work[item];
-    const int k = (int)(wi / (uint32_t)g.n_tiles);
-    const DetTile tile = tb.tiles[wi % (uint32_t)g.n_tiles];
-    const int l = tile.layer;
-    const LayerGeom& lg = g.layer[l];
-    const int w = lg.w, h = lg.h;
-    const int x0 = tile.tx * TW, y0 = tile.ty * TH;
-    const uint8_t* src;
-    int pitch;
-    if (l == 0) {
-      src = b.frames + (long long)k * b.frame_stride;
-      pitch = b.pitch;
-    } else {
-      src = s.pyr + (long long)k * g.pyr_bytes + lg.pyr_off;
-      pitch = lg.pitch;
+  uint32_t item = blockIdx.x * WARPS + warp;
+  int buf = 0;
+  Item nxt{};
+  if (item < count_items) {
+    nxt = decode(g, b, s, tb, item);
+    stage(inbuf, nxt, lane);
+  }
+  cp_async_commit();
+  for (; item < count_items; item += stride) {
+    const Item it = nxt;
+    const uint8_t* in = inbuf + buf * IN_BYTES;
+    // prefetch the next tile into the other buffer, then wait for this one
+    if (item + stride < count_items) {
+      nxt = decode(g, b, s, tb, item + stride);
+      stage(inbuf + (buf ^ 1) * IN_BYTES, nxt, lane);
     }
-    const bool vec = ((reinterpret_cast<uintptr_t>(src) | (uintptr_t)pitch) & 15) == 0;
+    cp_async_commit();
+    for (int q = lane; q < SC_BYTES / 16; q += 32)
+      reinterpret_cast<uint4*>(sc)[q] = make_uint4(0u, 0u, 0u, 0u);
+    detw[lane] = detw[lane + 32] = 0u;
+    passw[lane] = passw[lane + 32] = 0u;
+    cp_async_wait<1>();
+    __syncwarp();
+    const int k = it.k, l = it.l, w = it.w, h = it.h, x0 = it.x0, y0 = it.y0;
 
-    // A. stage rows y0-4 .. y0+TH+3, columns x0-16 .. x0+TW+15 (zeros outside)
-    for (int q = tid; q < IN_H * (IN_W / 16); q += blockDim.x) {
-      const int r = q / (IN_W / 16), c = (q % (IN_W / 16)) * 16;
-      const int gy = y0 - 4 + r, gx = x0 - 16 + c;
-      uint8_t* d = in + r * IN_W + c;
-      if (gy >= 0 && gy < h && vec && gx >= 0 && gx + 16 <= w) {
-        *reinterpret_cast<uint4*>(d) =
-            __ldg(reinterpret_cast<const uint4*>(src + (long long)gy * pitch + gx));
-      } else {
-        const bool row_ok = gy >= 0 && gy < h;
+    // B. prefilter the score rows y0-1 .. y0+TH (input rows 3 .. TH+4); lane
+    //    owns the word x0+4*lane .. +3 of every row and keeps its candidate
+    //    bits: 4 per row, rows 0..15 in m64, rows 16..17 in m_hi.
+    const bool interior = x0 - 1 >= 3 && x0 + TW < w - 3 && y0 - 1 >= 3 && y0 + TH < h - 3;
+    unsigned long long m64 = 0ull;
+    uint32_t m_hi = 0u, m_edge = 0u;
+    if (!none) {
+      const int c = 16 + 4 * lane;
+      const int x = x0 + 4 * lane;
+      uint32_t colmask = 0x80808080u;  // pixels of this word inside the scorable band
+      if (!interior) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          d[j] = (row_ok && gx + j >= 0 && gx + j < w) ? src[(long long)gy * pitch + gx + j] : 0;
+        for (int i = 0; i < 4; ++i)
+          if (x + i < 3 || x + i >= w - 3) colmask &= ~(0x80u << (8 * i));
+      }
+#pragma unroll
+      for (int rr = 0; rr < SC_H; ++rr) {
+        uint32_t keep = prefilter(in, (rr + 3) * IN_W + c, t1_low7, t1_high) & colmask;
+        if (!interior) {
+          const int y = y0 - 1 + rr;
+          if (y < 3 || y >= h - 3) keep = 0;
+        }
+        const uint32_t nb = nibble(keep);
+        if (rr < 16) m64 |= (unsigned long long)nb << (4 * rr);
+        else m_hi |= nb << (4 * (rr - 16));
+      }
+      // the score region's edge columns x0-1 and x0+TW: lane rr < SC_H owns row rr
+      if (lane < SC_H) {
+        const int y = y0 - 1 + lane;
+        if (y >= 3 && y < h - 3) {
+          const int r = (lane + 3) * IN_W;
+          if (x0 - 1 >= 3 && x0 - 1 < w - 3 &&
+              (prefilter(in, r + 12, t1_low7, t1_high) & 0x80000000u))
+            m_edge |= 1u;
+          if (x0 + TW >= 3 && x0 + TW < w - 3 &&
+              (prefilter(in, r + 16 + TW, t1_low7, t1_high) & 0x80u))
+            m_edge |= 2u;
+        }
       }
     }
-    for (int q = tid; q < SC_H * SC_W; q += blockDim.x) sc[q] = 0;
-    if (tid < TH * (TW / 32)) detw[tid] = 0;
-    if (tid == 0) ncand = 0;
-    __syncthreads();
 
-    // B. prefilter, 4 pixels per word; word j of score row rr covers
-    //    x = x0-4+4j .. x0-1+4j, y = y0-1+rr; in smem: row rr+3, column 12+4j.
-    for (int base = 0; base < PWORDS; base += blockDim.x) {
-      const int q = base + tid;
-      uint32_t keep = 0;
-      int r = 0, c = 0;
-      if (q < PWORDS && !none) {
-        const int rr = q / PW, j = q % PW;
-        r = rr + 3;
-        c = 12 + 4 * j;
-        const uint8_t* row = in + r * IN_W + c;
-        const uint32_t C = ld32(row), Cp = ld32(row - 4), Cn = ld32(row + 4);
-        const uint32_t N = ld32(row - 3 * IN_W), S = ld32(row + 3 * IN_W);
-        const uint32_t E = __funnelshift_r(C, Cn, 24);  // x+3
-        const uint32_t Wd = __funnelshift_r(Cp, C, 8);  // x-3
-        const uint32_t gN = bytes_ge(__vabsdiffu4(N, C), t1_low7, t1_high);
-        const uint32_t gS = bytes_ge(__vabsdiffu4(S, C), t1_low7, t1_high);
-        const uint32_t gE = bytes_ge(__vabsdiffu4(E, C), t1_low7, t1_high);
-        const uint32_t gW = bytes_ge(__vabsdiffu4(Wd, C), t1_low7, t1_high);
-        keep = (gN | gS) & (gE | gW) & 0x80808080u;
-        if (keep) {
-          // only the score region, and no pixel within 3 of the layer edge
-          const int gy = y0 - 1 + rr, gx = x0 - 4 + 4 * j;
-          if (gy < 3 || gy >= h - 3) keep = 0;
+    // C. exact scores. The lanes' candidates are packed into one list (warp
+    //    scan of the per-lane counts), 64 per round, two per lane; a window
+    //    of LIST entries at a time. A pixel of the tile scoring >= t is marked
+    //    in the pass bitmap.
+    const int n = __popcll(m64) + __popc(m_hi) + __popc(m_edge);
+    int incl = n;
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int x = gx + i;
-            const bool ok = x >= 3 && x < w - 3 && x >= x0 - 1 && x <= x0 + TW;
-            if (!ok) keep &= ~(0x80u << (8 * i));
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int w0 = 0; w0 < total; w0 += LIST) {
+      // this window's entries: input offsets of the candidates, in lane order
+      int idx = incl - n;
+      if (idx < w0 + LIST && idx + n > w0) {
+        unsigned long long mm = m64;
+        uint32_t mh = m_hi, me = m_edge;
+        while ((mm | mh | me) && idx < w0 + LIST) {
+          int o;
+          if (mm) {
+            const int bb = __ffsll((long long)mm) - 1;
+            mm &= mm - 1;
+            o = cand_off(bb, lane);
+          } else if (mh) {
+            const int bb = __ffs(mh) - 1;
+            mh &= mh - 1;
+            o = cand_off(64 + bb, lane);
+          } else {
+            const int e = __ffs(me) - 1;
+            me &= me - 1;
+            o = (lane + 3) * IN_W + (e ? 16 + TW : 15);
+          }
+          if (idx >= w0) list[idx - w0] = (uint16_t)o;
+          ++idx;
+        }
+      }
+      __syncwarp();
+      const int cnt = min(LIST, total - w0);
+      for (int base = 0; base < cnt; base += 64) {
+        const int i1 = base + 2 * lane;
+        if (i1 < cnt) {
+          const bool two = i1 + 1 < cnt;
+          const int o1 = list[i1], o2 = two ? list[i1 + 1] : o1;
+          const uint32_t sp = score_pair(in, o1, o2);
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            if (j == 0 || two) {
+              const int o = j ? o2 : o1;
+              const uint32_t v = (sp >> (16 * j)) & 0xffffu;
+              const bool ok = v >= t;
+              sc[sc_of(o)] = ok ? (uint8_t)v : 0;
+              const int r = o / IN_W, c = o % IN_W;  // tile pixel: rows 4..TH+3, cols 16..TW+15
+              if (ok && r >= 4 && r < TH + 4 && c >= 16 && c < TW + 16) {
+                const int ly = r - 4, lx = c - 16;
+                atomicOr(&passw[ly * (TW / 32) + (lx >> 5)], 1u << (lx & 31));
+              }
+            }
           }
         }
       }
-      unsigned bal[4];
-      int tot = 0;
+      __syncwarp();
+    }
+
+    // D. strict 3x3 maxima among the tile's passing pixels
+    const LayerGeom& lg = g.layer[l];
+    uint8_t* dscore = s.det_score + (long long)k * g.score_bytes + lg.score_off;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        bal[i] = __ballot_sync(0xffffffffu, (keep >> (8 * i + 7)) & 1u);
-        tot += __popc(bal[i]);
-      }
-      if (tot) {
-        int wbase = 0;
-        if (lane == 0) wbase = atomicAdd(&ncand, tot);
-        wbase = __shfl_sync(0xffffffffu, wbase, 0);
-        const unsigned lt = (1u << lane) - 1u;
-        int off = wbase;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          if ((bal[i] >> lane) & 1u) cand[off + __popc(bal[i] & lt)] = (uint16_t)((r << 8) | (c + i));
-          off += __popc(bal[i]);
+    for (int j = 0; j < DET_WORDS / 32; ++j) {
+      const int idx = lane + 32 * j;
+      const int ly = idx / (TW / 32), lx0 = (idx % (TW / 32)) * 32;
+      uint32_t pw = passw[idx];
+      while (pw) {
+        const int bb = __ffs(pw) - 1;
+        pw &= pw - 1;
+        const int lx = lx0 + bb;
+        const uint8_t* q = sc + (ly + 1) * SC_P + 4 + lx;
+        const int v = q[0];
+        if (v > q[-SC_P - 1] && v > q[-SC_P] && v > q[-SC_P + 1] && v > q[-1] && v > q[1] &&
+            v > q[SC_P - 1] && v > q[SC_P] && v > q[SC_P + 1]) {
+          atomicOr(&detw[idx], 1u << bb);
+          dscore[(long long)(y0 + ly) * lg.pitch + x0 + lx] = (uint8_t)v;
         }
       }
     }
-    __syncthreads();
+    __syncwarp();
 
-    // C. exact scores of the candidates, two per thread
-    const int nc = ncand;
-    for (int pi = tid; 2 * pi < nc; pi += blockDim.x) {
-      const int e1 = cand[2 * pi], e2 = cand[min(2 * pi + 1, nc - 1)];
-      const int o1 = (e1 >> 8) * IN_W + (e1 & 255), o2 = (e2 >> 8) * IN_W + (e2 & 255);
-      const uint32_t sp = score_pair(in, o1, o2);
-      const uint32_t s1 = sp & 0xffffu, s2 = sp >> 16;
-      sc[((e1 >> 8) - 3) * SC_W + (e1 & 255) - 15] = s1 >= (uint32_t)p.t ? (uint8_t)s1 : 0;
-      if (2 * pi + 1 < nc)
-        sc[((e2 >> 8) - 3) * SC_W + (e2 & 255) - 15] = s2 >= (uint32_t)p.t ? (uint8_t)s2 : 0;
+    // E. the tile's bitmap words (TH rows x TW/32 words)
+    uint32_t* bits = s.det_bits + (long long)k * g.bit_words + lg.bit_off;
+#pragma unroll
+    for (int j = 0; j < DET_WORDS / 32; ++j) {
+      const int idx = lane + 32 * j;
+      const int ly = idx / (TW / 32), wx = x0 / 32 + idx % (TW / 32);
+      if (y0 + ly < h && wx < lg.wpr) bits[(long long)(y0 + ly) * lg.wpr + wx] = detw[idx];
     }
-    __syncthreads();
-
-    // D. strict 3x3 maxima among the tile's own pixels
-    uint8_t* dscore = s.det_score + (long long)k * g.score_bytes + lg.score_off;
-    for (int ci = tid; ci < nc; ci += blockDim.x) {
-      const int e = cand[ci];
-      const int r = e >> 8, c = e & 255;
-      if (r < 4 || r >= TH + 4 || c < 16 || c >= TW + 16) continue;
-      const uint8_t* sp = sc + (r - 3) * SC_W + (c - 15);
-      const int v = sp[0];
-      if (v == 0) continue;
-      const bool is_max = v > sp[-SC_W - 1] && v > sp[-SC_W] && v > sp[-SC_W + 1] && v > sp[-1] &&
-                          v > sp[1] && v > sp[SC_W - 1] && v > sp[SC_W] && v > sp[SC_W + 1];
-      if (is_max) {
-        const int lx = c - 16, ly = r - 4;
-        atomicOr(&detw[ly * (TW / 32) + (lx >> 5)], 1u << (lx & 31));
-        dscore[(long long)(y0 + ly) * lg.pitch + x0 + lx] = (uint8_t)v;
-      }
-    }
-    __syncthreads();
-
-    // E. the tile's bitmap words
-    if (tid < TH * (TW / 32)) {
-      const int ly = tid / (TW / 32), wx = tid % (TW / 32);
-      const int gy = y0 + ly, gw = x0 / 32 + wx;
-      if (gy < h && gw < lg.wpr)
-        s.det_bits[(long long)k * g.bit_words + lg.bit_off + (long long)gy * lg.wpr + gw] = detw[tid];
-    }
-    __syncthreads();
+    __syncwarp();
+    buf ^= 1;
   }
+  cp_async_wait<0>();
 }
 
 }  // namespace
@@ -242,7 +363,8 @@ int detect_grid_size() {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_detect, kDetThreads, 0);
+  cudaFuncSetAttribute(k_detect, cudaFuncAttributeMaxDynamicSharedMemorySize, WARPS * WARP_SMEM);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_detect, kDetThreads, WARPS * WARP_SMEM);
   if (sms <= 0) sms = 1;
   if (per_sm <= 0) per_sm = 1;
   return sms * per_sm;
@@ -250,7 +372,7 @@ int detect_grid_size() {
 
 void launch_detect(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                    const Params& p, int grid, cudaStream_t st) {
-  k_detect<<<grid, kDetThreads, 0, st>>>(g, b, s, tb, p);
+  k_detect<<<grid, kDetThreads, WARPS * WARP_SMEM, st>>>(g, b, s, tb, p);
 }
 
 }  // namespace fkd

@@ -5,30 +5,30 @@
 namespace fkd {
 namespace {
 
-// One warp per bin, walking the batch's frames 32 at a time.
+// One CTA per bin, walking the batch's frames 256 at a time.
 //   mask:  first frame of the stream or FKD_MASK_FULL -> 1; FKD_MASK_ID ->
 //          sum |L_n - L_{n-1}| > T_I * (pixels of the bin) (Eq. 2 read as
 //          "detect where the content changed"); FKD_MASK_KB -> keypoints of
 //          D_{n-1} in the bin >= T_H (Eqs. 3-4, batches of one frame).
 //   src:   Eq. 1 applied frame after frame means a bin of frame k shows the
 //          detections of the last frame m <= k in which the bin was active;
-//          src = m, or -1 when no such frame is in the batch (the kept set).
-//          Per bin this is a running "last set index", done with a ballot
-//          and a count of leading zeros per 32 frames.
-__global__ void k_mask(Geometry g, Tables tb, Batch b, Scratch s, Params p, State st,
-                       int reset_base_slot) {
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nthreads = gridDim.x * blockDim.x;
-  for (int k = gtid; k < b.T; k += nthreads) s.frame_totals[k] = 0;
-  if (gtid == 0) {
-    *s.work_count = 0;
-    if (reset_base_slot >= 0) s.out_base[reset_base_slot] = 0;
+//          src = m, or -1 when no such frame is in the batch (the kept set):
+//          an inclusive max-scan of (active ? k : -1) over the frames.
+__global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Batch b, Scratch s,
+                                                       Params p, State st, int reset_base_slot) {
+  __shared__ int wmax[kMaskThreads / 32];
+  const int bin = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (bin == 0) {
+    for (int k = tid; k < b.T; k += kMaskThreads) s.frame_totals[k] = 0;
+    if (tid == 0) {
+      *s.work_count = 0;
+      if (reset_base_slot >= 0) s.out_base[reset_base_slot] = 0;
+    }
   }
-  const int bin = gtid >> 5, lane = threadIdx.x & 31;
-  if (bin >= g.NB) return;
+  if (tid == 0) st.cnt_out[bin] = 0;
   int carry = -1;
-  for (int k0 = 0; k0 < b.T; k0 += 32) {
-    const int k = k0 + lane;
+  for (int k0 = 0; k0 < b.T; k0 += kMaskThreads) {
+    const int k = k0 + tid;
     int m = 0;
     if (k < b.T) {
       const long long n = b.first_frame + k;
@@ -43,14 +43,24 @@ __global__ void k_mask(Geometry g, Tables tb, Batch b, Scratch s, Params p, Stat
       }
       s.mask[(long long)k * g.NB + bin] = (uint8_t)m;
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, m);
-    const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-    const unsigned mine = bal & upto;
-    const int src = mine ? k0 + 31 - __clz(mine) : carry;
-    if (k < b.T) s.src[(long long)k * g.NB + bin] = src;
-    if (bal) carry = k0 + 31 - __clz(bal);
+    int v = m ? k : -1;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int o = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v = max(v, o);
+    }
+    if (lane == 31) wmax[warp] = v;
+    __syncthreads();
+    int before = carry, all = carry;
+#pragma unroll
+    for (int w = 0; w < kMaskThreads / 32; ++w) {
+      if (w < warp) before = max(before, wmax[w]);
+      all = max(all, wmax[w]);
+    }
+    if (k < b.T) s.src[(long long)k * g.NB + bin] = max(v, before);
+    carry = all;
+    __syncthreads();
   }
-  if (lane == 0) st.cnt_out[bin] = 0;
 }
 
 // One thread per (frame, tile): a tile is active when any bin its pixels map
@@ -91,9 +101,7 @@ __global__ void k_worklist(Geometry g, Tables tb, Batch b, Scratch s) {
 
 void launch_mask(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                  const Params& p, const State& state, cudaStream_t st, int reset_base_slot) {
-  const int threads = 256;
-  const int blocks = (g.NB * 32 + threads - 1) / threads;
-  k_mask<<<blocks, threads, 0, st>>>(g, tb, b, s, p, state, reset_base_slot);
+  k_mask<<<g.NB, kMaskThreads, 0, st>>>(g, tb, b, s, p, state, reset_base_slot);
 }
 
 void launch_worklist(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,

@@ -1,209 +1,362 @@
 // k_pyramid.cu -- pyramid of octaves / intra-octaves and per-bin change sums.
 //
-// One CTA owns a 96 x 96 tile of c_0 of one frame. It loads the tile into
-// shared memory with 16-byte vector loads, builds every layer of the tile in
-// shared memory (Sec. 2: octaves c_i by 2x2 half-sampling, intra-octaves d_i
-// by 2/3 resampling of c_0 then half-sampling), writes layers >= 1 to the
-// frame's pyramid buffer, and -- for the intensity difference mask (Eq. 2,
-// Sec. 3.1, which reuses the pyramid) -- adds |L_n - L_{n-1}| of the mask
-// layer into the per-bin sums. The previous frame's mask layer is rebuilt
-// from its c_0 tile in shared memory rather than read back, so the frames
-// of a batch have no dependency on one another here.
+// One CTA owns a 96 x 96 tile of c_0 of one frame. It copies the tile into
+// shared memory with cp.async, builds every layer of the tile there (Sec. 2:
+// octaves c_i by 2x2 half-sampling, intra-octaves d_i by 2/3 resampling of
+// c_0 then half-sampling), storing each output word both to shared memory
+// (input of the next layer) and straight to the frame's pyramid buffer, and
+// -- for the intensity difference mask (Eq. 2, Sec. 3.1, which reuses the
+// pyramid) -- adds |L_n - L_{n-1}| of the mask layer into the per-bin sums.
+// The previous frame's mask layer is rebuilt from its c_0 tile in shared
+// memory rather than read back, so the frames of a batch do not depend on
+// one another here. The kernel is instantiated per (octaves, intra-octaves)
+// so that every level's size is a compile-time constant.
+//
+// 96 is a multiple of 3 * 2^5: for O <= 6 every layer's tile is whole, so the
+// 2x2 box and the 3x3 -> 2x2 resampling never cross a tile edge.
 #include "fkd_internal.cuh"
 
 namespace fkd {
 namespace {
 
-// Shared-memory layout of one tile's pyramid for O <= 6: c_i is (96>>i)^2
-// bytes, d_i is (64>>i)^2 bytes.
-__host__ __device__ constexpr int c_size(int i) { return (kPyrTile >> i) * (kPyrTile >> i); }
-__host__ __device__ constexpr int d_size(int i) { return ((2 * kPyrTile / 3) >> i) * ((2 * kPyrTile / 3) >> i); }
-__host__ __device__ constexpr int c_off(int i) { return i == 0 ? 0 : c_off(i - 1) + c_size(i - 1); }
-__host__ __device__ constexpr int d_off(int i) { return i == 0 ? c_off(6) : d_off(i - 1) + d_size(i - 1); }
-constexpr int kPyrSmem = (d_off(6) + 15) / 16 * 16;
+constexpr int P = kPyrTile;  // 96
+constexpr int NT = kPyrThreads;
+__host__ __device__ constexpr int c_side(int i) { return P >> i; }
+__host__ __device__ constexpr int d_side(int i) { return (2 * P / 3) >> i; }
+__host__ __device__ constexpr int r16(int v) { return (v + 15) / 16 * 16; }
+__host__ __device__ constexpr int c_off(int i) { return i == 0 ? 0 : r16(c_off(i - 1) + c_side(i - 1) * c_side(i - 1)); }
+__host__ __device__ constexpr int d_off(int i) { return i == 0 ? r16(c_off(6)) : r16(d_off(i - 1) + d_side(i - 1) * d_side(i - 1)); }
+constexpr int kPyrSmem = d_off(6);
+
+// Offsets of a level chosen at run time (no recursion in device code).
+__device__ __forceinline__ int c_off_rt(int i) {
+  int o = 0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j)
+    if (j < i) o = r16(o + c_side(j) * c_side(j));
+  return o;
+}
+__device__ __forceinline__ int d_off_rt(int i) {
+  int o = d_off(0);
+#pragma unroll
+  for (int j = 0; j < 6; ++j)
+    if (j < i) o = r16(o + d_side(j) * d_side(j));
+  return o;
+}
 constexpr int kLocalBins = 1024;
 
-struct Level {
-  int off, n;  // smem offset and tile side
-};
-
-__device__ __forceinline__ Level level_of(int layer, int intra) {
-  int i = intra ? layer >> 1 : layer;
-  bool is_d = intra && (layer & 1);
-  Level lv;
-  lv.off = is_d ? d_off(i) : c_off(i);
-  lv.n = is_d ? ((2 * kPyrTile / 3) >> i) : (kPyrTile >> i);
-  return lv;
+__device__ __forceinline__ uint32_t ld32(const uint8_t* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
 }
 
-// Load a 96 x 96 tile of a frame (zeros outside the frame).
-__device__ void load_c0(uint8_t* dst, const uint8_t* frame, int pitch, int gx0, int gy0, int W,
-                        int H) {
+// Where a level's outputs go in global memory: the tile's first pixel of the
+// layer, the layer pitch, and how much of the tile lies inside the layer.
+struct Out {
+  uint8_t* p;
+  int pitch, nx, ny;
+};
+
+// Start copying the 96 x 96 tile at (gx0, gy0) of a frame (zeros outside the
+// frame): cp.async with zero fill when the frame allows 16-byte copies, plain
+// byte loads otherwise. The caller commits, waits and syncs.
+__device__ __forceinline__ void load_c0(uint8_t* dst, const uint8_t* frame, int pitch, int gx0,
+                                        int gy0, int W, int H) {
   const bool vec = ((reinterpret_cast<uintptr_t>(frame) | (uintptr_t)pitch) & 15) == 0;
-  constexpr int kChunks = kPyrTile / 16;
-  for (int q = threadIdx.x; q < kPyrTile * kChunks; q += blockDim.x) {
-    int r = q / kChunks, c = (q % kChunks) * 16;
-    int gy = gy0 + r, gx = gx0 + c;
-    uint8_t* d = dst + r * kPyrTile + c;
-    if (gy < H && vec && gx + 16 <= W) {
-      *reinterpret_cast<uint4*>(d) =
-          __ldg(reinterpret_cast<const uint4*>(frame + (size_t)gy * pitch + gx));
-    } else {
-      for (int j = 0; j < 16; ++j)
-        d[j] = (gy < H && gx + j < W) ? frame[(size_t)gy * pitch + gx + j] : 0;
+  constexpr int kChunks = P / 16;
+#pragma unroll
+  for (int q0 = 0; q0 < P * kChunks; q0 += NT) {
+    const int q = q0 + threadIdx.x;
+    if (q < P * kChunks) {
+      const int r = q / kChunks, c = (q % kChunks) * 16;
+      const int gy = gy0 + r, gx = gx0 + c;
+      uint8_t* d = dst + r * P + c;
+      if (vec) {
+        const int bytes = gy < H ? max(0, min(16, W - gx)) : 0;
+        cp_async16(d, bytes ? frame + (size_t)gy * pitch + gx : frame, bytes);
+      } else {
+        uint32_t wd[4] = {0u, 0u, 0u, 0u};
+        if (gy < H) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (gx + j < W) wd[j >> 2] |= (uint32_t)frame[(size_t)gy * pitch + gx + j] << (8 * (j & 3));
+        }
+        *reinterpret_cast<uint4*>(d) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+      }
     }
   }
 }
 
-// 2x2 box mean, round half up: src is n x n, dst (n/2) x (n/2).
-__device__ void half_sample(const uint8_t* src, int n, uint8_t* dst) {
-  const int m = n / 2;
-  for (int q = threadIdx.x; q < m * m; q += blockDim.x) {
-    int y = q / m, x = q % m;
-    const uint8_t* s = src + (2 * y) * n + 2 * x;
-    unsigned sum = s[0] + s[1] + s[n] + s[n + 1] + 2u;
-    dst[q] = (uint8_t)(sum >> 2);
+// 2x2 box mean with round-half-up of an N x N level into (N/2) x (N/2).
+// Four outputs per step when N/2 is a multiple of 4: the even and odd bytes
+// of two input rows are spread into 16-bit lanes, summed with +2, shifted by
+// 2 and repacked. WRITE: also store the outputs inside the layer to `o`.
+template <int N, bool WRITE>
+__device__ __forceinline__ void half_level(const uint8_t* src, uint8_t* dst, const Out& o) {
+  constexpr int M = N / 2;
+  if constexpr (M % 4 == 0) {
+    constexpr int WPR = M / 4, TOTAL = M * WPR;
+#pragma unroll
+    for (int q0 = 0; q0 < TOTAL; q0 += NT) {
+      const int q = q0 + threadIdx.x;
+      if (TOTAL % NT == 0 || q < TOTAL) {
+        const int y = q / WPR, xw = q % WPR;
+        const uint8_t* a = src + (2 * y) * N + 8 * xw;
+        const uint32_t a0 = ld32(a), a1 = ld32(a + 4), b0 = ld32(a + N), b1 = ld32(a + N + 4);
+        const uint32_t lo = __byte_perm(a0, 0, 0x4240) + __byte_perm(a0, 0, 0x4341) +
+                            __byte_perm(b0, 0, 0x4240) + __byte_perm(b0, 0, 0x4341) + 0x00020002u;
+        const uint32_t hi = __byte_perm(a1, 0, 0x4240) + __byte_perm(a1, 0, 0x4341) +
+                            __byte_perm(b1, 0, 0x4240) + __byte_perm(b1, 0, 0x4341) + 0x00020002u;
+        // lanes hold sums <= 1022; >> 2 leaves each result in its lane's low byte
+        const uint32_t v = __byte_perm((lo >> 2) & 0x00ff00ffu, (hi >> 2) & 0x00ff00ffu, 0x6420);
+        *reinterpret_cast<uint32_t*>(dst + y * M + 4 * xw) = v;
+        if (WRITE && y < o.ny) {
+          const int x = 4 * xw;
+          uint8_t* gp = o.p + (long long)y * o.pitch + x;
+          if (x + 4 <= o.nx) {
+            *reinterpret_cast<uint32_t*>(gp) = v;
+          } else {
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+              if (x + j < o.nx) gp[j] = (uint8_t)(v >> (8 * j));
+          }
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q0 = 0; q0 < M * M; q0 += NT) {
+      const int q = q0 + threadIdx.x;
+      if (q < M * M) {
+        const int y = q / M, x = q % M;
+        const uint8_t* sp = src + (2 * y) * N + 2 * x;
+        const uint8_t v = (uint8_t)((sp[0] + sp[1] + sp[N] + sp[N + 1] + 2u) >> 2);
+        dst[q] = v;
+        if (WRITE && y < o.ny && x < o.nx) o.p[(long long)y * o.pitch + x] = v;
+      }
+    }
   }
 }
 
 // 2/3 resampling of the 96 x 96 c_0 tile into the 64 x 64 d_0 tile: each 3x3
 // block gives a 2x2 block; an output is the mean of its 1.5 x 1.5 footprint
-// (weights 4, 2, 2, 1 over 9), rounded to nearest.
-__device__ void two_thirds(const uint8_t* src, uint8_t* dst) {
-  constexpr int nb = kPyrTile / 3, n = kPyrTile, m = 2 * kPyrTile / 3;
-  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
-    int by = q / nb, bx = q % nb;
-    const uint8_t* s = src + (3 * by) * n + 3 * bx;
-    unsigned p00 = s[0], p01 = s[1], p02 = s[2];
-    unsigned p10 = s[n], p11 = s[n + 1], p12 = s[n + 2];
-    unsigned p20 = s[2 * n], p21 = s[2 * n + 1], p22 = s[2 * n + 2];
-    uint8_t* d = dst + (2 * by) * m + 2 * bx;
-    d[0] = (uint8_t)((4u * p00 + 2u * p01 + 2u * p10 + p11 + 4u) / 9u);
-    d[1] = (uint8_t)((4u * p02 + 2u * p01 + 2u * p12 + p11 + 4u) / 9u);
-    d[m] = (uint8_t)((4u * p20 + 2u * p21 + 2u * p10 + p11 + 4u) / 9u);
-    d[m + 1] = (uint8_t)((4u * p22 + 2u * p21 + 2u * p12 + p11 + 4u) / 9u);
-  }
-}
-
-// Build layers 1 .. up_to (inclusive) of the tile from its c_0.
-__device__ void build_levels(uint8_t* pyr, int O, int intra, int up_to) {
-  const int step = intra ? 2 : 1;
-  for (int i = 1; i < O; ++i) {
-    if (i * step > up_to) break;
-    half_sample(pyr + c_off(i - 1), kPyrTile >> (i - 1), pyr + c_off(i));
-    __syncthreads();
-  }
-  if (intra && up_to >= 1) {
-    two_thirds(pyr, pyr + d_off(0));
-    __syncthreads();
-    for (int i = 1; i < O; ++i) {
-      if (2 * i + 1 > up_to) break;
-      half_sample(pyr + d_off(i - 1), (2 * kPyrTile / 3) >> (i - 1), pyr + d_off(i));
-      __syncthreads();
+// (weights 4 for the corner it sits on, 2 and 2 for the half-covered edge
+// pixels, 1 for the quarter-covered centre, over 9), rounded to nearest.
+template <bool WRITE>
+__device__ __forceinline__ void two_thirds(const uint8_t* src, uint8_t* dst, const Out& o) {
+  constexpr int NB = P / 3, N = P, M = 2 * P / 3;
+#pragma unroll
+  for (int q0 = 0; q0 < NB * NB; q0 += NT) {
+    const int q = q0 + threadIdx.x;
+    const int by = q / NB, bx = q % NB;
+    const uint8_t* sp = src + (3 * by) * N + 3 * bx;
+    const unsigned p00 = sp[0], p01 = sp[1], p02 = sp[2];
+    const unsigned p10 = sp[N], p11 = sp[N + 1], p12 = sp[N + 2];
+    const unsigned p20 = sp[2 * N], p21 = sp[2 * N + 1], p22 = sp[2 * N + 2];
+    const unsigned e01 = 2u * p01 + p11, e21 = 2u * p21 + p11;
+    const unsigned top = ((4u * p00 + e01 + 2u * p10 + 4u) / 9u) | (((4u * p02 + e01 + 2u * p12 + 4u) / 9u) << 8);
+    const unsigned bot = ((4u * p20 + e21 + 2u * p10 + 4u) / 9u) | (((4u * p22 + e21 + 2u * p12 + 4u) / 9u) << 8);
+    uint8_t* d = dst + (2 * by) * M + 2 * bx;
+    *reinterpret_cast<uint16_t*>(d) = (uint16_t)top;
+    *reinterpret_cast<uint16_t*>(d + M) = (uint16_t)bot;
+    if (WRITE) {
+      const int x = 2 * bx, y = 2 * by;
+      uint8_t* gp = o.p + (long long)y * o.pitch + x;
+      if (x + 2 <= o.nx) {
+        if (y < o.ny) *reinterpret_cast<uint16_t*>(gp) = (uint16_t)top;
+        if (y + 1 < o.ny) *reinterpret_cast<uint16_t*>(gp + o.pitch) = (uint16_t)bot;
+      } else if (x < o.nx) {
+        if (y < o.ny) gp[0] = (uint8_t)top;
+        if (y + 1 < o.ny) gp[o.pitch] = (uint8_t)bot;
+      }
     }
   }
 }
 
+__device__ __forceinline__ Out out_of(const Geometry& g, uint8_t* pyr, int l, int side, int tx,
+                                      int ty) {
+  const LayerGeom& lg = g.layer[l];
+  const int gx0 = tx * side, gy0 = ty * side;
+  Out o;
+  o.p = pyr + lg.pyr_off + (long long)gy0 * lg.pitch + gx0;
+  o.pitch = lg.pitch;
+  o.nx = min(side, lg.w - gx0);
+  o.ny = min(side, lg.h - gy0);
+  return o;
+}
+
+// Octave chain c_I .. c_{O-1}, one level per step, up to layer `up_to`.
+template <int O, int INTRA, int I, bool WRITE>
+__device__ __forceinline__ void octaves(const Geometry& g, uint8_t* pyr, uint8_t* t, int tx, int ty,
+                                        int up_to) {
+  if constexpr (I < O) {
+    constexpr int l = INTRA ? 2 * I : I;
+    if (l > up_to) return;
+    half_level<c_side(I - 1), WRITE>(t + c_off(I - 1), t + c_off(I),
+                                     WRITE ? out_of(g, pyr, l, c_side(I), tx, ty) : Out{});
+    __syncthreads();
+    octaves<O, INTRA, I + 1, WRITE>(g, pyr, t, tx, ty, up_to);
+  }
+}
+
+// Intra-octave chain d_I .. d_{O-1}.
+template <int O, int I, bool WRITE>
+__device__ __forceinline__ void intra_octaves(const Geometry& g, uint8_t* pyr, uint8_t* t, int tx,
+                                              int ty, int up_to) {
+  if constexpr (I < O) {
+    constexpr int l = 2 * I + 1;
+    if (l > up_to) return;
+    half_level<d_side(I - 1), WRITE>(t + d_off(I - 1), t + d_off(I),
+                                     WRITE ? out_of(g, pyr, l, d_side(I), tx, ty) : Out{});
+    __syncthreads();
+    intra_octaves<O, I + 1, WRITE>(g, pyr, t, tx, ty, up_to);
+  }
+}
+
+template <int O, int INTRA, bool WRITE>
+__device__ __forceinline__ void build(const Geometry& g, uint8_t* pyr, uint8_t* t, int tx, int ty,
+                                      int up_to) {
+  octaves<O, INTRA, 1, WRITE>(g, pyr, t, tx, ty, up_to);
+  if constexpr (INTRA == 1) {
+    if (up_to >= 1) {
+      two_thirds<WRITE>(t, t + d_off(0), WRITE ? out_of(g, pyr, 1, d_side(0), tx, ty) : Out{});
+      __syncthreads();
+      intra_octaves<O, 1, WRITE>(g, pyr, t, tx, ty, up_to);
+    }
+  }
+}
+
+template <int O, int INTRA>
 __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Geometry g, Tables tb, Batch b, Scratch s,
                                                          Params p) {
   __shared__ __align__(16) uint8_t cur[kPyrSmem];
   __shared__ __align__(16) uint8_t prv[kPyrSmem];
   __shared__ uint32_t bins[kLocalBins];
+  __shared__ uint16_t tcol[P], trow[P];
 
   const int k = blockIdx.z;
   const int tx = blockIdx.x, ty = blockIdx.y;
   const uint8_t* frame = b.frames + (long long)k * b.frame_stride;
-  load_c0(cur, frame, b.pitch, tx * kPyrTile, ty * kPyrTile, g.W, g.H);
+  load_c0(cur, frame, b.pitch, tx * P, ty * P, g.W, g.H);
 
   const bool diff = p.mask_mode == FKD_MASK_ID && (b.first_frame + k) > 0;
+  const int ml = g.mask_layer;
+  const LayerGeom& mlg = g.layer[ml];
+  const bool ml_d = INTRA && (ml & 1);
+  const int ml_i = INTRA ? ml >> 1 : ml;
+  const int mn = ml_d ? d_side(ml_i) : c_side(ml_i);
+  const int moff = ml_d ? d_off_rt(ml_i) : c_off_rt(ml_i);
+  const int mgx0 = tx * mn, mgy0 = ty * mn;
+  const int mnx = min(mn, mlg.w - mgx0), mny = min(mn, mlg.h - mgy0);
   if (diff) {
     const uint8_t* pf = k == 0 ? b.prev : frame - b.frame_stride;
     const int pp = k == 0 ? b.prev_pitch : b.pitch;
-    load_c0(prv, pf, pp, tx * kPyrTile, ty * kPyrTile, g.W, g.H);
+    load_c0(prv, pf, pp, tx * P, ty * P, g.W, g.H);
+    for (int q = threadIdx.x; q < kLocalBins; q += NT) bins[q] = 0;
+    for (int q = threadIdx.x; q < mn; q += NT) {
+      tcol[q] = q < mnx ? tb.colblk[mlg.col_off + mgx0 + q] : 0;
+      trow[q] = q < mny ? tb.rowblk[mlg.row_off + mgy0 + q] : 0;
+    }
   }
-  for (int q = threadIdx.x; q < kLocalBins; q += blockDim.x) bins[q] = 0;
+  cp_async_commit();
+  cp_async_wait<0>();
   __syncthreads();
 
-  build_levels(cur, g.O, g.intra, g.L - 1);
-  if (diff && g.mask_layer > 0) build_levels(prv, g.O, g.intra, g.mask_layer);
-
-  // write layers >= 1 of the tile
   uint8_t* pyr = s.pyr + (long long)k * g.pyr_bytes;
-  for (int l = 1; l < g.L; ++l) {
-    const LayerGeom& lg = g.layer[l];
-    Level lv = level_of(l, g.intra);
-    const int gx0 = tx * lv.n, gy0 = ty * lv.n;
-    const int nx = min(lv.n, lg.w - gx0), ny = min(lv.n, lg.h - gy0);
-    if (nx <= 0 || ny <= 0) continue;
-    uint8_t* dst = pyr + lg.pyr_off;
-    for (int q = threadIdx.x; q < nx * ny; q += blockDim.x) {
-      int y = q / nx, x = q % nx;
-      dst[(long long)(gy0 + y) * lg.pitch + gx0 + x] = cur[lv.off + y * lv.n + x];
-    }
-  }
+  build<O, INTRA, true>(g, pyr, cur, tx, ty, g.L - 1);
+  if (!diff || mnx <= 0 || mny <= 0) return;
+  if (ml > 0) build<O, INTRA, false>(g, pyr, prv, tx, ty, ml);
 
-  if (!diff) return;
-
-  // Per-bin sums of |L_n - L_{n-1}| on the mask layer. Each thread walks a
-  // column of the layer tile, keeps a running sum while the bin row is the
-  // same, and flushes it into a shared-memory bin when the row changes.
-  const int ml = g.mask_layer;
-  const LayerGeom& lg = g.layer[ml];
-  const Level lv = level_of(ml, g.intra);
-  const int gx0 = tx * lv.n, gy0 = ty * lv.n;
-  const int nx = min(lv.n, lg.w - gx0), ny = min(lv.n, lg.h - gy0);
-  if (nx <= 0 || ny <= 0) return;
-  const uint16_t* colblk = tb.colblk + lg.col_off;
-  const uint16_t* rowblk = tb.rowblk + lg.row_off;
-  const int cb_lo = colblk[gx0], rb_lo = rowblk[gy0];
-  const int ncols = colblk[gx0 + nx - 1] - cb_lo + 1;
-  const int nrows = rowblk[gy0 + ny - 1] - rb_lo + 1;
+  // Per-bin sums of |L_n - L_{n-1}| on the mask layer. Thread -> a 4-pixel
+  // column word and a band of rows; the running sum is flushed into a shared
+  // bin whenever the bin row changes (and split by pixel when the word's
+  // pixels straddle bin columns).
+  const int cb_lo = tcol[0], rb_lo = trow[0];
+  const int ncols = tcol[mnx - 1] - cb_lo + 1, nrows = trow[mny - 1] - rb_lo + 1;
   const bool local = ncols * nrows <= kLocalBins;
   unsigned long long* gsum = s.bsum + (long long)k * g.NB;
-
-  const int groups = max(1, (int)blockDim.x / nx);
-  const int rows_per = (ny + groups - 1) / groups;
-  const int x = threadIdx.x % nx, grp = threadIdx.x / nx;
-  if (grp < groups) {
-    const int cb = colblk[gx0 + x];
-    const uint8_t* a = cur + lv.off + x;
-    const uint8_t* c = prv + lv.off + x;
-    uint32_t acc = 0;
-    int rb_cur = -1;
-    const int y_end = min(ny, (grp + 1) * rows_per);
-    for (int y = grp * rows_per; y < y_end; ++y) {
-      int rb = rowblk[gy0 + y];
-      if (rb != rb_cur) {
-        if (rb_cur >= 0 && acc) {
-          if (local) atomicAdd(&bins[(rb_cur - rb_lo) * ncols + (cb - cb_lo)], acc);
-          else atomicAdd(&gsum[rb_cur * g.N_c + cb], (unsigned long long)acc);
+  const uint8_t* A = cur + moff;
+  const uint8_t* B = prv + moff;
+  auto flush = [&](int rb, int cb, uint32_t v) {
+    if (!v) return;
+    if (local) atomicAdd(&bins[(rb - rb_lo) * ncols + (cb - cb_lo)], v);
+    else atomicAdd(&gsum[rb * g.N_c + cb], (unsigned long long)v);
+  };
+  if ((mn & 3) == 0) {
+    const int wcols = (mnx + 3) / 4;
+    const int groups = max(1, NT / wcols);
+    const int rows_per = (mny + groups - 1) / groups;
+    const int wc = threadIdx.x % wcols, grp = threadIdx.x / wcols;
+    if (grp < groups) {
+      const int x = 4 * wc;
+      const int nv = min(4, mnx - x);
+      const uint32_t vmask = nv == 4 ? 0xffffffffu : ((1u << (8 * nv)) - 1u);
+      const int c0 = tcol[x], c3 = tcol[x + nv - 1];
+      uint32_t acc = 0, acc_hi = 0;
+      int rb_cur = -1;
+      const int y_end = min(mny, (grp + 1) * rows_per);
+      for (int y = grp * rows_per; y < y_end; ++y) {
+        const int rb = trow[y];
+        if (rb != rb_cur) {
+          if (rb_cur >= 0) {
+            flush(rb_cur, c0, acc);
+            if (c3 != c0) flush(rb_cur, c3, acc_hi);
+          }
+          rb_cur = rb;
+          acc = acc_hi = 0;
         }
-        rb_cur = rb;
-        acc = 0;
+        const uint32_t a = ld32(A + y * mn + x) & vmask, c = ld32(B + y * mn + x) & vmask;
+        if (c3 == c0) {
+          acc += __vsadu4(a, c);
+        } else {
+          // the word straddles bin columns: split it pixel by pixel (bins
+          // narrower than 4 pixels put middle pixels in further bins)
+          for (int i = 0; i < nv; ++i) {
+            const int ci = tcol[x + i];
+            const uint32_t d = __vabsdiffu4((a >> (8 * i)) & 0xffu, (c >> (8 * i)) & 0xffu);
+            if (ci == c0) acc += d;
+            else if (ci == c3) acc_hi += d;
+            else flush(rb, ci, d);
+          }
+        }
       }
-      int dv = (int)a[y * lv.n] - (int)c[y * lv.n];
-      acc += (uint32_t)(dv < 0 ? -dv : dv);
+      if (rb_cur >= 0) {
+        flush(rb_cur, c0, acc);
+        if (c3 != c0) flush(rb_cur, c3, acc_hi);
+      }
     }
-    if (rb_cur >= 0 && acc) {
-      if (local) atomicAdd(&bins[(rb_cur - rb_lo) * ncols + (cb - cb_lo)], acc);
-      else atomicAdd(&gsum[rb_cur * g.N_c + cb], (unsigned long long)acc);
+  } else {
+    for (int q = threadIdx.x; q < mnx * mny; q += NT) {
+      const int y = q / mnx, x = q % mnx;
+      const int dv = (int)A[y * mn + x] - (int)B[y * mn + x];
+      flush(trow[y], tcol[x], (uint32_t)(dv < 0 ? -dv : dv));
     }
   }
   if (local) {
     __syncthreads();
-    for (int q = threadIdx.x; q < ncols * nrows; q += blockDim.x) {
-      uint32_t v = bins[q];
+    for (int q = threadIdx.x; q < ncols * nrows; q += NT) {
+      const uint32_t v = bins[q];
       if (v) atomicAdd(&gsum[(rb_lo + q / ncols) * g.N_c + cb_lo + q % ncols], (unsigned long long)v);
     }
   }
+}
+
+template <int O, int INTRA>
+void launch_t(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s, const Params& p,
+              cudaStream_t st) {
+  dim3 grid(g.pyr_tiles_x, g.pyr_tiles_y, b.T);
+  k_pyramid<O, INTRA><<<grid, kPyrThreads, 0, st>>>(g, tb, b, s, p);
 }
 
 }  // namespace
 
 void launch_pyramid(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                     const Params& p, cudaStream_t st) {
-  dim3 grid(g.pyr_tiles_x, g.pyr_tiles_y, b.T);
-  k_pyramid<<<grid, kPyrThreads, 0, st>>>(g, tb, b, s, p);
+  using L = void (*)(const Geometry&, const Tables&, const Batch&, const Scratch&, const Params&,
+                     cudaStream_t);
+  static const L table[2][6] = {
+      {launch_t<1, 0>, launch_t<2, 0>, launch_t<3, 0>, launch_t<4, 0>, launch_t<5, 0>, launch_t<6, 0>},
+      {launch_t<1, 1>, launch_t<2, 1>, launch_t<3, 1>, launch_t<4, 1>, launch_t<5, 1>, launch_t<6, 1>}};
+  table[g.intra ? 1 : 0][g.O - 1](g, tb, b, s, p, st);
 }
 
 }  // namespace fkd
