@@ -247,6 +247,38 @@ typedef struct {
 int fkd_profile_enable(fkd_stream* s, int on);
 int fkd_profile_read(fkd_stream* s, fkd_profile* out, int reset);
 
+/*
+ * Allocation-free variant (the paper has no counterpart; it exists for
+ * callers of this library that cannot let it allocate device memory: an
+ * application that gives all GPU memory to its own allocator or budget at
+ * start-up, a plugin inside a host program that owns the device memory, a
+ * real-time loop that must not pay for cudaMalloc / cudaFree and the
+ * synchronisation they imply).
+ *
+ * fkd_id_mask_noalloc computes the intensity-difference detection mask of
+ * one frame pair -- bin (r, c) is 1 when the sum of |cur - prev| over its
+ * pixels of the full-resolution frame exceeds T_I times their number, the
+ * test fkd_push_frames applies with FKD_MASK_ID and mask_layer 0 -- without
+ * allocating anything. cur, prev: device W x H frames sharing `pitch`;
+ * mask_out: device buffer of N_r*N_c bytes (row-major); cuda_stream: the
+ * cudaStream_t to run on (NULL: legacy default stream). Asynchronous.
+ *
+ * Its per-bin sums live in a fixed array of FKD_NOALLOC_MAX_BINS 64-bit
+ * counters (32 KiB) in this library's device memory, present on every GPU
+ * that loads the library until the process exits. The first call made while
+ * a given device is current looks the array's address up on that device
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call clears the counters it uses and then reuses the same array, so
+ * calls that overlap on the GPU (on different streams, or different host
+ * threads) race and give wrong masks: serialise them.
+ * Errors: FKD_E_ARG (NULL buffer, sizes outside 1..16384, pitch < W, a bin
+ * grid that does not fit the frame, N_r*N_c > FKD_NOALLOC_MAX_BINS, T_I < 0),
+ * FKD_E_CUDA. Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+#define FKD_NOALLOC_MAX_BINS 4096
+int fkd_id_mask_noalloc(const uint8_t* cur, const uint8_t* prev, int W, int H, size_t pitch, int N_r,
+                        int N_c, int T_I, uint8_t* mask_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

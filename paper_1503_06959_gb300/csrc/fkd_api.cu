@@ -39,6 +39,16 @@ long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
+int fkd::set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
 struct fkd_stream {
   fkd_params p{};
   Geometry g{};

@@ -165,4 +165,7 @@ void launch_emit(const Geometry& g, const Tables& tb, const Batch& b, const Scra
                  const State& state, const Output& out, cudaStream_t st);
 int detect_grid_size();
 
+// Record a message for fkd_last_error (printf format) and return `code`.
+int set_error(int code, const char* fmt, ...);
+
 }  // namespace fkd

@@ -27,7 +27,7 @@ EXPORTS = [
     "fkd_last_error", "fkd_params_default", "fkd_create_stream", "fkd_destroy_stream",
     "fkd_num_layers", "fkd_layer_info", "fkd_push_frame", "fkd_get_keypoints", "fkd_get_mask",
     "fkd_push_frames", "fkd_synchronize", "fkd_frame_count", "fkd_device_keypoints",
-    "fkd_reset_stream", "fkd_profile_enable", "fkd_profile_read",
+    "fkd_reset_stream", "fkd_profile_enable", "fkd_profile_read", "fkd_id_mask_noalloc",
 ]
 STAGES = ["pyramid", "mask", "worklist", "detect", "count", "emit"]
 
@@ -81,6 +81,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.fkd_reset_stream.argtypes = [vp]
     lib.fkd_profile_enable.argtypes = [vp, c_int]
     lib.fkd_profile_read.argtypes = [vp, P(fkd_profile), c_int]
+    lib.fkd_id_mask_noalloc.argtypes = [vp, vp, c_int, c_int, c_size, c_int, c_int, c_int, vp, vp]
     for name in EXPORTS:
         if name != "fkd_last_error":
             getattr(lib, name).restype = c_int
@@ -236,6 +237,20 @@ class Stream:
             self.close()
         except Exception:
             pass
+
+
+def id_mask_noalloc(cur, prev, N_r: int, N_c: int, T_I: int, mask_out, cuda_stream: int | None = None):
+    """fkd_id_mask_noalloc: the intensity-difference mask of one frame pair
+    computed without any device allocation (for callers that manage all
+    device memory themselves). cur, prev: torch CUDA uint8 H x W frames with
+    the same row stride; mask_out: torch CUDA uint8 tensor of N_r*N_c bytes.
+    Asynchronous on `cuda_stream` (default: the legacy default stream)."""
+    lib = load()
+    H, W = cur.shape
+    assert tuple(prev.shape) == (H, W) and cur.stride(0) == prev.stride(0)
+    assert cur.stride(1) == 1 and prev.stride(1) == 1 and mask_out.numel() == N_r * N_c
+    _check(lib.fkd_id_mask_noalloc(_ptr(cur), _ptr(prev), W, H, cur.stride(0), N_r, N_c, T_I,
+                                   _ptr(mask_out), ctypes.c_void_p(cuda_stream or 0)))
 
 
 def split_frames(records: np.ndarray, offsets: np.ndarray):
