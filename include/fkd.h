@@ -248,6 +248,74 @@ int fkd_profile_enable(fkd_stream* s, int on);
 int fkd_profile_read(fkd_stream* s, fkd_profile* out, int reset);
 
 /*
+ * Groups: many streams, one frame of each per tick, one launch sequence.
+ *
+ * A group serves many independent video streams of any sizes (for example a
+ * mix of 320x240 ... 1920x1080 cameras). Each call to fkd_group_tick takes
+ * the next frame of any subset of the group's streams and runs steps 1-4 for
+ * all of them with one launch per kernel (persistent grids looping over the
+ * tick's work), optionally replayed from a captured CUDA graph. The result of
+ * every stream is bit-identical to feeding its frames to its own fkd_stream
+ * one by one. All streams of a group share O and intra (the pyramid kernel
+ * is compiled per octave count); every other parameter is per stream.
+ * Streams keep device copies of their last two frames, so a tick's frames
+ * may come from transient buffers.
+ */
+typedef struct fkd_group fkd_group;
+
+/* Create an empty group for streams with O octaves (1..6) and intra
+ * (0 or 1), bound to cuda_stream (NULL: legacy default stream).
+ * Errors: FKD_E_ARG, FKD_E_CUDA. */
+int fkd_group_create(int O, int intra, void* cuda_stream, fkd_group** out);
+
+/* Wait for the group's work and free it and all its streams. NULL: no-op. */
+int fkd_group_destroy(fkd_group* g);
+
+/* Add a stream (p->O and p->intra must match the group's; p->T_max is
+ * ignored). *stream_id receives its index (ids are not reused). *bytes, if
+ * not NULL, receives the device memory the stream holds. Waits for the
+ * group's pending work. Errors: FKD_E_ARG, FKD_E_CUDA. */
+int fkd_group_add_stream(fkd_group* g, const fkd_params* p, int W, int H, int* stream_id,
+                         size_t* bytes);
+
+/* Remove a stream and free its device memory (waits for pending work).
+ * Errors: FKD_E_ARG (unknown id). */
+int fkd_group_remove_stream(fkd_group* g, int stream_id);
+
+/* One tick: frame frames[i] (device memory, row pitch pitches[i]) is the next
+ * frame of stream ids[i], for i < n; a stream appears at most once. The
+ * frames must stay valid until the tick has run (fkd_group_synchronize, or
+ * any later call that waits). Asynchronous. Errors: FKD_E_ARG, FKD_E_CUDA. */
+int fkd_group_tick(fkd_group* g, int n, const int* ids, const uint8_t* const* frames,
+                   const size_t* pitches);
+
+/* Replay ticks from captured CUDA graphs (on, the default) or launch the
+ * kernels one by one (off). */
+int fkd_group_use_graph(fkd_group* g, int on);
+
+/* Wait for the group's work. Errors: FKD_E_CUDA. */
+int fkd_group_synchronize(fkd_group* g);
+
+/* The last tick's D_n of stream `id` (sorted by (layer, y, x)) into host
+ * memory, as fkd_get_keypoints. Waits. Errors: FKD_E_ARG, FKD_E_STATE (the
+ * stream has no frame yet), FKD_E_CAPACITY. */
+int fkd_group_get_keypoints(fkd_group* g, int id, fkd_keypoint* out, size_t cap, size_t* n_out);
+
+/* The last tick's mask of stream `id` (N_r*N_c bytes) into host memory. */
+int fkd_group_get_mask(fkd_group* g, int id, uint8_t* out);
+
+/* Device pointers of stream `id`'s last result: K_max records and the device
+ * uint32 count. Valid until its next tick. Errors: FKD_E_ARG, FKD_E_STATE. */
+int fkd_group_device_keypoints(fkd_group* g, int id, const fkd_keypoint** records,
+                               const uint32_t** count_dev);
+
+/* Summed CUDA-event times of the group's kernels over the ticks since the
+ * last read (same stages and semantics as fkd_profile_read; `frames` counts
+ * the frames of those ticks). */
+int fkd_group_profile_enable(fkd_group* g, int on);
+int fkd_group_profile_read(fkd_group* g, fkd_profile* out, int reset);
+
+/*
  * Allocation-free variant (the paper has no counterpart; it exists for
  * callers of this library that cannot let it allocate device memory: an
  * application that gives all GPU memory to its own allocator or budget at

@@ -54,6 +54,7 @@ struct fkd_stream {
   Geometry g{};
   cudaStream_t st = nullptr;
   std::vector<void*> allocs;
+  size_t bytes_held = 0;  // device bytes this stream allocated
 
   uint16_t* colblk = nullptr;
   uint16_t* rowblk = nullptr;
@@ -114,6 +115,7 @@ struct fkd_stream {
     cudaError_t e = cudaMalloc(&d, std::max<size_t>(count, 1) * sizeof(T));
     if (e != cudaSuccess) return fail(FKD_E_CUDA, "cudaMalloc(%zu) failed: %s", count * sizeof(T), cudaGetErrorString(e));
     allocs.push_back(d);
+    bytes_held += std::max<size_t>(count, 1) * sizeof(T);
     *p = static_cast<T*>(d);
     return FKD_OK;
   }
@@ -638,6 +640,412 @@ int fkd_device_keypoints(fkd_stream* s, const fkd_keypoint** records, const uint
   if (!s->have_frame_result) return fail(FKD_E_STATE, "no frame pushed with fkd_push_frame");
   *records = s->rec;
   *count_dev = s->rec_offsets + 1;
+  return FKD_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ groups
+
+namespace {
+
+struct GroupStream {
+  fkd_stream* s = nullptr;  // T_max = 1
+  uint8_t* last[2] = {nullptr, nullptr};
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct fkd_group {
+  int O = 1, intra = 0;
+  cudaStream_t st = nullptr;
+  std::vector<GroupStream> streams;  // indexed by stream id; s == nullptr once removed
+  StreamDev* d_devs = nullptr;
+  int devs_cap = 0;
+  TickHeader* d_hdr = nullptr;       // followed by kMaxTickItems TickItems
+  TickItem* d_items = nullptr;
+  unsigned char* h_tick[2] = {nullptr, nullptr};  // pinned copies of header + items
+  cudaEvent_t tick_done[2] = {nullptr, nullptr};
+  uint32_t* d_work = nullptr;
+  long long work_cap = 0;
+  uint32_t* d_work_count = nullptr;
+  int grid_pyr = 1, grid_small = 1, grid_det = 1, grid_asm = 1;
+  bool use_graph = true;
+  bool graph_valid = false;
+  int graph_items = 0;               // items copied per tick by the captured graphs
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  long long ticks = 0;
+  bool profiling = false;
+  std::vector<fkd_stream::Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  fkd_profile prof{};
+  unsigned long long tile_seen[2] = {0, 0};
+
+  cudaEvent_t take_event() {
+    if (!event_pool.empty()) {
+      cudaEvent_t e = event_pool.back();
+      event_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void drop_graphs() {
+    for (auto& ge : graph)
+      if (ge) {
+        cudaGraphExecDestroy(ge);
+        ge = nullptr;
+      }
+    graph_valid = false;
+  }
+};
+
+namespace {
+
+// Tick upload: the header, then the items at a 64-byte aligned offset (they
+// hold 8-byte fields that the kernels load directly).
+constexpr size_t kItemsOffset = 64;
+static_assert(sizeof(TickHeader) <= kItemsOffset, "tick header fits before the items");
+static_assert(alignof(TickItem) <= 64 && sizeof(TickItem) % alignof(TickItem) == 0, "aligned items");
+constexpr size_t kTickBytes = kItemsOffset + kMaxTickItems * sizeof(TickItem);
+
+StreamDev make_dev(const fkd_stream* s, uint8_t* const last[2]) {
+  StreamDev d{};
+  d.g = s->g;
+  d.tb = Tables{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins};
+  d.s = s->s;
+  d.p = Params{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode};
+  for (int i = 0; i < 2; ++i) {
+    d.state_bits[i] = s->state_bits[i];
+    d.state_score[i] = s->state_score[i];
+    d.state_cnt[i] = s->state_cnt[i];
+    d.last[i] = last[i];
+  }
+  d.rec = s->rec;
+  d.rec_offsets = s->rec_offsets;
+  d.K_max = s->p.K_max;
+  return d;
+}
+
+// The tick's launch sequence: upload of header + items, then the kernels.
+int group_launch(fkd_group* G, int b, int n_items, fkd_stream::Pending* pd) {
+  auto mark = [&](int i) {
+    if (pd) {
+      pd->ev[i] = G->take_event();
+      cudaEventRecord(pd->ev[i], G->st);
+    }
+  };
+  CK(cudaMemcpyAsync(G->d_hdr, G->h_tick[b], kItemsOffset + (size_t)n_items * sizeof(TickItem),
+                     cudaMemcpyHostToDevice, G->st));
+  mark(0);
+  launch_group_pyramid(G->O, G->intra, G->d_devs, G->d_hdr, G->d_items, G->grid_pyr, G->st);
+  mark(1);
+  launch_group_mask(G->d_devs, G->d_hdr, G->d_items, G->d_work_count, G->grid_small, G->st);
+  mark(2);
+  launch_group_worklist(G->d_devs, G->d_hdr, G->d_items, G->d_work, G->d_work_count, G->grid_small, G->st);
+  mark(3);
+  launch_group_detect(G->d_devs, G->d_items, G->d_work, G->d_work_count, G->grid_det, G->st);
+  mark(4);
+  launch_group_count(G->d_devs, G->d_hdr, G->d_items, G->grid_asm, G->st);
+  mark(5);
+  launch_group_emit(G->d_devs, G->d_hdr, G->d_items, G->grid_asm, G->st);
+  mark(6);
+  CK(cudaGetLastError());
+  return FKD_OK;
+}
+
+int group_capture(fkd_group* G, int n_items) {
+  G->drop_graphs();
+  for (int b = 0; b < 2; ++b) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(G->st, cudaStreamCaptureModeThreadLocal));
+    int rc = group_launch(G, b, n_items, nullptr);
+    cudaError_t e = cudaStreamEndCapture(G->st, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(FKD_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&G->graph[b], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(FKD_E_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+  }
+  G->graph_valid = true;
+  G->graph_items = n_items;
+  return FKD_OK;
+}
+
+fkd_stream* group_member(fkd_group* G, int id) {
+  if (!G || id < 0 || id >= (int)G->streams.size()) return nullptr;
+  return G->streams[id].s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fkd_group_create(int O, int intra, void* cuda_stream, fkd_group** out) {
+  if (!out) return fail(FKD_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (O < 1 || O > 6 || (intra != 0 && intra != 1)) return fail(FKD_E_ARG, "O must be 1..6, intra 0 or 1");
+  fkd_group* G = new (std::nothrow) fkd_group();
+  if (!G) return fail(FKD_E_ARG, "out of host memory");
+  G->O = O;
+  G->intra = intra;
+  G->st = static_cast<cudaStream_t>(cuda_stream);
+  G->use_graph = G->st != nullptr;  // the legacy default stream cannot be captured
+  auto bail = [&](int rc) {
+    fkd_group_destroy(G);
+    return rc;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&G->d_hdr, kTickBytes)) != cudaSuccess ||
+      (e = cudaMalloc(&G->d_work_count, 4)) != cudaSuccess ||
+      (e = cudaHostAlloc(&G->h_tick[0], kTickBytes, cudaHostAllocDefault)) != cudaSuccess ||
+      (e = cudaHostAlloc(&G->h_tick[1], kTickBytes, cudaHostAllocDefault)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&G->tick_done[0], cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&G->tick_done[1], cudaEventDisableTiming)) != cudaSuccess)
+    return bail(fail(FKD_E_CUDA, "group allocation failed: %s", cudaGetErrorString(e)));
+  G->d_items = reinterpret_cast<TickItem*>(reinterpret_cast<unsigned char*>(G->d_hdr) + kItemsOffset);
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  G->grid_pyr = group_pyramid_grid(O, intra);
+  G->grid_det = detect_grid_size();
+  G->grid_small = sms * 8;
+  G->grid_asm = sms * 8;
+  *out = G;
+  return FKD_OK;
+}
+
+int fkd_group_destroy(fkd_group* G) {
+  if (!G) return FKD_OK;
+  cudaStreamSynchronize(G->st);
+  G->drop_graphs();
+  for (auto& gs : G->streams)
+    if (gs.s) fkd_destroy_stream(gs.s);
+  cudaFree(G->d_devs);
+  cudaFree(G->d_hdr);
+  cudaFree(G->d_work);
+  cudaFree(G->d_work_count);
+  for (int b = 0; b < 2; ++b) {
+    if (G->h_tick[b]) cudaFreeHost(G->h_tick[b]);
+    if (G->tick_done[b]) cudaEventDestroy(G->tick_done[b]);
+  }
+  for (auto& pd : G->pending)
+    for (cudaEvent_t e : pd.ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : G->event_pool) cudaEventDestroy(e);
+  delete G;
+  return FKD_OK;
+}
+
+int fkd_group_add_stream(fkd_group* G, const fkd_params* p, int W, int H, int* stream_id, size_t* bytes) {
+  if (!G || !p || !stream_id) return fail(FKD_E_ARG, "NULL argument");
+  if (p->O != G->O || p->intra != G->intra)
+    return fail(FKD_E_ARG, "stream O/intra (%d/%d) differ from the group's (%d/%d)", p->O, p->intra, G->O, G->intra);
+  CK(cudaStreamSynchronize(G->st));
+  fkd_params q = *p;
+  q.T_max = 1;
+  fkd_stream* s = nullptr;
+  int rc = fkd_create_stream(&q, W, H, G->st, &s);
+  if (rc) return rc;
+  GroupStream gs;
+  gs.s = s;
+  const size_t lbytes = (size_t)s->g.layer[0].pitch * (size_t)H;
+  for (int i = 0; i < 2; ++i)
+    if ((rc = s->alloc(&gs.last[i], lbytes))) {
+      fkd_destroy_stream(s);
+      return rc;
+    }
+  gs.bytes = s->bytes_held;
+  const int id = (int)G->streams.size();
+  // device descriptors (grow: the captured graphs hold the old pointer)
+  if (id >= G->devs_cap) {
+    const int cap = std::max(16, 2 * G->devs_cap);
+    StreamDev* nd = nullptr;
+    cudaError_t e = cudaMalloc(&nd, (size_t)cap * sizeof(StreamDev));
+    if (e != cudaSuccess) {
+      fkd_destroy_stream(s);
+      return fail(FKD_E_CUDA, "cudaMalloc failed: %s", cudaGetErrorString(e));
+    }
+    if (G->d_devs) {
+      CK(cudaMemcpy(nd, G->d_devs, (size_t)G->devs_cap * sizeof(StreamDev), cudaMemcpyDeviceToDevice));
+      cudaFree(G->d_devs);
+    }
+    G->d_devs = nd;
+    G->devs_cap = cap;
+    G->drop_graphs();
+  }
+  const StreamDev d = make_dev(s, gs.last);
+  CK(cudaMemcpy(G->d_devs + id, &d, sizeof d, cudaMemcpyHostToDevice));
+  // the tick's active-tile list holds at most the tiles of all live streams
+  long long need = 0;
+  for (auto& o : G->streams)
+    if (o.s) need += o.s->g.n_tiles;
+  need += s->g.n_tiles;
+  if (need > G->work_cap) {
+    const long long cap = std::max(need, 2 * G->work_cap);
+    cudaFree(G->d_work);
+    G->d_work = nullptr;
+    cudaError_t e = cudaMalloc(&G->d_work, (size_t)cap * 4);
+    if (e != cudaSuccess) {
+      fkd_destroy_stream(s);
+      G->work_cap = 0;
+      return fail(FKD_E_CUDA, "cudaMalloc failed: %s", cudaGetErrorString(e));
+    }
+    G->work_cap = cap;
+    G->drop_graphs();
+  }
+  G->streams.push_back(gs);
+  *stream_id = id;
+  if (bytes) *bytes = gs.bytes;
+  return FKD_OK;
+}
+
+int fkd_group_remove_stream(fkd_group* G, int id) {
+  fkd_stream* s = group_member(G, id);
+  if (!s) return fail(FKD_E_ARG, "unknown stream id %d", id);
+  CK(cudaStreamSynchronize(G->st));
+  fkd_destroy_stream(s);
+  G->streams[id].s = nullptr;
+  return FKD_OK;
+}
+
+int fkd_group_use_graph(fkd_group* G, int on) {
+  if (!G) return fail(FKD_E_ARG, "group is NULL");
+  G->use_graph = on && G->st != nullptr;
+  return FKD_OK;
+}
+
+int fkd_group_tick(fkd_group* G, int n, const int* ids, const uint8_t* const* frames, const size_t* pitches) {
+  if (!G || n < 0 || (n > 0 && (!ids || !frames || !pitches))) return fail(FKD_E_ARG, "NULL argument");
+  if (n > kMaxTickItems) return fail(FKD_E_ARG, "more than %d streams in one tick", kMaxTickItems);
+  if (n == 0) return FKD_OK;
+  const int b = (int)(G->ticks & 1);
+  CK(cudaEventSynchronize(G->tick_done[b]));  // the pinned buffer's previous upload is done
+  TickHeader* h = reinterpret_cast<TickHeader*>(G->h_tick[b]);
+  TickItem* items = reinterpret_cast<TickItem*>(G->h_tick[b] + kItemsOffset);
+  int pyr = 0, bins = 0, tiles = 0, chunks = 0;
+  for (int i = 0; i < n; ++i) {
+    fkd_stream* s = group_member(G, ids[i]);
+    if (!s) return fail(FKD_E_ARG, "unknown stream id %d", ids[i]);
+    if (!frames[i] || pitches[i] < (size_t)s->g.W || pitches[i] > (1u << 30))
+      return fail(FKD_E_ARG, "bad frame or pitch for stream %d", ids[i]);
+    for (int j = 0; j < i; ++j)
+      if (ids[j] == ids[i]) return fail(FKD_E_ARG, "stream %d twice in one tick", ids[i]);
+    TickItem& it = items[i];
+    it.sid = ids[i];
+    it.state_cur = s->state_cur;
+    it.frame_index = s->frame;
+    it.frame = frames[i];
+    it.pitch = (int)pitches[i];
+    it.pyr_base = pyr;
+    it.bin_base = bins;
+    it.tile_base = tiles;
+    it.chunk_base = chunks;
+    pyr += s->g.pyr_tiles_x * s->g.pyr_tiles_y;
+    bins += s->g.NB;
+    tiles += s->g.n_tiles;
+    chunks += s->g.n_chunks;
+  }
+  if ((long long)tiles > G->work_cap) return fail(FKD_E_ARG, "tick larger than the group's work list");
+  h->n_items = n;
+  h->total_pyr = pyr;
+  h->total_bins = bins;
+  h->total_tiles = tiles;
+  h->total_chunks = chunks;
+
+  if (G->profiling) {
+    fkd_stream::Pending pd{};
+    int rc = group_launch(G, b, n, &pd);
+    if (rc) return rc;
+    pd.frames = n;
+    G->pending.push_back(pd);
+  } else if (G->use_graph) {
+    int live = 0;
+    for (auto& gs : G->streams) live += gs.s ? 1 : 0;
+    if (!G->graph_valid || G->graph_items < n) {
+      int rc = group_capture(G, std::max(n, live));
+      if (rc) return rc;
+    }
+    CK(cudaGraphLaunch(G->graph[b], G->st));
+  } else {
+    int rc = group_launch(G, b, n, nullptr);
+    if (rc) return rc;
+  }
+  CK(cudaEventRecord(G->tick_done[b], G->st));
+  G->ticks += 1;
+  for (int i = 0; i < n; ++i) {
+    fkd_stream* s = G->streams[ids[i]].s;
+    s->state_cur ^= 1;
+    s->frame += 1;
+    s->have_frame_result = true;
+    s->last_mask = s->s.mask;
+  }
+  return FKD_OK;
+}
+
+int fkd_group_synchronize(fkd_group* G) {
+  if (!G) return fail(FKD_E_ARG, "group is NULL");
+  CK(cudaStreamSynchronize(G->st));
+  return FKD_OK;
+}
+
+int fkd_group_get_keypoints(fkd_group* G, int id, fkd_keypoint* out, size_t cap, size_t* n_out) {
+  fkd_stream* s = group_member(G, id);
+  if (!s) return fail(FKD_E_ARG, "unknown stream id %d", id);
+  return fkd_get_keypoints(s, out, cap, n_out);
+}
+
+int fkd_group_get_mask(fkd_group* G, int id, uint8_t* out) {
+  fkd_stream* s = group_member(G, id);
+  if (!s) return fail(FKD_E_ARG, "unknown stream id %d", id);
+  return fkd_get_mask(s, out);
+}
+
+int fkd_group_device_keypoints(fkd_group* G, int id, const fkd_keypoint** records, const uint32_t** count_dev) {
+  fkd_stream* s = group_member(G, id);
+  if (!s) return fail(FKD_E_ARG, "unknown stream id %d", id);
+  return fkd_device_keypoints(s, records, count_dev);
+}
+
+int fkd_group_profile_enable(fkd_group* G, int on) {
+  if (!G) return fail(FKD_E_ARG, "group is NULL");
+  G->profiling = on != 0;
+  return FKD_OK;
+}
+
+int fkd_group_profile_read(fkd_group* G, fkd_profile* out, int reset) {
+  if (!G || !out) return fail(FKD_E_ARG, "NULL argument");
+  CK(cudaStreamSynchronize(G->st));
+  for (auto& pd : G->pending) {
+    for (int i = 0; i < FKD_NUM_STAGES; ++i) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, pd.ev[i], pd.ev[i + 1]));
+      G->prof.ms[i] += ms;
+      G->prof.launches[i] += 1;
+    }
+    G->prof.batches += 1;
+    G->prof.frames += (uint64_t)pd.frames;
+    for (cudaEvent_t e : pd.ev) G->event_pool.push_back(e);
+  }
+  G->pending.clear();
+  unsigned long long tiles = 0, px = 0;
+  for (auto& gs : G->streams)
+    if (gs.s) {
+      unsigned long long ts[2];
+      CK(cudaMemcpy(ts, gs.s->s.tile_stats, 16, cudaMemcpyDeviceToHost));
+      tiles += ts[0] - gs.s->tile_stats_seen[0];
+      px += ts[1] - gs.s->tile_stats_seen[1];
+      gs.s->tile_stats_seen[0] = ts[0];
+      gs.s->tile_stats_seen[1] = ts[1];
+    }
+  G->prof.tiles += tiles;
+  G->prof.tile_pixels += px;
+  *out = G->prof;
+  if (reset) G->prof = fkd_profile{};
   return FKD_OK;
 }
 

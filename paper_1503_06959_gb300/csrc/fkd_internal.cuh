@@ -150,6 +150,73 @@ struct Output {
   int base_slot;                   // out_base slot read; the other one is written
 };
 
+// ---------------------------------------------------------------- groups
+// A group runs one frame of each of many streams (any mix of sizes) per
+// tick, with one launch per kernel for the whole tick. Each stream's static
+// description lives in device memory (StreamDev); each tick uploads one
+// TickItem per participating stream and a TickHeader with the totals. The
+// group kernels are persistent (fixed grids looping over the tick's work),
+// so one captured CUDA graph replays every tick whatever its composition.
+
+// Resident description of one stream of a group (device memory).
+struct StreamDev {
+  Geometry g;
+  Tables tb;
+  Scratch s;                 // sized for one frame (T_max = 1)
+  Params p;
+  uint32_t* state_bits[2];
+  uint8_t* state_score[2];
+  uint32_t* state_cnt[2];
+  uint8_t* last[2];          // copies of the stream's last two frames (c_0, pitch layer[0].pitch)
+  fkd_keypoint* rec;         // D_n of the last tick (K_max records)
+  uint32_t* rec_offsets;     // [2]
+  long long K_max;
+};
+
+// One participating stream of a tick.
+struct TickItem {
+  int sid;                   // index of the stream's StreamDev
+  int state_cur;             // kept-set buffer holding D_{n-1}
+  long long frame_index;     // n
+  const uint8_t* frame;      // I_n (device), row pitch `pitch`
+  int pitch;
+  int pyr_base, bin_base, tile_base, chunk_base;  // prefix sums of the tick's work
+};
+
+struct TickHeader {
+  int n_items;
+  int total_pyr, total_bins, total_tiles, total_chunks;
+};
+
+constexpr int kMaxTickItems = 1024;
+
+// Group launchers (persistent grids; all asynchronous on `st`).
+int group_pyramid_grid(int O, int intra);
+void launch_group_pyramid(int O, int intra, const StreamDev* devs, const TickHeader* hdr,
+                          const TickItem* items, int grid, cudaStream_t st);
+void launch_group_mask(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
+                       uint32_t* work_count, int grid, cudaStream_t st);
+void launch_group_worklist(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
+                           uint32_t* work, uint32_t* work_count, int grid, cudaStream_t st);
+void launch_group_detect(const StreamDev* devs, const TickItem* items, const uint32_t* work,
+                         const uint32_t* work_count, int grid, cudaStream_t st);
+void launch_group_count(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
+                        int grid, cudaStream_t st);
+void launch_group_emit(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
+                       int grid, cudaStream_t st);
+
+// Index of the item whose [base, next base) range holds j (bases ascending).
+template <typename F>
+__device__ __forceinline__ int find_item(int n, int j, F base_of) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (base_of(mid) <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Launchers (all asynchronous on `st`).
 void launch_pyramid(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                     const Params& p, cudaStream_t st);

@@ -33,12 +33,13 @@ __device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* red) {
   return t;
 }
 
-__global__ void __launch_bounds__(kAsmThreads) k_count(Geometry g, Tables tb, Batch b, Scratch s,
-                                                       State st) {
+// Merge and count one chunk of frame k; ends with the block reduction's
+// barriers, so a CTA can run it again at once.
+__device__ __forceinline__ void count_chunk(const Geometry& g, const Tables& tb, const Scratch& s,
+                                            const State& st, int k, int chunk) {
   __shared__ int xs[kXsSmem];
   __shared__ uint32_t red[kAsmThreads / 32];
-  const int k = blockIdx.y;
-  const AsmChunk ch = tb.chunks[blockIdx.x];
+  const AsmChunk ch = tb.chunks[chunk];
   const LayerGeom& lg = g.layer[ch.layer];
   const int wpr = lg.wpr, w = lg.w;
   const int nwords = (ch.y1 - ch.y0) * wpr;
@@ -86,17 +87,25 @@ __global__ void __launch_bounds__(kAsmThreads) k_count(Geometry g, Tables tb, Ba
   }
   const uint32_t tot = block_sum(cnt, red);
   if (threadIdx.x == 0) {
-    s.chunk_counts[(long long)k * g.n_chunks + blockIdx.x] = tot;
+    s.chunk_counts[(long long)k * g.n_chunks + chunk] = tot;
     if (tot) atomicAdd(&s.frame_totals[k], tot);
   }
+  __syncthreads();  // xs and red are reused by the next chunk of this CTA
 }
 
-__global__ void __launch_bounds__(kAsmThreads) k_emit(Geometry g, Tables tb, Batch b, Scratch s,
-                                                      State st, Output out) {
+__device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb, const Scratch& s,
+                                             const State& st, const Output& out, int k, bool last,
+                                             const AsmChunk& ch, const LayerGeom& lg, int j0,
+                                             const uint32_t* words, unsigned long long idx);
+
+// Emit the records of one chunk of frame k of a batch of T frames; the last
+// frame also writes the new kept set. Ends with a barrier.
+__device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, const Scratch& s,
+                                           const State& st, const Output& out, int k, int T,
+                                           int chunk) {
   __shared__ uint32_t red[kAsmThreads / 32];
   __shared__ uint32_t wsum[kAsmThreads / 32];
-  const int k = blockIdx.y, chunk = blockIdx.x;
-  const bool last = k == b.T - 1;
+  const bool last = k == T - 1;
   const AsmChunk ch = tb.chunks[chunk];
   const LayerGeom& lg = g.layer[ch.layer];
   const int wpr = lg.wpr;
@@ -145,8 +154,15 @@ __global__ void __launch_bounds__(kAsmThreads) k_emit(Geometry g, Tables tb, Bat
   uint32_t before = 0;
   for (int q = 0; q < wid; ++q) before += wsum[q];
   unsigned long long idx = call_base + frame_base + chunk_base + before + incl - cnt;
-  if (cnt == 0) return;
+  if (cnt) emit_records(g, tb, s, st, out, k, last, ch, lg, j0, words, idx);
+  __syncthreads();  // red and wsum are reused by the next chunk of this CTA
+}
 
+__device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb, const Scratch& s,
+                                             const State& st, const Output& out, int k, bool last,
+                                             const AsmChunk& ch, const LayerGeom& lg, int j0,
+                                             const uint32_t* words, unsigned long long idx) {
+  const int wpr = lg.wpr;
   const int* src_k = s.src + (long long)k * g.NB;
   const uint16_t* colblk = tb.colblk + lg.col_off;
   int y = ch.y0 + j0 / wpr, wx = j0 % wpr;
@@ -187,11 +203,65 @@ __global__ void __launch_bounds__(kAsmThreads) k_emit(Geometry g, Tables tb, Bat
   }
 }
 
+__global__ void __launch_bounds__(kAsmThreads) k_count(Geometry g, Tables tb, Scratch s, State st) {
+  count_chunk(g, tb, s, st, blockIdx.y, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kAsmThreads) k_emit(Geometry g, Tables tb, Batch b, Scratch s,
+                                                      State st, Output out) {
+  emit_chunk(g, tb, s, st, out, blockIdx.y, b.T, blockIdx.x);
+}
+
+__device__ __forceinline__ State state_of(const StreamDev& d, int cur) {
+  State st;
+  st.bits_in = d.state_bits[cur];
+  st.score_in = d.state_score[cur];
+  st.cnt_in = d.state_cnt[cur];
+  st.bits_out = d.state_bits[cur ^ 1];
+  st.score_out = d.state_score[cur ^ 1];
+  st.cnt_out = d.state_cnt[cur ^ 1];
+  return st;
+}
+
+// Group tick: persistent CTAs over the chunks of every participating frame.
+__global__ void __launch_bounds__(kAsmThreads) k_group_count(const StreamDev* devs, const TickHeader* hdr,
+                                                             const TickItem* items) {
+  const int n = hdr->n_items, total = hdr->total_chunks;
+  for (int j = blockIdx.x; j < total; j += gridDim.x) {
+    const int i = find_item(n, j, [&](int q) { return items[q].chunk_base; });
+    const TickItem it = items[i];
+    const StreamDev& d = devs[it.sid];
+    count_chunk(d.g, d.tb, d.s, state_of(d, it.state_cur), 0, j - it.chunk_base);
+  }
+}
+
+__global__ void __launch_bounds__(kAsmThreads) k_group_emit(const StreamDev* devs, const TickHeader* hdr,
+                                                            const TickItem* items) {
+  const int n = hdr->n_items, total = hdr->total_chunks;
+  for (int j = blockIdx.x; j < total; j += gridDim.x) {
+    const int i = find_item(n, j, [&](int q) { return items[q].chunk_base; });
+    const TickItem it = items[i];
+    const StreamDev& d = devs[it.sid];
+    Output o{d.rec, d.K_max, d.rec_offsets, 0};
+    emit_chunk(d.g, d.tb, d.s, state_of(d, it.state_cur), o, 0, 1, j - it.chunk_base);
+  }
+}
+
 }  // namespace
+
+void launch_group_count(const StreamDev* devs, const TickHeader* hdr, const TickItem* items, int grid,
+                        cudaStream_t st) {
+  k_group_count<<<grid, kAsmThreads, 0, st>>>(devs, hdr, items);
+}
+
+void launch_group_emit(const StreamDev* devs, const TickHeader* hdr, const TickItem* items, int grid,
+                       cudaStream_t st) {
+  k_group_emit<<<grid, kAsmThreads, 0, st>>>(devs, hdr, items);
+}
 
 void launch_count(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                   const State& state, cudaStream_t st) {
-  k_count<<<dim3(g.n_chunks, b.T), kAsmThreads, 0, st>>>(g, tb, b, s, state);
+  k_count<<<dim3(g.n_chunks, b.T), kAsmThreads, 0, st>>>(g, tb, s, state);
 }
 
 void launch_emit(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,

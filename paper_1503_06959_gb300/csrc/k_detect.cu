@@ -112,32 +112,85 @@ __device__ __forceinline__ uint32_t nibble(uint32_t keep) {
   return (((keep >> 7) & 0x01010101u) * 0x00204081u >> 21) & 0xfu;
 }
 
+// One (frame, tile) work item, with everything the kernel body needs.
 struct Item {
-  int k, l, x0, y0, w, h;
-  const uint8_t* src;
+  int x0, y0, w, h;          // tile origin, layer size
+  const uint8_t* src;        // the layer (row 0)
   int pitch;
+  uint32_t* bits;            // the frame's keypoint bitmap of this layer (row 0)
+  int wpr;
+  uint8_t* dscore;           // the frame's score map of this layer (row 0)
+  int dpitch;
+  int t;                     // segment-test threshold
 };
 
-__device__ __forceinline__ Item decode(const Geometry& g, const Batch& b, const Scratch& s,
-                                       const Tables& tb, uint32_t item) {
-  const uint32_t wi = s.work[item];
-  const DetTile tile = tb.tiles[wi % (uint32_t)g.n_tiles];
-  Item it;
-  it.k = (int)(wi / (uint32_t)g.n_tiles);
-  it.l = tile.layer;
-  it.w = g.layer[it.l].w;
-  it.h = g.layer[it.l].h;
-  it.x0 = tile.tx * TW;
-  it.y0 = tile.ty * TH;
-  if (it.l == 0) {
-    it.src = b.frames + (long long)it.k * b.frame_stride;
-    it.pitch = b.pitch;
-  } else {
-    it.src = s.pyr + (long long)it.k * g.pyr_bytes + g.layer[it.l].pyr_off;
-    it.pitch = g.layer[it.l].pitch;
+// Work items of one stream's batch of T frames.
+struct SingleSrc {
+  Geometry g;
+  Batch b;
+  Scratch s;
+  Tables tb;
+  Params p;
+  __device__ __forceinline__ uint32_t count() const { return *s.work_count; }
+  __device__ __forceinline__ Item decode(uint32_t item) const {
+    const uint32_t wi = s.work[item];
+    const DetTile tile = tb.tiles[wi % (uint32_t)g.n_tiles];
+    const int k = (int)(wi / (uint32_t)g.n_tiles);
+    const LayerGeom& lg = g.layer[tile.layer];
+    Item it;
+    it.w = lg.w;
+    it.h = lg.h;
+    it.x0 = tile.tx * TW;
+    it.y0 = tile.ty * TH;
+    if (tile.layer == 0) {
+      it.src = b.frames + (long long)k * b.frame_stride;
+      it.pitch = b.pitch;
+    } else {
+      it.src = s.pyr + (long long)k * g.pyr_bytes + lg.pyr_off;
+      it.pitch = lg.pitch;
+    }
+    it.bits = s.det_bits + (long long)k * g.bit_words + lg.bit_off;
+    it.wpr = lg.wpr;
+    it.dscore = s.det_score + (long long)k * g.score_bytes + lg.score_off;
+    it.dpitch = lg.pitch;
+    it.t = p.t;
+    return it;
   }
-  return it;
-}
+};
+
+// Work items of a group tick (one frame of each of many streams).
+struct GroupSrc {
+  const StreamDev* devs;
+  const TickItem* items;
+  const uint32_t* work;
+  const uint32_t* work_count;
+  __device__ __forceinline__ uint32_t count() const { return *work_count; }
+  __device__ __forceinline__ Item decode(uint32_t item) const {
+    const uint32_t wi = work[item];
+    const TickItem ti = items[wi >> 22];
+    const StreamDev& d = devs[ti.sid];
+    const DetTile tile = d.tb.tiles[wi & 0x3fffffu];
+    const LayerGeom& lg = d.g.layer[tile.layer];
+    Item it;
+    it.w = lg.w;
+    it.h = lg.h;
+    it.x0 = tile.tx * TW;
+    it.y0 = tile.ty * TH;
+    if (tile.layer == 0) {
+      it.src = ti.frame;
+      it.pitch = ti.pitch;
+    } else {
+      it.src = d.s.pyr + lg.pyr_off;
+      it.pitch = lg.pitch;
+    }
+    it.bits = d.s.det_bits + lg.bit_off;
+    it.wpr = lg.wpr;
+    it.dscore = d.s.det_score + lg.score_off;
+    it.dpitch = lg.pitch;
+    it.t = d.p.t;
+    return it;
+  }
+};
 
 // A. stage input rows y0-4 .. y0+TH+3, columns x0-16 .. x0+TW+15, zeros
 // outside the layer. x0 is a multiple of 128, so each 16-byte chunk is either
@@ -172,8 +225,8 @@ __device__ __forceinline__ int cand_off(int b, int lane) {
 // Score-map offset of the pixel at input offset o.
 __device__ __forceinline__ int sc_of(int o) { return (o / IN_W - 3) * SC_P + (o % IN_W) - 12; }
 
-__global__ void __launch_bounds__(kDetThreads, 2) k_detect(Geometry g, Batch b, Scratch s,
-                                                           Tables tb, Params p) {
+template <class Src>
+__global__ void __launch_bounds__(kDetThreads, 2) k_detect(Src src) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* inbuf = smem + warp * WARP_SMEM;
@@ -182,19 +235,14 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Geometry g, Batch b, 
   uint32_t* passw = detw + DET_WORDS;
   uint16_t* list = reinterpret_cast<uint16_t*>(passw + DET_WORDS);
 
-  const uint32_t count_items = *s.work_count;
-  const uint32_t t = (uint32_t)p.t;
-  const uint32_t t1 = t + 1u;  // score >= t  <=>  some arc beyond I_p +- t
-  const uint32_t t1_low7 = (t1 & 0x7fu) * 0x01010101u;
-  const bool t1_high = t1 >= 128u;
-  const bool none = t1 > 255u;
+  const uint32_t count_items = src.count();
   const uint32_t stride = gridDim.x * WARPS;
 
   uint32_t item = blockIdx.x * WARPS + warp;
   int buf = 0;
   Item nxt{};
   if (item < count_items) {
-    nxt = decode(g, b, s, tb, item);
+    nxt = src.decode(item);
     stage(inbuf, nxt, lane);
   }
   cp_async_commit();
@@ -203,7 +251,7 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Geometry g, Batch b, 
     const uint8_t* in = inbuf + buf * IN_BYTES;
     // prefetch the next tile into the other buffer, then wait for this one
     if (item + stride < count_items) {
-      nxt = decode(g, b, s, tb, item + stride);
+      nxt = src.decode(item + stride);
       stage(inbuf + (buf ^ 1) * IN_BYTES, nxt, lane);
     }
     cp_async_commit();
@@ -213,7 +261,12 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Geometry g, Batch b, 
     passw[lane] = passw[lane + 32] = 0u;
     cp_async_wait<1>();
     __syncwarp();
-    const int k = it.k, l = it.l, w = it.w, h = it.h, x0 = it.x0, y0 = it.y0;
+    const int w = it.w, h = it.h, x0 = it.x0, y0 = it.y0;
+    const uint32_t t = (uint32_t)it.t;
+    const uint32_t t1 = t + 1u;  // score >= t  <=>  some arc beyond I_p +- t
+    const uint32_t t1_low7 = (t1 & 0x7fu) * 0x01010101u;
+    const bool t1_high = t1 >= 128u;
+    const bool none = t1 > 255u;
 
     // B. prefilter the score rows y0-1 .. y0+TH (input rows 3 .. TH+4); lane
     //    owns the word x0+4*lane .. +3 of every row and keeps its candidate
@@ -321,8 +374,7 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Geometry g, Batch b, 
     }
 
     // D. strict 3x3 maxima among the tile's passing pixels
-    const LayerGeom& lg = g.layer[l];
-    uint8_t* dscore = s.det_score + (long long)k * g.score_bytes + lg.score_off;
+    uint8_t* dscore = it.dscore;
 #pragma unroll
     for (int j = 0; j < DET_WORDS / 32; ++j) {
       const int idx = lane + 32 * j;
@@ -337,19 +389,19 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Geometry g, Batch b, 
         if (v > q[-SC_P - 1] && v > q[-SC_P] && v > q[-SC_P + 1] && v > q[-1] && v > q[1] &&
             v > q[SC_P - 1] && v > q[SC_P] && v > q[SC_P + 1]) {
           atomicOr(&detw[idx], 1u << bb);
-          dscore[(long long)(y0 + ly) * lg.pitch + x0 + lx] = (uint8_t)v;
+          dscore[(long long)(y0 + ly) * it.dpitch + x0 + lx] = (uint8_t)v;
         }
       }
     }
     __syncwarp();
 
     // E. the tile's bitmap words (TH rows x TW/32 words)
-    uint32_t* bits = s.det_bits + (long long)k * g.bit_words + lg.bit_off;
+    uint32_t* bits = it.bits;
 #pragma unroll
     for (int j = 0; j < DET_WORDS / 32; ++j) {
       const int idx = lane + 32 * j;
       const int ly = idx / (TW / 32), wx = x0 / 32 + idx % (TW / 32);
-      if (y0 + ly < h && wx < lg.wpr) bits[(long long)(y0 + ly) * lg.wpr + wx] = detw[idx];
+      if (y0 + ly < h && wx < it.wpr) bits[(long long)(y0 + ly) * it.wpr + wx] = detw[idx];
     }
     __syncwarp();
     buf ^= 1;
@@ -363,8 +415,9 @@ int detect_grid_size() {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaFuncSetAttribute(k_detect, cudaFuncAttributeMaxDynamicSharedMemorySize, WARPS * WARP_SMEM);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_detect, kDetThreads, WARPS * WARP_SMEM);
+  cudaFuncSetAttribute(k_detect<SingleSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, WARPS * WARP_SMEM);
+  cudaFuncSetAttribute(k_detect<GroupSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, WARPS * WARP_SMEM);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_detect<SingleSrc>, kDetThreads, WARPS * WARP_SMEM);
   if (sms <= 0) sms = 1;
   if (per_sm <= 0) per_sm = 1;
   return sms * per_sm;
@@ -372,7 +425,12 @@ int detect_grid_size() {
 
 void launch_detect(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                    const Params& p, int grid, cudaStream_t st) {
-  k_detect<<<grid, kDetThreads, WARPS * WARP_SMEM, st>>>(g, b, s, tb, p);
+  k_detect<SingleSrc><<<grid, kDetThreads, WARPS * WARP_SMEM, st>>>(SingleSrc{g, b, s, tb, p});
+}
+
+void launch_group_detect(const StreamDev* devs, const TickItem* items, const uint32_t* work,
+                         const uint32_t* work_count, int grid, cudaStream_t st) {
+  k_detect<GroupSrc><<<grid, kDetThreads, WARPS * WARP_SMEM, st>>>(GroupSrc{devs, items, work, work_count});
 }
 
 }  // namespace fkd

@@ -97,7 +97,86 @@ __global__ void k_worklist(Geometry g, Tables tb, Batch b, Scratch s) {
   if (act) s.work[base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
 }
 
+// Group tick, one frame per stream: the mask and source frame of every bin
+// of every participating stream (src = 0 for active bins, -1 = kept set).
+__global__ void k_group_mask(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
+                             uint32_t* work_count) {
+  const int n = hdr->n_items, total = hdr->total_bins;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gtid == 0) *work_count = 0;
+  for (int j = gtid; j < total; j += gridDim.x * blockDim.x) {
+    const int i = find_item(n, j, [&](int q) { return items[q].bin_base; });
+    const TickItem it = items[i];
+    const StreamDev& d = devs[it.sid];
+    const int bin = j - it.bin_base;
+    int m;
+    if (it.frame_index == 0 || d.p.mask_mode == FKD_MASK_FULL) {
+      m = 1;
+    } else if (d.p.mask_mode == FKD_MASK_ID) {
+      m = d.s.bsum[bin] > (unsigned long long)d.p.T_I * d.tb.npix[bin];
+      d.s.bsum[bin] = 0;
+    } else {
+      m = d.state_cnt[it.state_cur][bin] >= (uint32_t)d.p.T_H;
+    }
+    d.s.mask[bin] = (uint8_t)m;
+    d.s.src[bin] = m ? 0 : -1;
+    d.state_cnt[it.state_cur ^ 1][bin] = 0;
+    if (bin == 0) {
+      d.s.frame_totals[0] = 0;
+      d.s.out_base[0] = 0;
+    }
+  }
+}
+
+// Group tick: active (stream, tile) items of every participating stream,
+// compacted into one list (item index << 22 | tile).
+__global__ void k_group_worklist(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
+                                 uint32_t* work, uint32_t* work_count) {
+  const int n = hdr->n_items, total = hdr->total_tiles;
+  const int lane = threadIdx.x & 31;
+  for (int j0 = blockIdx.x * blockDim.x; j0 < total; j0 += gridDim.x * blockDim.x) {
+    const int j = j0 + threadIdx.x;
+    bool act = false;
+    uint32_t entry = 0;
+    if (j < total) {
+      const int i = find_item(n, j, [&](int q) { return items[q].tile_base; });
+      const TickItem it = items[i];
+      const StreamDev& d = devs[it.sid];
+      const int tile = j - it.tile_base;
+      const DetTile t = d.tb.tiles[tile];
+      for (int r = t.rb0; r <= t.rb1 && !act; ++r)
+        for (int c = t.cb0; c <= t.cb1; ++c)
+          if (d.s.mask[r * d.g.N_c + c]) { act = true; break; }
+      if (act) {
+        entry = ((uint32_t)i << 22) | (uint32_t)tile;
+        const LayerGeom& lg = d.g.layer[t.layer];
+        const uint32_t area =
+            (uint32_t)(min(kDetTW, lg.w - t.tx * kDetTW) * min(kDetTH, lg.h - t.ty * kDetTH));
+        atomicAdd(&d.s.tile_stats[0], 1ull);
+        atomicAdd(&d.s.tile_stats[1], (unsigned long long)area);
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, act);
+    if (bal == 0) continue;
+    const int leader = __ffs(bal) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(work_count, (uint32_t)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (act) work[base + __popc(bal & ((1u << lane) - 1u))] = entry;
+  }
+}
+
 }  // namespace
+
+void launch_group_mask(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
+                       uint32_t* work_count, int grid, cudaStream_t st) {
+  k_group_mask<<<grid, 256, 0, st>>>(devs, hdr, items, work_count);
+}
+
+void launch_group_worklist(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
+                           uint32_t* work, uint32_t* work_count, int grid, cudaStream_t st) {
+  k_group_worklist<<<grid, 256, 0, st>>>(devs, hdr, items, work, work_count);
+}
 
 void launch_mask(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                  const Params& p, const State& state, cudaStream_t st, int reset_base_slot) {

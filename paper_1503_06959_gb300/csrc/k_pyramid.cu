@@ -225,20 +225,20 @@ __device__ __forceinline__ void build(const Geometry& g, uint8_t* pyr, uint8_t* 
   }
 }
 
+// One 96 x 96 tile of c_0 of one frame: pyramid, layer writes, per-bin change
+// sums (if `diff`), and a copy of the c_0 tile to `keep` (if not null, pitch
+// `keep_pitch`). Ends with a barrier, so a CTA can run it again at once.
 template <int O, int INTRA>
-__global__ void __launch_bounds__(kPyrThreads) k_pyramid(Geometry g, Tables tb, Batch b, Scratch s,
-                                                         Params p) {
+__device__ __forceinline__ void pyramid_tile(const Geometry& g, const Tables& tb, const uint8_t* frame,
+                                             int pitch, const uint8_t* prevf, int prev_pitch,
+                                             bool diff, uint8_t* pyr, unsigned long long* gsum,
+                                             uint8_t* keep, int keep_pitch, int tx, int ty) {
   __shared__ __align__(16) uint8_t cur[kPyrSmem];
   __shared__ __align__(16) uint8_t prv[kPyrSmem];
   __shared__ uint32_t bins[kLocalBins];
   __shared__ uint16_t tcol[P], trow[P];
 
-  const int k = blockIdx.z;
-  const int tx = blockIdx.x, ty = blockIdx.y;
-  const uint8_t* frame = b.frames + (long long)k * b.frame_stride;
-  load_c0(cur, frame, b.pitch, tx * P, ty * P, g.W, g.H);
-
-  const bool diff = p.mask_mode == FKD_MASK_ID && (b.first_frame + k) > 0;
+  load_c0(cur, frame, pitch, tx * P, ty * P, g.W, g.H);
   const int ml = g.mask_layer;
   const LayerGeom& mlg = g.layer[ml];
   const bool ml_d = INTRA && (ml & 1);
@@ -248,9 +248,7 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Geometry g, Tables tb, 
   const int mgx0 = tx * mn, mgy0 = ty * mn;
   const int mnx = min(mn, mlg.w - mgx0), mny = min(mn, mlg.h - mgy0);
   if (diff) {
-    const uint8_t* pf = k == 0 ? b.prev : frame - b.frame_stride;
-    const int pp = k == 0 ? b.prev_pitch : b.pitch;
-    load_c0(prv, pf, pp, tx * P, ty * P, g.W, g.H);
+    load_c0(prv, prevf, prev_pitch, tx * P, ty * P, g.W, g.H);
     for (int q = threadIdx.x; q < kLocalBins; q += NT) bins[q] = 0;
     for (int q = threadIdx.x; q < mn; q += NT) {
       tcol[q] = q < mnx ? tb.colblk[mlg.col_off + mgx0 + q] : 0;
@@ -261,82 +259,128 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Geometry g, Tables tb, 
   cp_async_wait<0>();
   __syncthreads();
 
-  uint8_t* pyr = s.pyr + (long long)k * g.pyr_bytes;
-  build<O, INTRA, true>(g, pyr, cur, tx, ty, g.L - 1);
-  if (!diff || mnx <= 0 || mny <= 0) return;
-  if (ml > 0) build<O, INTRA, false>(g, pyr, prv, tx, ty, ml);
-
-  // Per-bin sums of |L_n - L_{n-1}| on the mask layer. Thread -> a 4-pixel
-  // column word and a band of rows; the running sum is flushed into a shared
-  // bin whenever the bin row changes (and split by pixel when the word's
-  // pixels straddle bin columns).
-  const int cb_lo = tcol[0], rb_lo = trow[0];
-  const int ncols = tcol[mnx - 1] - cb_lo + 1, nrows = trow[mny - 1] - rb_lo + 1;
-  const bool local = ncols * nrows <= kLocalBins;
-  unsigned long long* gsum = s.bsum + (long long)k * g.NB;
-  const uint8_t* A = cur + moff;
-  const uint8_t* B = prv + moff;
-  auto flush = [&](int rb, int cb, uint32_t v) {
-    if (!v) return;
-    if (local) atomicAdd(&bins[(rb - rb_lo) * ncols + (cb - cb_lo)], v);
-    else atomicAdd(&gsum[rb * g.N_c + cb], (unsigned long long)v);
-  };
-  if ((mn & 3) == 0) {
-    const int wcols = (mnx + 3) / 4;
-    const int groups = max(1, NT / wcols);
-    const int rows_per = (mny + groups - 1) / groups;
-    const int wc = threadIdx.x % wcols, grp = threadIdx.x / wcols;
-    if (grp < groups) {
-      const int x = 4 * wc;
-      const int nv = min(4, mnx - x);
-      const uint32_t vmask = nv == 4 ? 0xffffffffu : ((1u << (8 * nv)) - 1u);
-      const int c0 = tcol[x], c3 = tcol[x + nv - 1];
-      uint32_t acc = 0, acc_hi = 0;
-      int rb_cur = -1;
-      const int y_end = min(mny, (grp + 1) * rows_per);
-      for (int y = grp * rows_per; y < y_end; ++y) {
-        const int rb = trow[y];
-        if (rb != rb_cur) {
-          if (rb_cur >= 0) {
-            flush(rb_cur, c0, acc);
-            if (c3 != c0) flush(rb_cur, c3, acc_hi);
-          }
-          rb_cur = rb;
-          acc = acc_hi = 0;
-        }
-        const uint32_t a = ld32(A + y * mn + x) & vmask, c = ld32(B + y * mn + x) & vmask;
-        if (c3 == c0) {
-          acc += __vsadu4(a, c);
+  if (keep) {  // the frame's own copy of c_0, kept for the next frame's change test
+    const int gx0 = tx * P, gy0 = ty * P;
+    const int nx = min(P, g.W - gx0), ny = min(P, g.H - gy0);
+    for (int q = threadIdx.x; q < P * (P / 4); q += NT) {
+      const int y = q / (P / 4), x = 4 * (q % (P / 4));
+      if (y < ny && x < nx) {
+        uint8_t* d = keep + (long long)(gy0 + y) * keep_pitch + gx0 + x;
+        const uint32_t v = ld32(cur + y * P + x);
+        if (x + 4 <= nx) {
+          *reinterpret_cast<uint32_t*>(d) = v;
         } else {
-          // the word straddles bin columns: split it pixel by pixel (bins
-          // narrower than 4 pixels put middle pixels in further bins)
-          for (int i = 0; i < nv; ++i) {
-            const int ci = tcol[x + i];
-            const uint32_t d = __vabsdiffu4((a >> (8 * i)) & 0xffu, (c >> (8 * i)) & 0xffu);
-            if (ci == c0) acc += d;
-            else if (ci == c3) acc_hi += d;
-            else flush(rb, ci, d);
-          }
+          for (int j = 0; j < nx - x; ++j) d[j] = (uint8_t)(v >> (8 * j));
         }
       }
-      if (rb_cur >= 0) {
-        flush(rb_cur, c0, acc);
-        if (c3 != c0) flush(rb_cur, c3, acc_hi);
-      }
-    }
-  } else {
-    for (int q = threadIdx.x; q < mnx * mny; q += NT) {
-      const int y = q / mnx, x = q % mnx;
-      const int dv = (int)A[y * mn + x] - (int)B[y * mn + x];
-      flush(trow[y], tcol[x], (uint32_t)(dv < 0 ? -dv : dv));
     }
   }
-  if (local) {
-    __syncthreads();
-    for (int q = threadIdx.x; q < ncols * nrows; q += NT) {
-      const uint32_t v = bins[q];
-      if (v) atomicAdd(&gsum[(rb_lo + q / ncols) * g.N_c + cb_lo + q % ncols], (unsigned long long)v);
+  build<O, INTRA, true>(g, pyr, cur, tx, ty, g.L - 1);
+  if (diff && mnx > 0 && mny > 0) {
+    if (ml > 0) build<O, INTRA, false>(g, pyr, prv, tx, ty, ml);
+    // Per-bin sums of |L_n - L_{n-1}| on the mask layer. Thread -> a 4-pixel
+    // column word and a band of rows; the running sum is flushed into a
+    // shared bin whenever the bin row changes (and split by pixel when the
+    // word's pixels straddle bin columns).
+    const int cb_lo = tcol[0], rb_lo = trow[0];
+    const int ncols = tcol[mnx - 1] - cb_lo + 1, nrows = trow[mny - 1] - rb_lo + 1;
+    const bool local = ncols * nrows <= kLocalBins;
+    const uint8_t* A = cur + moff;
+    const uint8_t* B = prv + moff;
+    auto flush = [&](int rb, int cb, uint32_t v) {
+      if (!v) return;
+      if (local) atomicAdd(&bins[(rb - rb_lo) * ncols + (cb - cb_lo)], v);
+      else atomicAdd(&gsum[rb * g.N_c + cb], (unsigned long long)v);
+    };
+    if ((mn & 3) == 0) {
+      const int wcols = (mnx + 3) / 4;
+      const int groups = max(1, NT / wcols);
+      const int rows_per = (mny + groups - 1) / groups;
+      const int wc = threadIdx.x % wcols, grp = threadIdx.x / wcols;
+      if (grp < groups) {
+        const int x = 4 * wc;
+        const int nv = min(4, mnx - x);
+        const uint32_t vmask = nv == 4 ? 0xffffffffu : ((1u << (8 * nv)) - 1u);
+        const int c0 = tcol[x], c3 = tcol[x + nv - 1];
+        uint32_t acc = 0, acc_hi = 0;
+        int rb_cur = -1;
+        const int y_end = min(mny, (grp + 1) * rows_per);
+        for (int y = grp * rows_per; y < y_end; ++y) {
+          const int rb = trow[y];
+          if (rb != rb_cur) {
+            if (rb_cur >= 0) {
+              flush(rb_cur, c0, acc);
+              if (c3 != c0) flush(rb_cur, c3, acc_hi);
+            }
+            rb_cur = rb;
+            acc = acc_hi = 0;
+          }
+          const uint32_t a = ld32(A + y * mn + x) & vmask, c = ld32(B + y * mn + x) & vmask;
+          if (c3 == c0) {
+            acc += __vsadu4(a, c);
+          } else {
+            // the word straddles bin columns: split it pixel by pixel (bins
+            // narrower than 4 pixels put middle pixels in further bins)
+            for (int i = 0; i < nv; ++i) {
+              const int ci = tcol[x + i];
+              const uint32_t d = __vabsdiffu4((a >> (8 * i)) & 0xffu, (c >> (8 * i)) & 0xffu);
+              if (ci == c0) acc += d;
+              else if (ci == c3) acc_hi += d;
+              else flush(rb, ci, d);
+            }
+          }
+        }
+        if (rb_cur >= 0) {
+          flush(rb_cur, c0, acc);
+          if (c3 != c0) flush(rb_cur, c3, acc_hi);
+        }
+      }
+    } else {
+      for (int q = threadIdx.x; q < mnx * mny; q += NT) {
+        const int y = q / mnx, x = q % mnx;
+        const int dv = (int)A[y * mn + x] - (int)B[y * mn + x];
+        flush(trow[y], tcol[x], (uint32_t)(dv < 0 ? -dv : dv));
+      }
     }
+    if (local) {
+      __syncthreads();
+      for (int q = threadIdx.x; q < ncols * nrows; q += NT) {
+        const uint32_t v = bins[q];
+        if (v) atomicAdd(&gsum[(rb_lo + q / ncols) * g.N_c + cb_lo + q % ncols], (unsigned long long)v);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int O, int INTRA>
+__global__ void __launch_bounds__(kPyrThreads) k_pyramid(Geometry g, Tables tb, Batch b, Scratch s,
+                                                         Params p) {
+  const int k = blockIdx.z;
+  const uint8_t* frame = b.frames + (long long)k * b.frame_stride;
+  const bool diff = p.mask_mode == FKD_MASK_ID && (b.first_frame + k) > 0;
+  const uint8_t* pf = k == 0 ? b.prev : frame - b.frame_stride;
+  const int pp = k == 0 ? b.prev_pitch : b.pitch;
+  pyramid_tile<O, INTRA>(g, tb, frame, b.pitch, pf, pp, diff, s.pyr + (long long)k * g.pyr_bytes,
+                         s.bsum + (long long)k * g.NB, nullptr, 0, blockIdx.x, blockIdx.y);
+}
+
+// Group tick: persistent CTAs over the c_0 tiles of every participating frame.
+template <int O, int INTRA>
+__global__ void __launch_bounds__(kPyrThreads) k_group_pyramid(const StreamDev* devs,
+                                                               const TickHeader* hdr,
+                                                               const TickItem* items) {
+  const int n = hdr->n_items, total = hdr->total_pyr;
+  for (int j = blockIdx.x; j < total; j += gridDim.x) {
+    const int i = find_item(n, j, [&](int q) { return items[q].pyr_base; });
+    const TickItem it = items[i];
+    const StreamDev& d = devs[it.sid];
+    const int local = j - it.pyr_base;
+    const int tx = local % d.g.pyr_tiles_x, ty = local / d.g.pyr_tiles_x;
+    const bool diff = d.p.mask_mode == FKD_MASK_ID && it.frame_index > 0;
+    const int kp = d.g.layer[0].pitch;
+    pyramid_tile<O, INTRA>(d.g, d.tb, it.frame, it.pitch, d.last[(it.frame_index + 1) & 1], kp, diff,
+                           d.s.pyr, d.s.bsum, d.last[it.frame_index & 1], kp, tx, ty);
   }
 }
 
@@ -345,6 +389,12 @@ void launch_t(const Geometry& g, const Tables& tb, const Batch& b, const Scratch
               cudaStream_t st) {
   dim3 grid(g.pyr_tiles_x, g.pyr_tiles_y, b.T);
   k_pyramid<O, INTRA><<<grid, kPyrThreads, 0, st>>>(g, tb, b, s, p);
+}
+
+template <int O, int INTRA>
+void launch_group_t(const StreamDev* devs, const TickHeader* hdr, const TickItem* items, int grid,
+                    cudaStream_t st) {
+  k_group_pyramid<O, INTRA><<<grid, kPyrThreads, 0, st>>>(devs, hdr, items);
 }
 
 }  // namespace
@@ -357,6 +407,31 @@ void launch_pyramid(const Geometry& g, const Tables& tb, const Batch& b, const S
       {launch_t<1, 0>, launch_t<2, 0>, launch_t<3, 0>, launch_t<4, 0>, launch_t<5, 0>, launch_t<6, 0>},
       {launch_t<1, 1>, launch_t<2, 1>, launch_t<3, 1>, launch_t<4, 1>, launch_t<5, 1>, launch_t<6, 1>}};
   table[g.intra ? 1 : 0][g.O - 1](g, tb, b, s, p, st);
+}
+
+int group_pyramid_grid(int O, int intra) {
+  using K = void (*)(const StreamDev*, const TickHeader*, const TickItem*);
+  static const K table[2][6] = {
+      {k_group_pyramid<1, 0>, k_group_pyramid<2, 0>, k_group_pyramid<3, 0>, k_group_pyramid<4, 0>,
+       k_group_pyramid<5, 0>, k_group_pyramid<6, 0>},
+      {k_group_pyramid<1, 1>, k_group_pyramid<2, 1>, k_group_pyramid<3, 1>, k_group_pyramid<4, 1>,
+       k_group_pyramid<5, 1>, k_group_pyramid<6, 1>}};
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, table[intra ? 1 : 0][O - 1], kPyrThreads, 0);
+  return max(1, sms) * max(1, per_sm);
+}
+
+void launch_group_pyramid(int O, int intra, const StreamDev* devs, const TickHeader* hdr,
+                          const TickItem* items, int grid, cudaStream_t st) {
+  using L = void (*)(const StreamDev*, const TickHeader*, const TickItem*, int, cudaStream_t);
+  static const L table[2][6] = {
+      {launch_group_t<1, 0>, launch_group_t<2, 0>, launch_group_t<3, 0>, launch_group_t<4, 0>,
+       launch_group_t<5, 0>, launch_group_t<6, 0>},
+      {launch_group_t<1, 1>, launch_group_t<2, 1>, launch_group_t<3, 1>, launch_group_t<4, 1>,
+       launch_group_t<5, 1>, launch_group_t<6, 1>}};
+  table[intra ? 1 : 0][O - 1](devs, hdr, items, grid, st);
 }
 
 }  // namespace fkd

@@ -28,6 +28,10 @@ EXPORTS = [
     "fkd_num_layers", "fkd_layer_info", "fkd_push_frame", "fkd_get_keypoints", "fkd_get_mask",
     "fkd_push_frames", "fkd_synchronize", "fkd_frame_count", "fkd_device_keypoints",
     "fkd_reset_stream", "fkd_profile_enable", "fkd_profile_read", "fkd_id_mask_noalloc",
+    "fkd_group_create", "fkd_group_destroy", "fkd_group_add_stream", "fkd_group_remove_stream",
+    "fkd_group_tick", "fkd_group_use_graph", "fkd_group_synchronize", "fkd_group_get_keypoints",
+    "fkd_group_get_mask", "fkd_group_device_keypoints", "fkd_group_profile_enable",
+    "fkd_group_profile_read",
 ]
 STAGES = ["pyramid", "mask", "worklist", "detect", "count", "emit"]
 
@@ -82,6 +86,18 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.fkd_profile_enable.argtypes = [vp, c_int]
     lib.fkd_profile_read.argtypes = [vp, P(fkd_profile), c_int]
     lib.fkd_id_mask_noalloc.argtypes = [vp, vp, c_int, c_int, c_size, c_int, c_int, c_int, vp, vp]
+    lib.fkd_group_create.argtypes = [c_int, c_int, vp, P(vp)]
+    lib.fkd_group_destroy.argtypes = [vp]
+    lib.fkd_group_add_stream.argtypes = [vp, P(fkd_params), c_int, c_int, P(c_int), P(c_size)]
+    lib.fkd_group_remove_stream.argtypes = [vp, c_int]
+    lib.fkd_group_tick.argtypes = [vp, c_int, P(c_int), P(vp), P(c_size)]
+    lib.fkd_group_use_graph.argtypes = [vp, c_int]
+    lib.fkd_group_synchronize.argtypes = [vp]
+    lib.fkd_group_get_keypoints.argtypes = [vp, c_int, vp, c_size, P(c_size)]
+    lib.fkd_group_get_mask.argtypes = [vp, c_int, vp]
+    lib.fkd_group_device_keypoints.argtypes = [vp, c_int, P(vp), P(vp)]
+    lib.fkd_group_profile_enable.argtypes = [vp, c_int]
+    lib.fkd_group_profile_read.argtypes = [vp, P(fkd_profile), c_int]
     for name in EXPORTS:
         if name != "fkd_last_error":
             getattr(lib, name).restype = c_int
@@ -230,6 +246,84 @@ class Stream:
     def close(self):
         if getattr(self, "_h", None):
             _lib.fkd_destroy_stream(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Group:
+    """Many streams, one frame of each per tick (fkd_group_*)."""
+
+    def __init__(self, O: int, intra: int, cuda_stream: int | None = None):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.fkd_group_create(O, intra, ctypes.c_void_p(cuda_stream or 0), ctypes.byref(h)))
+        self._h = h
+        self.O, self.intra = O, intra
+        self.streams = {}
+
+    def add_stream(self, W: int, H: int, *, N_r: int = 8, N_c: int = 8, T_I: int = 4,
+                   T_H: int = 1, t: int = 20, mask_mode: int = FKD_MASK_ID, mask_layer: int = 0,
+                   K_max: int = 65536) -> tuple[int, int]:
+        p = params_default()
+        p.N_r, p.N_c, p.T_I, p.T_H, p.O, p.intra, p.t = N_r, N_c, T_I, T_H, self.O, self.intra, t
+        p.mask_mode, p.mask_layer, p.K_max = mask_mode, mask_layer, K_max
+        sid, nbytes = ctypes.c_int(), ctypes.c_size_t()
+        _check(_lib.fkd_group_add_stream(self._h, ctypes.byref(p), W, H, ctypes.byref(sid),
+                                         ctypes.byref(nbytes)))
+        self.streams[sid.value] = (W, H, N_r, N_c, K_max)
+        return sid.value, nbytes.value
+
+    def remove_stream(self, sid: int):
+        _check(_lib.fkd_group_remove_stream(self._h, sid))
+        self.streams.pop(sid, None)
+
+    def tick(self, ids, frames):
+        """frames: torch CUDA uint8 (H x W) tensors, one per id."""
+        n = len(ids)
+        ia = (ctypes.c_int * n)(*ids)
+        fa = (ctypes.c_void_p * n)(*[f.data_ptr() for f in frames])
+        pa = (ctypes.c_size_t * n)(*[f.stride(0) for f in frames])
+        _check(_lib.fkd_group_tick(self._h, n, ia, fa, pa))
+
+    def use_graph(self, on: bool):
+        _check(_lib.fkd_group_use_graph(self._h, int(on)))
+
+    def synchronize(self):
+        _check(_lib.fkd_group_synchronize(self._h))
+
+    def get_keypoints(self, sid: int, cap: int | None = None) -> np.ndarray:
+        if cap is None:
+            cap = self.streams[sid][4] if sid in self.streams else 1
+        out = np.zeros(cap, KEYPOINT_DTYPE)
+        n = ctypes.c_size_t()
+        _check(_lib.fkd_group_get_keypoints(self._h, sid, _ptr(out), cap, ctypes.byref(n)))
+        return out[:n.value].copy()
+
+    def get_mask(self, sid: int) -> np.ndarray:
+        W, H, N_r, N_c, _ = self.streams[sid]
+        out = np.zeros(N_r * N_c, np.uint8)
+        _check(_lib.fkd_group_get_mask(self._h, sid, _ptr(out)))
+        return out.reshape(N_r, N_c)
+
+    def profile_enable(self, on: bool = True):
+        _check(_lib.fkd_group_profile_enable(self._h, int(on)))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        p = fkd_profile()
+        _check(_lib.fkd_group_profile_read(self._h, ctypes.byref(p), int(reset)))
+        return {"ms": {STAGES[i]: p.ms[i] for i in range(6)},
+                "launches": {STAGES[i]: int(p.launches[i]) for i in range(6)},
+                "batches": int(p.batches), "frames": int(p.frames), "tiles": int(p.tiles),
+                "tile_pixels": int(p.tile_pixels)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.fkd_group_destroy(self._h)
             self._h = None
 
     def __del__(self):
