@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -185,6 +186,228 @@ def run_reference(args):
     return 0
 
 
+def _group_run(streams, frames_dev, mode, warm, ticks_timed, fkd, torch):
+    """Tick every stream once per tick through one group; returns
+    (seconds for the timed ticks, profile, keypoints per tick)."""
+    st = torch.cuda.Stream()
+    g = fkd.Group(streams[0].O, streams[0].intra, cuda_stream=st.cuda_stream)
+    ids = [g.add_stream(c.W, c.H, N_r=c.N_r, N_c=c.N_c, T_I=c.T_I, t=c.t, mask_mode=mode,
+                        K_max=1 << 17)[0] for c in streams]
+    n_frames = frames_dev[0].shape[0]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for n in range(warm):
+        g.tick(ids, [f[n] for f in frames_dev])
+    g.synchronize()
+    g.profile_read()
+    g.profile_enable(True)
+    e0.record(st)
+    for n in range(warm, warm + ticks_timed):
+        g.tick(ids, [f[n % n_frames] for f in frames_dev])
+    e1.record(st)
+    e1.synchronize()
+    prof = g.profile_read()
+    kps = sum(len(g.get_keypoints(i)) for i in ids)
+    g.close()
+    return e0.elapsed_time(e1) / 1e3, prof, kps
+
+
+def run_config3(args):
+    """64 streams of mixed resolution, one frame of each per tick in one
+    persistent launch sequence (group), frames resident in HBM."""
+    import torch
+    from paper_1503_06959_gb300 import fkd
+    per_res = args.streams_per_res
+    streams = synth.config3_streams(per_res)
+    F = args.frames or 24
+    frames_dev = []
+    for j, c in enumerate(streams):
+        frames_dev.append(torch.from_numpy(synth.source_for(c, 3, j).frames(F)).cuda())
+    warm = 3
+    res = {}
+    for name, mode in (("masked", fkd.FKD_MASK_ID), ("full", fkd.FKD_MASK_FULL)):
+        sec, prof, kps = _group_run(streams, frames_dev, mode, warm, F - warm, fkd, torch)
+        ticks = F - warm
+        res[name] = {"frames_per_s": len(streams) * ticks / sec, "ms_per_tick": sec / ticks * 1e3,
+                     "stage_ms_per_tick": {k: v / max(1, prof["batches"]) for k, v in prof["ms"].items()},
+                     "keypoints_last_tick": kps, "tile_pixels_per_tick": prof["tile_pixels"] / max(1, prof["batches"])}
+    mpix = sum(c.W * c.H for c in streams) / 1e6
+    line = {"metric": "frames/s (group of mixed-resolution streams, bit-exact keypoints)",
+            "value": res["masked"]["frames_per_s"], "unit": "frames/s", "n_gpus": 1,
+            "steps": F - warm, "warmup": warm, "ms_per_step": res["masked"]["ms_per_tick"],
+            "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"{len(streams)} streams ({per_res} each of 320x240, 640x480, "
+                                   f"1280x720, 1920x1080), O=4 + intra-octaves, one frame of each per tick, "
+                                   f"moving area U[5%,60%], {F} frames per stream resident in HBM",
+                       "mpix_per_tick": mpix},
+            "mpix_per_s": res["masked"]["frames_per_s"] / len(streams) * mpix,
+            "masked": res["masked"], "full_frame": res["full"],
+            "masked_over_full": res["masked"]["frames_per_s"] / res["full"]["frames_per_s"]}
+    print(json.dumps(line))
+    return 0
+
+
+def run_config5(args):
+    """8 streams of 3840x2160, 5 octaves: moving and static segments."""
+    import torch
+    from paper_1503_06959_gb300 import fkd
+    cfg = synth.config5()
+    seg = args.segment
+    F = 2 * seg
+    n_streams = args.streams_5
+    frames_dev = []
+    for j in range(n_streams):
+        src = synth.VideoSource(cfg.W, cfg.H, seed=1000 + 500 + j,
+                                **dict(cfg.source, static_segments=(seg, 0)))
+        frames_dev.append(torch.from_numpy(src.frames(F)).cuda())
+    out = {}
+    for name, mode in (("masked", fkd.FKD_MASK_ID), ("full", fkd.FKD_MASK_FULL)):
+        st = torch.cuda.Stream()
+        g = fkd.Group(cfg.O, cfg.intra, cuda_stream=st.cuda_stream)
+        ids = [g.add_stream(cfg.W, cfg.H, N_r=cfg.N_r, N_c=cfg.N_c, T_I=cfg.T_I, t=cfg.t,
+                            mask_mode=mode, K_max=1 << 20)[0] for _ in range(n_streams)]
+        segs = {}
+        for part, rng in (("moving", range(0, seg)), ("static", range(seg, F))):
+            g.synchronize()
+            g.profile_read()
+            g.profile_enable(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            lat = []
+            first = rng[0] + (2 if part == "moving" else 0)
+            for n in rng:
+                if n == first:
+                    g.synchronize()
+                    g.profile_read()
+                    e0.record(st)
+                t0 = time.perf_counter()
+                g.tick(ids, [f[n] for f in frames_dev])
+                g.synchronize()
+                if n >= first:
+                    lat.append((time.perf_counter() - t0) * 1e3)
+            e1.record(st)
+            e1.synchronize()
+            prof = g.profile_read()
+            ticks = len(rng) - (first - rng[0])
+            sec = e0.elapsed_time(e1) / 1e3
+            det_ms = prof["ms"]["detect"] / max(1, prof["batches"])
+            det_bytes = prof["tile_pixels"] / max(1, prof["batches"]) * 1.125
+            segs[part] = {"frames_per_s": n_streams * ticks / sec,
+                          "tick_latency_ms_p50": float(np.percentile(lat, 50)),
+                          "tick_latency_ms_p99": float(np.percentile(lat, 99)),
+                          "stage_ms_per_tick": {k: v / max(1, prof["batches"]) for k, v in prof["ms"].items()},
+                          "detect_hbm_gbs": det_bytes / (det_ms / 1e3) / 1e9 if det_ms else None,
+                          "tile_pixels_per_tick": prof["tile_pixels"] / max(1, prof["batches"])}
+        out[name] = segs
+        g.close()
+    line = {"metric": "frames/s and tick latency (3840x2160 stress: moving vs static segments)",
+            "value": out["masked"]["moving"]["frames_per_s"], "unit": "frames/s", "n_gpus": 1,
+            "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"{n_streams} streams of 3840x2160, O=5 + intra-octaves, "
+                                   f"{seg} moving then {seg} static frames, N(0,2) noise"},
+            "masked": out["masked"], "full_frame": out["full"]}
+    print(json.dumps(line))
+    return 0
+
+
+def run_config4(args):
+    """Serving: streams of mixed resolution producing frames at 30 fps with
+    Poisson jitter, submitted as they arrive; continuous batching."""
+    import threading
+    from paper_1503_06959_gb300 import fkd
+    per_res = args.serve_streams_per_res
+    seconds = args.serve_seconds
+    res_list = [(320, 240), (640, 480), (1280, 720), (1920, 1080)]
+    pool = {}
+    for k, (W, H) in enumerate(res_list):
+        src = synth.VideoSource(W, H, seed=1000 + 400 + k, n_movers=4,
+                                mover_size=int(math.sqrt(0.3 * W * H / 4)), speed=(1, 4))
+        pool[(W, H)] = src.frames(args.pool)
+    out = {}
+    for name, mode in (("masked", fkd.FKD_MASK_ID), ("full", fkd.FKD_MASK_FULL)):
+        srv = fkd.Server(4, 1, budget_bytes=args.budget_gb << 30, max_tick_keypoints=1 << 23)
+        streams = []
+        rejected = 0
+        for k, (W, H) in enumerate(res_list):
+            for j in range(per_res):
+                try:
+                    sid = srv.open_stream(W, H, N_r=12, N_c=16, T_I=4, t=30, mask_mode=mode,
+                                          K_max=1 << 17)
+                    streams.append((sid, W, H, k * per_res + j))
+                except fkd.FkdError as e:
+                    if e.code != fkd.FKD_E_BUDGET:
+                        raise
+                    rejected += 1
+        rng = np.random.default_rng(4)
+        events = []
+        for sid, W, H, j in streams:
+            t = float(rng.uniform(0, 1 / 30))
+            n = 0
+            while t < seconds:
+                events.append((t, sid, (W, H), (j * 7 + n) % args.pool))
+                t += float(rng.exponential(1 / 30))
+                n += 1
+        events.sort()
+        halves = [events[0::2], events[1::2]]
+        t_start = time.monotonic_ns() + 200_000_000
+        refused = [0]
+
+        def feed(evs):
+            for t, sid, res, fi in evs:
+                due = t_start + int(t * 1e9)
+                wait = (due - time.monotonic_ns()) / 1e9
+                if wait > 0:
+                    time.sleep(wait)
+                try:
+                    srv.submit(sid, pool[res][fi], arrival_ns=due)
+                except fkd.FkdError as e:
+                    if e.code != fkd.FKD_E_CAPACITY:
+                        raise
+                    refused[0] += 1
+
+        truncated = [0]
+
+        def consume(stop):
+            while not stop.is_set():
+                for sid, *_ in streams:
+                    while True:
+                        try:
+                            if srv.poll(sid) is None:
+                                break
+                        except fkd.FkdError as e:
+                            if e.code != fkd.FKD_E_CAPACITY:
+                                raise
+                            truncated[0] += 1
+                time.sleep(0.002)
+
+        stop = threading.Event()
+        cons = threading.Thread(target=consume, args=(stop,))
+        cons.start()
+        feeders = [threading.Thread(target=feed, args=(h,)) for h in halves]
+        for f in feeders:
+            f.start()
+        for f in feeders:
+            f.join()
+        srv.drain(120000)
+        stop.set()
+        cons.join()
+        st = srv.stats()
+        out[name] = {"streams_admitted": len(streams), "streams_rejected": rejected,
+                     "offered_fps": len(events) / seconds, "fps": st["fps"],
+                     "frames_done": st["frames_done"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                     "max_ms": st["max_ms"], "mean_batch": st["mean_batch"], "ticks": st["ticks"],
+                     "frames_refused_queue_full": refused[0], "results_truncated": truncated[0],
+                     "device_bytes": st["bytes_in_use"]}
+        srv.close()
+    line = {"metric": "frames/s and p99 latency (serving, continuous batching)",
+            "value": out["masked"]["fps"], "unit": "frames/s", "n_gpus": 1, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": f"{4 * per_res} streams ({per_res} each of 320x240 .. 1920x1080), "
+                                   f"30 fps Poisson arrivals for {seconds} s, O=4 + intra-octaves, "
+                                   f"budget {args.budget_gb} GB"},
+            "masked": out["masked"], "full_frame": out["full"]}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -195,11 +418,26 @@ def main():
     ap.add_argument("--ref-frames", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--latency-frames", type=int, default=300)
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5],
+                    help="2: the 640x480 clip (default line); 3: stream group; 4: serving; 5: 4K stress")
+    ap.add_argument("--streams-per-res", type=int, default=16)
+    ap.add_argument("--serve-streams-per-res", type=int, default=64)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--pool", type=int, default=12)
+    ap.add_argument("--budget-gb", type=int, default=8)
+    ap.add_argument("--segment", type=int, default=20)
+    ap.add_argument("--streams-5", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == 3:
+        return run_config3(args)
+    if args.config == 4:
+        return run_config4(args)
+    if args.config == 5:
+        return run_config5(args)
 
     import torch
     from paper_1503_06959_gb300 import fkd

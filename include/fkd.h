@@ -316,6 +316,77 @@ int fkd_group_profile_enable(fkd_group* g, int on);
 int fkd_group_profile_read(fkd_group* g, fkd_profile* out, int reset);
 
 /*
+ * Serving loop: frames of many streams arriving at any time.
+ *
+ * A server owns a group (above) and a worker thread. fkd_server_submit
+ * copies a host frame into the stream's queue (a ring of 4 pinned frames) and
+ * returns; the worker continuously batches: each round it takes the oldest
+ * waiting frame of every stream that has one -- frames that arrived while
+ * the previous round was on the GPU join the next round -- uploads them,
+ * runs one group tick for all of them, and, while that tick runs, brings the
+ * previous round's keypoints back to the streams' result queues. Streams are
+ * admitted against a device-memory budget and release their memory when
+ * closed. Latency is measured per frame from its arrival time (submit) to
+ * its keypoints being on the host. Every stream's results are bit-identical
+ * to running it alone. All functions are thread-safe.
+ */
+typedef struct fkd_server fkd_server;
+
+typedef struct {
+  uint64_t frames_done;       /* frames whose keypoints reached the host      */
+  uint64_t ticks;             /* rounds launched                               */
+  uint64_t rejected_frames;   /* submits refused because a queue was full      */
+  uint64_t rejected_streams;  /* opens refused by the memory budget            */
+  double p50_ms, p99_ms;      /* per-frame latency, arrival to results on host */
+  double max_ms, mean_ms;
+  double fps;                 /* frames done per second, first arrival to last */
+  double mean_batch;          /* frames per round                              */
+  size_t bytes_in_use;        /* device bytes charged to the budget            */
+  size_t budget_bytes;
+} fkd_server_stats;
+
+/* Create a server for streams with O octaves and intra (as fkd_group_create),
+ * a device-memory budget in bytes (covering its own buffers and every
+ * admitted stream), and room for max_tick_keypoints records per round.
+ * Errors: FKD_E_ARG, FKD_E_BUDGET (the server's own buffers exceed the
+ * budget), FKD_E_CUDA. */
+int fkd_server_create(int O, int intra, size_t budget_bytes, size_t max_tick_keypoints,
+                      fkd_server** out);
+
+/* Stop the worker (frames on the GPU finish), free everything. NULL: no-op. */
+int fkd_server_destroy(fkd_server* s);
+
+/* Admit a stream (p->O and p->intra as the server's). Errors: FKD_E_BUDGET
+ * (its device memory would exceed the budget, or 1024 streams are open),
+ * FKD_E_ARG, FKD_E_CUDA. */
+int fkd_server_open_stream(fkd_server* s, const fkd_params* p, int W, int H, int* id);
+
+/* Close a stream: frames already on the GPU finish, waiting frames and
+ * unread results are dropped, its memory returns to the budget. */
+int fkd_server_close_stream(fkd_server* s, int id);
+
+/* Queue the next frame of stream `id` (host memory, copied before the call
+ * returns). arrival_ns: its arrival time on the steady clock
+ * (CLOCK_MONOTONIC), or <= 0 for "now". Errors: FKD_E_CAPACITY (4 frames of
+ * this stream already waiting; the frame is not queued), FKD_E_ARG,
+ * FKD_E_CUDA (an earlier round failed). */
+int fkd_server_submit(fkd_server* s, int id, const uint8_t* frame, size_t pitch, int64_t arrival_ns);
+
+/* Take the oldest finished frame of stream `id`: its index n and D_n
+ * (sorted by (layer, y, x)) into host memory. Errors: FKD_E_STATE (nothing
+ * finished yet), FKD_E_CAPACITY (more than cap records: the result stays
+ * queued; or the frame exceeded K_max or the round's capacity: the result
+ * is dropped), FKD_E_ARG. */
+int fkd_server_poll(fkd_server* s, int id, int64_t* frame_index, fkd_keypoint* out, size_t cap,
+                    size_t* n_out);
+
+/* Wait until no frame is waiting or on the GPU. Errors: FKD_E_TIMEOUT. */
+int fkd_server_drain(fkd_server* s, int timeout_ms);
+
+/* Statistics since creation or the last reset (reset != 0 clears them). */
+int fkd_server_get_stats(fkd_server* s, fkd_server_stats* out, int reset);
+
+/*
  * Allocation-free variant (the paper has no counterpart; it exists for
  * callers of this library that cannot let it allocate device memory: an
  * application that gives all GPU memory to its own allocator or budget at

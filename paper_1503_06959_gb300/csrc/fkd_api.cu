@@ -652,6 +652,8 @@ namespace {
 struct GroupStream {
   fkd_stream* s = nullptr;  // T_max = 1
   uint8_t* last[2] = {nullptr, nullptr};
+  fkd_keypoint* rec1 = nullptr;  // results of odd frames (even frames use the stream's own)
+  uint32_t* off1 = nullptr;
   size_t bytes = 0;
 };
 
@@ -711,7 +713,7 @@ static_assert(sizeof(TickHeader) <= kItemsOffset, "tick header fits before the i
 static_assert(alignof(TickItem) <= 64 && sizeof(TickItem) % alignof(TickItem) == 0, "aligned items");
 constexpr size_t kTickBytes = kItemsOffset + kMaxTickItems * sizeof(TickItem);
 
-StreamDev make_dev(const fkd_stream* s, uint8_t* const last[2]) {
+StreamDev make_dev(const fkd_stream* s, uint8_t* const last[2], fkd_keypoint* rec1, uint32_t* off1) {
   StreamDev d{};
   d.g = s->g;
   d.tb = Tables{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins};
@@ -723,8 +725,10 @@ StreamDev make_dev(const fkd_stream* s, uint8_t* const last[2]) {
     d.state_cnt[i] = s->state_cnt[i];
     d.last[i] = last[i];
   }
-  d.rec = s->rec;
-  d.rec_offsets = s->rec_offsets;
+  d.rec[0] = s->rec;
+  d.rec_offsets[0] = s->rec_offsets;
+  d.rec[1] = rec1;
+  d.rec_offsets[1] = off1;
   d.K_max = s->p.K_max;
   return d;
 }
@@ -859,6 +863,10 @@ int fkd_group_add_stream(fkd_group* G, const fkd_params* p, int W, int H, int* s
       fkd_destroy_stream(s);
       return rc;
     }
+  if ((rc = s->alloc(&gs.rec1, (size_t)s->p.K_max)) || (rc = s->alloc(&gs.off1, 2))) {
+    fkd_destroy_stream(s);
+    return rc;
+  }
   gs.bytes = s->bytes_held;
   const int id = (int)G->streams.size();
   // device descriptors (grow: the captured graphs hold the old pointer)
@@ -878,7 +886,7 @@ int fkd_group_add_stream(fkd_group* G, const fkd_params* p, int W, int H, int* s
     G->devs_cap = cap;
     G->drop_graphs();
   }
-  const StreamDev d = make_dev(s, gs.last);
+  const StreamDev d = make_dev(s, gs.last, gs.rec1, gs.off1);
   CK(cudaMemcpy(G->d_devs + id, &d, sizeof d, cudaMemcpyHostToDevice));
   // the tick's active-tile list holds at most the tiles of all live streams
   long long need = 0;
@@ -993,10 +1001,35 @@ int fkd_group_synchronize(fkd_group* G) {
   return FKD_OK;
 }
 
+namespace {
+// Result buffers of the stream's last processed frame.
+int group_last_result(fkd_group* G, int id, fkd_stream** s, const fkd_keypoint** rec, const uint32_t** off) {
+  *s = group_member(G, id);
+  if (!*s) return fail(FKD_E_ARG, "unknown stream id %d", id);
+  if ((*s)->frame == 0) return fail(FKD_E_STATE, "stream %d has no frame yet", id);
+  const bool odd = (((*s)->frame - 1) & 1) != 0;
+  *rec = odd ? G->streams[id].rec1 : (*s)->rec;
+  *off = odd ? G->streams[id].off1 : (*s)->rec_offsets;
+  return FKD_OK;
+}
+}  // namespace
+
 int fkd_group_get_keypoints(fkd_group* G, int id, fkd_keypoint* out, size_t cap, size_t* n_out) {
-  fkd_stream* s = group_member(G, id);
-  if (!s) return fail(FKD_E_ARG, "unknown stream id %d", id);
-  return fkd_get_keypoints(s, out, cap, n_out);
+  if (!n_out || (!out && cap > 0)) return fail(FKD_E_ARG, "NULL argument");
+  fkd_stream* s;
+  const fkd_keypoint* rec;
+  const uint32_t* off;
+  int rc = group_last_result(G, id, &s, &rec, &off);
+  if (rc) return rc;
+  uint32_t o[2];
+  CK(cudaMemcpyAsync(o, off, 8, cudaMemcpyDeviceToHost, G->st));
+  CK(cudaStreamSynchronize(G->st));
+  const size_t n = o[1] - o[0];
+  *n_out = n;
+  if (n > (size_t)s->p.K_max) return fail(FKD_E_CAPACITY, "frame has %zu keypoints > K_max %d", n, s->p.K_max);
+  if (n > cap) return fail(FKD_E_CAPACITY, "frame has %zu keypoints > cap %zu", n, cap);
+  if (n) CK(cudaMemcpy(out, rec, n * sizeof(fkd_keypoint), cudaMemcpyDeviceToHost));
+  return FKD_OK;
 }
 
 int fkd_group_get_mask(fkd_group* G, int id, uint8_t* out) {
@@ -1006,9 +1039,15 @@ int fkd_group_get_mask(fkd_group* G, int id, uint8_t* out) {
 }
 
 int fkd_group_device_keypoints(fkd_group* G, int id, const fkd_keypoint** records, const uint32_t** count_dev) {
-  fkd_stream* s = group_member(G, id);
-  if (!s) return fail(FKD_E_ARG, "unknown stream id %d", id);
-  return fkd_device_keypoints(s, records, count_dev);
+  if (!records || !count_dev) return fail(FKD_E_ARG, "NULL argument");
+  fkd_stream* s;
+  const fkd_keypoint* rec;
+  const uint32_t* off;
+  int rc = group_last_result(G, id, &s, &rec, &off);
+  if (rc) return rc;
+  *records = rec;
+  *count_dev = off + 1;
+  return FKD_OK;
 }
 
 int fkd_group_profile_enable(fkd_group* G, int on) {
@@ -1050,3 +1089,31 @@ int fkd_group_profile_read(fkd_group* G, fkd_profile* out, int reset) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------- internal (server)
+
+namespace fkd {
+
+int group_result_ref(fkd_group* G, int id, long long frame_index, ResultRef* ref) {
+  fkd_stream* s = group_member(G, id);
+  if (!s) return fail(FKD_E_ARG, "unknown stream id %d", id);
+  const bool odd = (frame_index & 1) != 0;
+  ref->rec = odd ? G->streams[id].rec1 : s->rec;
+  ref->off = odd ? G->streams[id].off1 : s->rec_offsets;
+  ref->cap = s->p.K_max;
+  return FKD_OK;
+}
+
+long long group_stream_frames(fkd_group* G, int id) {
+  fkd_stream* s = group_member(G, id);
+  return s ? s->frame : -1;
+}
+
+int group_stream_kmax(fkd_group* G, int id) {
+  fkd_stream* s = group_member(G, id);
+  return s ? s->p.K_max : 0;
+}
+
+cudaStream_t group_cuda_stream(fkd_group* G) { return G->st; }
+
+}  // namespace fkd

@@ -168,8 +168,8 @@ struct StreamDev {
   uint8_t* state_score[2];
   uint32_t* state_cnt[2];
   uint8_t* last[2];          // copies of the stream's last two frames (c_0, pitch layer[0].pitch)
-  fkd_keypoint* rec;         // D_n of the last tick (K_max records)
-  uint32_t* rec_offsets;     // [2]
+  fkd_keypoint* rec[2];      // D_n of frame n in rec[n & 1] (K_max records each)
+  uint32_t* rec_offsets[2];  // [2] each: 0 and |D_n|
   long long K_max;
 };
 
@@ -205,6 +205,21 @@ void launch_group_count(const StreamDev* devs, const TickHeader* hdr, const Tick
 void launch_group_emit(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
                        int grid, cudaStream_t st);
 
+// Where one stream's result of one frame lives (device): K_max records and
+// the offsets pair (0, |D_n|).
+struct ResultRef {
+  const fkd_keypoint* rec;
+  const uint32_t* off;
+  long long cap;  // records rec can hold (K_max)
+};
+
+// counts[i] = |D_n| of refs[i] (may exceed its cap); offsets[i] = records
+// gathered before item i, each item contributing min(count, cap), offsets[n]
+// = their total; records copied to out (up to out_cap) in that order.
+// `offsets` holds n + 1 words followed by the n counts.
+void launch_gather(const ResultRef* refs, int n, uint32_t* offsets, fkd_keypoint* out, long long out_cap,
+                   cudaStream_t st);
+
 // Index of the item whose [base, next base) range holds j (bases ascending).
 template <typename F>
 __device__ __forceinline__ int find_item(int n, int j, F base_of) {
@@ -234,5 +249,11 @@ int detect_grid_size();
 
 // Record a message for fkd_last_error (printf format) and return `code`.
 int set_error(int code, const char* fmt, ...);
+
+// Group internals used by the serving loop.
+int group_result_ref(fkd_group* G, int id, long long frame_index, ResultRef* ref);
+long long group_stream_frames(fkd_group* G, int id);
+int group_stream_kmax(fkd_group* G, int id);
+cudaStream_t group_cuda_stream(fkd_group* G);
 
 }  // namespace fkd

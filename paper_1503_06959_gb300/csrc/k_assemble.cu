@@ -242,7 +242,8 @@ __global__ void __launch_bounds__(kAsmThreads) k_group_emit(const StreamDev* dev
     const int i = find_item(n, j, [&](int q) { return items[q].chunk_base; });
     const TickItem it = items[i];
     const StreamDev& d = devs[it.sid];
-    Output o{d.rec, d.K_max, d.rec_offsets, 0};
+    const int par = (int)(it.frame_index & 1);
+    Output o{d.rec[par], d.K_max, d.rec_offsets[par], 0};
     emit_chunk(d.g, d.tb, d.s, state_of(d, it.state_cur), o, 0, 1, j - it.chunk_base);
   }
 }

@@ -31,7 +31,9 @@ EXPORTS = [
     "fkd_group_create", "fkd_group_destroy", "fkd_group_add_stream", "fkd_group_remove_stream",
     "fkd_group_tick", "fkd_group_use_graph", "fkd_group_synchronize", "fkd_group_get_keypoints",
     "fkd_group_get_mask", "fkd_group_device_keypoints", "fkd_group_profile_enable",
-    "fkd_group_profile_read",
+    "fkd_group_profile_read", "fkd_server_create", "fkd_server_destroy", "fkd_server_open_stream",
+    "fkd_server_close_stream", "fkd_server_submit", "fkd_server_poll", "fkd_server_drain",
+    "fkd_server_get_stats",
 ]
 STAGES = ["pyramid", "mask", "worklist", "detect", "count", "emit"]
 
@@ -47,6 +49,15 @@ class fkd_profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_uint64 * 6),
                 ("batches", ctypes.c_uint64), ("frames", ctypes.c_uint64),
                 ("tiles", ctypes.c_uint64), ("tile_pixels", ctypes.c_uint64)]
+
+
+class fkd_server_stats(ctypes.Structure):
+    _fields_ = [("frames_done", ctypes.c_uint64), ("ticks", ctypes.c_uint64),
+                ("rejected_frames", ctypes.c_uint64), ("rejected_streams", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("fps", ctypes.c_double), ("mean_batch", ctypes.c_double),
+                ("bytes_in_use", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t)]
 
 
 class FkdError(RuntimeError):
@@ -98,6 +109,14 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.fkd_group_device_keypoints.argtypes = [vp, c_int, P(vp), P(vp)]
     lib.fkd_group_profile_enable.argtypes = [vp, c_int]
     lib.fkd_group_profile_read.argtypes = [vp, P(fkd_profile), c_int]
+    lib.fkd_server_create.argtypes = [c_int, c_int, c_size, c_size, P(vp)]
+    lib.fkd_server_destroy.argtypes = [vp]
+    lib.fkd_server_open_stream.argtypes = [vp, P(fkd_params), c_int, c_int, P(c_int)]
+    lib.fkd_server_close_stream.argtypes = [vp, c_int]
+    lib.fkd_server_submit.argtypes = [vp, c_int, vp, c_size, ctypes.c_int64]
+    lib.fkd_server_poll.argtypes = [vp, c_int, P(ctypes.c_int64), vp, c_size, P(c_size)]
+    lib.fkd_server_drain.argtypes = [vp, c_int]
+    lib.fkd_server_get_stats.argtypes = [vp, P(fkd_server_stats), c_int]
     for name in EXPORTS:
         if name != "fkd_last_error":
             getattr(lib, name).restype = c_int
@@ -324,6 +343,68 @@ class Group:
     def close(self):
         if getattr(self, "_h", None):
             _lib.fkd_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop over many streams (fkd_server_*): submit host frames as
+    they arrive, poll keypoints as they finish."""
+
+    def __init__(self, O: int, intra: int, budget_bytes: int, max_tick_keypoints: int = 1 << 22):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.fkd_server_create(O, intra, budget_bytes, max_tick_keypoints, ctypes.byref(h)))
+        self._h = h
+        self.O, self.intra = O, intra
+        self.streams = {}
+
+    def open_stream(self, W: int, H: int, *, N_r: int = 8, N_c: int = 8, T_I: int = 4,
+                    T_H: int = 1, t: int = 20, mask_mode: int = FKD_MASK_ID, mask_layer: int = 0,
+                    K_max: int = 16384) -> int:
+        p = params_default()
+        p.N_r, p.N_c, p.T_I, p.T_H, p.O, p.intra, p.t = N_r, N_c, T_I, T_H, self.O, self.intra, t
+        p.mask_mode, p.mask_layer, p.K_max = mask_mode, mask_layer, K_max
+        sid = ctypes.c_int()
+        _check(_lib.fkd_server_open_stream(self._h, ctypes.byref(p), W, H, ctypes.byref(sid)))
+        self.streams[sid.value] = (W, H, K_max)
+        return sid.value
+
+    def close_stream(self, sid: int):
+        _check(_lib.fkd_server_close_stream(self._h, sid))
+        self.streams.pop(sid, None)
+
+    def submit(self, sid: int, frame: np.ndarray, arrival_ns: int = 0):
+        frame = np.ascontiguousarray(frame, dtype=np.uint8)
+        _check(_lib.fkd_server_submit(self._h, sid, _ptr(frame), frame.strides[0], arrival_ns))
+
+    def poll(self, sid: int):
+        """(frame index, keypoints) of the oldest finished frame, or None."""
+        cap = self.streams.get(sid, (0, 0, 1))[2]
+        out = np.zeros(cap, KEYPOINT_DTYPE)
+        idx, n = ctypes.c_int64(), ctypes.c_size_t()
+        rc = _lib.fkd_server_poll(self._h, sid, ctypes.byref(idx), _ptr(out), cap, ctypes.byref(n))
+        if rc == FKD_E_STATE:
+            return None
+        _check(rc)
+        return idx.value, out[:n.value].copy()
+
+    def drain(self, timeout_ms: int = 60000):
+        _check(_lib.fkd_server_drain(self._h, timeout_ms))
+
+    def stats(self, reset: bool = False) -> dict:
+        st = fkd_server_stats()
+        _check(_lib.fkd_server_get_stats(self._h, ctypes.byref(st), int(reset)))
+        return {f: getattr(st, f) for f, _ in fkd_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.fkd_server_destroy(self._h)
             self._h = None
 
     def __del__(self):
