@@ -63,6 +63,7 @@ struct fkd_stream {
   DetTile* tiles = nullptr;
   AsmChunk* chunks = nullptr;
   uint32_t* wbins = nullptr;
+  uint32_t* wmask = nullptr;
 
   Scratch s{};
   uint32_t* state_bits[2] = {nullptr, nullptr};
@@ -181,7 +182,7 @@ int build_geometry(fkd_stream* s, int W, int H) {
   std::vector<int> xstart;
   std::vector<DetTile> tiles;
   std::vector<AsmChunk> chunks;
-  std::vector<uint32_t> wbins;
+  std::vector<uint32_t> wbins, wmask;
   long long pyr = 0, score = 0, bits = 0;
   for (int l = 0; l < g.L; ++l) {
     LayerGeom& lg = g.layer[l];
@@ -214,7 +215,12 @@ int build_geometry(fkd_stream* s, int W, int H) {
     lg.wb_off = (int)wbins.size();
     for (int wx = 0; wx < lg.wpr; ++wx) {
       const int x1 = std::min(32 * wx + 32, lg.w) - 1;
-      wbins.push_back((uint32_t)colblk[lg.col_off + 32 * wx] | ((uint32_t)colblk[lg.col_off + x1] << 16));
+      const uint16_t c0 = colblk[lg.col_off + 32 * wx];
+      wbins.push_back((uint32_t)c0 | ((uint32_t)colblk[lg.col_off + x1] << 16));
+      uint32_t m = 0;
+      for (int x = 32 * wx; x <= x1; ++x)
+        if (colblk[lg.col_off + x] == c0) m |= 1u << (x - 32 * wx);
+      wmask.push_back(m);
     }
     // assembly chunks: bands of whole rows, about kAsmChunkWords words each
     if (lg.wpr > 0) {
@@ -256,8 +262,9 @@ int build_geometry(fkd_stream* s, int W, int H) {
   if ((rc = s->alloc(&s->colblk, colblk.size())) || (rc = s->alloc(&s->rowblk, rowblk.size())) ||
       (rc = s->alloc(&s->xstart, xstart.size())) || (rc = s->alloc(&s->npix, npix.size())) ||
       (rc = s->alloc(&s->tiles, tiles.size())) || (rc = s->alloc(&s->chunks, chunks.size())) ||
-      (rc = s->alloc(&s->wbins, wbins.size())))
+      (rc = s->alloc(&s->wbins, wbins.size())) || (rc = s->alloc(&s->wmask, wmask.size())))
     return rc;
+  CK(cudaMemcpy(s->wmask, wmask.data(), wmask.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->chunks, chunks.data(), chunks.size() * sizeof(AsmChunk), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->wbins, wbins.data(), wbins.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->colblk, colblk.data(), colblk.size() * 2, cudaMemcpyHostToDevice));
@@ -283,10 +290,12 @@ int allocate_state(fkd_stream* s) {
       (rc = s->alloc(&sc.det_score, (size_t)(T * g.score_bytes))) ||
       (rc = s->alloc(&sc.chunk_counts, (size_t)(T * std::max(g.n_chunks, 1)))) ||
       (rc = s->alloc(&sc.merged, (size_t)(T * std::max(g.bit_words, 1LL)))) ||
+      (rc = s->alloc(&sc.bases, (size_t)(T + 1))) || (rc = s->alloc(&sc.done, 1)) ||
       (rc = s->alloc(&sc.frame_totals, (size_t)T)) || (rc = s->alloc(&sc.out_base, 2)) ||
       (rc = s->alloc(&sc.overflow, 1)) || (rc = s->alloc(&sc.tile_stats, 2)))
     return rc;
   CK(cudaMemset(sc.tile_stats, 0, 16));
+  CK(cudaMemset(sc.done, 0, 4));
   for (int i = 0; i < 2; ++i) {
     if ((rc = s->alloc(&s->state_bits[i], (size_t)std::max(g.bit_words, 1LL))) ||
         (rc = s->alloc(&s->state_score[i], (size_t)g.score_bytes)) ||
@@ -296,6 +305,7 @@ int allocate_state(fkd_stream* s) {
     CK(cudaMemset(s->state_cnt[i], 0, (size_t)g.NB * 4));
   }
   CK(cudaMemset(sc.bsum, 0, (size_t)(T * g.NB) * 8));
+  sc.bsum_stride = (int)T;
   CK(cudaMemset(sc.overflow, 0, 4));
   CK(cudaMemset(sc.out_base, 0, 16));
   if ((rc = s->alloc(&s->rec, (size_t)s->p.K_max)) || (rc = s->alloc(&s->rec_offsets, 2)) ||
@@ -319,7 +329,7 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   b.prev_pitch = s->prev_pitch;
   b.c0_vec = 0;
   Params pr{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode};
-  Tables tb{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins};
+  Tables tb{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask};
   State stt{};
   stt.bits_in = s->state_bits[s->state_cur];
   stt.score_in = s->state_score[s->state_cur];
@@ -346,7 +356,7 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   mark(3);
   launch_detect(s->g, tb, b, s->s, pr, s->detect_grid, s->st);
   mark(4);
-  launch_count(s->g, tb, b, s->s, stt, s->st);
+  launch_count(s->g, tb, b, s->s, stt, s->st);  // its last CTA also fills s->s.bases
   mark(5);
   launch_emit(s->g, tb, b, s->s, stt, o, s->st);
   mark(6);
@@ -716,8 +726,9 @@ constexpr size_t kTickBytes = kItemsOffset + kMaxTickItems * sizeof(TickItem);
 StreamDev make_dev(const fkd_stream* s, uint8_t* const last[2], fkd_keypoint* rec1, uint32_t* off1) {
   StreamDev d{};
   d.g = s->g;
-  d.tb = Tables{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins};
+  d.tb = Tables{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask};
   d.s = s->s;
+  d.s.bases = nullptr;  // group ticks (one frame) compute their offsets in place
   d.p = Params{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode};
   for (int i = 0; i < 2; ++i) {
     d.state_bits[i] = s->state_bits[i];

@@ -97,6 +97,7 @@ struct Tables {
   const DetTile* tiles;    // per detection tile of a frame
   const AsmChunk* chunks;  // per assembly chunk of a frame
   const uint32_t* wbins;   // per layer, per bitmap word column: first | last bin column << 16
+  const uint32_t* wmask;   // per layer, per bitmap word column: bits of the word in its first bin
 };
 
 // Arguments of one batch of T consecutive frames of one stream.
@@ -118,7 +119,8 @@ struct Params {
 // Device scratch of a stream, sized for T_max frames.
 struct Scratch {
   uint8_t* pyr;                    // [T_max][pyr_bytes]
-  unsigned long long* bsum;        // [T_max][NB]; kept zero between batches
+  unsigned long long* bsum;        // [NB][bsum_stride]: bin-major, frame k at bin*bsum_stride + k; kept zero
+  int bsum_stride;                 // T_max (1 in groups)
   uint8_t* mask;                   // [T_max][NB]
   int* src;                        // [T_max][NB]: batch frame whose detections the bin shows, -1 = kept set
   uint32_t* work;                  // [T_max * n_tiles] active (frame, tile) items
@@ -127,6 +129,8 @@ struct Scratch {
   uint8_t* det_score;              // [T_max][score_bytes]
   uint32_t* chunk_counts;          // [T_max][n_chunks]
   uint32_t* merged;                // [T_max][bit_words]: D_n bitmap of every frame of the batch
+  uint32_t* bases;                 // [T_max + 1]: records of the batch before each frame, then the total
+  uint32_t* done;                  // [1]: chunks counted (last-CTA scan)
   uint32_t* frame_totals;          // [T_max]
   unsigned long long* out_base;    // [2]: running output offset (ping-pong)
   int* overflow;                   // [1]

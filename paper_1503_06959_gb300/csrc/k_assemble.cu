@@ -33,64 +33,99 @@ __device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* red) {
   return t;
 }
 
-// Merge and count one chunk of frame k; ends with the block reduction's
-// barriers, so a CTA can run it again at once.
+// Bits of word j of the chunk (bin row r's sources in srcrow) taken from the
+// frames the bins point to: words of one or two bins take a precomputed split
+// mask, wider words (coarse layers, narrow bins) walk their bins.
+__device__ __forceinline__ uint32_t merge_word(const Geometry& g, const Tables& tb, const Scratch& s,
+                                               const State& st, const LayerGeom& lg, const int* xst,
+                                               const int* srcrow, long long word0, int j, int wx) {
+  const uint32_t wb = tb.wbins[lg.wb_off + wx];
+  const int c_lo = wb & 0xffffu, c_hi = wb >> 16;
+  const uint32_t* det0 = s.det_bits + word0;
+  if (c_hi - c_lo <= 1) {
+    const uint32_t m = tb.wmask[lg.wb_off + wx];
+    const int sf0 = srcrow[c_lo], sf1 = srcrow[c_hi];
+    const uint32_t b0 = sf0 < 0 ? st.bits_in[word0 + j] : det0[(long long)sf0 * g.bit_words + j];
+    const uint32_t b1 = sf1 == sf0 ? b0 : (sf1 < 0 ? st.bits_in[word0 + j] : det0[(long long)sf1 * g.bit_words + j]);
+    return (b0 & m) | (b1 & ~m);
+  }
+  const int xlo = wx * 32, xhi = min(xlo + 32, lg.w);
+  uint32_t word = 0;
+  for (int c = c_lo; c <= c_hi; ++c) {
+    const int a = max(xst[c], xlo) - xlo, e = min(xst[c + 1], xhi) - xlo;
+    if (e <= a) continue;
+    const uint32_t m = (e - a == 32) ? 0xffffffffu : (((1u << (e - a)) - 1u) << a);
+    const int sf = srcrow[c];
+    word |= (sf < 0 ? st.bits_in[word0 + j] : det0[(long long)sf * g.bit_words + j]) & m;
+  }
+  return word;
+}
+
+// Merge and count one chunk of frame k: each warp adds its popcounts to the
+// chunk's and the frame's counters (zeroed by the active-tile kernel). With
+// s.bases, the warp that finishes last of `total_warps` also turns the T frame
+// totals into record offsets. No block-wide barrier.
 __device__ __forceinline__ void count_chunk(const Geometry& g, const Tables& tb, const Scratch& s,
-                                            const State& st, int k, int chunk) {
-  __shared__ int xs[kXsSmem];
-  __shared__ uint32_t red[kAsmThreads / 32];
+                                            const State& st, int k, int chunk, int T, int total_warps) {
   const AsmChunk ch = tb.chunks[chunk];
   const LayerGeom& lg = g.layer[ch.layer];
-  const int wpr = lg.wpr, w = lg.w;
+  const int wpr = lg.wpr;
   const int nwords = (ch.y1 - ch.y0) * wpr;
   const long long word0 = lg.bit_off + (long long)ch.y0 * wpr;
-  const int* xsg = tb.xstart + lg.xs_off;
-  const bool xs_local = g.N_c < kXsSmem;
-  if (xs_local)
-    for (int q = threadIdx.x; q <= g.N_c; q += kAsmThreads) xs[q] = xsg[q];
-  __syncthreads();
-  const int* xst = xs_local ? xs : xsg;
-
+  const int* xst = tb.xstart + lg.xs_off;
   const int* src_k = s.src + (long long)k * g.NB;
-  const uint32_t* det0 = s.det_bits + word0;
   uint32_t* out = s.merged + (long long)k * g.bit_words + word0;
-  int j = threadIdx.x * kAsmWordsPerThread;
-  int y = ch.y0 + j / wpr, wx = j % wpr;
-  const int* srcrow = src_k + (j < nwords ? tb.rowblk[lg.row_off + y] : 0) * g.N_c;
+  // words tid, tid + 256, ...: coalesced; the count does not care about order
+  const float inv_wpr = 1.0f / (float)wpr;
   uint32_t cnt = 0;
-  for (int jj = 0; jj < kAsmWordsPerThread && j < nwords; ++jj, ++j) {
-    const uint32_t wb = tb.wbins[lg.wb_off + wx];
-    const int c_lo = wb & 0xffffu, c_hi = wb >> 16;
-    uint32_t word;
-    if (c_lo == c_hi) {
-      const int sf = srcrow[c_lo];
-      word = sf < 0 ? st.bits_in[word0 + j] : det0[(long long)sf * g.bit_words + j];
-    } else {
-      const int xlo = wx * 32, xhi = min(xlo + 32, w);
-      word = 0;
-      for (int c = c_lo; c <= c_hi; ++c) {
-        const int a = max(xst[c], xlo) - xlo, e = min(xst[c + 1], xhi) - xlo;
-        if (e <= a) continue;
-        const uint32_t m = (e - a == 32) ? 0xffffffffu : (((1u << (e - a)) - 1u) << a);
-        const int sf = srcrow[c];
-        const uint32_t bits = sf < 0 ? st.bits_in[word0 + j] : det0[(long long)sf * g.bit_words + j];
-        word |= bits & m;
+#pragma unroll
+  for (int jj = 0; jj < kAsmWordsPerThread; ++jj) {
+    const int j = threadIdx.x + jj * kAsmThreads;
+    if (j < nwords) {
+      int yy = __float2int_rz((float)j * inv_wpr);  // j / wpr, fixed up below
+      if (yy * wpr > j) --yy;
+      if ((yy + 1) * wpr <= j) ++yy;
+      const int wx = j - yy * wpr;
+      const int* srcrow = src_k + tb.rowblk[lg.row_off + ch.y0 + yy] * g.N_c;
+      const uint32_t word = merge_word(g, tb, s, st, lg, xst, srcrow, word0, j, wx);
+      out[j] = word;
+      cnt += __popc(word);
+    }
+  }
+  const int lane = threadIdx.x & 31;
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  bool last_warp = false;
+  if (lane == 0) {
+    if (cnt) {
+      atomicAdd(&s.chunk_counts[(long long)k * g.n_chunks + chunk], cnt);
+      atomicAdd(&s.frame_totals[k], cnt);
+    }
+    if (s.bases) {
+      __threadfence();
+      last_warp = atomicAdd(s.done, 1u) == (unsigned)(total_warps - 1);
+    }
+  }
+  if (__shfl_sync(0xffffffffu, (int)last_warp, 0)) {
+    // exclusive scan of the frame totals, 32 at a time
+    __threadfence();
+    uint32_t carry = 0;
+    for (int e0 = 0; e0 < T; e0 += 32) {
+      const int e = e0 + lane;
+      const uint32_t c = e < T ? __ldcg(&s.frame_totals[e]) : 0u;
+      uint32_t incl = c;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
       }
+      if (e < T) s.bases[e] = carry + incl - c;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
     }
-    out[j] = word;
-    cnt += __popc(word);
-    if (++wx == wpr) {
-      wx = 0;
-      ++y;
-      if (y < ch.y1) srcrow = src_k + tb.rowblk[lg.row_off + y] * g.N_c;
+    if (lane == 0) {
+      s.bases[T] = carry;
+      *s.done = 0u;
     }
   }
-  const uint32_t tot = block_sum(cnt, red);
-  if (threadIdx.x == 0) {
-    s.chunk_counts[(long long)k * g.n_chunks + chunk] = tot;
-    if (tot) atomicAdd(&s.frame_totals[k], tot);
-  }
-  __syncthreads();  // xs and red are reused by the next chunk of this CTA
 }
 
 __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb, const Scratch& s,
@@ -105,6 +140,7 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
                                            int chunk) {
   __shared__ uint32_t red[kAsmThreads / 32];
   __shared__ uint32_t wsum[kAsmThreads / 32];
+  __shared__ __align__(16) uint32_t stage_words[kAsmChunkWords];
   const bool last = k == T - 1;
   const AsmChunk ch = tb.chunks[chunk];
   const LayerGeom& lg = g.layer[ch.layer];
@@ -113,12 +149,26 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
   const long long word0 = lg.bit_off + (long long)ch.y0 * wpr;
 
   // offsets: base of this call + earlier frames + earlier chunks of this frame
-  uint32_t part = 0;
-  for (int q = threadIdx.x; q < k; q += kAsmThreads) part += s.frame_totals[q];
-  const uint32_t frame_base = block_sum(part, red);
-  part = 0;
-  for (int q = threadIdx.x; q < chunk; q += kAsmThreads) part += s.chunk_counts[(long long)k * g.n_chunks + q];
-  const uint32_t chunk_base = block_sum(part, red);
+  uint32_t frame_base, chunk_base;
+  if (s.bases) {
+    // warp 0 sums the earlier chunks of this frame (few) and shares it
+    if (threadIdx.x < 32) {
+      uint32_t part = 0;
+      for (int q = threadIdx.x; q < chunk; q += 32) part += s.chunk_counts[(long long)k * g.n_chunks + q];
+      part = __reduce_add_sync(0xffffffffu, part);
+      if (threadIdx.x == 0) red[0] = part;
+    }
+    __syncthreads();
+    frame_base = s.bases[k];
+    chunk_base = red[0];
+  } else {
+    uint32_t part = 0;
+    for (int q = threadIdx.x; q < k; q += kAsmThreads) part += s.frame_totals[q];
+    frame_base = block_sum(part, red);
+    part = 0;
+    for (int q = threadIdx.x; q < chunk; q += kAsmThreads) part += s.chunk_counts[(long long)k * g.n_chunks + q];
+    chunk_base = block_sum(part, red);
+  }
   const unsigned long long call_base = s.out_base[out.base_slot];
   if (chunk == 0 && threadIdx.x == 0) {
     out.offsets[k] = (uint32_t)(call_base + frame_base);
@@ -129,18 +179,30 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
     }
   }
 
-  // this thread's words (contiguous, so the scan order is the canonical order)
-  const int j0 = threadIdx.x * kAsmWordsPerThread;
+  // the chunk's words, loaded coalesced into shared memory; each thread then
+  // takes 8 contiguous ones, so the scan order is the canonical order
   const uint32_t* merged = s.merged + (long long)k * g.bit_words + word0;
+#pragma unroll
+  for (int jj = 0; jj < kAsmWordsPerThread; ++jj) {
+    const int j = threadIdx.x + jj * kAsmThreads;
+    const uint32_t v = j < nwords ? merged[j] : 0u;
+    stage_words[j] = v;
+    if (last && j < nwords) st.bits_out[word0 + j] = v;
+  }
+  __syncthreads();
+  const int j0 = threadIdx.x * kAsmWordsPerThread;
   uint32_t words[kAsmWordsPerThread];
   uint32_t cnt = 0;
 #pragma unroll
-  for (int jj = 0; jj < kAsmWordsPerThread; ++jj) {
-    const int j = j0 + jj;
-    words[jj] = j < nwords ? merged[j] : 0u;
-    cnt += __popc(words[jj]);
-    if (last && j < nwords) st.bits_out[word0 + j] = words[jj];
+  for (int jj = 0; jj < kAsmWordsPerThread; jj += 4) {
+    const uint4 v = *reinterpret_cast<const uint4*>(&stage_words[j0 + jj]);
+    words[jj] = v.x;
+    words[jj + 1] = v.y;
+    words[jj + 2] = v.z;
+    words[jj + 3] = v.w;
   }
+#pragma unroll
+  for (int jj = 0; jj < kAsmWordsPerThread; ++jj) cnt += __popc(words[jj]);
   // exclusive scan of cnt over the CTA
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t incl = cnt;
@@ -203,8 +265,8 @@ __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb
   }
 }
 
-__global__ void __launch_bounds__(kAsmThreads) k_count(Geometry g, Tables tb, Scratch s, State st) {
-  count_chunk(g, tb, s, st, blockIdx.y, blockIdx.x);
+__global__ void __launch_bounds__(kAsmThreads) k_count(Geometry g, Tables tb, Scratch s, State st, int T) {
+  count_chunk(g, tb, s, st, blockIdx.y, blockIdx.x, T, gridDim.x * gridDim.y * (kAsmThreads / 32));
 }
 
 __global__ void __launch_bounds__(kAsmThreads) k_emit(Geometry g, Tables tb, Batch b, Scratch s,
@@ -231,7 +293,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_group_count(const StreamDev* de
     const int i = find_item(n, j, [&](int q) { return items[q].chunk_base; });
     const TickItem it = items[i];
     const StreamDev& d = devs[it.sid];
-    count_chunk(d.g, d.tb, d.s, state_of(d, it.state_cur), 0, j - it.chunk_base);
+    count_chunk(d.g, d.tb, d.s, state_of(d, it.state_cur), 0, j - it.chunk_base, 1, 0);
   }
 }
 
@@ -262,7 +324,7 @@ void launch_group_emit(const StreamDev* devs, const TickHeader* hdr, const TickI
 
 void launch_count(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                   const State& state, cudaStream_t st) {
-  k_count<<<dim3(g.n_chunks, b.T), kAsmThreads, 0, st>>>(g, tb, s, state);
+  k_count<<<dim3(g.n_chunks, b.T), kAsmThreads, 0, st>>>(g, tb, s, state, b.T);
 }
 
 void launch_emit(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,

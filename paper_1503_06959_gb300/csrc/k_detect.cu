@@ -38,8 +38,9 @@ constexpr int IN_BYTES = IN_W * IN_H;
 constexpr int SC_BYTES = SC_P * SC_H;
 constexpr int DET_WORDS = TH * (TW / 32);
 constexpr int LIST = 512;  // candidate list window per warp (entries)
-// per warp: input (double-buffered), score map, keypoint and pass bitmaps, candidate list
-constexpr int WARP_SMEM = 2 * IN_BYTES + SC_BYTES + 2 * DET_WORDS * 4 + LIST * 2;
+constexpr int PASS = 256;  // passing-pixel list per warp (entries); beyond it the pass bitmap is scanned
+// per warp: input (double-buffered), score map, keypoint and pass bitmaps, candidate and pass lists
+constexpr int WARP_SMEM = 2 * IN_BYTES + SC_BYTES + 2 * DET_WORDS * 4 + LIST * 2 + PASS * 2;
 static_assert(TW == 32 * 4, "one 4-pixel word per lane per row");
 static_assert(SC_H * 4 <= 72 && SC_H > 16, "a lane's candidate bits: 16 rows in 64 bits + 2 rows");
 static_assert(IN_BYTES % 16 == 0 && SC_BYTES % 16 == 0, "16-byte aligned slices");
@@ -122,6 +123,10 @@ struct Item {
   uint8_t* dscore;           // the frame's score map of this layer (row 0)
   int dpitch;
   int t;                     // segment-test threshold
+  const uint8_t* mask;       // the frame's bin mask (null: every bin active)
+  const uint16_t* colblk;    // bin column of each layer column
+  const uint16_t* rowblk;    // bin row of each layer row
+  int N_c;
 };
 
 // Work items of one stream's batch of T frames.
@@ -154,6 +159,10 @@ struct SingleSrc {
     it.dscore = s.det_score + (long long)k * g.score_bytes + lg.score_off;
     it.dpitch = lg.pitch;
     it.t = p.t;
+    it.mask = p.mask_mode == FKD_MASK_FULL ? nullptr : s.mask + (long long)k * g.NB;
+    it.colblk = tb.colblk + lg.col_off;
+    it.rowblk = tb.rowblk + lg.row_off;
+    it.N_c = g.N_c;
     return it;
   }
 };
@@ -188,15 +197,66 @@ struct GroupSrc {
     it.dscore = d.s.det_score + lg.score_off;
     it.dpitch = lg.pitch;
     it.t = d.p.t;
+    it.mask = d.p.mask_mode == FKD_MASK_FULL ? nullptr : d.s.mask;
+    it.colblk = d.tb.colblk + lg.col_off;
+    it.rowblk = d.tb.rowblk + lg.row_off;
+    it.N_c = d.g.N_c;
     return it;
   }
 };
+
+// Which score rows of the tile each lane must score: a pixel needs a score
+// only if its 3x3 neighbourhood holds a pixel of an active bin (detections
+// there use it for suppression; elsewhere assembly ignores the result).
+// Returns one bit per score row (bit rr: row y0-1+rr) for this lane's word
+// x0+4*lane .. +3, dilated by one pixel each way; all ones when every bin is
+// active or the tile spans more than 32 bin rows.
+__device__ __forceinline__ uint32_t active_rows(const Item& it, int lane) {
+  if (!it.mask) return 0xffffffffu;
+  const int x = it.x0 + 4 * lane;
+  const int xa = max(0, min(it.w - 1, x - 1)), xb = max(0, min(it.w - 1, x + 4));
+  const int ca = it.colblk[xa], cb = it.colblk[xb];
+  // bin row of each dilated score row: rows y0-2 .. y0+TH+1, one per lane
+  const int yr = max(0, min(it.h - 1, it.y0 - 2 + lane));
+  const int rb = lane < TH + 4 ? (int)it.rowblk[yr] : 0;
+  const int r_lo = __shfl_sync(0xffffffffu, rb, 0), r_hi = __shfl_sync(0xffffffffu, rb, TH + 3);
+  if (r_hi - r_lo >= 32) return 0xffffffffu;
+  uint32_t binrows = 0;  // bit (r - r_lo): bin row r active within [ca, cb]
+  for (int r = r_lo; r <= r_hi; ++r)
+    for (int c = ca; c <= cb; ++c)
+      if (it.mask[r * it.N_c + c]) {
+        binrows |= 1u << (r - r_lo);
+        break;
+      }
+  uint32_t rows = 0;
+#pragma unroll
+  for (int rr = 0; rr < SC_H; ++rr) {
+    // score row rr needs rows rr-1 .. rr+1, i.e. dilated rows rr .. rr+2
+    const int a = __shfl_sync(0xffffffffu, rb, rr) - r_lo, b = __shfl_sync(0xffffffffu, rb, rr + 2) - r_lo;
+    const uint32_t span = (b - a == 31) ? 0xffffffffu : ((2u << (b - a)) - 1u);
+    if ((binrows >> a) & span) rows |= 1u << rr;
+  }
+  return rows;
+}
 
 // A. stage input rows y0-4 .. y0+TH+3, columns x0-16 .. x0+TW+15, zeros
 // outside the layer. x0 is a multiple of 128, so each 16-byte chunk is either
 // wholly left of the layer or starts inside it.
 __device__ __forceinline__ void stage(uint8_t* in, const Item& it, int lane) {
   const bool vec = ((reinterpret_cast<uintptr_t>(it.src) | (uintptr_t)it.pitch) & 15) == 0;
+  if (vec && it.x0 >= 16 && it.x0 + TW + 16 <= it.w && it.y0 >= 4 && it.y0 + TH + 4 <= it.h) {
+    // the whole staged rectangle lies inside the layer: no checks, no zero fill
+    const uint8_t* base = it.src + (long long)(it.y0 - 4) * it.pitch + (it.x0 - 16);
+#pragma unroll
+    for (int q0 = 0; q0 < IN_H * (IN_W / 16); q0 += 32) {
+      const int q = q0 + lane;
+      if ((IN_H * (IN_W / 16)) % 32 == 0 || q < IN_H * (IN_W / 16)) {
+        const int r = q / (IN_W / 16), c = (q % (IN_W / 16)) * 16;
+        cp_async16(in + r * IN_W + c, base + (long long)r * it.pitch + c, 16);
+      }
+    }
+    return;
+  }
   for (int q = lane; q < IN_H * (IN_W / 16); q += 32) {
     const int r = q / (IN_W / 16), c = (q % (IN_W / 16)) * 16;
     const int gy = it.y0 - 4 + r, gx = it.x0 - 16 + c;
@@ -234,6 +294,7 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Src src) {
   uint32_t* detw = reinterpret_cast<uint32_t*>(sc + SC_BYTES);
   uint32_t* passw = detw + DET_WORDS;
   uint16_t* list = reinterpret_cast<uint16_t*>(passw + DET_WORDS);
+  uint16_t* plist = list + LIST;
 
   const uint32_t count_items = src.count();
   const uint32_t stride = gridDim.x * WARPS;
@@ -274,7 +335,9 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Src src) {
     const bool interior = x0 - 1 >= 3 && x0 + TW < w - 3 && y0 - 1 >= 3 && y0 + TH < h - 3;
     unsigned long long m64 = 0ull;
     uint32_t m_hi = 0u, m_edge = 0u;
-    if (!none) {
+    const uint32_t act = active_rows(it, lane);
+    const uint32_t act_any = __reduce_or_sync(0xffffffffu, act);
+    if (!none && act_any) {
       const int c = 16 + 4 * lane;
       const int x = x0 + 4 * lane;
       uint32_t colmask = 0x80808080u;  // pixels of this word inside the scorable band
@@ -285,7 +348,9 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Src src) {
       }
 #pragma unroll
       for (int rr = 0; rr < SC_H; ++rr) {
+        if (!((act_any >> rr) & 1u)) continue;  // no lane needs this row
         uint32_t keep = prefilter(in, (rr + 3) * IN_W + c, t1_low7, t1_high) & colmask;
+        if (!((act >> rr) & 1u)) keep = 0;
         if (!interior) {
           const int y = y0 - 1 + rr;
           if (y < 3 || y >= h - 3) keep = 0;
@@ -294,15 +359,17 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Src src) {
         if (rr < 16) m64 |= (unsigned long long)nb << (4 * rr);
         else m_hi |= nb << (4 * (rr - 16));
       }
-      // the score region's edge columns x0-1 and x0+TW: lane rr < SC_H owns row rr
+      // the score region's edge columns x0-1 and x0+TW: lane rr < SC_H owns row
+      // rr; they are needed when the tile's first / last word is
+      const uint32_t act_l = __shfl_sync(0xffffffffu, act, 0), act_r = __shfl_sync(0xffffffffu, act, 31);
       if (lane < SC_H) {
         const int y = y0 - 1 + lane;
         if (y >= 3 && y < h - 3) {
           const int r = (lane + 3) * IN_W;
-          if (x0 - 1 >= 3 && x0 - 1 < w - 3 &&
+          if (((act_l >> lane) & 1u) && x0 - 1 >= 3 && x0 - 1 < w - 3 &&
               (prefilter(in, r + 12, t1_low7, t1_high) & 0x80000000u))
             m_edge |= 1u;
-          if (x0 + TW >= 3 && x0 + TW < w - 3 &&
+          if (((act_r >> lane) & 1u) && x0 + TW >= 3 && x0 + TW < w - 3 &&
               (prefilter(in, r + 16 + TW, t1_low7, t1_high) & 0x80u))
             m_edge |= 2u;
         }
@@ -321,6 +388,7 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Src src) {
       if (lane >= d) incl += v;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int npass = 0;  // passing tile pixels (warp-uniform)
     for (int w0 = 0; w0 < total; w0 += LIST) {
       // this window's entries: input offsets of the candidates, in lane order
       int idx = incl - n;
@@ -350,6 +418,8 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Src src) {
       const int cnt = min(LIST, total - w0);
       for (int base = 0; base < cnt; base += 64) {
         const int i1 = base + 2 * lane;
+        bool pass[2] = {false, false};
+        int po[2] = {0, 0};
         if (i1 < cnt) {
           const bool two = i1 + 1 < cnt;
           const int o1 = list[i1], o2 = two ? list[i1 + 1] : o1;
@@ -365,16 +435,39 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Src src) {
               if (ok && r >= 4 && r < TH + 4 && c >= 16 && c < TW + 16) {
                 const int ly = r - 4, lx = c - 16;
                 atomicOr(&passw[ly * (TW / 32) + (lx >> 5)], 1u << (lx & 31));
+                pass[j] = true;
+                po[j] = o;
               }
             }
           }
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const unsigned bal = __ballot_sync(0xffffffffu, pass[j]);
+          const int at = npass + __popc(bal & ((1u << lane) - 1u));
+          if (pass[j] && at < PASS) plist[at] = (uint16_t)po[j];
+          npass += __popc(bal);
         }
       }
       __syncwarp();
     }
 
-    // D. strict 3x3 maxima among the tile's passing pixels
+    // D. strict 3x3 maxima among the tile's passing pixels: from the pass
+    //    list, or from the pass bitmap when the list overflowed
     uint8_t* dscore = it.dscore;
+    if (npass <= PASS) {
+      for (int i = lane; i < npass; i += 32) {
+        const int o = plist[i];
+        const int ly = o / IN_W - 4, lx = o % IN_W - 16;
+        const uint8_t* q = sc + (ly + 1) * SC_P + 4 + lx;
+        const int v = q[0];
+        if (v > q[-SC_P - 1] && v > q[-SC_P] && v > q[-SC_P + 1] && v > q[-1] && v > q[1] &&
+            v > q[SC_P - 1] && v > q[SC_P] && v > q[SC_P + 1]) {
+          atomicOr(&detw[ly * (TW / 32) + (lx >> 5)], 1u << (lx & 31));
+          dscore[(long long)(y0 + ly) * it.dpitch + x0 + lx] = (uint8_t)v;
+        }
+      }
+    } else
 #pragma unroll
     for (int j = 0; j < DET_WORDS / 32; ++j) {
       const int idx = lane + 32 * j;

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Ba
       if (n == 0 || p.mask_mode == FKD_MASK_FULL) {
         m = 1;
       } else if (p.mask_mode == FKD_MASK_ID) {
-        unsigned long long* sum = s.bsum + (long long)k * g.NB + bin;
+        unsigned long long* sum = s.bsum + (long long)bin * s.bsum_stride + k;
         m = *sum > (unsigned long long)p.T_I * tb.npix[bin];
         *sum = 0;  // ready for the next batch
       } else {
@@ -69,6 +69,8 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Ba
 __global__ void k_worklist(Geometry g, Tables tb, Batch b, Scratch s) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = (long long)b.T * g.n_tiles;
+  for (long long q = i; q < (long long)b.T * g.n_chunks; q += (long long)gridDim.x * blockDim.x)
+    s.chunk_counts[q] = 0;  // summed by the assembly count pass
   bool act = false;
   uint32_t area = 0;
   if (i < total) {
@@ -125,6 +127,7 @@ __global__ void k_group_mask(const StreamDev* devs, const TickHeader* hdr, const
       d.s.frame_totals[0] = 0;
       d.s.out_base[0] = 0;
     }
+    for (int q = bin; q < d.g.n_chunks; q += d.g.NB) d.s.chunk_counts[q] = 0;
   }
 }
 

@@ -232,7 +232,7 @@ template <int O, int INTRA>
 __device__ __forceinline__ void pyramid_tile(const Geometry& g, const Tables& tb, const uint8_t* frame,
                                              int pitch, const uint8_t* prevf, int prev_pitch,
                                              bool diff, uint8_t* pyr, unsigned long long* gsum,
-                                             uint8_t* keep, int keep_pitch, int tx, int ty) {
+                                             int gstride, uint8_t* keep, int keep_pitch, int tx, int ty) {
   __shared__ __align__(16) uint8_t cur[kPyrSmem];
   __shared__ __align__(16) uint8_t prv[kPyrSmem];
   __shared__ uint32_t bins[kLocalBins];
@@ -290,7 +290,7 @@ __device__ __forceinline__ void pyramid_tile(const Geometry& g, const Tables& tb
     auto flush = [&](int rb, int cb, uint32_t v) {
       if (!v) return;
       if (local) atomicAdd(&bins[(rb - rb_lo) * ncols + (cb - cb_lo)], v);
-      else atomicAdd(&gsum[rb * g.N_c + cb], (unsigned long long)v);
+      else atomicAdd(&gsum[(long long)(rb * g.N_c + cb) * gstride], (unsigned long long)v);
     };
     if ((mn & 3) == 0) {
       const int wcols = (mnx + 3) / 4;
@@ -346,7 +346,9 @@ __device__ __forceinline__ void pyramid_tile(const Geometry& g, const Tables& tb
       __syncthreads();
       for (int q = threadIdx.x; q < ncols * nrows; q += NT) {
         const uint32_t v = bins[q];
-        if (v) atomicAdd(&gsum[(rb_lo + q / ncols) * g.N_c + cb_lo + q % ncols], (unsigned long long)v);
+        if (v)
+          atomicAdd(&gsum[(long long)((rb_lo + q / ncols) * g.N_c + cb_lo + q % ncols) * gstride],
+                    (unsigned long long)v);
       }
     }
   }
@@ -362,7 +364,7 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Geometry g, Tables tb, 
   const uint8_t* pf = k == 0 ? b.prev : frame - b.frame_stride;
   const int pp = k == 0 ? b.prev_pitch : b.pitch;
   pyramid_tile<O, INTRA>(g, tb, frame, b.pitch, pf, pp, diff, s.pyr + (long long)k * g.pyr_bytes,
-                         s.bsum + (long long)k * g.NB, nullptr, 0, blockIdx.x, blockIdx.y);
+                         s.bsum + k, s.bsum_stride, nullptr, 0, blockIdx.x, blockIdx.y);
 }
 
 // Group tick: persistent CTAs over the c_0 tiles of every participating frame.
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(kPyrThreads) k_group_pyramid(const StreamDev* 
     const bool diff = d.p.mask_mode == FKD_MASK_ID && it.frame_index > 0;
     const int kp = d.g.layer[0].pitch;
     pyramid_tile<O, INTRA>(d.g, d.tb, it.frame, it.pitch, d.last[(it.frame_index + 1) & 1], kp, diff,
-                           d.s.pyr, d.s.bsum, d.last[it.frame_index & 1], kp, tx, ty);
+                           d.s.pyr, d.s.bsum, 1, d.last[it.frame_index & 1], kp, tx, ty);
   }
 }
 
