@@ -19,7 +19,6 @@
 namespace fkd {
 namespace {
 
-constexpr int kXsSmem = 1024;  // bin-column starts kept in shared memory when N_c < this
 
 __device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

@@ -42,7 +42,7 @@ constexpr int PASS = 256;  // passing-pixel list per warp (entries); beyond it t
 // per warp: input (double-buffered), score map, keypoint and pass bitmaps, candidate and pass lists
 constexpr int WARP_SMEM = 2 * IN_BYTES + SC_BYTES + 2 * DET_WORDS * 4 + LIST * 2 + PASS * 2;
 static_assert(TW == 32 * 4, "one 4-pixel word per lane per row");
-static_assert(SC_H * 4 <= 72 && SC_H > 16, "a lane's candidate bits: 16 rows in 64 bits + 2 rows");
+static_assert(LIST >= 256 && LIST <= 65535, "a flush leaves room for one more row (128)");
 static_assert(IN_BYTES % 16 == 0 && SC_BYTES % 16 == 0, "16-byte aligned slices");
 
 // Per byte: bit 7 set where e >= T1 (T1 in 1..255, the same in every byte).
@@ -105,12 +105,6 @@ __device__ __forceinline__ uint32_t score_pair(const uint8_t* in, int o1, int o2
   const uint32_t sb = __vsub2(a, __vadd2(ip, 0x00010001u));
   const uint32_t sd = __vsub2(__vsub2(ip, 0x00010001u), bmin);
   return __vimax_s16x2_relu(sb, sd);
-}
-
-// Bit 7 of each byte of `keep` gathered into a nibble (byte i -> bit i): the
-// four bits land on distinct positions of the product, so nothing carries.
-__device__ __forceinline__ uint32_t nibble(uint32_t keep) {
-  return (((keep >> 7) & 0x01010101u) * 0x00204081u >> 21) & 0xfu;
 }
 
 // One (frame, tile) work item, with everything the kernel body needs.
@@ -278,10 +272,6 @@ __device__ __forceinline__ void stage(uint8_t* in, const Item& it, int lane) {
   }
 }
 
-// Input offset of candidate bit b of a lane's mask (4 bits per score row).
-__device__ __forceinline__ int cand_off(int b, int lane) {
-  return ((b >> 2) + 3) * IN_W + 16 + 4 * lane + (b & 3);
-}
 // Score-map offset of the pixel at input offset o.
 __device__ __forceinline__ int sc_of(int o) { return (o / IN_W - 3) * SC_P + (o % IN_W) - 12; }
 
@@ -329,99 +319,25 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Src src) {
     const bool t1_high = t1 >= 128u;
     const bool none = t1 > 255u;
 
-    // B. prefilter the score rows y0-1 .. y0+TH (input rows 3 .. TH+4); lane
-    //    owns the word x0+4*lane .. +3 of every row and keeps its candidate
-    //    bits: 4 per row, rows 0..15 in m64, rows 16..17 in m_hi.
+    // B+C. prefilter the score rows y0-1 .. y0+TH (input rows 3 .. TH+4), lane
+    //      -> word x0+4*lane .. +3; candidates go to the warp's list with one
+    //      ballot per byte position, and the list is scored -- two candidates
+    //      per lane, 64 per round -- whenever it fills up and at the end. A
+    //      pixel of the tile scoring >= t goes to the pass list (and bitmap).
     const bool interior = x0 - 1 >= 3 && x0 + TW < w - 3 && y0 - 1 >= 3 && y0 + TH < h - 3;
-    unsigned long long m64 = 0ull;
-    uint32_t m_hi = 0u, m_edge = 0u;
     const uint32_t act = active_rows(it, lane);
     const uint32_t act_any = __reduce_or_sync(0xffffffffu, act);
-    if (!none && act_any) {
-      const int c = 16 + 4 * lane;
-      const int x = x0 + 4 * lane;
-      uint32_t colmask = 0x80808080u;  // pixels of this word inside the scorable band
-      if (!interior) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (x + i < 3 || x + i >= w - 3) colmask &= ~(0x80u << (8 * i));
-      }
-#pragma unroll
-      for (int rr = 0; rr < SC_H; ++rr) {
-        if (!((act_any >> rr) & 1u)) continue;  // no lane needs this row
-        uint32_t keep = prefilter(in, (rr + 3) * IN_W + c, t1_low7, t1_high) & colmask;
-        if (!((act >> rr) & 1u)) keep = 0;
-        if (!interior) {
-          const int y = y0 - 1 + rr;
-          if (y < 3 || y >= h - 3) keep = 0;
-        }
-        const uint32_t nb = nibble(keep);
-        if (rr < 16) m64 |= (unsigned long long)nb << (4 * rr);
-        else m_hi |= nb << (4 * (rr - 16));
-      }
-      // the score region's edge columns x0-1 and x0+TW: lane rr < SC_H owns row
-      // rr; they are needed when the tile's first / last word is
-      const uint32_t act_l = __shfl_sync(0xffffffffu, act, 0), act_r = __shfl_sync(0xffffffffu, act, 31);
-      if (lane < SC_H) {
-        const int y = y0 - 1 + lane;
-        if (y >= 3 && y < h - 3) {
-          const int r = (lane + 3) * IN_W;
-          if (((act_l >> lane) & 1u) && x0 - 1 >= 3 && x0 - 1 < w - 3 &&
-              (prefilter(in, r + 12, t1_low7, t1_high) & 0x80000000u))
-            m_edge |= 1u;
-          if (((act_r >> lane) & 1u) && x0 + TW >= 3 && x0 + TW < w - 3 &&
-              (prefilter(in, r + 16 + TW, t1_low7, t1_high) & 0x80u))
-            m_edge |= 2u;
-        }
-      }
-    }
-
-    // C. exact scores. The lanes' candidates are packed into one list (warp
-    //    scan of the per-lane counts), 64 per round, two per lane; a window
-    //    of LIST entries at a time. A pixel of the tile scoring >= t is marked
-    //    in the pass bitmap.
-    const int n = __popcll(m64) + __popc(m_hi) + __popc(m_edge);
-    int incl = n;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += v;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const unsigned lt = (1u << lane) - 1u;
+    int count = 0;  // candidates in the list (warp-uniform)
     int npass = 0;  // passing tile pixels (warp-uniform)
-    for (int w0 = 0; w0 < total; w0 += LIST) {
-      // this window's entries: input offsets of the candidates, in lane order
-      int idx = incl - n;
-      if (idx < w0 + LIST && idx + n > w0) {
-        unsigned long long mm = m64;
-        uint32_t mh = m_hi, me = m_edge;
-        while ((mm | mh | me) && idx < w0 + LIST) {
-          int o;
-          if (mm) {
-            const int bb = __ffsll((long long)mm) - 1;
-            mm &= mm - 1;
-            o = cand_off(bb, lane);
-          } else if (mh) {
-            const int bb = __ffs(mh) - 1;
-            mh &= mh - 1;
-            o = cand_off(64 + bb, lane);
-          } else {
-            const int e = __ffs(me) - 1;
-            me &= me - 1;
-            o = (lane + 3) * IN_W + (e ? 16 + TW : 15);
-          }
-          if (idx >= w0) list[idx - w0] = (uint16_t)o;
-          ++idx;
-        }
-      }
+    auto flush = [&]() {
       __syncwarp();
-      const int cnt = min(LIST, total - w0);
-      for (int base = 0; base < cnt; base += 64) {
+      for (int base = 0; base < count; base += 64) {
         const int i1 = base + 2 * lane;
         bool pass[2] = {false, false};
         int po[2] = {0, 0};
-        if (i1 < cnt) {
-          const bool two = i1 + 1 < cnt;
+        if (i1 < count) {
+          const bool two = i1 + 1 < count;
           const int o1 = list[i1], o2 = two ? list[i1 + 1] : o1;
           const uint32_t sp = score_pair(in, o1, o2);
 #pragma unroll
@@ -444,13 +360,63 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Src src) {
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const unsigned bal = __ballot_sync(0xffffffffu, pass[j]);
-          const int at = npass + __popc(bal & ((1u << lane) - 1u));
+          const int at = npass + __popc(bal & lt);
           if (pass[j] && at < PASS) plist[at] = (uint16_t)po[j];
           npass += __popc(bal);
         }
       }
       __syncwarp();
+      count = 0;
+    };
+    // keep: bit 7 of byte i set -> candidate at input offset o0 + i
+    auto append = [&](uint32_t keep, int o0) {
+      if (!__any_sync(0xffffffffu, keep)) return;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const unsigned bal = __ballot_sync(0xffffffffu, (keep >> (8 * i + 7)) & 1u);
+        if ((bal >> lane) & 1u) list[count + __popc(bal & lt)] = (uint16_t)(o0 + i);
+        count += __popc(bal);
+      }
+      if (count > LIST - 128) flush();
+    };
+    if (!none && act_any) {
+      const int c = 16 + 4 * lane;
+      const int x = x0 + 4 * lane;
+      uint32_t colmask = 0x80808080u;  // pixels of this word inside the scorable band
+      if (!interior) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (x + i < 3 || x + i >= w - 3) colmask &= ~(0x80u << (8 * i));
+      }
+#pragma unroll 1
+      for (int rr = 0; rr < SC_H; ++rr) {
+        if (!((act_any >> rr) & 1u)) continue;  // no lane needs this row
+        uint32_t keep = prefilter(in, (rr + 3) * IN_W + c, t1_low7, t1_high) & colmask;
+        if (!((act >> rr) & 1u)) keep = 0;
+        if (!interior) {
+          const int y = y0 - 1 + rr;
+          if (y < 3 || y >= h - 3) keep = 0;
+        }
+        append(keep, (rr + 3) * IN_W + c);
+      }
+      // the score region's edge columns x0-1 and x0+TW: lane rr < SC_H owns
+      // row rr; they are needed when the tile's first / last word is
+      const uint32_t act_l = __shfl_sync(0xffffffffu, act, 0), act_r = __shfl_sync(0xffffffffu, act, 31);
+      uint32_t kl = 0, kr = 0;
+      if (lane < SC_H) {
+        const int y = y0 - 1 + lane;
+        if (y >= 3 && y < h - 3) {
+          const int r = (lane + 3) * IN_W;
+          if (((act_l >> lane) & 1u) && x0 - 1 >= 3 && x0 - 1 < w - 3)
+            kl = prefilter(in, r + 12, t1_low7, t1_high) & 0x80000000u;
+          if (((act_r >> lane) & 1u) && x0 + TW >= 3 && x0 + TW < w - 3)
+            kr = prefilter(in, r + 16 + TW, t1_low7, t1_high) & 0x80u;
+        }
+      }
+      append(kl, (lane + 3) * IN_W + 12);
+      append(kr, (lane + 3) * IN_W + 16 + TW);
     }
+    if (count) flush();
 
     // D. strict 3x3 maxima among the tile's passing pixels: from the pass
     //    list, or from the pass bitmap when the list overflowed
