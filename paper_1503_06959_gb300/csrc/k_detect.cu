@@ -39,8 +39,10 @@ constexpr int SC_BYTES = SC_P * SC_H;
 constexpr int DET_WORDS = TH * (TW / 32);
 constexpr int LIST = 512;  // candidate list window per warp (entries)
 constexpr int PASS = 256;  // passing-pixel list per warp (entries); beyond it the pass bitmap is scanned
-// per warp: input (double-buffered), score map, keypoint and pass bitmaps, candidate and pass lists
-constexpr int WARP_SMEM = 2 * IN_BYTES + SC_BYTES + 2 * DET_WORDS * 4 + LIST * 2 + PASS * 2;
+constexpr int NBUF = 1;        // input buffers per warp (2: the next tile loads during this one; no gain measured)
+constexpr int MIN_BLOCKS = 2;  // CTAs resident per SM the register budget is sized for
+// per warp: input buffer(s), score map, keypoint and pass bitmaps, candidate and pass lists
+constexpr int WARP_SMEM = NBUF * IN_BYTES + SC_BYTES + 2 * DET_WORDS * 4 + LIST * 2 + PASS * 2;
 static_assert(TW == 32 * 4, "one 4-pixel word per lane per row");
 static_assert(LIST >= 256 && LIST <= 65535, "a flush leaves room for one more row (128)");
 static_assert(IN_BYTES % 16 == 0 && SC_BYTES % 16 == 0, "16-byte aligned slices");
@@ -276,11 +278,11 @@ __device__ __forceinline__ void stage(uint8_t* in, const Item& it, int lane) {
 __device__ __forceinline__ int sc_of(int o) { return (o / IN_W - 3) * SC_P + (o % IN_W) - 12; }
 
 template <class Src>
-__global__ void __launch_bounds__(kDetThreads, 2) k_detect(Src src) {
+__global__ void __launch_bounds__(kDetThreads, MIN_BLOCKS) k_detect(Src src) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* inbuf = smem + warp * WARP_SMEM;
-  uint8_t* sc = inbuf + 2 * IN_BYTES;
+  uint8_t* sc = inbuf + NBUF * IN_BYTES;
   uint32_t* detw = reinterpret_cast<uint32_t*>(sc + SC_BYTES);
   uint32_t* passw = detw + DET_WORDS;
   uint16_t* list = reinterpret_cast<uint16_t*>(passw + DET_WORDS);
@@ -292,25 +294,29 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Src src) {
   uint32_t item = blockIdx.x * WARPS + warp;
   int buf = 0;
   Item nxt{};
-  if (item < count_items) {
+  if (NBUF == 2 && item < count_items) {
     nxt = src.decode(item);
     stage(inbuf, nxt, lane);
   }
   cp_async_commit();
   for (; item < count_items; item += stride) {
-    const Item it = nxt;
+    const Item it = NBUF == 2 ? nxt : src.decode(item);
     const uint8_t* in = inbuf + buf * IN_BYTES;
-    // prefetch the next tile into the other buffer, then wait for this one
-    if (item + stride < count_items) {
-      nxt = src.decode(item + stride);
-      stage(inbuf + (buf ^ 1) * IN_BYTES, nxt, lane);
+    if (NBUF == 2) {
+      // prefetch the next tile into the other buffer, then wait for this one
+      if (item + stride < count_items) {
+        nxt = src.decode(item + stride);
+        stage(inbuf + (buf ^ 1) * IN_BYTES, nxt, lane);
+      }
+    } else {
+      stage(inbuf, it, lane);
     }
     cp_async_commit();
     for (int q = lane; q < SC_BYTES / 16; q += 32)
       reinterpret_cast<uint4*>(sc)[q] = make_uint4(0u, 0u, 0u, 0u);
     detw[lane] = detw[lane + 32] = 0u;
     passw[lane] = passw[lane + 32] = 0u;
-    cp_async_wait<1>();
+    cp_async_wait<NBUF - 1>();
     __syncwarp();
     const int w = it.w, h = it.h, x0 = it.x0, y0 = it.y0;
     const uint32_t t = (uint32_t)it.t;
@@ -463,7 +469,7 @@ __global__ void __launch_bounds__(kDetThreads, 2) k_detect(Src src) {
       if (y0 + ly < h && wx < it.wpr) bits[(long long)(y0 + ly) * it.wpr + wx] = detw[idx];
     }
     __syncwarp();
-    buf ^= 1;
+    buf ^= NBUF - 1;
   }
   cp_async_wait<0>();
 }
