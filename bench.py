@@ -186,14 +186,17 @@ def run_reference(args):
     return 0
 
 
-def _group_run(streams, frames_dev, mode, warm, ticks_timed, fkd, torch):
-    """Tick every stream once per tick through one group; returns
-    (seconds for the timed ticks, profile, keypoints per tick)."""
+def _group_run(streams, frames_dev, mode, warm, ticks_timed, fkd, torch, tune_ticks=3):
+    """Tick every stream once per tick through one group, after tuning the
+    detection launch shape on the first `tune_ticks` ticks; returns (seconds
+    for the timed ticks, profile, keypoints per tick, chosen shape)."""
     st = torch.cuda.Stream()
     g = fkd.Group(streams[0].O, streams[0].intra, cuda_stream=st.cuda_stream)
     ids = [g.add_stream(c.W, c.H, N_r=c.N_r, N_c=c.N_c, T_I=c.T_I, t=c.t, mask_mode=mode,
                         K_max=1 << 17)[0] for c in streams]
     n_frames = frames_dev[0].shape[0]
+    shape, tune_ms = g.autotune(ids, [[f[n] for f in frames_dev] for n in range(tune_ticks)], reps=2)
+    shape["tuned_ms_for_ticks"] = [tune_ticks, tune_ms]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for n in range(warm):
         g.tick(ids, [f[n] for f in frames_dev])
@@ -208,7 +211,7 @@ def _group_run(streams, frames_dev, mode, warm, ticks_timed, fkd, torch):
     prof = g.profile_read()
     kps = sum(len(g.get_keypoints(i)) for i in ids)
     g.close()
-    return e0.elapsed_time(e1) / 1e3, prof, kps
+    return e0.elapsed_time(e1) / 1e3, prof, kps, shape
 
 
 def run_config3(args):
@@ -225,9 +228,10 @@ def run_config3(args):
     warm = 3
     res = {}
     for name, mode in (("masked", fkd.FKD_MASK_ID), ("full", fkd.FKD_MASK_FULL)):
-        sec, prof, kps = _group_run(streams, frames_dev, mode, warm, F - warm, fkd, torch)
+        sec, prof, kps, shape = _group_run(streams, frames_dev, mode, warm, F - warm, fkd, torch)
         ticks = F - warm
         res[name] = {"frames_per_s": len(streams) * ticks / sec, "ms_per_tick": sec / ticks * 1e3,
+                     "launch_shape": shape,
                      "stage_ms_per_tick": {k: v / max(1, prof["batches"]) for k, v in prof["ms"].items()},
                      "keypoints_last_tick": kps, "tile_pixels_per_tick": prof["tile_pixels"] / max(1, prof["batches"])}
     mpix = sum(c.W * c.H for c in streams) / 1e6
@@ -501,6 +505,9 @@ def main():
 
     masked = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_ID, **common)
     full = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_FULL, **common)
+    # detection launch shape: autotuned per stream on the step's own frames
+    shape_masked, tune_ms_masked = masked.autotune(frames, reps=2)
+    shape_full, tune_ms_full = full.autotune(frames, reps=2)
 
     # warm up and check parity of the first frames against the oracle once
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
@@ -527,6 +534,7 @@ def main():
     # frame-by-frame latency (device frames): push_frame + get_keypoints per frame
     lat = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_ID, N_r=cfg.N_r, N_c=cfg.N_c,
                      T_I=cfg.T_I, O=cfg.O, intra=cfg.intra, t=cfg.t, cuda_stream=handle)
+    lat.set_launch_config(shape_masked)
     nlat = min(args.latency_frames, T)
     lat_ms = []
     for n in range(nlat):
@@ -546,6 +554,7 @@ def main():
     hf, ho = host_frames.numpy(), host_out.numpy()
     hoff, hm = host_off.numpy().view(np.uint32), host_masks.numpy()
     e2e_stream = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_ID, **common)
+    e2e_stream.set_launch_config(shape_masked)
     for _ in range(2):
         e2e_stream.reset()
         e2e_stream.push_frames(hf, out=ho, offsets=hoff, masks=hm)
@@ -624,7 +633,9 @@ def main():
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": workload_desc(cfg, T), "frames_per_step": T,
                    "l2": "flushed between steps (256 MB write outside the timed events)",
-                   "parallelism": f"one stream per GPU x {world}"},
+                   "parallelism": f"one stream per GPU x {world}",
+                   "launch_shape": {"masked": shape_masked, "full": shape_full,
+                                    "tuned_step_ms": {"masked": tune_ms_masked, "full": tune_ms_full}}},
         "mpix_per_s": value * cfg.W * cfg.H / 1e6,
         "full_frame": {"value": full_fps, "unit": "frames/s", "keypoints_per_step": kp_full,
                        "stage_ms_per_step": {k: v / max(1, prof_full["batches"])

@@ -248,6 +248,42 @@ int fkd_profile_enable(fkd_stream* s, int on);
 int fkd_profile_read(fkd_stream* s, fkd_profile* out, int reset);
 
 /*
+ * Launch shape of the detection kernel and its autotuner. The paper (Sec. 2,
+ * Sec. 3.1) fixes what is computed, not how the work is cut: the segment test
+ * runs on tiles of tile_w x tile_h output pixels of one layer (tile_w = 128,
+ * one 4-pixel word per lane), one tile per warp at a time, warps_per_cta
+ * tiles in flight per CTA, ctas_per_sm persistent CTAs per SM. Smaller tiles
+ * follow the active bins more closely (less work outside them); taller ones
+ * re-read less halo. Every shape gives bit-identical keypoints.
+ */
+#define FKD_TILE_W 128
+typedef struct {
+  int32_t tile_h;        /* 8, 16 or 24 output rows per tile            */
+  int32_t warps_per_cta; /* 4 or 8 tiles in flight per CTA              */
+  int32_t ctas_per_sm;   /* 1 .. resident limit of that shape           */
+} fkd_launch_config;
+
+/* The shape the stream uses now (tile_h 16, 8 warps, as many CTAs per SM as
+ * fit, unless set or tuned). Errors: FKD_E_ARG. */
+int fkd_get_launch_config(const fkd_stream* s, fkd_launch_config* out);
+
+/* Use shape *c for the stream's next batches (waits for pending work).
+ * Errors: FKD_E_ARG (tile_h, warps_per_cta outside the lists above, or
+ * ctas_per_sm outside 1 .. the number that fits on an SM). */
+int fkd_set_launch_config(fkd_stream* s, const fkd_launch_config* c);
+
+/* Autotuner: times a batch of the T frames at `frames` (device memory, row
+ * pitch `pitch`, frame k at frames + k * frame_stride; T <= T_max) under every
+ * candidate shape (tile_h x warps_per_cta x ctas_per_sm), `reps` timed runs
+ * each after one untimed run, keeps the fastest (smallest of its runs, CUDA
+ * events around the whole launch sequence), and returns it in *best and its
+ * time in *best_ms (either may be NULL). Each run starts from a reset stream,
+ * so the stream's history is discarded: tune before the first push. Results
+ * of the runs are dropped. Errors: FKD_E_ARG, FKD_E_CUDA. */
+int fkd_autotune(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t frame_stride, int T, int reps,
+                 fkd_launch_config* best, float* best_ms);
+
+/*
  * Groups: many streams, one frame of each per tick, one launch sequence.
  *
  * A group serves many independent video streams of any sizes (for example a
@@ -314,6 +350,21 @@ int fkd_group_device_keypoints(fkd_group* g, int id, const fkd_keypoint** record
  * the frames of those ticks). */
 int fkd_group_profile_enable(fkd_group* g, int on);
 int fkd_group_profile_read(fkd_group* g, fkd_profile* out, int reset);
+
+/* The detection launch shape of the whole group (one persistent launch runs
+ * the tiles of all its streams), as fkd_get/set_launch_config. Setting it
+ * waits for pending work and re-captures the tick graphs on the next tick. */
+int fkd_group_get_launch_config(const fkd_group* g, fkd_launch_config* out);
+int fkd_group_set_launch_config(fkd_group* g, const fkd_launch_config* c);
+
+/* Group autotuner: m ticks over streams ids[0..n-1], tick j taking frame
+ * frames[j * n + i] (device memory, row pitch pitches[i]) for stream ids[i],
+ * timed under every candidate shape as fkd_autotune does (reps timed
+ * sequences after one untimed one, each starting from reset streams). Keeps
+ * the fastest shape; every stream of the group is reset afterwards. Errors:
+ * FKD_E_ARG, FKD_E_CUDA. */
+int fkd_group_autotune(fkd_group* g, int n, const int* ids, int m, const uint8_t* const* frames,
+                       const size_t* pitches, int reps, fkd_launch_config* best, float* best_ms);
 
 /*
  * Serving loop: frames of many streams arriving at any time.

@@ -60,7 +60,10 @@ struct fkd_stream {
   uint16_t* rowblk = nullptr;
   int* xstart = nullptr;
   uint32_t* npix = nullptr;
-  DetTile* tiles = nullptr;
+  DetTile* tiles = nullptr;                  // the current shape's tiles
+  DetTile* tile_shape[kDetShapes] = {};      // per tile shape
+  int n_tiles_shape[kDetShapes] = {};
+  int n_tiles_max = 0;
   AsmChunk* chunks = nullptr;
   uint32_t* wbins = nullptr;
   uint32_t* wmask = nullptr;
@@ -85,7 +88,8 @@ struct fkd_stream {
   const uint8_t* prev = nullptr;
   int prev_pitch = 0;
   long long frame = 0;
-  int detect_grid = 0;
+  DetLaunch dl{};
+  fkd_launch_config lc{};
   bool have_frame_result = false;
 
   // profiling: events around each stage of each batch, read back lazily
@@ -180,7 +184,7 @@ int build_geometry(fkd_stream* s, int W, int H) {
 
   std::vector<uint16_t> colblk, rowblk;
   std::vector<int> xstart;
-  std::vector<DetTile> tiles;
+  std::vector<DetTile> tiles[kDetShapes];
   std::vector<AsmChunk> chunks;
   std::vector<uint32_t> wbins, wmask;
   long long pyr = 0, score = 0, bits = 0;
@@ -227,27 +231,36 @@ int build_geometry(fkd_stream* s, int W, int H) {
       const int rows = std::max(1, kAsmChunkWords / lg.wpr);
       for (int y0 = 0; y0 < lg.h; y0 += rows) chunks.push_back(AsmChunk{l, y0, std::min(lg.h, y0 + rows)});
     }
-    lg.tile_off = (int)tiles.size();
-    if (lg.w > 0 && lg.h > 0) {
-      for (int ty = 0; ty * kDetTH < lg.h; ++ty)
+    // detection tiles of every shape: kDetTW x TH rectangles, row-major
+    for (int k = 0; k < kDetShapes && lg.w > 0 && lg.h > 0; ++k) {
+      const int TH = kDetTH[k];
+      for (int ty = 0; ty * TH < lg.h; ++ty)
         for (int tx = 0; tx * kDetTW < lg.w; ++tx) {
           DetTile t{};
           t.layer = (uint16_t)l;
           t.tx = (uint16_t)tx;
           t.ty = (uint16_t)ty;
-          const int x1 = std::min((tx + 1) * kDetTW, lg.w) - 1, y1 = std::min((ty + 1) * kDetTH, lg.h) - 1;
+          const int x1 = std::min((tx + 1) * kDetTW, lg.w) - 1, y1 = std::min((ty + 1) * TH, lg.h) - 1;
+          t.area = (uint16_t)((x1 - tx * kDetTW + 1) * (y1 - ty * TH + 1));
           t.cb0 = colblk[lg.col_off + tx * kDetTW];
           t.cb1 = colblk[lg.col_off + x1];
-          t.rb0 = rowblk[lg.row_off + ty * kDetTH];
+          t.rb0 = rowblk[lg.row_off + ty * TH];
           t.rb1 = rowblk[lg.row_off + y1];
-          tiles.push_back(t);
+          tiles[k].push_back(t);
         }
     }
   }
   g.pyr_bytes = std::max(pyr, 256LL);
   g.score_bytes = score;
   g.bit_words = bits;
-  g.n_tiles = (int)tiles.size();
+  size_t all_tiles = 0;
+  for (int k = 0; k < kDetShapes; ++k) {
+    s->n_tiles_shape[k] = (int)tiles[k].size();
+    s->n_tiles_max = std::max(s->n_tiles_max, s->n_tiles_shape[k]);
+    all_tiles += tiles[k].size();
+  }
+  g.det_shape = kDetDefaultShape;
+  g.n_tiles = s->n_tiles_shape[g.det_shape];
   g.n_chunks = (int)chunks.size();
   g.pyr_tiles_x = (W + kPyrTile - 1) / kPyrTile;
   g.pyr_tiles_y = (H + kPyrTile - 1) / kPyrTile;
@@ -261,7 +274,7 @@ int build_geometry(fkd_stream* s, int W, int H) {
   int rc;
   if ((rc = s->alloc(&s->colblk, colblk.size())) || (rc = s->alloc(&s->rowblk, rowblk.size())) ||
       (rc = s->alloc(&s->xstart, xstart.size())) || (rc = s->alloc(&s->npix, npix.size())) ||
-      (rc = s->alloc(&s->tiles, tiles.size())) || (rc = s->alloc(&s->chunks, chunks.size())) ||
+      (rc = s->alloc(&s->tile_shape[0], all_tiles)) || (rc = s->alloc(&s->chunks, chunks.size())) ||
       (rc = s->alloc(&s->wbins, wbins.size())) || (rc = s->alloc(&s->wmask, wmask.size())))
     return rc;
   CK(cudaMemcpy(s->wmask, wmask.data(), wmask.size() * 4, cudaMemcpyHostToDevice));
@@ -271,8 +284,12 @@ int build_geometry(fkd_stream* s, int W, int H) {
   CK(cudaMemcpy(s->rowblk, rowblk.data(), rowblk.size() * 2, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->xstart, xstart.data(), xstart.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->npix, npix.data(), npix.size() * 4, cudaMemcpyHostToDevice));
-  if (!tiles.empty())
-    CK(cudaMemcpy(s->tiles, tiles.data(), tiles.size() * sizeof(DetTile), cudaMemcpyHostToDevice));
+  for (int k = 0; k < kDetShapes; ++k) {
+    if (k > 0) s->tile_shape[k] = s->tile_shape[k - 1] + tiles[k - 1].size();
+    if (!tiles[k].empty())
+      CK(cudaMemcpy(s->tile_shape[k], tiles[k].data(), tiles[k].size() * sizeof(DetTile), cudaMemcpyHostToDevice));
+  }
+  s->tiles = s->tile_shape[g.det_shape];
   return FKD_OK;
 }
 
@@ -284,7 +301,7 @@ int allocate_state(fkd_stream* s) {
   if ((rc = s->alloc(&sc.pyr, (size_t)(T * g.pyr_bytes))) ||
       (rc = s->alloc(&sc.bsum, (size_t)(T * g.NB))) || (rc = s->alloc(&sc.mask, (size_t)(T * g.NB))) ||
       (rc = s->alloc(&sc.src, (size_t)(T * g.NB))) ||
-      (rc = s->alloc(&sc.work, (size_t)(T * std::max(g.n_tiles, 1)))) ||
+      (rc = s->alloc(&sc.work, (size_t)(T * std::max(s->n_tiles_max, 1)))) ||
       (rc = s->alloc(&sc.work_count, 1)) ||
       (rc = s->alloc(&sc.det_bits, (size_t)(T * std::max(g.bit_words, 1LL)))) ||
       (rc = s->alloc(&sc.det_score, (size_t)(T * g.score_bytes))) ||
@@ -354,7 +371,7 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   mark(2);
   launch_worklist(s->g, tb, b, s->s, s->st);
   mark(3);
-  launch_detect(s->g, tb, b, s->s, pr, s->detect_grid, s->st);
+  launch_detect(s->g, tb, b, s->s, pr, s->dl, s->st);
   mark(4);
   launch_count(s->g, tb, b, s->s, stt, s->st);  // its last CTA also fills s->s.bases
   mark(5);
@@ -372,6 +389,82 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   s->frame += T;
   s->last_mask = s->s.mask + (long long)(T - 1) * s->g.NB;
   return FKD_OK;
+}
+
+// T frames in device memory as one batch (frame by frame for keypoint
+// binning, whose mask needs the previous frame's keypoints); masks, if not
+// NULL, receive each frame's mask.
+int run_frames(fkd_stream* s, const uint8_t* dframes, int dpitch, long long dstride, int T, fkd_keypoint* drec,
+               long long cap, uint32_t* doff, uint8_t* masks, cudaMemcpyKind mask_kind) {
+  const bool serial = s->p.mask_mode == FKD_MASK_KB;
+  int slot = 0;
+  for (int k0 = 0; k0 < T;) {
+    const int n = serial ? 1 : T;
+    int rc = run_batch(s, dframes + (long long)k0 * dstride, dpitch, dstride, n, drec, cap, doff + k0, slot, k0 == 0);
+    if (rc) return rc;
+    if (masks)
+      CK(cudaMemcpyAsync(masks + (size_t)k0 * s->g.NB, s->s.mask, (size_t)n * s->g.NB, mask_kind, s->st));
+    slot ^= 1;
+    k0 += n;
+  }
+  s->have_frame_result = false;
+  return FKD_OK;
+}
+
+void reset_history(fkd_stream* s) {
+  s->frame = 0;
+  s->prev = nullptr;
+  s->prev_pitch = 0;
+  s->have_frame_result = false;
+  s->last_mask = nullptr;
+}
+
+// Check a launch shape and turn it into the kernel's launch arguments.
+int resolve_launch(const fkd_launch_config* c, DetLaunch* dl) {
+  if (!c) return fail(FKD_E_ARG, "launch config is NULL");
+  int shape = -1;
+  for (int k = 0; k < kDetShapes; ++k)
+    if (c->tile_h == kDetTH[k]) shape = k;
+  if (shape < 0) return fail(FKD_E_ARG, "tile_h %d: use 8, 16 or 24", c->tile_h);
+  if (c->warps_per_cta != 4 && c->warps_per_cta != 8)
+    return fail(FKD_E_ARG, "warps_per_cta %d: use 4 or 8", c->warps_per_cta);
+  const int fit = detect_ctas_per_sm(shape, c->warps_per_cta);
+  if (c->ctas_per_sm < 1 || c->ctas_per_sm > fit)
+    return fail(FKD_E_ARG, "ctas_per_sm %d outside 1..%d for tile_h %d, %d warps", c->ctas_per_sm, fit, c->tile_h,
+                c->warps_per_cta);
+  dl->shape = shape;
+  dl->warps = c->warps_per_cta;
+  dl->grid = c->ctas_per_sm * sm_count();
+  return FKD_OK;
+}
+
+fkd_launch_config default_launch() {
+  fkd_launch_config c{};
+  c.tile_h = kDetTH[kDetDefaultShape];
+  c.warps_per_cta = kDetMaxThreads / 32;
+  c.ctas_per_sm = std::max(1, detect_ctas_per_sm(kDetDefaultShape, c.warps_per_cta));
+  return c;
+}
+
+// Point the stream's tables at the tiles of `dl.shape` (no pending work may
+// still use the stream's work list).
+void apply_launch(fkd_stream* s, const fkd_launch_config& c, const DetLaunch& dl) {
+  s->lc = c;
+  s->dl = dl;
+  s->g.det_shape = dl.shape;
+  s->g.n_tiles = s->n_tiles_shape[dl.shape];
+  s->tiles = s->tile_shape[dl.shape];
+}
+
+// Every candidate shape of the autotuner.
+std::vector<fkd_launch_config> launch_candidates() {
+  std::vector<fkd_launch_config> v;
+  for (int k = 0; k < kDetShapes; ++k)
+    for (int warps = 4; warps <= 8; warps += 4) {
+      const int fit = detect_ctas_per_sm(k, warps);
+      for (int c = 1; c <= fit; ++c) v.push_back(fkd_launch_config{kDetTH[k], warps, c});
+    }
+  return v;
 }
 
 bool is_pinned(const void* p) {
@@ -423,7 +516,16 @@ int fkd_create_stream(const fkd_params* p, int W, int H, void* cuda_stream, fkd_
     return rc;
   }
   s->staging_pitch = round_up(W, 16);
-  s->detect_grid = detect_grid_size();
+  {
+    const fkd_launch_config c = default_launch();
+    DetLaunch dl{};
+    if ((rc = resolve_launch(&c, &dl))) {
+      s->release();
+      delete s;
+      return rc;
+    }
+    apply_launch(s, c, dl);
+  }
   *out = s;
   return FKD_OK;
 }
@@ -504,21 +606,9 @@ int fkd_push_frames(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t f
   }
 
   // 3. the batch (frame by frame for keypoint binning)
-  const bool serial = s->p.mask_mode == FKD_MASK_KB;
-  int slot = 0;
-  for (int k0 = 0; k0 < T;) {
-    const int n = serial ? 1 : T;
-    int rc = run_batch(s, dframes + (long long)k0 * dstride, dpitch, dstride, n, drec, (long long)cap,
-                       doff + k0, slot, k0 == 0);
-    if (rc) return rc;
-    if (masks) {
-      CK(cudaMemcpyAsync(masks + (size_t)k0 * g.NB, s->s.mask, (size_t)n * g.NB,
-                         out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->st));
-    }
-    slot ^= 1;
-    k0 += n;
-  }
-  s->have_frame_result = false;
+  int rc = run_frames(s, dframes, dpitch, dstride, T, drec, (long long)cap, doff, masks,
+                      out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  if (rc) return rc;
 
   if (out_on_device) return FKD_OK;
   CK(cudaMemcpyAsync(offsets, doff, (size_t)(T + 1) * 4, cudaMemcpyDeviceToHost, s->st));
@@ -605,11 +695,80 @@ int fkd_frame_count(const fkd_stream* s, int64_t* n) {
 int fkd_reset_stream(fkd_stream* s) {
   if (!s) return fail(FKD_E_ARG, "stream is NULL");
   CK(cudaStreamSynchronize(s->st));
-  s->frame = 0;
-  s->prev = nullptr;
-  s->prev_pitch = 0;
-  s->have_frame_result = false;
-  s->last_mask = nullptr;
+  reset_history(s);
+  return FKD_OK;
+}
+
+int fkd_get_launch_config(const fkd_stream* s, fkd_launch_config* out) {
+  if (!s || !out) return fail(FKD_E_ARG, "NULL argument");
+  *out = s->lc;
+  return FKD_OK;
+}
+
+int fkd_set_launch_config(fkd_stream* s, const fkd_launch_config* c) {
+  if (!s) return fail(FKD_E_ARG, "stream is NULL");
+  DetLaunch dl{};
+  int rc = resolve_launch(c, &dl);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s->st));
+  apply_launch(s, *c, dl);
+  return FKD_OK;
+}
+
+int fkd_autotune(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t frame_stride, int T, int reps,
+                 fkd_launch_config* best, float* best_ms) {
+  if (!s || !frames) return fail(FKD_E_ARG, "NULL argument");
+  const Geometry& g = s->g;
+  if (T < 1 || T > s->p.T_max) return fail(FKD_E_ARG, "T=%d outside 1..T_max=%d", T, s->p.T_max);
+  if (pitch < (size_t)g.W || pitch > (1u << 30)) return fail(FKD_E_ARG, "pitch %zu < W=%d", pitch, g.W);
+  if (T > 1 && frame_stride < pitch * (size_t)g.H) return fail(FKD_E_ARG, "frame_stride too small");
+  if (reps < 1 || reps > 100) return fail(FKD_E_ARG, "reps %d outside 1..100", reps);
+  CK(cudaStreamSynchronize(s->st));
+  const bool prof = s->profiling;
+  s->profiling = false;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  CK(cudaEventCreate(&ev[0]));
+  CK(cudaEventCreate(&ev[1]));
+  // records go to the per-frame result buffer (K_max of them; the rest are
+  // dropped), offsets to the host-output offsets
+  fkd_launch_config win = s->lc;
+  float win_ms = -1.f;
+  int rc = FKD_OK;
+  for (const fkd_launch_config& c : launch_candidates()) {
+    DetLaunch dl{};
+    if ((rc = resolve_launch(&c, &dl))) break;
+    apply_launch(s, c, dl);
+    float best_c = -1.f;
+    for (int r = 0; r <= reps && rc == FKD_OK; ++r) {
+      reset_history(s);
+      cudaEventRecord(ev[0], s->st);
+      rc = run_frames(s, frames, (int)pitch, (long long)frame_stride, T, s->rec, s->p.K_max, s->host_offsets,
+                      nullptr, cudaMemcpyDeviceToDevice);
+      cudaEventRecord(ev[1], s->st);
+      cudaError_t e = cudaEventSynchronize(ev[1]);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (e != cudaSuccess && rc == FKD_OK) rc = fail(FKD_E_CUDA, "autotune timing failed: %s", cudaGetErrorString(e));
+      if (r > 0 && (best_c < 0.f || ms < best_c)) best_c = ms;
+    }
+    if (rc) break;
+    if (win_ms < 0.f || best_c < win_ms) {
+      win_ms = best_c;
+      win = c;
+    }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  s->profiling = prof;
+  DetLaunch dl{};
+  if (resolve_launch(&win, &dl) == FKD_OK) apply_launch(s, win, dl);
+  reset_history(s);
+  cudaMemsetAsync(s->s.overflow, 0, 4, s->st);
+  cudaStreamSynchronize(s->st);
+  cudaMemcpy(s->tile_stats_seen, s->s.tile_stats, 16, cudaMemcpyDeviceToHost);  // tuning runs are not profiled
+  if (rc) return rc;
+  if (best) *best = win;
+  if (best_ms) *best_ms = win_ms;
   return FKD_OK;
 }
 
@@ -682,7 +841,9 @@ struct fkd_group {
   uint32_t* d_work = nullptr;
   long long work_cap = 0;
   uint32_t* d_work_count = nullptr;
-  int grid_pyr = 1, grid_small = 1, grid_det = 1, grid_asm = 1;
+  int grid_pyr = 1, grid_small = 1, grid_asm = 1;
+  fkd_launch_config lc{};            // detection launch shape of every stream
+  DetLaunch dl{};
   bool use_graph = true;
   bool graph_valid = false;
   int graph_items = 0;               // items copied per tick by the captured graphs
@@ -761,7 +922,7 @@ int group_launch(fkd_group* G, int b, int n_items, fkd_stream::Pending* pd) {
   mark(2);
   launch_group_worklist(G->d_devs, G->d_hdr, G->d_items, G->d_work, G->d_work_count, G->grid_small, G->st);
   mark(3);
-  launch_group_detect(G->d_devs, G->d_items, G->d_work, G->d_work_count, G->grid_det, G->st);
+  launch_group_detect(G->d_devs, G->d_items, G->d_work, G->d_work_count, G->dl, G->st);
   mark(4);
   launch_group_count(G->d_devs, G->d_hdr, G->d_items, G->grid_asm, G->st);
   mark(5);
@@ -828,7 +989,8 @@ int fkd_group_create(int O, int intra, void* cuda_stream, fkd_group** out) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   G->grid_pyr = group_pyramid_grid(O, intra);
-  G->grid_det = detect_grid_size();
+  G->lc = default_launch();
+  if (int rc = resolve_launch(&G->lc, &G->dl)) return bail(rc);
   G->grid_small = sms * 8;
   G->grid_asm = sms * 8;
   *out = G;
@@ -879,6 +1041,7 @@ int fkd_group_add_stream(fkd_group* G, const fkd_params* p, int W, int H, int* s
     return rc;
   }
   gs.bytes = s->bytes_held;
+  apply_launch(s, G->lc, G->dl);
   const int id = (int)G->streams.size();
   // device descriptors (grow: the captured graphs hold the old pointer)
   if (id >= G->devs_cap) {
@@ -902,8 +1065,8 @@ int fkd_group_add_stream(fkd_group* G, const fkd_params* p, int W, int H, int* s
   // the tick's active-tile list holds at most the tiles of all live streams
   long long need = 0;
   for (auto& o : G->streams)
-    if (o.s) need += o.s->g.n_tiles;
-  need += s->g.n_tiles;
+    if (o.s) need += o.s->n_tiles_max;
+  need += s->n_tiles_max;
   if (need > G->work_cap) {
     const long long cap = std::max(need, 2 * G->work_cap);
     cudaFree(G->d_work);
@@ -1096,6 +1259,88 @@ int fkd_group_profile_read(fkd_group* G, fkd_profile* out, int reset) {
   G->prof.tile_pixels += px;
   *out = G->prof;
   if (reset) G->prof = fkd_profile{};
+  return FKD_OK;
+}
+
+int fkd_group_get_launch_config(const fkd_group* G, fkd_launch_config* out) {
+  if (!G || !out) return fail(FKD_E_ARG, "NULL argument");
+  *out = G->lc;
+  return FKD_OK;
+}
+
+int fkd_group_set_launch_config(fkd_group* G, const fkd_launch_config* c) {
+  if (!G) return fail(FKD_E_ARG, "group is NULL");
+  DetLaunch dl{};
+  int rc = resolve_launch(c, &dl);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(G->st));
+  G->lc = *c;
+  G->dl = dl;
+  for (int id = 0; id < (int)G->streams.size(); ++id) {
+    GroupStream& gs = G->streams[id];
+    if (!gs.s) continue;
+    apply_launch(gs.s, *c, dl);
+    const StreamDev d = make_dev(gs.s, gs.last, gs.rec1, gs.off1);
+    CK(cudaMemcpy(G->d_devs + id, &d, sizeof d, cudaMemcpyHostToDevice));
+  }
+  G->drop_graphs();
+  return FKD_OK;
+}
+
+int fkd_group_autotune(fkd_group* G, int n, const int* ids, int m, const uint8_t* const* frames,
+                       const size_t* pitches, int reps, fkd_launch_config* best, float* best_ms) {
+  if (!G || n < 1 || m < 1 || !ids || !frames || !pitches) return fail(FKD_E_ARG, "NULL argument or empty tick");
+  if (reps < 1 || reps > 100) return fail(FKD_E_ARG, "reps %d outside 1..100", reps);
+  for (int i = 0; i < n; ++i)
+    if (!group_member(G, ids[i])) return fail(FKD_E_ARG, "unknown stream id %d", ids[i]);
+  CK(cudaStreamSynchronize(G->st));
+  const bool prof = G->profiling;
+  G->profiling = false;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  CK(cudaEventCreate(&ev[0]));
+  CK(cudaEventCreate(&ev[1]));
+  auto reset_all = [&]() {
+    for (auto& gs : G->streams)
+      if (gs.s) reset_history(gs.s);
+  };
+  const fkd_launch_config start = G->lc;
+  fkd_launch_config win = start;
+  float win_ms = -1.f;
+  int rc = FKD_OK;
+  for (const fkd_launch_config& c : launch_candidates()) {
+    if ((rc = fkd_group_set_launch_config(G, &c))) break;
+    float best_c = -1.f;
+    for (int r = 0; r <= reps && rc == FKD_OK; ++r) {
+      reset_all();
+      cudaEventRecord(ev[0], G->st);
+      for (int j = 0; j < m && rc == FKD_OK; ++j) rc = fkd_group_tick(G, n, ids, frames + (size_t)j * n, pitches);
+      cudaEventRecord(ev[1], G->st);
+      cudaError_t e = cudaEventSynchronize(ev[1]);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (e != cudaSuccess && rc == FKD_OK) rc = fail(FKD_E_CUDA, "autotune timing failed: %s", cudaGetErrorString(e));
+      if (r > 0 && (best_c < 0.f || ms < best_c)) best_c = ms;
+    }
+    if (rc) break;
+    if (win_ms < 0.f || best_c < win_ms) {
+      win_ms = best_c;
+      win = c;
+    }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  G->profiling = prof;
+  const int rc2 = fkd_group_set_launch_config(G, rc ? &start : &win);
+  reset_all();
+  for (auto& gs : G->streams)
+    if (gs.s) {
+      cudaMemset(gs.s->s.overflow, 0, 4);
+      cudaMemcpy(gs.s->tile_stats_seen, gs.s->s.tile_stats, 16, cudaMemcpyDeviceToHost);
+    }
+  if (rc) return rc;
+  if (rc2) return rc2;
+  if (best) *best = win;
+  if (best_ms) *best_ms = win_ms;
   return FKD_OK;
 }
 

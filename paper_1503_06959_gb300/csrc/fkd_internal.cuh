@@ -19,12 +19,23 @@ constexpr int kPyrTile = 96;
 constexpr int kPyrThreads = 256;
 
 // Detection tile (output pixels) handled by one warp: one 4-pixel word per
-// lane per row. The staged input adds a 4-pixel halo (3 for the ring, 1 for
-// the suppression neighbours), widened to 16 bytes left and right so that
-// rows load as aligned 16-byte vectors.
+// lane per row, kDetTW wide and kDetTH[shape] high. The staged input adds a
+// 4-pixel halo (3 for the ring, 1 for the suppression neighbours), widened to
+// 16 bytes left and right so that rows load as aligned 16-byte vectors.
+// The launch shape (tile height, warps per CTA, CTAs per SM) is chosen per
+// stream or group, by default or by the autotuner.
 constexpr int kDetTW = 128;
-constexpr int kDetTH = 16;
-constexpr int kDetThreads = 256;
+constexpr int kDetShapes = 3;
+constexpr int kDetTH[kDetShapes] = {8, 16, 24};
+constexpr int kDetDefaultShape = 1;
+constexpr int kDetMaxThreads = 256;  // warps per CTA: 4 or 8
+
+// Launch shape of the detection kernel.
+struct DetLaunch {
+  int shape;  // index into kDetTH
+  int warps;  // warps (tiles in flight) per CTA
+  int grid;   // persistent CTAs
+};
 
 // Assembly: a chunk is a band of whole rows of one layer of the per-frame
 // keypoint bitmap, about kAsmChunkWords words, handled by one CTA.
@@ -60,7 +71,6 @@ struct LayerGeom {
   int wb_off;          // offset of the layer in the wbins table (wpr entries)
   int row_off;         // offset of the layer in the rowblk table (h entries)
   int xs_off;          // offset of the layer in the xstart table (N_c + 1 entries)
-  int tile_off;        // first detection tile of the layer
 };
 
 struct Geometry {
@@ -71,7 +81,8 @@ struct Geometry {
   long long pyr_bytes;    // per frame, layers >= 1
   long long score_bytes;  // per frame, all layers
   long long bit_words;    // per frame, all layers
-  int n_tiles;            // detection tiles per frame
+  int n_tiles;            // detection tiles per frame (current tile shape)
+  int det_shape;          // current tile shape (index into kDetTH)
   int n_chunks;           // assembly chunks per frame
   int pyr_tiles_x, pyr_tiles_y;
 };
@@ -81,10 +92,11 @@ struct AsmChunk {
   int layer, y0, y1;
 };
 
-// One detection tile: a kDetTW x kDetTH rectangle of one layer, and the
-// rectangle of bins its pixels map to (inclusive), for the activity test.
+// One detection tile: a kDetTW x kDetTH[shape] rectangle of one layer, its
+// pixel count inside the layer, and the rectangle of bins its pixels map to
+// (inclusive), for the activity test.
 struct DetTile {
-  uint16_t layer, tx, ty, pad;
+  uint16_t layer, tx, ty, area;
   uint16_t rb0, rb1, cb0, cb1;
 };
 
@@ -203,7 +215,7 @@ void launch_group_mask(const StreamDev* devs, const TickHeader* hdr, const TickI
 void launch_group_worklist(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
                            uint32_t* work, uint32_t* work_count, int grid, cudaStream_t st);
 void launch_group_detect(const StreamDev* devs, const TickItem* items, const uint32_t* work,
-                         const uint32_t* work_count, int grid, cudaStream_t st);
+                         const uint32_t* work_count, const DetLaunch& dl, cudaStream_t st);
 void launch_group_count(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
                         int grid, cudaStream_t st);
 void launch_group_emit(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
@@ -244,12 +256,15 @@ void launch_mask(const Geometry& g, const Tables& tb, const Batch& b, const Scra
 void launch_worklist(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                      cudaStream_t st);
 void launch_detect(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
-                   const Params& p, int grid, cudaStream_t st);
+                   const Params& p, const DetLaunch& dl, cudaStream_t st);
 void launch_count(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                   const State& state, cudaStream_t st);
 void launch_emit(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                  const State& state, const Output& out, cudaStream_t st);
-int detect_grid_size();
+// CTAs of the detection kernel resident per SM for a tile shape and warp
+// count (0 when it cannot launch), and the SM count.
+int detect_ctas_per_sm(int shape, int warps);
+int sm_count();
 
 // Record a message for fkd_last_error (printf format) and return `code`.
 int set_error(int code, const char* fmt, ...);

@@ -23,29 +23,36 @@
 //      never changes the outcome); write the tile's bitmap words and scores.
 // Bins are not consulted here: assembly takes each pixel from the frame its
 // bin points to, so the kernel only has to be right on the tiles it runs.
+#include <algorithm>
+
 #include "fkd_internal.cuh"
 
 namespace fkd {
 namespace {
 
-constexpr int TW = kDetTW, TH = kDetTH;   // 128 x 16 output pixels per warp
-constexpr int IN_W = TW + 32;             // input row: x in [x0-16, x0+TW+16)
-constexpr int IN_H = TH + 8;              // input rows: y in [y0-4, y0+TH+4)
-constexpr int SC_P = TW + 8;              // score row pitch; column = x - x0 + 4
-constexpr int SC_H = TH + 2;              // score rows: y in [y0-1, y0+TH]
-constexpr int WARPS = kDetThreads / 32;
-constexpr int IN_BYTES = IN_W * IN_H;
-constexpr int SC_BYTES = SC_P * SC_H;
-constexpr int DET_WORDS = TH * (TW / 32);
-constexpr int LIST = 512;  // candidate list window per warp (entries)
-constexpr int PASS = 256;  // passing-pixel list per warp (entries); beyond it the pass bitmap is scanned
+constexpr int TW = kDetTW;   // output pixels per tile row: one 4-pixel word per lane
+constexpr int IN_W = TW + 32;  // input row: x in [x0-16, x0+TW+16)
+constexpr int SC_P = TW + 8;   // score row pitch; column = x - x0 + 4
+constexpr int LIST = 512;      // candidate list window per warp (entries)
+constexpr int PASS = 256;      // passing-pixel list per warp (entries); beyond it the pass bitmap is scanned
 constexpr int NBUF = 1;        // input buffers per warp (2: the next tile loads during this one; no gain measured)
-constexpr int MIN_BLOCKS = 2;  // CTAs resident per SM the register budget is sized for
-// per warp: input buffer(s), score map, keypoint and pass bitmaps, candidate and pass lists
-constexpr int WARP_SMEM = NBUF * IN_BYTES + SC_BYTES + 2 * DET_WORDS * 4 + LIST * 2 + PASS * 2;
+constexpr int MIN_BLOCKS = 2;  // 256-thread CTAs resident per SM the register budget is sized for
 static_assert(TW == 32 * 4, "one 4-pixel word per lane per row");
 static_assert(LIST >= 256 && LIST <= 65535, "a flush leaves room for one more row (128)");
-static_assert(IN_BYTES % 16 == 0 && SC_BYTES % 16 == 0, "16-byte aligned slices");
+
+// Per-warp sizes for a tile height TH (output rows y0 .. y0+TH-1).
+template <int TH>
+struct Shape {
+  static constexpr int IN_H = TH + 8;            // input rows: y in [y0-4, y0+TH+4)
+  static constexpr int SC_H = TH + 2;            // score rows: y in [y0-1, y0+TH]
+  static constexpr int IN_BYTES = IN_W * IN_H;
+  static constexpr int SC_BYTES = SC_P * SC_H;
+  static constexpr int DET_WORDS = TH * (TW / 32);
+  // input buffer(s), score map, keypoint and pass bitmaps, candidate and pass lists
+  static constexpr int WARP_SMEM = NBUF * IN_BYTES + SC_BYTES + 2 * DET_WORDS * 4 + LIST * 2 + PASS * 2;
+  static_assert(TH % 8 == 0 && TH + 4 <= 32, "one lane per dilated score row; whole 32-word rounds");
+  static_assert(IN_BYTES % 16 == 0 && SC_BYTES % 16 == 0, "16-byte aligned slices");
+};
 
 // Per byte: bit 7 set where e >= T1 (T1 in 1..255, the same in every byte).
 __device__ __forceinline__ uint32_t bytes_ge(uint32_t e, uint32_t t1_low7, bool t1_high) {
@@ -133,6 +140,7 @@ struct SingleSrc {
   Tables tb;
   Params p;
   __device__ __forceinline__ uint32_t count() const { return *s.work_count; }
+  template <int TH>
   __device__ __forceinline__ Item decode(uint32_t item) const {
     const uint32_t wi = s.work[item];
     const DetTile tile = tb.tiles[wi % (uint32_t)g.n_tiles];
@@ -170,6 +178,7 @@ struct GroupSrc {
   const uint32_t* work;
   const uint32_t* work_count;
   __device__ __forceinline__ uint32_t count() const { return *work_count; }
+  template <int TH>
   __device__ __forceinline__ Item decode(uint32_t item) const {
     const uint32_t wi = work[item];
     const TickItem ti = items[wi >> 22];
@@ -207,7 +216,9 @@ struct GroupSrc {
 // Returns one bit per score row (bit rr: row y0-1+rr) for this lane's word
 // x0+4*lane .. +3, dilated by one pixel each way; all ones when every bin is
 // active or the tile spans more than 32 bin rows.
+template <int TH>
 __device__ __forceinline__ uint32_t active_rows(const Item& it, int lane) {
+  constexpr int SC_H = Shape<TH>::SC_H;
   if (!it.mask) return 0xffffffffu;
   const int x = it.x0 + 4 * lane;
   const int xa = max(0, min(it.w - 1, x - 1)), xb = max(0, min(it.w - 1, x + 4));
@@ -238,7 +249,9 @@ __device__ __forceinline__ uint32_t active_rows(const Item& it, int lane) {
 // A. stage input rows y0-4 .. y0+TH+3, columns x0-16 .. x0+TW+15, zeros
 // outside the layer. x0 is a multiple of 128, so each 16-byte chunk is either
 // wholly left of the layer or starts inside it.
+template <int TH>
 __device__ __forceinline__ void stage(uint8_t* in, const Item& it, int lane) {
+  constexpr int IN_H = Shape<TH>::IN_H;
   const bool vec = ((reinterpret_cast<uintptr_t>(it.src) | (uintptr_t)it.pitch) & 15) == 0;
   if (vec && it.x0 >= 16 && it.x0 + TW + 16 <= it.w && it.y0 >= 4 && it.y0 + TH + 4 <= it.h) {
     // the whole staged rectangle lies inside the layer: no checks, no zero fill
@@ -277,11 +290,13 @@ __device__ __forceinline__ void stage(uint8_t* in, const Item& it, int lane) {
 // Score-map offset of the pixel at input offset o.
 __device__ __forceinline__ int sc_of(int o) { return (o / IN_W - 3) * SC_P + (o % IN_W) - 12; }
 
-template <class Src>
-__global__ void __launch_bounds__(kDetThreads, MIN_BLOCKS) k_detect(Src src) {
+template <class Src, int TH>
+__global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) {
+  using Sh = Shape<TH>;
+  constexpr int SC_H = Sh::SC_H, IN_BYTES = Sh::IN_BYTES, SC_BYTES = Sh::SC_BYTES, DET_WORDS = Sh::DET_WORDS;
   extern __shared__ __align__(16) uint8_t smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint8_t* inbuf = smem + warp * WARP_SMEM;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+  uint8_t* inbuf = smem + warp * Sh::WARP_SMEM;
   uint8_t* sc = inbuf + NBUF * IN_BYTES;
   uint32_t* detw = reinterpret_cast<uint32_t*>(sc + SC_BYTES);
   uint32_t* passw = detw + DET_WORDS;
@@ -289,33 +304,33 @@ __global__ void __launch_bounds__(kDetThreads, MIN_BLOCKS) k_detect(Src src) {
   uint16_t* plist = list + LIST;
 
   const uint32_t count_items = src.count();
-  const uint32_t stride = gridDim.x * WARPS;
+  const uint32_t stride = gridDim.x * warps;
 
-  uint32_t item = blockIdx.x * WARPS + warp;
+  uint32_t item = blockIdx.x * warps + warp;
   int buf = 0;
   Item nxt{};
   if (NBUF == 2 && item < count_items) {
-    nxt = src.decode(item);
-    stage(inbuf, nxt, lane);
+    nxt = src.template decode<TH>(item);
+    stage<TH>(inbuf, nxt, lane);
   }
   cp_async_commit();
   for (; item < count_items; item += stride) {
-    const Item it = NBUF == 2 ? nxt : src.decode(item);
+    const Item it = NBUF == 2 ? nxt : src.template decode<TH>(item);
     const uint8_t* in = inbuf + buf * IN_BYTES;
     if (NBUF == 2) {
       // prefetch the next tile into the other buffer, then wait for this one
       if (item + stride < count_items) {
-        nxt = src.decode(item + stride);
-        stage(inbuf + (buf ^ 1) * IN_BYTES, nxt, lane);
+        nxt = src.template decode<TH>(item + stride);
+        stage<TH>(inbuf + (buf ^ 1) * IN_BYTES, nxt, lane);
       }
     } else {
-      stage(inbuf, it, lane);
+      stage<TH>(inbuf, it, lane);
     }
     cp_async_commit();
     for (int q = lane; q < SC_BYTES / 16; q += 32)
       reinterpret_cast<uint4*>(sc)[q] = make_uint4(0u, 0u, 0u, 0u);
-    detw[lane] = detw[lane + 32] = 0u;
-    passw[lane] = passw[lane + 32] = 0u;
+#pragma unroll
+    for (int q = lane; q < DET_WORDS; q += 32) detw[q] = passw[q] = 0u;
     cp_async_wait<NBUF - 1>();
     __syncwarp();
     const int w = it.w, h = it.h, x0 = it.x0, y0 = it.y0;
@@ -331,7 +346,7 @@ __global__ void __launch_bounds__(kDetThreads, MIN_BLOCKS) k_detect(Src src) {
     //      per lane, 64 per round -- whenever it fills up and at the end. A
     //      pixel of the tile scoring >= t goes to the pass list (and bitmap).
     const bool interior = x0 - 1 >= 3 && x0 + TW < w - 3 && y0 - 1 >= 3 && y0 + TH < h - 3;
-    const uint32_t act = active_rows(it, lane);
+    const uint32_t act = active_rows<TH>(it, lane);
     const uint32_t act_any = __reduce_or_sync(0xffffffffu, act);
     const unsigned lt = (1u << lane) - 1u;
     int count = 0;  // candidates in the list (warp-uniform)
@@ -476,26 +491,61 @@ __global__ void __launch_bounds__(kDetThreads, MIN_BLOCKS) k_detect(Src src) {
 
 }  // namespace
 
-int detect_grid_size() {
-  int dev = 0, sms = 0, per_sm = 0;
+template <int TH>
+int ctas_per_sm(int warps) {
+  constexpr int smem = Shape<TH>::WARP_SMEM;
+  const int max_smem = (kDetMaxThreads / 32) * smem;
+  if (cudaFuncSetAttribute(k_detect<SingleSrc, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem) ||
+      cudaFuncSetAttribute(k_detect<GroupSrc, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem))
+    return 0;
+  int n = 0, m = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_detect<SingleSrc, TH>, warps * 32, warps * smem) ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_detect<GroupSrc, TH>, warps * 32, warps * smem))
+    return 0;
+  return std::min(n, m);
+}
+
+static_assert(kDetShapes == 3, "one launch case per tile shape");
+
+int detect_ctas_per_sm(int shape, int warps) {
+  if (warps < 1 || warps > kDetMaxThreads / 32) return 0;
+  switch (shape) {
+    case 0: return ctas_per_sm<kDetTH[0]>(warps);
+    case 1: return ctas_per_sm<kDetTH[1]>(warps);
+    case 2: return ctas_per_sm<kDetTH[2]>(warps);
+    default: return 0;
+  }
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaFuncSetAttribute(k_detect<SingleSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, WARPS * WARP_SMEM);
-  cudaFuncSetAttribute(k_detect<GroupSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, WARPS * WARP_SMEM);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_detect<SingleSrc>, kDetThreads, WARPS * WARP_SMEM);
-  if (sms <= 0) sms = 1;
-  if (per_sm <= 0) per_sm = 1;
-  return sms * per_sm;
+  return sms > 0 ? sms : 1;
+}
+
+template <class Src>
+void launch_shape(const Src& src, const DetLaunch& dl, cudaStream_t st) {
+  switch (dl.shape) {
+#define FKD_DET_CASE(i)                                                                         \
+  case i:                                                                                       \
+    k_detect<Src, kDetTH[i]><<<dl.grid, dl.warps * 32, dl.warps * Shape<kDetTH[i]>::WARP_SMEM, st>>>(src); \
+    break;
+    FKD_DET_CASE(0)
+    FKD_DET_CASE(1)
+    FKD_DET_CASE(2)
+#undef FKD_DET_CASE
+  }
 }
 
 void launch_detect(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
-                   const Params& p, int grid, cudaStream_t st) {
-  k_detect<SingleSrc><<<grid, kDetThreads, WARPS * WARP_SMEM, st>>>(SingleSrc{g, b, s, tb, p});
+                   const Params& p, const DetLaunch& dl, cudaStream_t st) {
+  launch_shape(SingleSrc{g, b, s, tb, p}, dl, st);
 }
 
 void launch_group_detect(const StreamDev* devs, const TickItem* items, const uint32_t* work,
-                         const uint32_t* work_count, int grid, cudaStream_t st) {
-  k_detect<GroupSrc><<<grid, kDetThreads, WARPS * WARP_SMEM, st>>>(GroupSrc{devs, items, work, work_count});
+                         const uint32_t* work_count, const DetLaunch& dl, cudaStream_t st) {
+  launch_shape(GroupSrc{devs, items, work, work_count}, dl, st);
 }
 
 }  // namespace fkd

@@ -80,10 +80,7 @@ __global__ void k_worklist(Geometry g, Tables tb, Batch b, Scratch s) {
     for (int r = t.rb0; r <= t.rb1 && !act; ++r)
       for (int c = t.cb0; c <= t.cb1; ++c)
         if (m[r * g.N_c + c]) { act = true; break; }
-    if (act) {
-      const LayerGeom& lg = g.layer[t.layer];
-      area = (uint32_t)(min(kDetTW, lg.w - t.tx * kDetTW) * min(kDetTH, lg.h - t.ty * kDetTH));
-    }
+    if (act) area = t.area;
   }
   const unsigned bal = __ballot_sync(0xffffffffu, act);
   if (bal == 0) return;
@@ -152,11 +149,8 @@ __global__ void k_group_worklist(const StreamDev* devs, const TickHeader* hdr, c
           if (d.s.mask[r * d.g.N_c + c]) { act = true; break; }
       if (act) {
         entry = ((uint32_t)i << 22) | (uint32_t)tile;
-        const LayerGeom& lg = d.g.layer[t.layer];
-        const uint32_t area =
-            (uint32_t)(min(kDetTW, lg.w - t.tx * kDetTW) * min(kDetTH, lg.h - t.ty * kDetTH));
         atomicAdd(&d.s.tile_stats[0], 1ull);
-        atomicAdd(&d.s.tile_stats[1], (unsigned long long)area);
+        atomicAdd(&d.s.tile_stats[1], (unsigned long long)t.area);
       }
     }
     const unsigned bal = __ballot_sync(0xffffffffu, act);

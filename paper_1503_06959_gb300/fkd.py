@@ -33,7 +33,8 @@ EXPORTS = [
     "fkd_group_get_mask", "fkd_group_device_keypoints", "fkd_group_profile_enable",
     "fkd_group_profile_read", "fkd_server_create", "fkd_server_destroy", "fkd_server_open_stream",
     "fkd_server_close_stream", "fkd_server_submit", "fkd_server_poll", "fkd_server_drain",
-    "fkd_server_get_stats",
+    "fkd_server_get_stats", "fkd_get_launch_config", "fkd_set_launch_config", "fkd_autotune",
+    "fkd_group_get_launch_config", "fkd_group_set_launch_config", "fkd_group_autotune",
 ]
 STAGES = ["pyramid", "mask", "worklist", "detect", "count", "emit"]
 
@@ -58,6 +59,20 @@ class fkd_server_stats(ctypes.Structure):
                 ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
                 ("fps", ctypes.c_double), ("mean_batch", ctypes.c_double),
                 ("bytes_in_use", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t)]
+
+
+class fkd_launch_config(ctypes.Structure):
+    _fields_ = [("tile_h", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32)]
+
+
+def _lc_dict(c: fkd_launch_config) -> dict:
+    return {"tile_w": 128, "tile_h": c.tile_h, "warps_per_cta": c.warps_per_cta,
+            "ctas_per_sm": c.ctas_per_sm}
+
+
+def _lc(cfg: dict) -> fkd_launch_config:
+    return fkd_launch_config(cfg["tile_h"], cfg["warps_per_cta"], cfg["ctas_per_sm"])
 
 
 class FkdError(RuntimeError):
@@ -117,6 +132,14 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.fkd_server_poll.argtypes = [vp, c_int, P(ctypes.c_int64), vp, c_size, P(c_size)]
     lib.fkd_server_drain.argtypes = [vp, c_int]
     lib.fkd_server_get_stats.argtypes = [vp, P(fkd_server_stats), c_int]
+    lib.fkd_get_launch_config.argtypes = [vp, P(fkd_launch_config)]
+    lib.fkd_set_launch_config.argtypes = [vp, P(fkd_launch_config)]
+    lib.fkd_autotune.argtypes = [vp, vp, c_size, c_size, c_int, c_int, P(fkd_launch_config),
+                                 P(ctypes.c_float)]
+    lib.fkd_group_get_launch_config.argtypes = [vp, P(fkd_launch_config)]
+    lib.fkd_group_set_launch_config.argtypes = [vp, P(fkd_launch_config)]
+    lib.fkd_group_autotune.argtypes = [vp, c_int, P(c_int), c_int, P(vp), P(c_size), c_int,
+                                       P(fkd_launch_config), P(ctypes.c_float)]
     for name in EXPORTS:
         if name != "fkd_last_error":
             getattr(lib, name).restype = c_int
@@ -251,6 +274,25 @@ class Stream:
     def reset(self):
         _check(_lib.fkd_reset_stream(self._h))
 
+    # -- detection launch shape
+    def launch_config(self) -> dict:
+        c = fkd_launch_config()
+        _check(_lib.fkd_get_launch_config(self._h, ctypes.byref(c)))
+        return _lc_dict(c)
+
+    def set_launch_config(self, cfg: dict):
+        c = _lc(cfg)
+        _check(_lib.fkd_set_launch_config(self._h, ctypes.byref(c)))
+
+    def autotune(self, frames, reps: int = 2) -> tuple[dict, float]:
+        """Time every launch shape on T device frames (torch CUDA uint8,
+        T x H x W), keep the fastest; resets the stream. Returns (shape, ms)."""
+        assert _is_torch_cuda(frames) and frames.stride(2) == 1
+        c, ms = fkd_launch_config(), ctypes.c_float()
+        _check(_lib.fkd_autotune(self._h, _ptr(frames), frames.stride(1), frames.stride(0),
+                                 frames.shape[0], reps, ctypes.byref(c), ctypes.byref(ms)))
+        return _lc_dict(c), ms.value
+
     def profile_enable(self, on: bool = True):
         _check(_lib.fkd_profile_enable(self._h, int(on)))
 
@@ -311,6 +353,30 @@ class Group:
 
     def use_graph(self, on: bool):
         _check(_lib.fkd_group_use_graph(self._h, int(on)))
+
+    def launch_config(self) -> dict:
+        c = fkd_launch_config()
+        _check(_lib.fkd_group_get_launch_config(self._h, ctypes.byref(c)))
+        return _lc_dict(c)
+
+    def set_launch_config(self, cfg: dict):
+        c = _lc(cfg)
+        _check(_lib.fkd_group_set_launch_config(self._h, ctypes.byref(c)))
+
+    def autotune(self, ids, ticks, reps: int = 2) -> tuple[dict, float]:
+        """ticks: list of m lists, each holding one torch CUDA uint8 (H x W)
+        frame per id. Times every launch shape over the m ticks, keeps the
+        fastest and resets every stream of the group. Returns (shape, ms)."""
+        n, m = len(ids), len(ticks)
+        ia = (ctypes.c_int * n)(*ids)
+        flat = [f for tick in ticks for f in tick]
+        assert len(flat) == n * m
+        fa = (ctypes.c_void_p * (n * m))(*[f.data_ptr() for f in flat])
+        pa = (ctypes.c_size_t * n)(*[f.stride(0) for f in ticks[0]])
+        c, ms = fkd_launch_config(), ctypes.c_float()
+        _check(_lib.fkd_group_autotune(self._h, n, ia, m, fa, pa, reps, ctypes.byref(c),
+                                       ctypes.byref(ms)))
+        return _lc_dict(c), ms.value
 
     def synchronize(self):
         _check(_lib.fkd_group_synchronize(self._h))
