@@ -43,7 +43,18 @@ __device__ __forceinline__ int d_off_rt(int i) {
     if (j < i) o = r16(o + d_side(j) * d_side(j));
   return o;
 }
-constexpr int kLocalBins = 1024;
+constexpr int kLocalBins = 256;  // bins a tile may span and still sum in shared memory
+
+// Dynamic shared memory of a CTA: the tile's levels (c_0 first), then -- when
+// the change sums may be needed -- the previous frame's c_0 (all its levels
+// when the mask layer is not c_0), then the tile's bin sums.
+__host__ __device__ constexpr int prv_bytes(bool diff, int mask_layer) {
+  return !diff ? 0 : mask_layer > 0 ? kPyrSmem : P * P;
+}
+__host__ __device__ constexpr int pyr_smem(bool diff, int mask_layer) {
+  return kPyrSmem + prv_bytes(diff, mask_layer) + (diff ? kLocalBins * 4 : 0);
+}
+static_assert(kPyrSmem % 16 == 0 && (P * P) % 16 == 0, "16-byte aligned regions");
 
 __device__ __forceinline__ uint32_t ld32(const uint8_t* p) {
   return *reinterpret_cast<const uint32_t*>(p);
@@ -229,14 +240,15 @@ __device__ __forceinline__ void build(const Geometry& g, uint8_t* pyr, uint8_t* 
 // sums (if `diff`), and a copy of the c_0 tile to `keep` (if not null, pitch
 // `keep_pitch`). Ends with a barrier, so a CTA can run it again at once.
 template <int O, int INTRA>
-__device__ __forceinline__ void pyramid_tile(const Geometry& g, const Tables& tb, const uint8_t* frame,
-                                             int pitch, const uint8_t* prevf, int prev_pitch,
-                                             bool diff, uint8_t* pyr, unsigned long long* gsum,
-                                             int gstride, uint8_t* keep, int keep_pitch, int tx, int ty) {
-  __shared__ __align__(16) uint8_t cur[kPyrSmem];
-  __shared__ __align__(16) uint8_t prv[kPyrSmem];
-  __shared__ uint32_t bins[kLocalBins];
+__device__ __forceinline__ void pyramid_tile(uint8_t* smem, const Geometry& g, const Tables& tb,
+                                             const uint8_t* frame, int pitch, const uint8_t* prevf,
+                                             int prev_pitch, bool diff, uint8_t* pyr,
+                                             unsigned long long* gsum, int gstride, uint8_t* keep,
+                                             int keep_pitch, int tx, int ty) {
   __shared__ uint16_t tcol[P], trow[P];
+  uint8_t* cur = smem;
+  uint8_t* prv = smem + kPyrSmem;
+  uint32_t* bins = reinterpret_cast<uint32_t*>(prv + prv_bytes(true, g.mask_layer));
 
   load_c0(cur, frame, pitch, tx * P, ty * P, g.W, g.H);
   const int ml = g.mask_layer;
@@ -358,20 +370,22 @@ __device__ __forceinline__ void pyramid_tile(const Geometry& g, const Tables& tb
 template <int O, int INTRA>
 __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Geometry g, Tables tb, Batch b, Scratch s,
                                                          Params p) {
+  extern __shared__ __align__(16) uint8_t smem[];
   const int k = blockIdx.z;
   const uint8_t* frame = b.frames + (long long)k * b.frame_stride;
   const bool diff = p.mask_mode == FKD_MASK_ID && (b.first_frame + k) > 0;
   const uint8_t* pf = k == 0 ? b.prev : frame - b.frame_stride;
   const int pp = k == 0 ? b.prev_pitch : b.pitch;
-  pyramid_tile<O, INTRA>(g, tb, frame, b.pitch, pf, pp, diff, s.pyr + (long long)k * g.pyr_bytes,
+  pyramid_tile<O, INTRA>(smem, g, tb, frame, b.pitch, pf, pp, diff, s.pyr + (long long)k * g.pyr_bytes,
                          s.bsum + k, s.bsum_stride, nullptr, 0, blockIdx.x, blockIdx.y);
 }
 
 // Group tick: persistent CTAs over the c_0 tiles of every participating frame.
 template <int O, int INTRA>
-__global__ void __launch_bounds__(kPyrThreads) k_group_pyramid(const StreamDev* devs,
+__global__ void __launch_bounds__(kPyrThreads, 4) k_group_pyramid(const StreamDev* devs,
                                                                const TickHeader* hdr,
                                                                const TickItem* items) {
+  extern __shared__ __align__(16) uint8_t smem[];
   const int n = hdr->n_items, total = hdr->total_pyr;
   for (int j = blockIdx.x; j < total; j += gridDim.x) {
     const int i = find_item(n, j, [&](int q) { return items[q].pyr_base; });
@@ -381,7 +395,7 @@ __global__ void __launch_bounds__(kPyrThreads) k_group_pyramid(const StreamDev* 
     const int tx = local % d.g.pyr_tiles_x, ty = local / d.g.pyr_tiles_x;
     const bool diff = d.p.mask_mode == FKD_MASK_ID && it.frame_index > 0;
     const int kp = d.g.layer[0].pitch;
-    pyramid_tile<O, INTRA>(d.g, d.tb, it.frame, it.pitch, d.last[(it.frame_index + 1) & 1], kp, diff,
+    pyramid_tile<O, INTRA>(smem, d.g, d.tb, it.frame, it.pitch, d.last[(it.frame_index + 1) & 1], kp, diff,
                            d.s.pyr, d.s.bsum, 1, d.last[it.frame_index & 1], kp, tx, ty);
   }
 }
@@ -390,13 +404,15 @@ template <int O, int INTRA>
 void launch_t(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s, const Params& p,
               cudaStream_t st) {
   dim3 grid(g.pyr_tiles_x, g.pyr_tiles_y, b.T);
-  k_pyramid<O, INTRA><<<grid, kPyrThreads, 0, st>>>(g, tb, b, s, p);
+  const int smem = pyr_smem(p.mask_mode == FKD_MASK_ID, g.mask_layer);
+  k_pyramid<O, INTRA><<<grid, kPyrThreads, smem, st>>>(g, tb, b, s, p);
 }
 
 template <int O, int INTRA>
 void launch_group_t(const StreamDev* devs, const TickHeader* hdr, const TickItem* items, int grid,
                     cudaStream_t st) {
-  k_group_pyramid<O, INTRA><<<grid, kPyrThreads, 0, st>>>(devs, hdr, items);
+  // streams of a group may use any mask layer: room for the largest layout
+  k_group_pyramid<O, INTRA><<<grid, kPyrThreads, pyr_smem(true, 1), st>>>(devs, hdr, items);
 }
 
 }  // namespace
@@ -421,7 +437,8 @@ int group_pyramid_grid(int O, int intra) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, table[intra ? 1 : 0][O - 1], kPyrThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, table[intra ? 1 : 0][O - 1], kPyrThreads,
+                                                pyr_smem(true, 1));
   return max(1, sms) * max(1, per_sm);
 }
 
