@@ -245,7 +245,7 @@ __device__ __forceinline__ void pyramid_tile(uint8_t* smem, const Geometry& g, c
                                              int prev_pitch, bool diff, uint8_t* pyr,
                                              unsigned long long* gsum, int gstride, uint8_t* keep,
                                              int keep_pitch, int tx, int ty) {
-  __shared__ uint16_t tcol[P], trow[P];
+  __shared__ uint16_t tcol[P], trow[P], trun[P];
   uint8_t* cur = smem;
   uint8_t* prv = smem + kPyrSmem;
   uint32_t* bins = reinterpret_cast<uint32_t*>(prv + prv_bytes(true, g.mask_layer));
@@ -264,7 +264,14 @@ __device__ __forceinline__ void pyramid_tile(uint8_t* smem, const Geometry& g, c
     for (int q = threadIdx.x; q < kLocalBins; q += NT) bins[q] = 0;
     for (int q = threadIdx.x; q < mn; q += NT) {
       tcol[q] = q < mnx ? tb.colblk[mlg.col_off + mgx0 + q] : 0;
-      trow[q] = q < mny ? tb.rowblk[mlg.row_off + mgy0 + q] : 0;
+      const unsigned r = q < mny ? tb.rowblk[mlg.row_off + mgy0 + q] : 0u;
+      trow[q] = (uint16_t)r;
+      // end of the tile's run of rows in bin row r: layer row y is in bin
+      // row floor(floor(y*S/2) * N_r / H) (Eq. 3), so bin row r + 1 starts
+      // at row ceil(2 * ceil((r+1)*H/N_r) / S)
+      const unsigned qh = ((r + 1u) * (unsigned)g.H + (unsigned)g.N_r - 1u) / (unsigned)g.N_r;
+      const int next = (int)((2u * qh + (unsigned)mlg.S - 1u) / (unsigned)mlg.S) - mgy0;
+      trun[q] = (uint16_t)min(next, mny);
     }
   }
   cp_async_commit();
@@ -305,34 +312,45 @@ __device__ __forceinline__ void pyramid_tile(uint8_t* smem, const Geometry& g, c
       else atomicAdd(&gsum[(long long)(rb * g.N_c + cb) * gstride], (unsigned long long)v);
     };
     if ((mn & 3) == 0) {
-      const int wcols = (mnx + 3) / 4;
-      const int groups = max(1, NT / wcols);
-      const int rows_per = (mny + groups - 1) / groups;
-      const int wc = threadIdx.x % wcols, grp = threadIdx.x / wcols;
-      if (grp < groups) {
-        const int x = 4 * wc;
+      // warp w takes a band of rows, lane l the 4-pixel word column l
+      static_assert(P / 4 <= 32 && NT == 256, "one lane per word column, 8 row bands");
+      const int lane = threadIdx.x & 31, band = threadIdx.x >> 5;
+      const int wcols = (mnx + 3) >> 2;
+      const int rows_per = (mny + 7) >> 3;
+      const int ya = band * rows_per, yb = min(mny, ya + rows_per);
+      if (lane < wcols && ya < yb) {
+        const int x = 4 * lane;
         const int nv = min(4, mnx - x);
         const uint32_t vmask = nv == 4 ? 0xffffffffu : ((1u << (8 * nv)) - 1u);
         const int c0 = tcol[x], c3 = tcol[x + nv - 1];
-        uint32_t acc = 0, acc_hi = 0;
-        int rb_cur = -1;
-        const int y_end = min(mny, (grp + 1) * rows_per);
-        for (int y = grp * rows_per; y < y_end; ++y) {
-          const int rb = trow[y];
-          if (rb != rb_cur) {
-            if (rb_cur >= 0) {
-              flush(rb_cur, c0, acc);
-              if (c3 != c0) flush(rb_cur, c3, acc_hi);
-            }
-            rb_cur = rb;
-            acc = acc_hi = 0;
+        if (c3 == c0) {
+          // the word lies in one bin column: one sum per run of rows of one bin row
+          for (int y = ya; y < yb;) {
+            const int rb = trow[y], e = min(yb, (int)trun[y]);
+            const uint8_t* pa = A + y * mn + x;
+            const uint8_t* pb = B + y * mn + x;
+            uint32_t run = 0;
+#pragma unroll 4
+            for (int yy = y; yy < e; ++yy, pa += mn, pb += mn) run += __vsadu4(ld32(pa) & vmask, ld32(pb) & vmask);
+            flush(rb, c0, run);
+            y = e;
           }
-          const uint32_t a = ld32(A + y * mn + x) & vmask, c = ld32(B + y * mn + x) & vmask;
-          if (c3 == c0) {
-            acc += __vsadu4(a, c);
-          } else {
-            // the word straddles bin columns: split it pixel by pixel (bins
-            // narrower than 4 pixels put middle pixels in further bins)
+        } else {
+          // the word straddles bin columns: split it pixel by pixel (bins
+          // narrower than 4 pixels put middle pixels in further bins)
+          uint32_t acc = 0, acc_hi = 0;
+          int rb_cur = -1;
+          for (int y = ya; y < yb; ++y) {
+            const int rb = trow[y];
+            if (rb != rb_cur) {
+              if (rb_cur >= 0) {
+                flush(rb_cur, c0, acc);
+                flush(rb_cur, c3, acc_hi);
+              }
+              rb_cur = rb;
+              acc = acc_hi = 0;
+            }
+            const uint32_t a = ld32(A + y * mn + x) & vmask, c = ld32(B + y * mn + x) & vmask;
             for (int i = 0; i < nv; ++i) {
               const int ci = tcol[x + i];
               const uint32_t d = __vabsdiffu4((a >> (8 * i)) & 0xffu, (c >> (8 * i)) & 0xffu);
@@ -341,10 +359,10 @@ __device__ __forceinline__ void pyramid_tile(uint8_t* smem, const Geometry& g, c
               else flush(rb, ci, d);
             }
           }
-        }
-        if (rb_cur >= 0) {
-          flush(rb_cur, c0, acc);
-          if (c3 != c0) flush(rb_cur, c3, acc_hi);
+          if (rb_cur >= 0) {
+            flush(rb_cur, c0, acc);
+            flush(rb_cur, c3, acc_hi);
+          }
         }
       }
     } else {
