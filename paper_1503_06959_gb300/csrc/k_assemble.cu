@@ -19,6 +19,9 @@
 namespace fkd {
 namespace {
 
+constexpr int kEmitList = 4096;  // set bits of a chunk emitted from a shared list (denser chunks: per thread)
+static_assert(kAsmChunkWords * 32 <= 65536, "word * 32 + bit fits 16 bits");
+
 
 __device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -60,12 +63,14 @@ __device__ __forceinline__ uint32_t merge_word(const Geometry& g, const Tables& 
   return word;
 }
 
-// Merge and count one chunk of frame k: each warp adds its popcounts to the
+// Merge and count one chunk of frame k: the CTA adds its popcount to the
 // chunk's and the frame's counters (zeroed by the active-tile kernel). With
-// s.bases, the warp that finishes last of `total_warps` also turns the T frame
-// totals into record offsets. No block-wide barrier.
+// s.bases, the CTA that finishes last of `total_ctas` also turns the T frame
+// totals into record offsets. Ends with a barrier.
 __device__ __forceinline__ void count_chunk(const Geometry& g, const Tables& tb, const Scratch& s,
-                                            const State& st, int k, int chunk, int T, int total_warps) {
+                                            const State& st, int k, int chunk, int T, int total_ctas) {
+  __shared__ uint32_t red[kAsmThreads / 32];
+  __shared__ int last_cta;
   const AsmChunk ch = tb.chunks[chunk];
   const LayerGeom& lg = g.layer[ch.layer];
   const int wpr = lg.wpr;
@@ -92,19 +97,21 @@ __device__ __forceinline__ void count_chunk(const Geometry& g, const Tables& tb,
     }
   }
   const int lane = threadIdx.x & 31;
-  cnt = __reduce_add_sync(0xffffffffu, cnt);
-  bool last_warp = false;
-  if (lane == 0) {
+  cnt = block_sum(cnt, red);
+  if (threadIdx.x == 0) {
     if (cnt) {
       atomicAdd(&s.chunk_counts[(long long)k * g.n_chunks + chunk], cnt);
       atomicAdd(&s.frame_totals[k], cnt);
     }
+    bool last = false;
     if (s.bases) {
       __threadfence();
-      last_warp = atomicAdd(s.done, 1u) == (unsigned)(total_warps - 1);
+      last = atomicAdd(s.done, 1u) == (unsigned)(total_ctas - 1);
     }
+    last_cta = last;
   }
-  if (__shfl_sync(0xffffffffu, (int)last_warp, 0)) {
+  __syncthreads();
+  if (last_cta && threadIdx.x < 32) {
     // exclusive scan of the frame totals, 32 at a time
     __threadfence();
     uint32_t carry = 0;
@@ -125,6 +132,7 @@ __device__ __forceinline__ void count_chunk(const Geometry& g, const Tables& tb,
       *s.done = 0u;
     }
   }
+  __syncthreads();  // red and last_cta are reused by the next chunk of this CTA
 }
 
 __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb, const Scratch& s,
@@ -140,6 +148,7 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
   __shared__ uint32_t red[kAsmThreads / 32];
   __shared__ uint32_t wsum[kAsmThreads / 32];
   __shared__ __align__(16) uint32_t stage_words[kAsmChunkWords];
+  __shared__ uint16_t pos[kEmitList];  // set bits of the chunk in order: word * 32 + bit
   const bool last = k == T - 1;
   const AsmChunk ch = tb.chunks[chunk];
   const LayerGeom& lg = g.layer[ch.layer];
@@ -212,11 +221,65 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
   }
   if (lane == 31) wsum[wid] = incl;
   __syncthreads();
-  uint32_t before = 0;
-  for (int q = 0; q < wid; ++q) before += wsum[q];
-  unsigned long long idx = call_base + frame_base + chunk_base + before + incl - cnt;
-  if (cnt) emit_records(g, tb, s, st, out, k, last, ch, lg, j0, words, idx);
-  __syncthreads();  // red and wsum are reused by the next chunk of this CTA
+  uint32_t before = 0, total = 0;
+#pragma unroll
+  for (int q = 0; q < kAsmThreads / 32; ++q) {
+    before += q < wid ? wsum[q] : 0u;
+    total += wsum[q];
+  }
+  const unsigned long long base = call_base + frame_base + chunk_base;
+  if (total > (uint32_t)kEmitList) {
+    // a dense chunk: every thread emits its own words' records
+    if (cnt) emit_records(g, tb, s, st, out, k, last, ch, lg, j0, words, base + before + incl - cnt);
+    __syncthreads();  // red and wsum are reused by the next chunk of this CTA
+    return;
+  }
+  // list the set bits in order, then emit one record per thread (balanced,
+  // and consecutive threads write consecutive records)
+  uint32_t at = before + incl - cnt;
+#pragma unroll
+  for (int jj = 0; jj < kAsmWordsPerThread; ++jj) {
+    uint32_t wv = words[jj];
+    while (wv) {
+      const int bit = __ffs(wv) - 1;
+      wv &= wv - 1;
+      pos[at++] = (uint16_t)((j0 + jj) * 32 + bit);
+    }
+  }
+  __syncthreads();
+  const int wpr_ = wpr;
+  const float inv_wpr = 1.0f / (float)wpr_;
+  const int* src_k = s.src + (long long)k * g.NB;
+  const uint16_t* colblk = tb.colblk + lg.col_off;
+  for (uint32_t i = threadIdx.x; i < total; i += kAsmThreads) {
+    const int p = pos[i];
+    const int j = p >> 5;
+    int yy = __float2int_rz((float)j * inv_wpr);  // j / wpr, fixed up below
+    if (yy * wpr_ > j) --yy;
+    if ((yy + 1) * wpr_ <= j) ++yy;
+    const int y = ch.y0 + yy;
+    const int x = (j - yy * wpr_) * 32 + (p & 31);
+    const int r = tb.rowblk[lg.row_off + y];
+    const int c = colblk[x];
+    const int sf = src_k[r * g.N_c + c];
+    const long long so = lg.score_off + (long long)y * lg.pitch + x;
+    const uint8_t score = sf < 0 ? st.score_in[so] : s.det_score[(long long)sf * g.score_bytes + so];
+    const uint32_t flags = sf != k ? FKD_KP_PROPAGATED : 0u;
+    const unsigned long long idx = base + i;
+    if (idx < (unsigned long long)out.cap) {
+      uint2 rec;
+      rec.x = (uint32_t)x | ((uint32_t)y << 16);
+      rec.y = (uint32_t)ch.layer | ((uint32_t)score << 8) | (flags << 16);
+      reinterpret_cast<uint2*>(out.rec)[idx] = rec;
+    } else {
+      *s.overflow = 1;
+    }
+    if (last) {
+      st.score_out[so] = score;
+      atomicAdd(&st.cnt_out[r * g.N_c + c], 1u);
+    }
+  }
+  __syncthreads();  // red, wsum and pos are reused by the next chunk of this CTA
 }
 
 __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb, const Scratch& s,
@@ -265,7 +328,7 @@ __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb
 }
 
 __global__ void __launch_bounds__(kAsmThreads) k_count(Geometry g, Tables tb, Scratch s, State st, int T) {
-  count_chunk(g, tb, s, st, blockIdx.y, blockIdx.x, T, gridDim.x * gridDim.y * (kAsmThreads / 32));
+  count_chunk(g, tb, s, st, blockIdx.y, blockIdx.x, T, gridDim.x * gridDim.y);
 }
 
 __global__ void __launch_bounds__(kAsmThreads) k_emit(Geometry g, Tables tb, Batch b, Scratch s,
