@@ -33,12 +33,12 @@ namespace {
 constexpr int TW = kDetTW;   // output pixels per tile row: one 4-pixel word per lane
 constexpr int IN_W = TW + 32;  // input row: x in [x0-16, x0+TW+16)
 constexpr int SC_P = TW + 8;   // score row pitch; column = x - x0 + 4
-constexpr int LIST = 512;      // candidate list window per warp (entries)
+constexpr int RING = 256;      // candidate pixels waiting to be scored, per warp (power of two)
 constexpr int PASS = 256;      // passing-pixel list per warp (entries); beyond it the pass bitmap is scanned
 constexpr int NBUF = 1;        // input buffers per warp (2: the next tile loads during this one; no gain measured)
 constexpr int MIN_BLOCKS = 2;  // 256-thread CTAs resident per SM the register budget is sized for
 static_assert(TW == 32 * 4, "one 4-pixel word per lane per row");
-static_assert(LIST >= 256 && LIST <= 65535, "a flush leaves room for one more row (128)");
+static_assert(RING >= 64 + 128 && (RING & (RING - 1)) == 0, "a round leaves < 64, an expansion adds <= 128");
 
 // Per-warp sizes for a tile height TH (output rows y0 .. y0+TH-1).
 template <int TH>
@@ -48,8 +48,11 @@ struct Shape {
   static constexpr int IN_BYTES = IN_W * IN_H;
   static constexpr int SC_BYTES = SC_P * SC_H;
   static constexpr int DET_WORDS = TH * (TW / 32);
-  // input buffer(s), score map, keypoint and pass bitmaps, candidate and pass lists
-  static constexpr int WARP_SMEM = NBUF * IN_BYTES + SC_BYTES + 2 * DET_WORDS * 4 + LIST * 2 + PASS * 2;
+  static constexpr int WLIST = (SC_H * 34 + 7) / 8 * 8;  // candidate words: 32 per score row + 2 edge words
+  // input buffer(s), score map, keypoint and pass bitmaps, candidate words,
+  // candidate ring and pass list
+  static constexpr int WARP_SMEM =
+      NBUF * IN_BYTES + SC_BYTES + 2 * DET_WORDS * 4 + WLIST * 2 + RING * 2 + PASS * 2;
   static_assert(TH % 8 == 0 && TH + 4 <= 32, "one lane per dilated score row; whole 32-word rounds");
   static_assert(IN_BYTES % 16 == 0 && SC_BYTES % 16 == 0, "16-byte aligned slices");
 };
@@ -287,6 +290,12 @@ __device__ __forceinline__ void stage(uint8_t* in, const Item& it, int lane) {
   }
 }
 
+// Bit 7 of each byte of `keep` gathered into a nibble (byte i -> bit i): the
+// four bits land on distinct positions of the product, so nothing carries.
+__device__ __forceinline__ uint32_t nibble(uint32_t keep) {
+  return (((keep >> 7) & 0x01010101u) * 0x00204081u >> 21) & 0xfu;
+}
+
 // Score-map offset of the pixel at input offset o.
 __device__ __forceinline__ int sc_of(int o) { return (o / IN_W - 3) * SC_P + (o % IN_W) - 12; }
 
@@ -300,8 +309,9 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
   uint8_t* sc = inbuf + NBUF * IN_BYTES;
   uint32_t* detw = reinterpret_cast<uint32_t*>(sc + SC_BYTES);
   uint32_t* passw = detw + DET_WORDS;
-  uint16_t* list = reinterpret_cast<uint16_t*>(passw + DET_WORDS);
-  uint16_t* plist = list + LIST;
+  uint16_t* wlist = reinterpret_cast<uint16_t*>(passw + DET_WORDS);
+  uint16_t* ring = wlist + Sh::WLIST;
+  uint16_t* plist = ring + RING;
 
   const uint32_t count_items = src.count();
   const uint32_t stride = gridDim.x * warps;
@@ -340,65 +350,22 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
     const bool t1_high = t1 >= 128u;
     const bool none = t1 > 255u;
 
-    // B+C. prefilter the score rows y0-1 .. y0+TH (input rows 3 .. TH+4), lane
-    //      -> word x0+4*lane .. +3; candidates go to the warp's list with one
-    //      ballot per byte position, and the list is scored -- two candidates
-    //      per lane, 64 per round -- whenever it fills up and at the end. A
-    //      pixel of the tile scoring >= t goes to the pass list (and bitmap).
+    // B. prefilter the score rows y0-1 .. y0+TH (input rows 3 .. TH+4), lane
+    //    -> word x0+4*lane .. +3, and the two edge columns; words holding
+    //    candidates are compacted (one ballot per row) into the word list as
+    //    (input offset / 4) << 4 | candidate nibble.
     const bool interior = x0 - 1 >= 3 && x0 + TW < w - 3 && y0 - 1 >= 3 && y0 + TH < h - 3;
     const uint32_t act = active_rows<TH>(it, lane);
     const uint32_t act_any = __reduce_or_sync(0xffffffffu, act);
     const unsigned lt = (1u << lane) - 1u;
-    int count = 0;  // candidates in the list (warp-uniform)
+    int nw = 0;     // words in the list (warp-uniform)
     int npass = 0;  // passing tile pixels (warp-uniform)
-    auto flush = [&]() {
-      __syncwarp();
-      for (int base = 0; base < count; base += 64) {
-        const int i1 = base + 2 * lane;
-        bool pass[2] = {false, false};
-        int po[2] = {0, 0};
-        if (i1 < count) {
-          const bool two = i1 + 1 < count;
-          const int o1 = list[i1], o2 = two ? list[i1 + 1] : o1;
-          const uint32_t sp = score_pair(in, o1, o2);
-#pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            if (j == 0 || two) {
-              const int o = j ? o2 : o1;
-              const uint32_t v = (sp >> (16 * j)) & 0xffffu;
-              const bool ok = v >= t;
-              sc[sc_of(o)] = ok ? (uint8_t)v : 0;
-              const int r = o / IN_W, c = o % IN_W;  // tile pixel: rows 4..TH+3, cols 16..TW+15
-              if (ok && r >= 4 && r < TH + 4 && c >= 16 && c < TW + 16) {
-                const int ly = r - 4, lx = c - 16;
-                atomicOr(&passw[ly * (TW / 32) + (lx >> 5)], 1u << (lx & 31));
-                pass[j] = true;
-                po[j] = o;
-              }
-            }
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const unsigned bal = __ballot_sync(0xffffffffu, pass[j]);
-          const int at = npass + __popc(bal & lt);
-          if (pass[j] && at < PASS) plist[at] = (uint16_t)po[j];
-          npass += __popc(bal);
-        }
-      }
-      __syncwarp();
-      count = 0;
-    };
-    // keep: bit 7 of byte i set -> candidate at input offset o0 + i
-    auto append = [&](uint32_t keep, int o0) {
-      if (!__any_sync(0xffffffffu, keep)) return;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const unsigned bal = __ballot_sync(0xffffffffu, (keep >> (8 * i + 7)) & 1u);
-        if ((bal >> lane) & 1u) list[count + __popc(bal & lt)] = (uint16_t)(o0 + i);
-        count += __popc(bal);
-      }
-      if (count > LIST - 128) flush();
+    // keep: bit 7 of byte i set -> candidate at input offset o0 + i (o0 % 4 == 0)
+    auto add_word = [&](uint32_t keep, int o0) {
+      const uint32_t nib = nibble(keep);
+      const unsigned bal = __ballot_sync(0xffffffffu, nib != 0u);
+      if (nib) wlist[nw + __popc(bal & lt)] = (uint16_t)(((o0 >> 2) << 4) | nib);
+      nw += __popc(bal);
     };
     if (!none && act_any) {
       const int c = 16 + 4 * lane;
@@ -409,7 +376,7 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
         for (int i = 0; i < 4; ++i)
           if (x + i < 3 || x + i >= w - 3) colmask &= ~(0x80u << (8 * i));
       }
-#pragma unroll 1
+#pragma unroll 2
       for (int rr = 0; rr < SC_H; ++rr) {
         if (!((act_any >> rr) & 1u)) continue;  // no lane needs this row
         uint32_t keep = prefilter(in, (rr + 3) * IN_W + c, t1_low7, t1_high) & colmask;
@@ -418,7 +385,7 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
           const int y = y0 - 1 + rr;
           if (y < 3 || y >= h - 3) keep = 0;
         }
-        append(keep, (rr + 3) * IN_W + c);
+        add_word(keep, (rr + 3) * IN_W + c);
       }
       // the score region's edge columns x0-1 and x0+TW: lane rr < SC_H owns
       // row rr; they are needed when the tile's first / last word is
@@ -434,10 +401,66 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
             kr = prefilter(in, r + 16 + TW, t1_low7, t1_high) & 0x80u;
         }
       }
-      append(kl, (lane + 3) * IN_W + 12);
-      append(kr, (lane + 3) * IN_W + 16 + TW);
+      add_word(kl, (lane + 3) * IN_W + 12);
+      add_word(kr, (lane + 3) * IN_W + 16 + TW);
     }
-    if (count) flush();
+    __syncwarp();
+
+    // C. expand the words 32 at a time into candidate pixels (a ring), and
+    //    score the ring 64 at a time -- two candidates per lane in 16-bit
+    //    lanes. A pixel of the tile scoring >= t goes to the pass list (and
+    //    the pass bitmap).
+    int head = 0, tail = 0;  // ring positions (warp-uniform), taken mod RING
+    auto score_round = [&](int n) {
+      const int i1 = 2 * lane;
+      bool pass[2] = {false, false};
+      int po[2] = {0, 0};
+      if (i1 < n) {
+        const bool two = i1 + 1 < n;
+        const int o1 = ring[(tail + i1) & (RING - 1)];
+        const int o2 = two ? ring[(tail + i1 + 1) & (RING - 1)] : o1;
+        const uint32_t sp = score_pair(in, o1, o2);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          if (j == 0 || two) {
+            const int o = j ? o2 : o1;
+            const uint32_t v = (sp >> (16 * j)) & 0xffffu;
+            const bool ok = v >= t;
+            sc[sc_of(o)] = ok ? (uint8_t)v : 0;
+            const int r = o / IN_W, cc = o % IN_W;  // tile pixel: rows 4..TH+3, cols 16..TW+15
+            if (ok && r >= 4 && r < TH + 4 && cc >= 16 && cc < TW + 16) {
+              const int ly = r - 4, lx = cc - 16;
+              atomicOr(&passw[ly * (TW / 32) + (lx >> 5)], 1u << (lx & 31));
+              pass[j] = true;
+              po[j] = o;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const unsigned bal = __ballot_sync(0xffffffffu, pass[j]);
+        const int at = npass + __popc(bal & lt);
+        if (pass[j] && at < PASS) plist[at] = (uint16_t)po[j];
+        npass += __popc(bal);
+      }
+      tail += n;
+    };
+    for (int wb = 0; wb < nw; wb += 32) {
+      const uint32_t e = wb + lane < nw ? wlist[wb + lane] : 0u;
+      const uint32_t m = e & 15u;
+      const int o0 = (int)(e >> 4) << 2;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const unsigned bal = __ballot_sync(0xffffffffu, (m >> b) & 1u);
+        if ((m >> b) & 1u) ring[(head + __popc(bal & lt)) & (RING - 1)] = (uint16_t)(o0 + b);
+        head += __popc(bal);
+      }
+      __syncwarp();
+      while (head - tail >= 64) score_round(64);
+    }
+    if (head > tail) score_round(head - tail);
+    __syncwarp();
 
     // D. strict 3x3 maxima among the tile's passing pixels: from the pass
     //    list, or from the pass bitmap when the list overflowed
