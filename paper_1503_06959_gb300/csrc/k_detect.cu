@@ -52,7 +52,7 @@ struct Shape {
   // input buffer(s), score map, keypoint and pass bitmaps, candidate words,
   // candidate ring and pass list
   static constexpr int WARP_SMEM =
-      NBUF * IN_BYTES + SC_BYTES + 2 * DET_WORDS * 4 + WLIST * 2 + RING * 2 + PASS * 2;
+      NBUF * IN_BYTES + SC_BYTES + 2 * DET_WORDS * 4 + WLIST * 4 + RING * 2 + PASS * 2;
   static_assert(TH % 8 == 0 && TH + 4 <= 32, "one lane per dilated score row; whole 32-word rounds");
   static_assert(IN_BYTES % 16 == 0 && SC_BYTES % 16 == 0, "16-byte aligned slices");
 };
@@ -290,12 +290,6 @@ __device__ __forceinline__ void stage(uint8_t* in, const Item& it, int lane) {
   }
 }
 
-// Bit 7 of each byte of `keep` gathered into a nibble (byte i -> bit i): the
-// four bits land on distinct positions of the product, so nothing carries.
-__device__ __forceinline__ uint32_t nibble(uint32_t keep) {
-  return (((keep >> 7) & 0x01010101u) * 0x00204081u >> 21) & 0xfu;
-}
-
 // Score-map offset of the pixel at input offset o.
 __device__ __forceinline__ int sc_of(int o) { return (o / IN_W - 3) * SC_P + (o % IN_W) - 12; }
 
@@ -309,8 +303,8 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
   uint8_t* sc = inbuf + NBUF * IN_BYTES;
   uint32_t* detw = reinterpret_cast<uint32_t*>(sc + SC_BYTES);
   uint32_t* passw = detw + DET_WORDS;
-  uint16_t* wlist = reinterpret_cast<uint16_t*>(passw + DET_WORDS);
-  uint16_t* ring = wlist + Sh::WLIST;
+  uint32_t* wlist = passw + DET_WORDS;
+  uint16_t* ring = reinterpret_cast<uint16_t*>(wlist + Sh::WLIST);
   uint16_t* plist = ring + RING;
 
   const uint32_t count_items = src.count();
@@ -352,22 +346,31 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
 
     // B. prefilter the score rows y0-1 .. y0+TH (input rows 3 .. TH+4), lane
     //    -> word x0+4*lane .. +3, and the two edge columns; words holding
-    //    candidates are compacted (one ballot per row) into the word list as
-    //    (input offset / 4) << 4 | candidate nibble.
+    //    candidates are compacted (one ballot per row) into the word list,
+    //    each entry the prefilter bits (bit 7 of byte i: pixel i) with the
+    //    score row in bits 0-4 and the word column + 1 (0: left edge, 33:
+    //    right edge) in bits 8-13.
     const bool interior = x0 - 1 >= 3 && x0 + TW < w - 3 && y0 - 1 >= 3 && y0 + TH < h - 3;
-    const uint32_t act = active_rows<TH>(it, lane);
-    const uint32_t act_any = __reduce_or_sync(0xffffffffu, act);
     const unsigned lt = (1u << lane) - 1u;
     int nw = 0;     // words in the list (warp-uniform)
     int npass = 0;  // passing tile pixels (warp-uniform)
-    // keep: bit 7 of byte i set -> candidate at input offset o0 + i (o0 % 4 == 0)
-    auto add_word = [&](uint32_t keep, int o0) {
-      const uint32_t nib = nibble(keep);
-      const unsigned bal = __ballot_sync(0xffffffffu, nib != 0u);
-      if (nib) wlist[nw + __popc(bal & lt)] = (uint16_t)(((o0 >> 2) << 4) | nib);
+    auto add_word = [&](uint32_t entry) {
+      const unsigned bal = __ballot_sync(0xffffffffu, (entry & 0x80808080u) != 0u);
+      if (entry & 0x80808080u) wlist[nw + __popc(bal & lt)] = entry;
       nw += __popc(bal);
     };
-    if (!none && act_any) {
+    // rows this lane's word must score: active bins, inside the scorable band
+    uint32_t rows = active_rows<TH>(it, lane);
+    if (!interior) {
+#pragma unroll
+      for (int rr = 0; rr < SC_H; ++rr) {
+        const int y = y0 - 1 + rr;
+        if (y < 3 || y >= h - 3) rows &= ~(1u << rr);
+      }
+    }
+    constexpr uint32_t kAllRows = (SC_H == 32) ? 0xffffffffu : ((1u << SC_H) - 1u);
+    const uint32_t rows_any = __reduce_or_sync(0xffffffffu, rows);
+    if (!none && rows_any) {
       const int c = 16 + 4 * lane;
       const int x = x0 + 4 * lane;
       uint32_t colmask = 0x80808080u;  // pixels of this word inside the scorable band
@@ -376,33 +379,33 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
         for (int i = 0; i < 4; ++i)
           if (x + i < 3 || x + i >= w - 3) colmask &= ~(0x80u << (8 * i));
       }
+      const uint32_t code = (uint32_t)(lane + 1) << 8;
+      if (__all_sync(0xffffffffu, (rows & kAllRows) == kAllRows)) {
+        // every row of every word: no per-row tests
 #pragma unroll 2
-      for (int rr = 0; rr < SC_H; ++rr) {
-        if (!((act_any >> rr) & 1u)) continue;  // no lane needs this row
-        uint32_t keep = prefilter(in, (rr + 3) * IN_W + c, t1_low7, t1_high) & colmask;
-        if (!((act >> rr) & 1u)) keep = 0;
-        if (!interior) {
-          const int y = y0 - 1 + rr;
-          if (y < 3 || y >= h - 3) keep = 0;
+        for (int rr = 0; rr < SC_H; ++rr)
+          add_word((prefilter(in, (rr + 3) * IN_W + c, t1_low7, t1_high) & colmask) | code | (uint32_t)rr);
+      } else {
+#pragma unroll 2
+        for (int rr = 0; rr < SC_H; ++rr) {
+          if (!((rows_any >> rr) & 1u)) continue;  // no lane needs this row
+          const uint32_t keep = ((rows >> rr) & 1u) ? prefilter(in, (rr + 3) * IN_W + c, t1_low7, t1_high) & colmask : 0u;
+          add_word(keep | code | (uint32_t)rr);
         }
-        add_word(keep, (rr + 3) * IN_W + c);
       }
       // the score region's edge columns x0-1 and x0+TW: lane rr < SC_H owns
       // row rr; they are needed when the tile's first / last word is
-      const uint32_t act_l = __shfl_sync(0xffffffffu, act, 0), act_r = __shfl_sync(0xffffffffu, act, 31);
+      const uint32_t rows_l = __shfl_sync(0xffffffffu, rows, 0), rows_r = __shfl_sync(0xffffffffu, rows, 31);
       uint32_t kl = 0, kr = 0;
       if (lane < SC_H) {
-        const int y = y0 - 1 + lane;
-        if (y >= 3 && y < h - 3) {
-          const int r = (lane + 3) * IN_W;
-          if (((act_l >> lane) & 1u) && x0 - 1 >= 3 && x0 - 1 < w - 3)
-            kl = prefilter(in, r + 12, t1_low7, t1_high) & 0x80000000u;
-          if (((act_r >> lane) & 1u) && x0 + TW >= 3 && x0 + TW < w - 3)
-            kr = prefilter(in, r + 16 + TW, t1_low7, t1_high) & 0x80u;
-        }
+        const int r = (lane + 3) * IN_W;
+        if (((rows_l >> lane) & 1u) && x0 - 1 >= 3 && x0 - 1 < w - 3)
+          kl = prefilter(in, r + 12, t1_low7, t1_high) & 0x80000000u;
+        if (((rows_r >> lane) & 1u) && x0 + TW >= 3 && x0 + TW < w - 3)
+          kr = prefilter(in, r + 16 + TW, t1_low7, t1_high) & 0x80u;
       }
-      add_word(kl, (lane + 3) * IN_W + 12);
-      add_word(kr, (lane + 3) * IN_W + 16 + TW);
+      add_word(kl | (uint32_t)lane);
+      add_word(kr | (33u << 8) | (uint32_t)lane);
     }
     __syncwarp();
 
@@ -448,12 +451,14 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
     };
     for (int wb = 0; wb < nw; wb += 32) {
       const uint32_t e = wb + lane < nw ? wlist[wb + lane] : 0u;
-      const uint32_t m = e & 15u;
-      const int o0 = (int)(e >> 4) << 2;
+      // input offset of the word's first pixel: row (score row + 3), column
+      // 16 + 4 * word column = 12 + 4 * (word column + 1)
+      const int o0 = (int)((e & 31u) + 3u) * IN_W + 12 + 4 * (int)((e >> 8) & 63u);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const unsigned bal = __ballot_sync(0xffffffffu, (m >> b) & 1u);
-        if ((m >> b) & 1u) ring[(head + __popc(bal & lt)) & (RING - 1)] = (uint16_t)(o0 + b);
+        const bool has = (e >> (8 * b + 7)) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, has);
+        if (has) ring[(head + __popc(bal & lt)) & (RING - 1)] = (uint16_t)(o0 + b);
         head += __popc(bal);
       }
       __syncwarp();
