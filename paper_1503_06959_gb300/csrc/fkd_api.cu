@@ -309,7 +309,8 @@ int allocate_state(fkd_stream* s) {
       (rc = s->alloc(&sc.merged, (size_t)(T * std::max(g.bit_words, 1LL)))) ||
       (rc = s->alloc(&sc.bases, (size_t)(T + 1))) || (rc = s->alloc(&sc.done, 1)) ||
       (rc = s->alloc(&sc.frame_totals, (size_t)T)) || (rc = s->alloc(&sc.out_base, 2)) ||
-      (rc = s->alloc(&sc.overflow, 1)) || (rc = s->alloc(&sc.tile_stats, 2)))
+      (rc = s->alloc(&sc.overflow, 1)) || (rc = s->alloc(&sc.tile_stats, 2)) ||
+      (rc = s->alloc(&sc.ml_prev, (size_t)g.layer[g.mask_layer].pitch * std::max(g.layer[g.mask_layer].h, 1))))
     return rc;
   CK(cudaMemset(sc.tile_stats, 0, 16));
   CK(cudaMemset(sc.done, 0, 4));

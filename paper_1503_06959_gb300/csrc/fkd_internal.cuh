@@ -147,6 +147,7 @@ struct Scratch {
   unsigned long long* out_base;    // [2]: running output offset (ping-pong)
   int* overflow;                   // [1]
   unsigned long long* tile_stats;  // [2]: detection tiles and their layer pixels (running totals)
+  uint8_t* ml_prev;                // the mask layer of the stream's last frame (mask layers above c_0)
 };
 
 // The kept keypoint set D_{n-1} as a per-pixel bitmap + score map, ping-pong.

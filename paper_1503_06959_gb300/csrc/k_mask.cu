@@ -5,10 +5,41 @@
 namespace fkd {
 namespace {
 
+// Sum of |L_k - L_{k-1}| over the pixels of `bin` in the mask layer (a layer
+// above c_0), from the pyramid buffers of the batch; L_{-1} is the stream's
+// copy of the previous batch's last frame. Layer row y is in bin row
+// floor(floor(y*S/2) * N_r / H) (Eq. 3), so bin row r starts at row
+// ceil(2 * ceil(r*H/N_r) / S); columns come from the bin-column starts.
+__device__ __forceinline__ unsigned long long layer_change(const Geometry& g, const Tables& tb, const Batch& b,
+                                                           const Scratch& s, int bin, int k) {
+  const LayerGeom& lg = g.layer[g.mask_layer];
+  const int r = bin / g.N_c, c = bin % g.N_c;
+  const int x0 = tb.xstart[lg.xs_off + c], x1 = tb.xstart[lg.xs_off + c + 1];
+  auto row_start = [&](int rr) {
+    const long long q = ((long long)rr * g.H + g.N_r - 1) / g.N_r;
+    return (int)min((long long)lg.h, (2 * q + lg.S - 1) / lg.S);
+  };
+  const int y0 = row_start(r), y1 = row_start(r + 1);
+  const uint8_t* cur = s.pyr + (long long)k * g.pyr_bytes + lg.pyr_off;
+  const uint8_t* prv = k > 0 ? cur - g.pyr_bytes : s.ml_prev;
+  unsigned long long sum = 0;
+  for (int y = y0; y < y1; ++y) {
+    uint32_t row = 0;
+    for (int x = x0; x < x1; ++x) {
+      const int d = (int)cur[(long long)y * lg.pitch + x] - (int)prv[(long long)y * lg.pitch + x];
+      row += (uint32_t)(d < 0 ? -d : d);
+    }
+    sum += row;
+  }
+  return sum;
+}
+
 // One CTA per bin, walking the batch's frames 256 at a time.
 //   mask:  first frame of the stream or FKD_MASK_FULL -> 1; FKD_MASK_ID ->
 //          sum |L_n - L_{n-1}| > T_I * (pixels of the bin) (Eq. 2 read as
-//          "detect where the content changed"); FKD_MASK_KB -> keypoints of
+//          "detect where the content changed"), the sums of c_0 coming from
+//          the pyramid kernel and those of a coarser mask layer computed
+//          here from the batch's pyramids; FKD_MASK_KB -> keypoints of
 //          D_{n-1} in the bin >= T_H (Eqs. 3-4, batches of one frame).
 //   src:   Eq. 1 applied frame after frame means a bin of frame k shows the
 //          detections of the last frame m <= k in which the bin was active;
@@ -34,6 +65,8 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Ba
       const long long n = b.first_frame + k;
       if (n == 0 || p.mask_mode == FKD_MASK_FULL) {
         m = 1;
+      } else if (p.mask_mode == FKD_MASK_ID && g.mask_layer > 0) {
+        m = layer_change(g, tb, b, s, bin, k) > (unsigned long long)p.T_I * tb.npix[bin];
       } else if (p.mask_mode == FKD_MASK_ID) {
         unsigned long long* sum = s.bsum + (long long)bin * s.bsum_stride + k;
         m = *sum > (unsigned long long)p.T_I * tb.npix[bin];
@@ -60,6 +93,19 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Ba
     if (k < b.T) s.src[(long long)k * g.NB + bin] = max(v, before);
     carry = all;
     __syncthreads();
+  }
+  if (p.mask_mode == FKD_MASK_ID && g.mask_layer > 0) {
+    // the batch's last frame becomes L_{n-1} of the next batch (this bin's
+    // pixels only; frame 0 read the old ones before the barrier above)
+    const LayerGeom& lg = g.layer[g.mask_layer];
+    const int r = bin / g.N_c, c = bin % g.N_c;
+    const int x0 = tb.xstart[lg.xs_off + c], x1 = tb.xstart[lg.xs_off + c + 1];
+    const uint8_t* last = s.pyr + (long long)(b.T - 1) * g.pyr_bytes + lg.pyr_off;
+    for (int y = 0; y < lg.h; ++y) {
+      if (tb.rowblk[lg.row_off + y] != r) continue;
+      for (int x = x0 + tid; x < x1; x += kMaskThreads)
+        s.ml_prev[(long long)y * lg.pitch + x] = last[(long long)y * lg.pitch + x];
+    }
   }
 }
 

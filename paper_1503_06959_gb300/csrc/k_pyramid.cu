@@ -391,7 +391,8 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Geometry g, Tables tb, 
   extern __shared__ __align__(16) uint8_t smem[];
   const int k = blockIdx.z;
   const uint8_t* frame = b.frames + (long long)k * b.frame_stride;
-  const bool diff = p.mask_mode == FKD_MASK_ID && (b.first_frame + k) > 0;
+  // change sums of c_0 here; those of a coarser mask layer in the mask kernel
+  const bool diff = p.mask_mode == FKD_MASK_ID && g.mask_layer == 0 && (b.first_frame + k) > 0;
   const uint8_t* pf = k == 0 ? b.prev : frame - b.frame_stride;
   const int pp = k == 0 ? b.prev_pitch : b.pitch;
   pyramid_tile<O, INTRA>(smem, g, tb, frame, b.pitch, pf, pp, diff, s.pyr + (long long)k * g.pyr_bytes,
@@ -422,7 +423,7 @@ template <int O, int INTRA>
 void launch_t(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s, const Params& p,
               cudaStream_t st) {
   dim3 grid(g.pyr_tiles_x, g.pyr_tiles_y, b.T);
-  const int smem = pyr_smem(p.mask_mode == FKD_MASK_ID, g.mask_layer);
+  const int smem = pyr_smem(p.mask_mode == FKD_MASK_ID && g.mask_layer == 0, g.mask_layer);
   k_pyramid<O, INTRA><<<grid, kPyrThreads, smem, st>>>(g, tb, b, s, p);
 }
 

@@ -116,16 +116,48 @@ def test_config2_full_detection(clip2):
     assert {int(l) for l in rec["layer"]} == set(range(8)), "every layer must yield keypoints"
 
 
-@pytest.mark.parametrize("mask_layer", [-1, 3])
+def push_in_pieces(s, frames, pieces, exp_kp, exp_m):
+    """Feed frames as batches of the given sizes (1 = fkd_push_frame) and
+    compare every frame with the oracle."""
+    n = 0
+    for T in pieces:
+        if T == 1:
+            s.push_frame(frames[n])
+            assert_same_kp(s.get_keypoints(), exp_kp[n], f"frame {n}")
+            np.testing.assert_array_equal(s.get_mask(), exp_m[n])
+        else:
+            rec, off, masks = s.push_frames(frames[n:n + T])
+            for k, kp in enumerate(fkd.split_frames(rec, off)):
+                assert_same_kp(kp, exp_kp[n + k], f"frame {n + k}")
+                np.testing.assert_array_equal(masks[k], exp_m[n + k])
+        n += T
+    assert n == len(frames)
+
+
+@pytest.mark.parametrize("mask_layer", [-1, 3, 1])
 def test_mask_on_coarser_layer(clip2, mask_layer):
+    # the change sums of a coarser layer carry the previous batch's last
+    # frame across batches, single pushes and the camera step at frame 30
     cfg, frames = clip2
     g, o = both(params(cfg, mask_layer=mask_layer), "id")
-    exp_kp, exp_m = run_oracle(frames[:8], **o)
-    s = fkd.Stream(cfg.W, cfg.H, T_max=8, **g)
-    rec, off, masks = s.push_frames(frames[:8])
-    for k, kp in enumerate(fkd.split_frames(rec, off)):
-        assert_same_kp(kp, exp_kp[k], f"frame {k}")
-        np.testing.assert_array_equal(masks[k], exp_m[k])
+    exp_kp, exp_m = run_oracle(frames, **o)
+    s = fkd.Stream(cfg.W, cfg.H, T_max=14, **g)
+    push_in_pieces(s, frames, [8, 12, 1, 1, 14], exp_kp, exp_m)
+    assert any(m.sum() < m.size for m in exp_m[1:]), "the clip must have inactive bins"
+
+
+@pytest.mark.parametrize("W,H,O,intra,mask_layer", [
+    (333, 207, 3, 1, -1), (333, 207, 3, 1, 1), (97, 61, 2, 0, -1), (200, 150, 6, 1, -1)])
+def test_coarse_mask_layer_ragged(W, H, O, intra, mask_layer):
+    src = synth.VideoSource(W, H, seed=W + H + O, n_rect=10, n_movers=2, mover_size=min(W, H) // 3,
+                            speed=(1, 3))
+    frames = src.frames(9)
+    g, o = both(dict(N_r=5, N_c=7, T_I=2, O=O, intra=intra, t=10, mask_layer=mask_layer), "id")
+    exp_kp, exp_m = run_oracle(frames, **o)
+    s = fkd.Stream(W, H, T_max=4, **g)
+    push_in_pieces(s, frames, [3, 1, 4, 1], exp_kp, exp_m)
+    s.reset()
+    push_in_pieces(s, frames[:5], [2, 3], exp_kp[:5], exp_m[:5])
 
 
 @pytest.mark.parametrize("W,H,O,intra,N_r,N_c", [
