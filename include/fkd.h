@@ -294,8 +294,9 @@ int fkd_autotune(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t fram
  * every stream is bit-identical to feeding its frames to its own fkd_stream
  * one by one. All streams of a group share O and intra (the pyramid kernel
  * is compiled per octave count); every other parameter is per stream.
- * Streams keep device copies of their last two frames, so a tick's frames
- * may come from transient buffers.
+ * Streams keep on the device what the next frame's mask needs (copies of
+ * their last two frames for change sums on c_0, or of the last frame's
+ * coarser mask layer), so a tick's frames may come from transient buffers.
  */
 typedef struct fkd_group fkd_group;
 

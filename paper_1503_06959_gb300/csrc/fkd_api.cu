@@ -1031,8 +1031,11 @@ int fkd_group_add_stream(fkd_group* G, const fkd_params* p, int W, int H, int* s
   if (rc) return rc;
   GroupStream gs;
   gs.s = s;
+  // copies of the last two frames, for change sums on c_0 (coarser mask
+  // layers keep their own copy of the layer)
   const size_t lbytes = (size_t)s->g.layer[0].pitch * (size_t)H;
-  for (int i = 0; i < 2; ++i)
+  const bool c0_sums = s->p.mask_mode == FKD_MASK_ID && s->g.mask_layer == 0;
+  for (int i = 0; i < 2 && c0_sums; ++i)
     if ((rc = s->alloc(&gs.last[i], lbytes))) {
       fkd_destroy_stream(s);
       return rc;

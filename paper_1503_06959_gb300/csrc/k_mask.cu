@@ -5,28 +5,32 @@
 namespace fkd {
 namespace {
 
-// Sum of |L_k - L_{k-1}| over the pixels of `bin` in the mask layer (a layer
-// above c_0), from the pyramid buffers of the batch; L_{-1} is the stream's
-// copy of the previous batch's last frame. Layer row y is in bin row
+// The pixels of `bin` in the mask layer: columns [x0, x1) from the bin-column
+// starts; rows [y0, y1), since layer row y is in bin row
 // floor(floor(y*S/2) * N_r / H) (Eq. 3), so bin row r starts at row
-// ceil(2 * ceil(r*H/N_r) / S); columns come from the bin-column starts.
-__device__ __forceinline__ unsigned long long layer_change(const Geometry& g, const Tables& tb, const Batch& b,
-                                                           const Scratch& s, int bin, int k) {
+// ceil(2 * ceil(r*H/N_r) / S).
+struct BinRect {
+  int x0, x1, y0, y1;
+};
+__device__ __forceinline__ BinRect bin_rect(const Geometry& g, const Tables& tb, int bin) {
   const LayerGeom& lg = g.layer[g.mask_layer];
   const int r = bin / g.N_c, c = bin % g.N_c;
-  const int x0 = tb.xstart[lg.xs_off + c], x1 = tb.xstart[lg.xs_off + c + 1];
   auto row_start = [&](int rr) {
     const long long q = ((long long)rr * g.H + g.N_r - 1) / g.N_r;
     return (int)min((long long)lg.h, (2 * q + lg.S - 1) / lg.S);
   };
-  const int y0 = row_start(r), y1 = row_start(r + 1);
-  const uint8_t* cur = s.pyr + (long long)k * g.pyr_bytes + lg.pyr_off;
-  const uint8_t* prv = k > 0 ? cur - g.pyr_bytes : s.ml_prev;
+  return BinRect{tb.xstart[lg.xs_off + c], tb.xstart[lg.xs_off + c + 1], row_start(r), row_start(r + 1)};
+}
+
+// Sum of |L_n - L_{n-1}| over the pixels of `bin` in the mask layer (a layer
+// above c_0, row pitch `pitch` in both buffers).
+__device__ __forceinline__ unsigned long long layer_change(const BinRect& br, const uint8_t* cur,
+                                                           const uint8_t* prv, int pitch) {
   unsigned long long sum = 0;
-  for (int y = y0; y < y1; ++y) {
+  for (int y = br.y0; y < br.y1; ++y) {
     uint32_t row = 0;
-    for (int x = x0; x < x1; ++x) {
-      const int d = (int)cur[(long long)y * lg.pitch + x] - (int)prv[(long long)y * lg.pitch + x];
+    for (int x = br.x0; x < br.x1; ++x) {
+      const int d = (int)cur[(long long)y * pitch + x] - (int)prv[(long long)y * pitch + x];
       row += (uint32_t)(d < 0 ? -d : d);
     }
     sum += row;
@@ -66,7 +70,11 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Ba
       if (n == 0 || p.mask_mode == FKD_MASK_FULL) {
         m = 1;
       } else if (p.mask_mode == FKD_MASK_ID && g.mask_layer > 0) {
-        m = layer_change(g, tb, b, s, bin, k) > (unsigned long long)p.T_I * tb.npix[bin];
+        // L_{n-1} of the batch's first frame: the previous batch's last frame
+        const LayerGeom& lg = g.layer[g.mask_layer];
+        const uint8_t* cur = s.pyr + (long long)k * g.pyr_bytes + lg.pyr_off;
+        const uint8_t* prv = k > 0 ? cur - g.pyr_bytes : s.ml_prev;
+        m = layer_change(bin_rect(g, tb, bin), cur, prv, lg.pitch) > (unsigned long long)p.T_I * tb.npix[bin];
       } else if (p.mask_mode == FKD_MASK_ID) {
         unsigned long long* sum = s.bsum + (long long)bin * s.bsum_stride + k;
         m = *sum > (unsigned long long)p.T_I * tb.npix[bin];
@@ -98,14 +106,11 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Ba
     // the batch's last frame becomes L_{n-1} of the next batch (this bin's
     // pixels only; frame 0 read the old ones before the barrier above)
     const LayerGeom& lg = g.layer[g.mask_layer];
-    const int r = bin / g.N_c, c = bin % g.N_c;
-    const int x0 = tb.xstart[lg.xs_off + c], x1 = tb.xstart[lg.xs_off + c + 1];
+    const BinRect br = bin_rect(g, tb, bin);
     const uint8_t* last = s.pyr + (long long)(b.T - 1) * g.pyr_bytes + lg.pyr_off;
-    for (int y = 0; y < lg.h; ++y) {
-      if (tb.rowblk[lg.row_off + y] != r) continue;
-      for (int x = x0 + tid; x < x1; x += kMaskThreads)
+    for (int y = br.y0; y < br.y1; ++y)
+      for (int x = br.x0 + tid; x < br.x1; x += kMaskThreads)
         s.ml_prev[(long long)y * lg.pitch + x] = last[(long long)y * lg.pitch + x];
-    }
   }
 }
 
@@ -157,11 +162,25 @@ __global__ void k_group_mask(const StreamDev* devs, const TickHeader* hdr, const
     int m;
     if (it.frame_index == 0 || d.p.mask_mode == FKD_MASK_FULL) {
       m = 1;
+    } else if (d.p.mask_mode == FKD_MASK_ID && d.g.mask_layer > 0) {
+      // a coarser mask layer: this frame's layer against the stream's copy
+      // of the previous one, which then takes this frame's pixels of the bin
+      const LayerGeom& lg = d.g.layer[d.g.mask_layer];
+      const uint8_t* cur = d.s.pyr + lg.pyr_off;
+      const BinRect br = bin_rect(d.g, d.tb, bin);
+      m = layer_change(br, cur, d.s.ml_prev, lg.pitch) > (unsigned long long)d.p.T_I * d.tb.npix[bin];
     } else if (d.p.mask_mode == FKD_MASK_ID) {
       m = d.s.bsum[bin] > (unsigned long long)d.p.T_I * d.tb.npix[bin];
       d.s.bsum[bin] = 0;
     } else {
       m = d.state_cnt[it.state_cur][bin] >= (uint32_t)d.p.T_H;
+    }
+    if (d.p.mask_mode == FKD_MASK_ID && d.g.mask_layer > 0) {
+      const LayerGeom& lg = d.g.layer[d.g.mask_layer];
+      const BinRect br = bin_rect(d.g, d.tb, bin);
+      for (int y = br.y0; y < br.y1; ++y)
+        for (int x = br.x0; x < br.x1; ++x)
+          d.s.ml_prev[(long long)y * lg.pitch + x] = d.s.pyr[lg.pyr_off + (long long)y * lg.pitch + x];
     }
     d.s.mask[bin] = (uint8_t)m;
     d.s.src[bin] = m ? 0 : -1;

@@ -28,32 +28,12 @@ __host__ __device__ constexpr int c_off(int i) { return i == 0 ? 0 : r16(c_off(i
 __host__ __device__ constexpr int d_off(int i) { return i == 0 ? r16(c_off(6)) : r16(d_off(i - 1) + d_side(i - 1) * d_side(i - 1)); }
 constexpr int kPyrSmem = d_off(6);
 
-// Offsets of a level chosen at run time (no recursion in device code).
-__device__ __forceinline__ int c_off_rt(int i) {
-  int o = 0;
-#pragma unroll
-  for (int j = 0; j < 6; ++j)
-    if (j < i) o = r16(o + c_side(j) * c_side(j));
-  return o;
-}
-__device__ __forceinline__ int d_off_rt(int i) {
-  int o = d_off(0);
-#pragma unroll
-  for (int j = 0; j < 6; ++j)
-    if (j < i) o = r16(o + d_side(j) * d_side(j));
-  return o;
-}
 constexpr int kLocalBins = 256;  // bins a tile may span and still sum in shared memory
 
 // Dynamic shared memory of a CTA: the tile's levels (c_0 first), then -- when
-// the change sums may be needed -- the previous frame's c_0 (all its levels
-// when the mask layer is not c_0), then the tile's bin sums.
-__host__ __device__ constexpr int prv_bytes(bool diff, int mask_layer) {
-  return !diff ? 0 : mask_layer > 0 ? kPyrSmem : P * P;
-}
-__host__ __device__ constexpr int pyr_smem(bool diff, int mask_layer) {
-  return kPyrSmem + prv_bytes(diff, mask_layer) + (diff ? kLocalBins * 4 : 0);
-}
+// the change sums of c_0 may be needed -- the previous frame's c_0 tile and
+// the tile's bin sums.
+__host__ __device__ constexpr int pyr_smem(bool diff) { return kPyrSmem + (diff ? P * P + kLocalBins * 4 : 0); }
 static_assert(kPyrSmem % 16 == 0 && (P * P) % 16 == 0, "16-byte aligned regions");
 
 __device__ __forceinline__ uint32_t ld32(const uint8_t* p) {
@@ -236,9 +216,10 @@ __device__ __forceinline__ void build(const Geometry& g, uint8_t* pyr, uint8_t* 
   }
 }
 
-// One 96 x 96 tile of c_0 of one frame: pyramid, layer writes, per-bin change
-// sums (if `diff`), and a copy of the c_0 tile to `keep` (if not null, pitch
-// `keep_pitch`). Ends with a barrier, so a CTA can run it again at once.
+// One 96 x 96 tile of c_0 of one frame: pyramid, layer writes, per-bin sums
+// of |I_n - I_{n-1}| on c_0 (if `diff`; the mask layer is c_0), and a copy of
+// the c_0 tile to `keep` (if not null, pitch `keep_pitch`). Ends with a
+// barrier, so a CTA can run it again at once.
 template <int O, int INTRA>
 __device__ __forceinline__ void pyramid_tile(uint8_t* smem, const Geometry& g, const Tables& tb,
                                              const uint8_t* frame, int pitch, const uint8_t* prevf,
@@ -248,15 +229,11 @@ __device__ __forceinline__ void pyramid_tile(uint8_t* smem, const Geometry& g, c
   __shared__ uint16_t tcol[P], trow[P], trun[P];
   uint8_t* cur = smem;
   uint8_t* prv = smem + kPyrSmem;
-  uint32_t* bins = reinterpret_cast<uint32_t*>(prv + prv_bytes(true, g.mask_layer));
+  uint32_t* bins = reinterpret_cast<uint32_t*>(prv + P * P);
 
   load_c0(cur, frame, pitch, tx * P, ty * P, g.W, g.H);
-  const int ml = g.mask_layer;
-  const LayerGeom& mlg = g.layer[ml];
-  const bool ml_d = INTRA && (ml & 1);
-  const int ml_i = INTRA ? ml >> 1 : ml;
-  const int mn = ml_d ? d_side(ml_i) : c_side(ml_i);
-  const int moff = ml_d ? d_off_rt(ml_i) : c_off_rt(ml_i);
+  const LayerGeom& mlg = g.layer[0];
+  constexpr int mn = P;
   const int mgx0 = tx * mn, mgy0 = ty * mn;
   const int mnx = min(mn, mlg.w - mgx0), mny = min(mn, mlg.h - mgy0);
   if (diff) {
@@ -296,80 +273,71 @@ __device__ __forceinline__ void pyramid_tile(uint8_t* smem, const Geometry& g, c
   }
   build<O, INTRA, true>(g, pyr, cur, tx, ty, g.L - 1);
   if (diff && mnx > 0 && mny > 0) {
-    if (ml > 0) build<O, INTRA, false>(g, pyr, prv, tx, ty, ml);
-    // Per-bin sums of |L_n - L_{n-1}| on the mask layer. Thread -> a 4-pixel
+    // Per-bin sums of |I_n - I_{n-1}| on c_0. Thread -> a 4-pixel
     // column word and a band of rows; the running sum is flushed into a
     // shared bin whenever the bin row changes (and split by pixel when the
     // word's pixels straddle bin columns).
     const int cb_lo = tcol[0], rb_lo = trow[0];
     const int ncols = tcol[mnx - 1] - cb_lo + 1, nrows = trow[mny - 1] - rb_lo + 1;
     const bool local = ncols * nrows <= kLocalBins;
-    const uint8_t* A = cur + moff;
-    const uint8_t* B = prv + moff;
+    const uint8_t* A = cur;
+    const uint8_t* B = prv;
     auto flush = [&](int rb, int cb, uint32_t v) {
       if (!v) return;
       if (local) atomicAdd(&bins[(rb - rb_lo) * ncols + (cb - cb_lo)], v);
       else atomicAdd(&gsum[(long long)(rb * g.N_c + cb) * gstride], (unsigned long long)v);
     };
-    if ((mn & 3) == 0) {
-      // warp w takes a band of rows, lane l the 4-pixel word column l
-      static_assert(P / 4 <= 32 && NT == 256, "one lane per word column, 8 row bands");
-      const int lane = threadIdx.x & 31, band = threadIdx.x >> 5;
-      const int wcols = (mnx + 3) >> 2;
-      const int rows_per = (mny + 7) >> 3;
-      const int ya = band * rows_per, yb = min(mny, ya + rows_per);
-      if (lane < wcols && ya < yb) {
-        const int x = 4 * lane;
-        const int nv = min(4, mnx - x);
-        const uint32_t vmask = nv == 4 ? 0xffffffffu : ((1u << (8 * nv)) - 1u);
-        const int c0 = tcol[x], c3 = tcol[x + nv - 1];
-        if (c3 == c0) {
-          // the word lies in one bin column: one sum per run of rows of one bin row
-          for (int y = ya; y < yb;) {
-            const int rb = trow[y], e = min(yb, (int)trun[y]);
-            const uint8_t* pa = A + y * mn + x;
-            const uint8_t* pb = B + y * mn + x;
-            uint32_t run = 0;
+    // warp w takes a band of rows, lane l the 4-pixel word column l
+    static_assert(P / 4 <= 32 && NT == 256, "one lane per word column, 8 row bands");
+    const int lane = threadIdx.x & 31, band = threadIdx.x >> 5;
+    const int wcols = (mnx + 3) >> 2;
+    const int rows_per = (mny + 7) >> 3;
+    const int ya = band * rows_per, yb = min(mny, ya + rows_per);
+    if (lane < wcols && ya < yb) {
+      const int x = 4 * lane;
+      const int nv = min(4, mnx - x);
+      const uint32_t vmask = nv == 4 ? 0xffffffffu : ((1u << (8 * nv)) - 1u);
+      const int c0 = tcol[x], c3 = tcol[x + nv - 1];
+      if (c3 == c0) {
+        // the word lies in one bin column: one sum per run of rows of one bin row
+        for (int y = ya; y < yb;) {
+          const int rb = trow[y], e = min(yb, (int)trun[y]);
+          const uint8_t* pa = A + y * mn + x;
+          const uint8_t* pb = B + y * mn + x;
+          uint32_t run = 0;
 #pragma unroll 4
-            for (int yy = y; yy < e; ++yy, pa += mn, pb += mn) run += __vsadu4(ld32(pa) & vmask, ld32(pb) & vmask);
-            flush(rb, c0, run);
-            y = e;
-          }
-        } else {
-          // the word straddles bin columns: split it pixel by pixel (bins
-          // narrower than 4 pixels put middle pixels in further bins)
-          uint32_t acc = 0, acc_hi = 0;
-          int rb_cur = -1;
-          for (int y = ya; y < yb; ++y) {
-            const int rb = trow[y];
-            if (rb != rb_cur) {
-              if (rb_cur >= 0) {
-                flush(rb_cur, c0, acc);
-                flush(rb_cur, c3, acc_hi);
-              }
-              rb_cur = rb;
-              acc = acc_hi = 0;
+          for (int yy = y; yy < e; ++yy, pa += mn, pb += mn) run += __vsadu4(ld32(pa) & vmask, ld32(pb) & vmask);
+          flush(rb, c0, run);
+          y = e;
+        }
+      } else {
+        // the word straddles bin columns: split it pixel by pixel (bins
+        // narrower than 4 pixels put middle pixels in further bins)
+        uint32_t acc = 0, acc_hi = 0;
+        int rb_cur = -1;
+        for (int y = ya; y < yb; ++y) {
+          const int rb = trow[y];
+          if (rb != rb_cur) {
+            if (rb_cur >= 0) {
+              flush(rb_cur, c0, acc);
+              flush(rb_cur, c3, acc_hi);
             }
-            const uint32_t a = ld32(A + y * mn + x) & vmask, c = ld32(B + y * mn + x) & vmask;
-            for (int i = 0; i < nv; ++i) {
-              const int ci = tcol[x + i];
-              const uint32_t d = __vabsdiffu4((a >> (8 * i)) & 0xffu, (c >> (8 * i)) & 0xffu);
-              if (ci == c0) acc += d;
-              else if (ci == c3) acc_hi += d;
-              else flush(rb, ci, d);
-            }
+            rb_cur = rb;
+            acc = acc_hi = 0;
           }
-          if (rb_cur >= 0) {
-            flush(rb_cur, c0, acc);
-            flush(rb_cur, c3, acc_hi);
+          const uint32_t a = ld32(A + y * mn + x) & vmask, c = ld32(B + y * mn + x) & vmask;
+          for (int i = 0; i < nv; ++i) {
+            const int ci = tcol[x + i];
+            const uint32_t d = __vabsdiffu4((a >> (8 * i)) & 0xffu, (c >> (8 * i)) & 0xffu);
+            if (ci == c0) acc += d;
+            else if (ci == c3) acc_hi += d;
+            else flush(rb, ci, d);
           }
         }
-      }
-    } else {
-      for (int q = threadIdx.x; q < mnx * mny; q += NT) {
-        const int y = q / mnx, x = q % mnx;
-        const int dv = (int)A[y * mn + x] - (int)B[y * mn + x];
-        flush(trow[y], tcol[x], (uint32_t)(dv < 0 ? -dv : dv));
+        if (rb_cur >= 0) {
+          flush(rb_cur, c0, acc);
+          flush(rb_cur, c3, acc_hi);
+        }
       }
     }
     if (local) {
@@ -412,10 +380,13 @@ __global__ void __launch_bounds__(kPyrThreads, 4) k_group_pyramid(const StreamDe
     const StreamDev& d = devs[it.sid];
     const int local = j - it.pyr_base;
     const int tx = local % d.g.pyr_tiles_x, ty = local / d.g.pyr_tiles_x;
-    const bool diff = d.p.mask_mode == FKD_MASK_ID && it.frame_index > 0;
+    // change sums of c_0 here, against the stream's copy of its last frame;
+    // those of a coarser mask layer in the mask kernel
+    const bool c0_sums = d.p.mask_mode == FKD_MASK_ID && d.g.mask_layer == 0;
+    const bool diff = c0_sums && it.frame_index > 0;
     const int kp = d.g.layer[0].pitch;
     pyramid_tile<O, INTRA>(smem, d.g, d.tb, it.frame, it.pitch, d.last[(it.frame_index + 1) & 1], kp, diff,
-                           d.s.pyr, d.s.bsum, 1, d.last[it.frame_index & 1], kp, tx, ty);
+                           d.s.pyr, d.s.bsum, 1, c0_sums ? d.last[it.frame_index & 1] : nullptr, kp, tx, ty);
   }
 }
 
@@ -423,15 +394,14 @@ template <int O, int INTRA>
 void launch_t(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s, const Params& p,
               cudaStream_t st) {
   dim3 grid(g.pyr_tiles_x, g.pyr_tiles_y, b.T);
-  const int smem = pyr_smem(p.mask_mode == FKD_MASK_ID && g.mask_layer == 0, g.mask_layer);
+  const int smem = pyr_smem(p.mask_mode == FKD_MASK_ID && g.mask_layer == 0);
   k_pyramid<O, INTRA><<<grid, kPyrThreads, smem, st>>>(g, tb, b, s, p);
 }
 
 template <int O, int INTRA>
 void launch_group_t(const StreamDev* devs, const TickHeader* hdr, const TickItem* items, int grid,
                     cudaStream_t st) {
-  // streams of a group may use any mask layer: room for the largest layout
-  k_group_pyramid<O, INTRA><<<grid, kPyrThreads, pyr_smem(true, 1), st>>>(devs, hdr, items);
+  k_group_pyramid<O, INTRA><<<grid, kPyrThreads, pyr_smem(true), st>>>(devs, hdr, items);
 }
 
 }  // namespace
@@ -457,7 +427,7 @@ int group_pyramid_grid(int O, int intra) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, table[intra ? 1 : 0][O - 1], kPyrThreads,
-                                                pyr_smem(true, 1));
+                                                pyr_smem(true));
   return max(1, sms) * max(1, per_sm);
 }
 
