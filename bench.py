@@ -80,7 +80,8 @@ def profile_counters(kernel: str):
 def workload_desc(cfg, frames):
     return (f"{cfg.W}x{cfg.H} uint8 synthetic video, {frames} frames per step, O={cfg.O}"
             f"{' + intra-octaves' if cfg.intra else ''}, {cfg.N_c}x{cfg.N_r} bins (cols x rows), "
-            f"t={cfg.t}, T_I={cfg.T_I}, intensity-difference mask")
+            f"t={cfg.t}, T_I={cfg.T_I}, intensity-difference mask on "
+            f"{'the coarsest octave' if cfg.mask_layer == -1 else 'layer %d' % cfg.mask_layer}")
 
 
 class ClockSampler:
@@ -134,7 +135,7 @@ def cpu_oracle_fps(frames, cfg, seconds: float = 12.0):
     about `seconds` of CPU work: frames/s."""
     import oracle
     s = oracle.Stream(cfg.W, cfg.H, N_r=cfg.N_r, N_c=cfg.N_c, T_I=cfg.T_I, O=cfg.O,
-                      intra=cfg.intra, t=cfg.t, mask_mode=oracle.MASK_ID)
+                      intra=cfg.intra, t=cfg.t, mask_mode=oracle.MASK_ID, mask_layer=cfg.mask_layer)
     t0 = time.perf_counter()
     n = 0
     while n < len(frames) and (time.perf_counter() - t0) < seconds:
@@ -157,7 +158,7 @@ def run_reference(args):
 
     def one_step():
         s = oracle.Stream(cfg.W, cfg.H, N_r=cfg.N_r, N_c=cfg.N_c, T_I=cfg.T_I, O=cfg.O,
-                          intra=cfg.intra, t=cfg.t, mask_mode=oracle.MASK_ID)
+                          intra=cfg.intra, t=cfg.t, mask_mode=oracle.MASK_ID, mask_layer=cfg.mask_layer)
         for f in frames[:frames_per_step]:
             s.push(f)
             s.keypoints()
@@ -192,7 +193,7 @@ def _group_run(streams, frames_dev, mode, warm, ticks_timed, fkd, torch, tune_ti
     for the timed ticks, profile, keypoints per tick, chosen shape)."""
     st = torch.cuda.Stream()
     g = fkd.Group(streams[0].O, streams[0].intra, cuda_stream=st.cuda_stream)
-    ids = [g.add_stream(c.W, c.H, N_r=c.N_r, N_c=c.N_c, T_I=c.T_I, t=c.t, mask_mode=mode,
+    ids = [g.add_stream(c.W, c.H, N_r=c.N_r, N_c=c.N_c, T_I=c.T_I, t=c.t, mask_mode=mode, mask_layer=c.mask_layer,
                         K_max=1 << 17)[0] for c in streams]
     n_frames = frames_dev[0].shape[0]
     shape, tune_ms = g.autotune(ids, [[f[n] for f in frames_dev] for n in range(tune_ticks)], reps=2)
@@ -268,7 +269,8 @@ def run_config5(args):
         st = torch.cuda.Stream()
         g = fkd.Group(cfg.O, cfg.intra, cuda_stream=st.cuda_stream)
         ids = [g.add_stream(cfg.W, cfg.H, N_r=cfg.N_r, N_c=cfg.N_c, T_I=cfg.T_I, t=cfg.t,
-                            mask_mode=mode, K_max=1 << 20)[0] for _ in range(n_streams)]
+                            mask_mode=mode, mask_layer=cfg.mask_layer, K_max=1 << 20)[0]
+               for _ in range(n_streams)]
         segs = {}
         for part, rng in (("moving", range(0, seg)), ("static", range(seg, F))):
             g.synchronize()
@@ -334,7 +336,7 @@ def run_config4(args):
             for j in range(per_res):
                 try:
                     sid = srv.open_stream(W, H, N_r=12, N_c=16, T_I=4, t=30, mask_mode=mode,
-                                          K_max=1 << 17)
+                                          mask_layer=-1, K_max=1 << 17)
                     streams.append((sid, W, H, k * per_res + j))
                 except fkd.FkdError as e:
                     if e.code != fkd.FKD_E_BUDGET:
@@ -431,6 +433,8 @@ def main():
     ap.add_argument("--budget-gb", type=int, default=8)
     ap.add_argument("--segment", type=int, default=20)
     ap.add_argument("--streams-5", type=int, default=8)
+    ap.add_argument("--shape", default="",
+                    help="detection launch shape tile_h,warps_per_cta,ctas_per_sm (default: autotune)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -465,6 +469,7 @@ def main():
     torch_stream = torch.cuda.current_stream()
     handle = torch_stream.cuda_stream
     common = dict(N_r=cfg.N_r, N_c=cfg.N_c, T_I=cfg.T_I, O=cfg.O, intra=cfg.intra, t=cfg.t,
+                  mask_layer=cfg.mask_layer,
                   T_max=T, cuda_stream=handle)
     cap = T * 32768
     out = torch.empty(cap, dtype=torch.int64, device=dev)
@@ -506,8 +511,15 @@ def main():
     masked = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_ID, **common)
     full = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_FULL, **common)
     # detection launch shape: autotuned per stream on the step's own frames
-    shape_masked, tune_ms_masked = masked.autotune(frames, reps=2)
-    shape_full, tune_ms_full = full.autotune(frames, reps=2)
+    if args.shape:
+        th, wp, cp = (int(v) for v in args.shape.split(","))
+        shape_masked = shape_full = dict(tile_h=th, warps_per_cta=wp, ctas_per_sm=cp)
+        masked.set_launch_config(shape_masked)
+        full.set_launch_config(shape_full)
+        tune_ms_masked = tune_ms_full = None
+    else:
+        shape_masked, tune_ms_masked = masked.autotune(frames, reps=2)
+        shape_full, tune_ms_full = full.autotune(frames, reps=2)
 
     # warm up and check parity of the first frames against the oracle once
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
@@ -532,7 +544,7 @@ def main():
     full_fps = world * T * max(3, args.steps // 2) / (ms_full / 1e3)
 
     # frame-by-frame latency (device frames): push_frame + get_keypoints per frame
-    lat = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_ID, N_r=cfg.N_r, N_c=cfg.N_c,
+    lat = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_ID, N_r=cfg.N_r, N_c=cfg.N_c, mask_layer=cfg.mask_layer,
                      T_I=cfg.T_I, O=cfg.O, intra=cfg.intra, t=cfg.t, cuda_stream=handle)
     lat.set_launch_config(shape_masked)
     nlat = min(args.latency_frames, T)
@@ -648,7 +660,9 @@ def main():
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": roof,
-        "gpu_launches": 6 * args.steps,
+        # per step: pyramid, (layer sums for a mask layer above c_0), mask,
+        # worklist, detect, count, emit
+        "gpu_launches": (6 + (1 if cfg.mask_layer != 0 else 0)) * args.steps,
         "clocks": clk,
         "cpu_baseline": cpu,
         "wall_s_timed_region": t_wall,

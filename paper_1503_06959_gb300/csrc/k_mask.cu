@@ -22,20 +22,70 @@ __device__ __forceinline__ BinRect bin_rect(const Geometry& g, const Tables& tb,
   return BinRect{tb.xstart[lg.xs_off + c], tb.xstart[lg.xs_off + c + 1], row_start(r), row_start(r + 1)};
 }
 
-// Sum of |L_n - L_{n-1}| over the pixels of `bin` in the mask layer (a layer
-// above c_0, row pitch `pitch` in both buffers).
-__device__ __forceinline__ unsigned long long layer_change(const BinRect& br, const uint8_t* cur,
-                                                           const uint8_t* prv, int pitch) {
+// Sum of |L_n - L_{n-1}| over the pixels of a bin of the mask layer (a layer
+// above c_0, row pitch `pitch` in both buffers), by one warp: lane i takes
+// pixels i, i + 32, ... of the bin in row-major order. If `copy` is not null,
+// the warp then stores the bin's pixels of L_n there (same layout).
+__device__ __forceinline__ unsigned long long layer_change_warp(const BinRect& br, const uint8_t* cur,
+                                                                const uint8_t* prv, int pitch, uint8_t* copy) {
+  const int lane = threadIdx.x & 31;
+  const int bw = br.x1 - br.x0, npx = bw * max(0, br.y1 - br.y0);
   unsigned long long sum = 0;
-  for (int y = br.y0; y < br.y1; ++y) {
-    uint32_t row = 0;
-    for (int x = br.x0; x < br.x1; ++x) {
-      const int d = (int)cur[(long long)y * pitch + x] - (int)prv[(long long)y * pitch + x];
-      row += (uint32_t)(d < 0 ? -d : d);
+  for (int i = lane; i < npx; i += 32) {
+    const long long o = (long long)(br.y0 + i / bw) * pitch + br.x0 + i % bw;
+    const int d = (int)cur[o] - (int)prv[o];
+    sum += (unsigned long long)(d < 0 ? -d : d);
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+  if (copy) {
+    __syncwarp();
+    for (int i = lane; i < npx; i += 32) {
+      const long long o = (long long)(br.y0 + i / bw) * pitch + br.x0 + i % bw;
+      copy[o] = cur[o];
     }
-    sum += row;
   }
   return sum;
+}
+
+// Per-bin sums of |L_k - L_{k-1}| on a mask layer above c_0, one CTA per frame
+// of the batch, into the same per-bin sums the pyramid kernel fills for c_0
+// (L_{-1}: the stream's copy of the previous batch's last frame, refreshed by
+// k_mask). Thread t takes a run of consecutive pixels (row-major) and adds to
+// a shared bin whenever the bin changes.
+constexpr int kLayerSumBins = kMaxBins;
+__global__ void __launch_bounds__(kMaskThreads) k_layer_sums(Geometry g, Tables tb, Batch b, Scratch s) {
+  __shared__ unsigned long long bins[kLayerSumBins];
+  const int k = blockIdx.x;
+  const LayerGeom& lg = g.layer[g.mask_layer];
+  for (int q = threadIdx.x; q < g.NB; q += kMaskThreads) bins[q] = 0;
+  __syncthreads();
+  const uint8_t* cur = s.pyr + (long long)k * g.pyr_bytes + lg.pyr_off;
+  const uint8_t* prv = k > 0 ? cur - g.pyr_bytes : s.ml_prev;
+  const int npx = lg.w * lg.h;  // < 2^28 (layers are at most 16384 x 16384)
+  const int per = (npx + kMaskThreads - 1) / kMaskThreads;
+  const int i0 = min(npx, (int)threadIdx.x * per), n = min(npx, i0 + per) - i0;
+  int y = lg.w > 0 ? i0 / lg.w : 0, x = i0 - y * lg.w;
+  int cur_bin = -1;
+  unsigned long long acc = 0;
+  for (int i = 0; i < n; ++i) {
+    const int bin = tb.rowblk[lg.row_off + y] * g.N_c + tb.colblk[lg.col_off + x];
+    if (bin != cur_bin) {
+      if (acc) atomicAdd(&bins[cur_bin], acc);
+      cur_bin = bin;
+      acc = 0;
+    }
+    const long long o = (long long)y * lg.pitch + x;
+    const int d = (int)cur[o] - (int)prv[o];
+    acc += (unsigned long long)(d < 0 ? -d : d);
+    if (++x == lg.w) {
+      x = 0;
+      ++y;
+    }
+  }
+  if (acc) atomicAdd(&bins[cur_bin], acc);
+  __syncthreads();
+  for (int q = threadIdx.x; q < g.NB; q += kMaskThreads) s.bsum[(long long)q * s.bsum_stride + k] = bins[q];
 }
 
 // One CTA per bin, walking the batch's frames 256 at a time.
@@ -53,6 +103,9 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Ba
                                                        Params p, State st, int reset_base_slot) {
   __shared__ int wmax[kMaskThreads / 32];
   const int bin = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool layer_sums = p.mask_mode == FKD_MASK_ID && g.mask_layer > 0;
+  const BinRect br = bin_rect(g, tb, bin);
+  const LayerGeom& mlg = g.layer[g.mask_layer];
   if (bin == 0) {
     for (int k = tid; k < b.T; k += kMaskThreads) s.frame_totals[k] = 0;
     if (tid == 0) {
@@ -69,12 +122,6 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Ba
       const long long n = b.first_frame + k;
       if (n == 0 || p.mask_mode == FKD_MASK_FULL) {
         m = 1;
-      } else if (p.mask_mode == FKD_MASK_ID && g.mask_layer > 0) {
-        // L_{n-1} of the batch's first frame: the previous batch's last frame
-        const LayerGeom& lg = g.layer[g.mask_layer];
-        const uint8_t* cur = s.pyr + (long long)k * g.pyr_bytes + lg.pyr_off;
-        const uint8_t* prv = k > 0 ? cur - g.pyr_bytes : s.ml_prev;
-        m = layer_change(bin_rect(g, tb, bin), cur, prv, lg.pitch) > (unsigned long long)p.T_I * tb.npix[bin];
       } else if (p.mask_mode == FKD_MASK_ID) {
         unsigned long long* sum = s.bsum + (long long)bin * s.bsum_stride + k;
         m = *sum > (unsigned long long)p.T_I * tb.npix[bin];
@@ -102,15 +149,15 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Ba
     carry = all;
     __syncthreads();
   }
-  if (p.mask_mode == FKD_MASK_ID && g.mask_layer > 0) {
+  if (layer_sums) {
     // the batch's last frame becomes L_{n-1} of the next batch (this bin's
-    // pixels only; frame 0 read the old ones before the barrier above)
-    const LayerGeom& lg = g.layer[g.mask_layer];
-    const BinRect br = bin_rect(g, tb, bin);
-    const uint8_t* last = s.pyr + (long long)(b.T - 1) * g.pyr_bytes + lg.pyr_off;
-    for (int y = br.y0; y < br.y1; ++y)
-      for (int x = br.x0 + tid; x < br.x1; x += kMaskThreads)
-        s.ml_prev[(long long)y * lg.pitch + x] = last[(long long)y * lg.pitch + x];
+    // pixels only; frame 0 read the old ones before the barriers above)
+    const uint8_t* last = s.pyr + (long long)(b.T - 1) * g.pyr_bytes + mlg.pyr_off;
+    const int bw = br.x1 - br.x0, npx = bw * max(0, br.y1 - br.y0);
+    for (int i = tid; i < npx; i += kMaskThreads) {
+      const long long o = (long long)(br.y0 + i / bw) * mlg.pitch + br.x0 + i % bw;
+      s.ml_prev[o] = last[o];
+    }
   }
 }
 
@@ -151,45 +198,45 @@ __global__ void k_worklist(Geometry g, Tables tb, Batch b, Scratch s) {
 // of every participating stream (src = 0 for active bins, -1 = kept set).
 __global__ void k_group_mask(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
                              uint32_t* work_count) {
+  // one warp per (stream, bin) of the tick
   const int n = hdr->n_items, total = hdr->total_bins;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gtid == 0) *work_count = 0;
-  for (int j = gtid; j < total; j += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *work_count = 0;
+  for (int j = gwarp; j < total; j += nwarps) {
     const int i = find_item(n, j, [&](int q) { return items[q].bin_base; });
     const TickItem it = items[i];
     const StreamDev& d = devs[it.sid];
     const int bin = j - it.bin_base;
-    int m;
-    if (it.frame_index == 0 || d.p.mask_mode == FKD_MASK_FULL) {
-      m = 1;
-    } else if (d.p.mask_mode == FKD_MASK_ID && d.g.mask_layer > 0) {
+    unsigned long long change = 0;
+    if (d.p.mask_mode == FKD_MASK_ID && d.g.mask_layer > 0) {
       // a coarser mask layer: this frame's layer against the stream's copy
       // of the previous one, which then takes this frame's pixels of the bin
       const LayerGeom& lg = d.g.layer[d.g.mask_layer];
-      const uint8_t* cur = d.s.pyr + lg.pyr_off;
-      const BinRect br = bin_rect(d.g, d.tb, bin);
-      m = layer_change(br, cur, d.s.ml_prev, lg.pitch) > (unsigned long long)d.p.T_I * d.tb.npix[bin];
-    } else if (d.p.mask_mode == FKD_MASK_ID) {
-      m = d.s.bsum[bin] > (unsigned long long)d.p.T_I * d.tb.npix[bin];
-      d.s.bsum[bin] = 0;
-    } else {
-      m = d.state_cnt[it.state_cur][bin] >= (uint32_t)d.p.T_H;
+      change = layer_change_warp(bin_rect(d.g, d.tb, bin), d.s.pyr + lg.pyr_off, d.s.ml_prev, lg.pitch,
+                                 d.s.ml_prev);
     }
-    if (d.p.mask_mode == FKD_MASK_ID && d.g.mask_layer > 0) {
-      const LayerGeom& lg = d.g.layer[d.g.mask_layer];
-      const BinRect br = bin_rect(d.g, d.tb, bin);
-      for (int y = br.y0; y < br.y1; ++y)
-        for (int x = br.x0; x < br.x1; ++x)
-          d.s.ml_prev[(long long)y * lg.pitch + x] = d.s.pyr[lg.pyr_off + (long long)y * lg.pitch + x];
+    if (lane == 0) {
+      int m;
+      if (it.frame_index == 0 || d.p.mask_mode == FKD_MASK_FULL) {
+        m = 1;
+      } else if (d.p.mask_mode == FKD_MASK_ID && d.g.mask_layer > 0) {
+        m = change > (unsigned long long)d.p.T_I * d.tb.npix[bin];
+      } else if (d.p.mask_mode == FKD_MASK_ID) {
+        m = d.s.bsum[bin] > (unsigned long long)d.p.T_I * d.tb.npix[bin];
+        d.s.bsum[bin] = 0;
+      } else {
+        m = d.state_cnt[it.state_cur][bin] >= (uint32_t)d.p.T_H;
+      }
+      d.s.mask[bin] = (uint8_t)m;
+      d.s.src[bin] = m ? 0 : -1;
+      d.state_cnt[it.state_cur ^ 1][bin] = 0;
+      if (bin == 0) {
+        d.s.frame_totals[0] = 0;
+        d.s.out_base[0] = 0;
+      }
     }
-    d.s.mask[bin] = (uint8_t)m;
-    d.s.src[bin] = m ? 0 : -1;
-    d.state_cnt[it.state_cur ^ 1][bin] = 0;
-    if (bin == 0) {
-      d.s.frame_totals[0] = 0;
-      d.s.out_base[0] = 0;
-    }
-    for (int q = bin; q < d.g.n_chunks; q += d.g.NB) d.s.chunk_counts[q] = 0;
+    for (int q = bin + lane * d.g.NB; q < d.g.n_chunks; q += 32 * d.g.NB) d.s.chunk_counts[q] = 0;
   }
 }
 
@@ -242,6 +289,8 @@ void launch_group_worklist(const StreamDev* devs, const TickHeader* hdr, const T
 
 void launch_mask(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                  const Params& p, const State& state, cudaStream_t st, int reset_base_slot) {
+  if (p.mask_mode == FKD_MASK_ID && g.mask_layer > 0)
+    k_layer_sums<<<b.T, kMaskThreads, 0, st>>>(g, tb, b, s);
   k_mask<<<g.NB, kMaskThreads, 0, st>>>(g, tb, b, s, p, state, reset_base_slot);
 }
 

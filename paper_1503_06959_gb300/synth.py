@@ -124,6 +124,9 @@ class StreamConfig:
     N_c: int
     T_I: int
     source: dict
+    # layer of the intensity-difference test: -1 = the coarsest octave, the
+    # layer the paper's experiments use (Sec. 4); 0 = c_0
+    mask_layer: int = -1
 
 
 def config1() -> StreamConfig:
