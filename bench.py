@@ -55,9 +55,10 @@ KERNEL_SOURCES = {
 }
 
 
-def profile_counters(kernel: str):
+def profile_counters(kernel: str, shape: dict | None = None):
     """Counters of the committed ncu summary of `kernel` on this workload, if
-    the kernel's sources are unchanged since it was taken (else None)."""
+    the kernel's sources are unchanged since it was taken and, for the
+    detection kernel, it was taken at the launch shape in use (else None)."""
     import hashlib
     import re
     if kernel not in KERNEL_SOURCES:
@@ -71,9 +72,14 @@ def profile_counters(kernel: str):
     for f in KERNEL_SOURCES[kernel]:
         m.update(open(os.path.join(ROOT, "paper_1503_06959_gb300", "csrc", f), "rb").read())
     got = {k: re.search(k + r": (\S+)", text) for k in
-           ("source_sha256", "traffic_bytes_per_launch", "alu_warp_inst_per_launch")}
+           ("source_sha256", "traffic_bytes_per_launch", "alu_warp_inst_per_launch", "launch_shape")}
     if not got["source_sha256"] or got["source_sha256"].group(1) != m.hexdigest()[:16]:
         return None
+    if kernel == "detect" and shape is not None:
+        want = f"{shape['tile_h']},{shape['warps_per_cta']},{shape['ctas_per_sm']}"
+        if not got["launch_shape"] or got["launch_shape"].group(1) != want:
+            return None
+    got.pop("launch_shape")
     return {k: float(v.group(1)) for k, v in got.items() if v and k != "source_sha256"}
 
 
@@ -609,7 +615,7 @@ def main():
         bytes_per_launch = prof["frames"] / launches * layer_px / 8 * 2
         bytes_desc = "per frame: keypoint bitmap words read and written"
     achieved = bytes_per_launch / dur_s / 1e9
-    counters = profile_counters(dom) if T == cfg.frames else None
+    counters = profile_counters(dom, shape_masked) if T == cfg.frames else None
     hbm = {"achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
            "frac": achieved / pk["hbm_gbs"], "peak_source": f"{pk_kind} hbm_gbs",
            "bytes_per_launch": bytes_per_launch, "bytes": bytes_desc}

@@ -276,8 +276,9 @@ int fkd_set_launch_config(fkd_stream* s, const fkd_launch_config* c);
  * pitch `pitch`, frame k at frames + k * frame_stride; T <= T_max) under every
  * candidate shape (tile_h x warps_per_cta x ctas_per_sm), `reps` timed runs
  * each after one untimed run, keeps the fastest (smallest of its runs, CUDA
- * events around the whole launch sequence), and returns it in *best and its
- * time in *best_ms (either may be NULL). Each run starts from a reset stream,
+ * events around the whole launch sequence; the current shape is timed first
+ * and another replaces it only when more than 2 % faster), and returns it in
+ * *best and its time in *best_ms (either may be NULL). Each run starts from a reset stream,
  * so the stream's history is discarded: tune before the first push. Results
  * of the runs are dropped. Errors: FKD_E_ARG, FKD_E_CUDA. */
 int fkd_autotune(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t frame_stride, int T, int reps,

@@ -457,13 +457,18 @@ void apply_launch(fkd_stream* s, const fkd_launch_config& c, const DetLaunch& dl
   s->tiles = s->tile_shape[dl.shape];
 }
 
-// Every candidate shape of the autotuner.
-std::vector<fkd_launch_config> launch_candidates() {
-  std::vector<fkd_launch_config> v;
+// Every candidate shape of the autotuner, the current one first: a later
+// candidate wins only when it is faster by more than the margin, so that
+// near-ties keep the current shape instead of following timing noise.
+constexpr float kTuneMargin = 0.98f;
+std::vector<fkd_launch_config> launch_candidates(const fkd_launch_config& current) {
+  std::vector<fkd_launch_config> v{current};
   for (int k = 0; k < kDetShapes; ++k)
     for (int warps = 4; warps <= 8; warps += 4) {
       const int fit = detect_ctas_per_sm(k, warps);
-      for (int c = 1; c <= fit; ++c) v.push_back(fkd_launch_config{kDetTH[k], warps, c});
+      for (int c = 1; c <= fit; ++c)
+        if (kDetTH[k] != current.tile_h || warps != current.warps_per_cta || c != current.ctas_per_sm)
+          v.push_back(fkd_launch_config{kDetTH[k], warps, c});
     }
   return v;
 }
@@ -735,7 +740,7 @@ int fkd_autotune(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t fram
   fkd_launch_config win = s->lc;
   float win_ms = -1.f;
   int rc = FKD_OK;
-  for (const fkd_launch_config& c : launch_candidates()) {
+  for (const fkd_launch_config& c : launch_candidates(s->lc)) {
     DetLaunch dl{};
     if ((rc = resolve_launch(&c, &dl))) break;
     apply_launch(s, c, dl);
@@ -753,7 +758,7 @@ int fkd_autotune(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t fram
       if (r > 0 && (best_c < 0.f || ms < best_c)) best_c = ms;
     }
     if (rc) break;
-    if (win_ms < 0.f || best_c < win_ms) {
+    if (win_ms < 0.f || best_c < kTuneMargin * win_ms) {
       win_ms = best_c;
       win = c;
     }
@@ -1311,7 +1316,7 @@ int fkd_group_autotune(fkd_group* G, int n, const int* ids, int m, const uint8_t
   fkd_launch_config win = start;
   float win_ms = -1.f;
   int rc = FKD_OK;
-  for (const fkd_launch_config& c : launch_candidates()) {
+  for (const fkd_launch_config& c : launch_candidates(start)) {
     if ((rc = fkd_group_set_launch_config(G, &c))) break;
     float best_c = -1.f;
     for (int r = 0; r <= reps && rc == FKD_OK; ++r) {
@@ -1326,7 +1331,7 @@ int fkd_group_autotune(fkd_group* G, int n, const int* ids, int m, const uint8_t
       if (r > 0 && (best_c < 0.f || ms < best_c)) best_c = ms;
     }
     if (rc) break;
-    if (win_ms < 0.f || best_c < win_ms) {
+    if (win_ms < 0.f || best_c < kTuneMargin * win_ms) {
       win_ms = best_c;
       win = c;
     }
