@@ -83,6 +83,33 @@ def profile_counters(kernel: str, shape: dict | None = None):
     return {k: float(v.group(1)) for k, v in got.items() if v and k != "source_sha256"}
 
 
+# --- multi-GPU plumbing: one independent stream per rank, timings max-reduced
+def rank_env() -> tuple[int, int, int]:
+    """(world size, rank, local rank) from the torchrun environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def rank_clip(cfg, rank: int, frames: int):
+    """The clip rank `rank` processes: its own seeded stream (streams are
+    independent, so the ranks share no data and exchange nothing)."""
+    return synth.source_for(cfg, 2, stream=rank).frames(frames)
+
+
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of per-rank timings (the slowest rank decides)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_fps(world: int, frames_per_step: int, steps: int, ms_max: float) -> float:
+    """Frames of all ranks over the slowest rank's time (weak scaling)."""
+    return world * frames_per_step * steps / (ms_max / 1e3)
+
+
 def workload_desc(cfg, frames):
     return (f"{cfg.W}x{cfg.H} uint8 synthetic video, {frames} frames per step, O={cfg.O}"
             f"{' + intra-octaves' if cfg.intra else ''}, {cfg.N_c}x{cfg.N_r} bins (cols x rows), "
@@ -456,9 +483,7 @@ def main():
     import torch
     from paper_1503_06959_gb300 import fkd
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -470,7 +495,7 @@ def main():
 
     cfg = synth.config2()
     T = args.frames or cfg.frames
-    frames_np = synth.source_for(cfg, 2, stream=rank).frames(T)
+    frames_np = rank_clip(cfg, rank, T)
     frames = torch.from_numpy(frames_np).to(dev)
     torch_stream = torch.cuda.current_stream()
     handle = torch_stream.cuda_stream
@@ -542,12 +567,9 @@ def main():
     kp_full = int(off_full[T] - off_full[0])
 
     # max over ranks
-    t_local = torch.tensor([ms, ms_full], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms, ms_full = t_local.tolist()
-    value = world * T * args.steps / (ms / 1e3)
-    full_fps = world * T * max(3, args.steps // 2) / (ms_full / 1e3)
+    ms, ms_full = max_over_ranks([ms, ms_full], dist, dev)
+    value = whole_job_fps(world, T, args.steps, ms)
+    full_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_full)
 
     # frame-by-frame latency (device frames): push_frame + get_keypoints per frame
     lat = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_ID, N_r=cfg.N_r, N_c=cfg.N_c, mask_layer=cfg.mask_layer,
@@ -584,10 +606,8 @@ def main():
         e2e_stream.reset()
         e2e_stream.push_frames(hf, out=ho, offsets=hoff, masks=hm)
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_fps = world * T * e2e_steps / e2e_t.item()
+    (e2e_s,) = max_over_ranks([e2e_s], dist, dev)
+    e2e_fps = whole_job_fps(world, T, e2e_steps, e2e_s * 1e3)
     h2d = T * cfg.W * cfg.H
     d2h = int(hoff[T] - hoff[0]) * 8 + (T + 1) * 4 + T * cfg.N_r * cfg.N_c
 
