@@ -220,13 +220,14 @@ def run_reference(args):
     return 0
 
 
-def _group_run(streams, frames_dev, mode, warm, ticks_timed, fkd, torch, tune_ticks=3):
+def _group_run(streams, frames_dev, mode, warm, ticks_timed, fkd, torch, tune_ticks=3, mask_layer=None):
     """Tick every stream once per tick through one group, after tuning the
     detection launch shape on the first `tune_ticks` ticks; returns (seconds
     for the timed ticks, profile, keypoints per tick, chosen shape)."""
     st = torch.cuda.Stream()
     g = fkd.Group(streams[0].O, streams[0].intra, cuda_stream=st.cuda_stream)
-    ids = [g.add_stream(c.W, c.H, N_r=c.N_r, N_c=c.N_c, T_I=c.T_I, t=c.t, mask_mode=mode, mask_layer=c.mask_layer,
+    ids = [g.add_stream(c.W, c.H, N_r=c.N_r, N_c=c.N_c, T_I=c.T_I, t=c.t, mask_mode=mode,
+                        mask_layer=c.mask_layer if mask_layer is None else mask_layer,
                         K_max=1 << 17)[0] for c in streams]
     n_frames = frames_dev[0].shape[0]
     shape, tune_ms = g.autotune(ids, [[f[n] for f in frames_dev] for n in range(tune_ticks)], reps=2)
@@ -256,13 +257,17 @@ def run_config3(args):
     per_res = args.streams_per_res
     streams = synth.config3_streams(per_res)
     F = args.frames or 24
-    frames_dev = []
+    frames_dev, first_of_res = [], {}
     for j, c in enumerate(streams):
-        frames_dev.append(torch.from_numpy(synth.source_for(c, 3, j).frames(F)).cuda())
+        clip = synth.source_for(c, 3, j).frames(F)
+        first_of_res.setdefault((c.W, c.H), (c, clip[:6]))
+        frames_dev.append(torch.from_numpy(clip).cuda())
     warm = 3
     res = {}
-    for name, mode in (("masked", fkd.FKD_MASK_ID), ("full", fkd.FKD_MASK_FULL)):
-        sec, prof, kps, shape = _group_run(streams, frames_dev, mode, warm, F - warm, fkd, torch)
+    for name, mode, ml in (("masked", fkd.FKD_MASK_ID, None), ("masked_c0", fkd.FKD_MASK_ID, 0),
+                           ("full", fkd.FKD_MASK_FULL, None)):
+        sec, prof, kps, shape = _group_run(streams, frames_dev, mode, warm, F - warm, fkd, torch,
+                                           mask_layer=ml)
         ticks = F - warm
         res[name] = {"frames_per_s": len(streams) * ticks / sec, "ms_per_tick": sec / ticks * 1e3,
                      "launch_shape": shape,
@@ -279,7 +284,19 @@ def run_config3(args):
                        "mpix_per_tick": mpix},
             "mpix_per_s": res["masked"]["frames_per_s"] / len(streams) * mpix,
             "masked": res["masked"], "full_frame": res["full"],
+            "masked_c0": dict(res["masked_c0"], what="the intensity-difference test on c_0"),
             "masked_over_full": res["masked"]["frames_per_s"] / res["full"]["frames_per_s"]}
+    if not args.no_cpu_baseline:
+        # the oracle on the first frames of one stream per resolution (about
+        # 3 s each); the mix has equal counts per resolution
+        per_frame = []
+        for (W, H), (c, clip) in first_of_res.items():
+            fps_r, n_r, dt_r = cpu_oracle_fps(clip, c, seconds=3.0)
+            per_frame.append(1.0 / fps_r)
+        line["cpu_baseline"] = {"value": 1.0 / (sum(per_frame) / len(per_frame)), "unit": "frames/s",
+                                "cores": 1, "kind": "oracle",
+                                "sample": "first frames (about 3 s each) of one stream per resolution, "
+                                          "masked, one thread; frames/s of the equal-count mix"}
     print(json.dumps(line))
     return 0
 
@@ -292,17 +309,21 @@ def run_config5(args):
     seg = args.segment
     F = 2 * seg
     n_streams = args.streams_5
-    frames_dev = []
+    frames_dev, clip0 = [], None
     for j in range(n_streams):
         src = synth.VideoSource(cfg.W, cfg.H, seed=1000 + 500 + j,
                                 **dict(cfg.source, static_segments=(seg, 0)))
-        frames_dev.append(torch.from_numpy(src.frames(F)).cuda())
+        clip = src.frames(F)
+        if j == 0:
+            clip0 = clip[:4]
+        frames_dev.append(torch.from_numpy(clip).cuda())
     out = {}
-    for name, mode in (("masked", fkd.FKD_MASK_ID), ("full", fkd.FKD_MASK_FULL)):
+    for name, mode, ml in (("masked", fkd.FKD_MASK_ID, cfg.mask_layer), ("masked_c0", fkd.FKD_MASK_ID, 0),
+                           ("full", fkd.FKD_MASK_FULL, cfg.mask_layer)):
         st = torch.cuda.Stream()
         g = fkd.Group(cfg.O, cfg.intra, cuda_stream=st.cuda_stream)
         ids = [g.add_stream(cfg.W, cfg.H, N_r=cfg.N_r, N_c=cfg.N_c, T_I=cfg.T_I, t=cfg.t,
-                            mask_mode=mode, mask_layer=cfg.mask_layer, K_max=1 << 20)[0]
+                            mask_mode=mode, mask_layer=ml, K_max=1 << 20)[0]
                for _ in range(n_streams)]
         segs = {}
         for part, rng in (("moving", range(0, seg)), ("static", range(seg, F))):
@@ -342,7 +363,13 @@ def run_config5(args):
             "dtype": "u8", "data": "synthetic",
             "config": {"workload": f"{n_streams} streams of 3840x2160, O=5 + intra-octaves, "
                                    f"{seg} moving then {seg} static frames, N(0,2) noise"},
-            "masked": out["masked"], "full_frame": out["full"]}
+            "masked": out["masked"], "full_frame": out["full"],
+            "masked_c0": dict(out["masked_c0"], what="the intensity-difference test on c_0")}
+    if not args.no_cpu_baseline:
+        fps_o, n_o, dt_o = cpu_oracle_fps(clip0, cfg, seconds=10.0)
+        line["cpu_baseline"] = {"value": fps_o, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {n_o} frames of stream 0 (moving segment), masked, "
+                                          f"one thread, {dt_o:.1f} s"}
     print(json.dumps(line))
     return 0
 
@@ -566,10 +593,23 @@ def main():
     off_full = offsets.cpu().numpy().astype(np.int64)
     kp_full = int(off_full[T] - off_full[0])
 
+    # the same masked detection with the intensity test on c_0 (the library's
+    # default layer) beside the coarsest octave (the paper's experiments)
+    c0_common = dict(common, mask_layer=0)
+    masked_c0 = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_ID, **c0_common)
+    if args.shape:
+        masked_c0.set_launch_config(shape_masked)
+        shape_c0 = shape_masked
+    else:
+        shape_c0, _ = masked_c0.autotune(frames, reps=2)
+    ms_c0, prof_c0 = timed(masked_c0, max(3, args.steps // 2), 3, profile=True)
+    act_c0 = masks.float().mean().item()
+
     # max over ranks
-    ms, ms_full = max_over_ranks([ms, ms_full], dist, dev)
+    ms, ms_full, ms_c0 = max_over_ranks([ms, ms_full, ms_c0], dist, dev)
     value = whole_job_fps(world, T, args.steps, ms)
     full_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_full)
+    c0_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_c0)
 
     # frame-by-frame latency (device frames): push_frame + get_keypoints per frame
     lat = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_ID, N_r=cfg.N_r, N_c=cfg.N_c, mask_layer=cfg.mask_layer,
@@ -679,6 +719,11 @@ def main():
                        "stage_ms_per_step": {k: v / max(1, prof_full["batches"])
                                              for k, v in prof_full["ms"].items()}},
         "masked_over_full": value / full_fps,
+        "masked_c0": {"value": c0_fps, "unit": "frames/s", "active_bin_fraction": act_c0,
+                      "masked_over_full": c0_fps / full_fps, "launch_shape": shape_c0,
+                      "what": "the intensity-difference test on c_0 instead of the coarsest octave",
+                      "stage_ms_per_step": {k: v / max(1, prof_c0["batches"])
+                                            for k, v in prof_c0["ms"].items()}},
         "active_bin_fraction": act, "keypoints_per_step": kp_masked,
         "stage_ms_per_step": {k: v / max(1, prof["batches"]) for k, v in stage_ms.items()},
         "latency_ms": {"p50": p50, "p99": p99, "frames": len(lat_ms),
