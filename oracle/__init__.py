@@ -38,6 +38,7 @@ class _Params(ctypes.Structure):
         ("N_r", ctypes.c_int), ("N_c", ctypes.c_int), ("T_I", ctypes.c_int),
         ("T_H", ctypes.c_int), ("O", ctypes.c_int), ("intra", ctypes.c_int),
         ("t", ctypes.c_int), ("mask_mode", ctypes.c_int), ("mask_layer", ctypes.c_int),
+        ("nms_scale", ctypes.c_int),
     ]
 
 
@@ -139,9 +140,9 @@ class Stream:
 
     def __init__(self, W: int, H: int, *, N_r: int, N_c: int, T_I: int = 4, T_H: int = 1,
                  O: int = 1, intra: int = 0, t: int = 20, mask_mode: int = MASK_ID,
-                 mask_layer: int = 0):
+                 mask_layer: int = 0, nms_scale: int = 0):
         self.W, self.H, self.N_r, self.N_c = W, H, N_r, N_c
-        p = _Params(N_r, N_c, T_I, T_H, O, intra, t, mask_mode, mask_layer)
+        p = _Params(N_r, N_c, T_I, T_H, O, intra, t, mask_mode, mask_layer, nms_scale)
         h = ctypes.c_void_p()
         if _load().orc_stream_create(ctypes.byref(p), W, H, ctypes.byref(h)) != 0:
             raise ValueError("invalid oracle stream parameters")

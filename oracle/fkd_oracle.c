@@ -14,7 +14,8 @@
  *   2. detection mask M'_n on the N_r x N_c grid: intensity difference
  *      (Eq. 2, Sec. 3.1) or keypoint binning (Eqs. 3-4, Sec. 3.2)
  *   3. segment test with the 16-pixel radius-3 Bresenham ring, corner score,
- *      threshold t and 3x3 non-maximum suppression on every layer (Sec. 2)
+ *      threshold t and 3x3 non-maximum suppression on every layer (Sec. 2),
+ *      optionally over the scale-space neighbourhood (the adjacent layers)
  *   4. D_n = detections in active blocks united with the keypoints of
  *      D_{n-1} that lie in inactive blocks (Eq. 1).
  */
@@ -201,6 +202,7 @@ int orc_stream_create(const orc_params* p, int W, int H, orc_stream** out) {
   if (p->O < 1 || p->O > 12 || (p->intra != 0 && p->intra != 1)) return -1;
   if (p->t < 1 || p->t > 255 || p->T_I < 0 || p->T_H < 0) return -1;
   if (p->mask_mode < ORC_MASK_FULL || p->mask_mode > ORC_MASK_KB) return -1;
+  if (p->nms_scale != 0 && p->nms_scale != 1) return -1;
   orc_stream* s = (orc_stream*)calloc(1, sizeof(orc_stream));
   s->p = *p;
   s->W = W; s->H = H;
@@ -307,12 +309,16 @@ int orc_stream_push(orc_stream* s, const uint8_t* frame, size_t pitch, const uin
   /* ... and the detector runs on every layer (Sec. 2) at pixels of active
    * blocks: score >= t and strictly greater than all 8 neighbours' scores.
    * Neighbours are scored whatever their block's mask bit. */
+  uint8_t* scores[32];
+  for (int l = 0; l < s->L; ++l) {
+    int w = s->lw[l], h = s->lh[l];
+    scores[l] = (uint8_t*)malloc((size_t)w * h + 1);
+    if (w > 0 && h > 0) orc_score_image(s->pyr_cur + s->loff[l], w, h, scores[l]);
+  }
   for (int l = 0; l < s->L; ++l) {
     int w = s->lw[l], h = s->lh[l];
     if (w == 0 || h == 0) continue;
-    const uint8_t* img = s->pyr_cur + s->loff[l];
-    uint8_t* sc = (uint8_t*)malloc((size_t)w * h);
-    orc_score_image(img, w, h, sc);
+    const uint8_t* sc = scores[l];
     for (int y = 0; y < h; ++y)
       for (int x = 0; x < w; ++x) {
         int v = sc[y * w + x];
@@ -326,14 +332,33 @@ int orc_stream_push(orc_stream* s, const uint8_t* frame, size_t pitch, const uin
             int q = (qx >= 0 && qy >= 0 && qx < w && qy < h) ? sc[qy * w + qx] : 0;
             if (!(v > q)) is_max = 0;
           }
+        /* Scale-space neighbourhood (Sec. 2, "3x3 scale-space"): the layers
+         * just below and above in scale, each through the 3x3 window around
+         * its pixel that contains this pixel's centre. Pixel x of scale code
+         * S covers image columns [x*S/2, (x+1)*S/2), so its centre
+         * (x + 1/2)*S/2 lies in pixel floor((2x + 1) * S / (2 S')) of the
+         * layer with scale code S'. Pixels outside that layer count as 0. */
+        for (int dl = -1; dl <= 1 && is_max && p->nms_scale; dl += 2) {
+          int m = l + dl;
+          if (m < 0 || m >= s->L) continue;
+          int mw = s->lw[m], mh = s->lh[m];
+          int cx = (int)(((long)(2 * x + 1) * s->lS[l]) / (2L * s->lS[m]));
+          int cy = (int)(((long)(2 * y + 1) * s->lS[l]) / (2L * s->lS[m]));
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              int qx = cx + dx, qy = cy + dy;
+              int q = (qx >= 0 && qy >= 0 && qx < mw && qy < mh) ? scores[m][qy * mw + qx] : 0;
+              if (!(v > q)) is_max = 0;
+            }
+        }
         if (is_max) {
           orc_keypoint k;
           k.x = (uint16_t)x; k.y = (uint16_t)y; k.layer = (uint8_t)l; k.score = (uint8_t)v; k.flags = 0;
           kp_push(&next, &nn, &ncap, k);
         }
       }
-    free(sc);
   }
+  for (int l = 0; l < s->L; ++l) free(scores[l]);
   qsort(next, nn, sizeof(orc_keypoint), kp_cmp);
   free(s->kp);
   s->kp = next; s->nkp = nn; s->cap = ncap;

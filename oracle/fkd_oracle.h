@@ -44,6 +44,8 @@ typedef struct {
   int t;            /* segment-test threshold (Sec. 2)                  */
   int mask_mode;    /* ORC_MASK_FULL / ID / KB                          */
   int mask_layer;   /* layer the ID test reads; -1 = coarsest octave    */
+  int nms_scale;    /* 0: 3x3 maxima within the layer; 1: also against  */
+                    /* the 3x3 windows of the adjacent layers (Sec. 2)  */
 } orc_params;
 
 /* Geometry of layer l; returns 0, or -1 if l is out of range. */

@@ -446,3 +446,120 @@ def test_single_active_block_mixes_new_and_old():
     exp += [k[:4] + (1,) for k in d0 if blk(k) != 4]
     assert kp_tuples(s.keypoints()) == sorted(exp)
     assert any(k[4] == 0 for k in exp) and any(k[4] == 1 for k in exp)
+
+
+# --------------------------------------------------------------------------
+# scale-space non-maximum suppression (Sec. 2, "3x3 scale-space neighbourhood")
+
+
+def centre_pixel(x, S, S2):
+    """The pixel of a layer with scale code S2 whose image footprint
+    [x2*S2/2, (x2+1)*S2/2) holds the centre (x + 1/2)*S/2 of pixel x of a
+    layer with scale code S, found by search (not by formula)."""
+    c = Fraction(2 * x + 1, 2) * Fraction(S, 2)
+    x2 = 0
+    while Fraction((x2 + 1) * S2, 2) <= c:
+        x2 += 1
+    assert Fraction(x2 * S2, 2) <= c < Fraction((x2 + 1) * S2, 2)
+    return x2
+
+
+def brute_scale_detect(layers, Ss, t):
+    """In-layer strict 3x3 maxima that are also strictly above every score of
+    the 3x3 windows (around the centre pixel) of the layers just below and
+    above in scale; scores by brute force."""
+    sc = []
+    for img in layers:
+        h, w = img.shape
+        sc.append(np.array([[brute_score(img, x, y) for x in range(w)] for y in range(h)], int)
+                  if w and h else np.zeros((h, w), int))
+    out = []
+    for l, img in enumerate(layers):
+        h, w = img.shape
+        for y in range(h):
+            for x in range(w):
+                v = sc[l][y, x]
+                if v < t:
+                    continue
+                nb = [sc[l][y + dy, x + dx] if 0 <= y + dy < h and 0 <= x + dx < w else 0
+                      for dy in (-1, 0, 1) for dx in (-1, 0, 1) if (dx, dy) != (0, 0)]
+                for m in (l - 1, l + 1):
+                    if not 0 <= m < len(layers):
+                        continue
+                    mh, mw = layers[m].shape
+                    cx, cy = centre_pixel(x, Ss[l], Ss[m]), centre_pixel(y, Ss[l], Ss[m])
+                    nb += [sc[m][cy + dy, cx + dx] if 0 <= cy + dy < mh and 0 <= cx + dx < mw else 0
+                           for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+                if all(v > q for q in nb):
+                    out.append((l, y, x, int(v)))
+    return out
+
+
+def test_centre_pixel_search_agrees_with_the_integer_map():
+    # the oracle maps x -> floor((2x + 1) * S / (2 S2)); the search above
+    # finds the containing pixel from the footprints alone
+    for S, S2 in ((2, 3), (3, 2), (3, 4), (4, 3), (2, 4), (4, 2), (8, 12), (12, 8)):
+        for x in range(40):
+            assert centre_pixel(x, S, S2) == ((2 * x + 1) * S) // (2 * S2)
+
+
+def test_scale_nms_equals_bruteforce_on_small_pyramids():
+    rng = np.random.default_rng(77)
+    for trial, (O, intra) in enumerate(((2, 1), (3, 0), (2, 0))):
+        W, H = 36 + 6 * trial, 30 + 6 * trial
+        # plateaus and corners at two sizes, so that coarse layers have corners too
+        big = np.kron(rng.integers(0, 4, (H // 6 + 1, W // 6 + 1)), np.ones((6, 6), int))[:H, :W]
+        small = rng.integers(0, 3, (H, W))
+        img = np.clip(big * 60 + small * 12, 0, 255).astype(np.uint8)
+        t = 8
+        s = oracle.Stream(W, H, N_r=1, N_c=1, O=O, intra=intra, t=t, mask_mode=oracle.MASK_FULL,
+                          nms_scale=1)
+        s.push(img)
+        got = [(int(k["layer"]), int(k["y"]), int(k["x"]), int(k["score"])) for k in s.keypoints()]
+        layers = oracle.pyramid(img, O, intra)
+        Ss = [oracle.layer_geom(W, H, O, intra, l)[2] for l in range(len(layers))]
+        exp = sorted(brute_scale_detect(layers, Ss, t))
+        assert got == exp
+        assert len({k[0] for k in got}) > 1, "keypoints on more than one layer"
+
+
+def test_scale_nms_single_layer_is_in_layer_nms():
+    rng = np.random.default_rng(5)
+    img = np.clip(rng.normal(128, 60, (40, 52)), 0, 255).astype(np.uint8)
+    kps = []
+    for ns in (0, 1):
+        s = oracle.Stream(52, 40, N_r=2, N_c=2, O=1, intra=0, t=15, mask_mode=oracle.MASK_FULL,
+                          nms_scale=ns)
+        s.push(img)
+        kps.append(kp_tuples(s.keypoints()))
+    assert kps[0] == kps[1] and len(kps[0]) > 0
+
+
+def test_scale_nms_keeps_a_subset_and_removes_only_dominated_points():
+    rng = np.random.default_rng(9)
+    W, H, O, intra = 96, 72, 3, 1
+    img = np.clip(np.round(rng.integers(0, 256, (H, W)) / 32) * 32, 0, 255).astype(np.uint8)
+    res = {}
+    for ns in (0, 1):
+        s = oracle.Stream(W, H, N_r=3, N_c=4, O=O, intra=intra, t=10, mask_mode=oracle.MASK_FULL,
+                          nms_scale=ns)
+        s.push(img)
+        res[ns] = {(int(k["layer"]), int(k["y"]), int(k["x"])): int(k["score"]) for k in s.keypoints()}
+    assert set(res[1]) <= set(res[0]) and len(res[1]) < len(res[0])
+    layers = oracle.pyramid(img, O, intra)
+    Ss = [oracle.layer_geom(W, H, O, intra, l)[2] for l in range(len(layers))]
+    for (l, y, x), v in res[0].items():
+        if (l, y, x) in res[1]:
+            continue
+        # removed: some score in an adjacent layer's window is >= v
+        found = False
+        for m in (l - 1, l + 1):
+            if not 0 <= m < len(layers):
+                continue
+            mh, mw = layers[m].shape
+            cx, cy = centre_pixel(x, Ss[l], Ss[m]), centre_pixel(y, Ss[l], Ss[m])
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    if 0 <= cy + dy < mh and 0 <= cx + dx < mw and brute_score(layers[m], cx + dx, cy + dy) >= v:
+                        found = True
+        assert found, (l, y, x, v)
