@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define FKD_VERSION 1u
+#define FKD_VERSION 2u
 
 /* status codes */
 #define FKD_OK 0
@@ -80,6 +80,11 @@ extern "C" {
  *   K_max       capacity of the kept keypoint set of one frame (>= 1).
  *   T_max       most frames one fkd_push_frames call may carry (>= 1); it
  *               sizes the per-batch scratch.
+ *   nms_scale   0: a detection is a strict 3x3 maximum of scores within its
+ *               layer; 1: it must also be strictly above every score of the
+ *               3x3 window, in the layers just below and above in scale,
+ *               around the pixel containing its centre (Sec. 2, "3x3
+ *               scale-space neighbourhood"). 0 or 1.
  */
 typedef struct {
   uint32_t version; /* FKD_VERSION */
@@ -94,6 +99,7 @@ typedef struct {
   int32_t mask_layer;
   int32_t K_max;
   int32_t T_max;
+  int32_t nms_scale;
 } fkd_params;
 
 /*

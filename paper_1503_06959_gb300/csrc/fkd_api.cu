@@ -153,6 +153,7 @@ int validate(const fkd_params* p, int W, int H) {
   if (p->mask_layer < -1 || p->mask_layer >= L) return fail(FKD_E_ARG, "mask_layer %d outside -1..%d", p->mask_layer, L - 1);
   if (p->K_max < 1) return fail(FKD_E_ARG, "K_max must be >= 1");
   if (p->T_max < 1 || p->T_max > 65535) return fail(FKD_E_ARG, "T_max outside 1..65535");
+  if (p->nms_scale != 0 && p->nms_scale != 1) return fail(FKD_E_ARG, "nms_scale must be 0 or 1");
   return FKD_OK;
 }
 
@@ -346,7 +347,7 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   b.prev = s->prev;
   b.prev_pitch = s->prev_pitch;
   b.c0_vec = 0;
-  Params pr{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode};
+  Params pr{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode, s->p.nms_scale};
   Tables tb{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask};
   State stt{};
   stt.bits_in = s->state_bits[s->state_cur];
@@ -373,6 +374,7 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   launch_worklist(s->g, tb, b, s->s, s->st);
   mark(3);
   launch_detect(s->g, tb, b, s->s, pr, s->dl, s->st);
+  if (pr.nms_scale) launch_scale_nms(s->g, tb, b, s->s, pr, s->st);
   mark(4);
   launch_count(s->g, tb, b, s->s, stt, s->st);  // its last CTA also fills s->s.bases
   mark(5);
@@ -504,6 +506,7 @@ int fkd_params_default(fkd_params* p) {
   p->mask_layer = 0;
   p->K_max = 65536;
   p->T_max = 1;
+  p->nms_scale = 0;
   return FKD_OK;
 }
 
@@ -850,6 +853,7 @@ struct fkd_group {
   int grid_pyr = 1, grid_small = 1, grid_asm = 1;
   fkd_launch_config lc{};            // detection launch shape of every stream
   DetLaunch dl{};
+  bool any_nms_scale = false;        // some stream asked for scale-space suppression
   bool use_graph = true;
   bool graph_valid = false;
   int graph_items = 0;               // items copied per tick by the captured graphs
@@ -896,7 +900,7 @@ StreamDev make_dev(const fkd_stream* s, uint8_t* const last[2], fkd_keypoint* re
   d.tb = Tables{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask};
   d.s = s->s;
   d.s.bases = nullptr;  // group ticks (one frame) compute their offsets in place
-  d.p = Params{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode};
+  d.p = Params{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode, s->p.nms_scale};
   for (int i = 0; i < 2; ++i) {
     d.state_bits[i] = s->state_bits[i];
     d.state_score[i] = s->state_score[i];
@@ -929,6 +933,9 @@ int group_launch(fkd_group* G, int b, int n_items, fkd_stream::Pending* pd) {
   launch_group_worklist(G->d_devs, G->d_hdr, G->d_items, G->d_work, G->d_work_count, G->grid_small, G->st);
   mark(3);
   launch_group_detect(G->d_devs, G->d_items, G->d_work, G->d_work_count, G->dl, G->st);
+  // streams without scale-space suppression skip their items inside
+  if (G->any_nms_scale)
+    launch_group_scale_nms(G->d_devs, G->d_items, G->d_work, G->d_work_count, G->st);
   mark(4);
   launch_group_count(G->d_devs, G->d_hdr, G->d_items, G->grid_asm, G->st);
   mark(5);
@@ -1051,6 +1058,10 @@ int fkd_group_add_stream(fkd_group* G, const fkd_params* p, int W, int H, int* s
   }
   gs.bytes = s->bytes_held;
   apply_launch(s, G->lc, G->dl);
+  if (s->p.nms_scale && !G->any_nms_scale) {
+    G->any_nms_scale = true;
+    G->drop_graphs();  // the captured ticks lack the suppression pass
+  }
   const int id = (int)G->streams.size();
   // device descriptors (grow: the captured graphs hold the old pointer)
   if (id >= G->devs_cap) {

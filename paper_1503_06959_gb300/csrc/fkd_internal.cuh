@@ -28,6 +28,9 @@ constexpr int kDetTW = 128;
 constexpr int kDetShapes = 3;
 constexpr int kDetTH[kDetShapes] = {8, 16, 24};
 constexpr int kDetDefaultShape = 1;
+// kDetTH[shape] where device code needs it with a run-time index
+__host__ __device__ constexpr int det_th(int shape) { return shape == 0 ? 8 : shape == 1 ? 16 : 24; }
+static_assert(det_th(0) == kDetTH[0] && det_th(1) == kDetTH[1] && det_th(2) == kDetTH[2], "tile heights");
 constexpr int kDetMaxThreads = 256;  // warps per CTA: 4 or 8
 
 // Launch shape of the detection kernel.
@@ -126,6 +129,7 @@ struct Batch {
 
 struct Params {
   int T_I, T_H, t, mask_mode;
+  int nms_scale;  // 1: suppression also against the adjacent layers
 };
 
 // Device scratch of a stream, sized for T_max frames.
@@ -266,6 +270,12 @@ void launch_emit(const Geometry& g, const Tables& tb, const Batch& b, const Scra
 // count (0 when it cannot launch), and the SM count.
 int detect_ctas_per_sm(int shape, int warps);
 int sm_count();
+// Scale-space suppression of the detections of the active tiles (after the
+// detection kernel): single-stream batch and group tick.
+void launch_scale_nms(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
+                      const Params& p, cudaStream_t st);
+void launch_group_scale_nms(const StreamDev* devs, const TickItem* items, const uint32_t* work,
+                            const uint32_t* work_count, cudaStream_t st);
 
 // Record a message for fkd_last_error (printf format) and return `code`.
 int set_error(int code, const char* fmt, ...);

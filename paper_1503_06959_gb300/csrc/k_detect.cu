@@ -135,6 +135,23 @@ struct Item {
   int N_c;
 };
 
+// One layer of a frame, for the scale-space suppression.
+struct LayerView {
+  const uint8_t* p;  // null: no such layer
+  int pitch, w, h, S;
+};
+
+// What the scale-space suppression needs of a (frame, tile) work item.
+struct ScaleItem {
+  bool on;              // the stream asked for it
+  int layer, L, th, tx, ty, h, S;
+  uint32_t* bits;       // the frame's keypoint bitmap of the layer (row 0)
+  int wpr;
+  const uint8_t* dscore;
+  int dpitch;
+  LayerView adj[2];     // the layers just below and above in scale
+};
+
 // Work items of one stream's batch of T frames.
 struct SingleSrc {
   Geometry g;
@@ -171,6 +188,45 @@ struct SingleSrc {
     it.rowblk = tb.rowblk + lg.row_off;
     it.N_c = g.N_c;
     return it;
+  }
+  __device__ __forceinline__ ScaleItem scale_item(uint32_t item) const {
+    const uint32_t wi = s.work[item];
+    const DetTile tile = tb.tiles[wi % (uint32_t)g.n_tiles];
+    const int k = (int)(wi / (uint32_t)g.n_tiles);
+    ScaleItem si;
+    si.on = p.nms_scale != 0;
+    si.layer = tile.layer;
+    si.L = g.L;
+    si.th = det_th(g.det_shape);
+    si.tx = tile.tx;
+    si.ty = tile.ty;
+    const LayerGeom& lg = g.layer[tile.layer];
+    si.h = lg.h;
+    si.S = lg.S;
+    si.bits = s.det_bits + (long long)k * g.bit_words + lg.bit_off;
+    si.wpr = lg.wpr;
+    si.dscore = s.det_score + (long long)k * g.score_bytes + lg.score_off;
+    si.dpitch = lg.pitch;
+    for (int j = 0; j < 2; ++j) {
+      const int m = tile.layer + (j ? 1 : -1);
+      LayerView& v = si.adj[j];
+      if (m < 0 || m >= g.L) {
+        v = LayerView{nullptr, 0, 0, 0, 2};
+        continue;
+      }
+      const LayerGeom& lm = g.layer[m];
+      v.w = lm.w;
+      v.h = lm.h;
+      v.S = lm.S;
+      if (m == 0) {
+        v.p = b.frames + (long long)k * b.frame_stride;
+        v.pitch = b.pitch;
+      } else {
+        v.p = s.pyr + (long long)k * g.pyr_bytes + lm.pyr_off;
+        v.pitch = lm.pitch;
+      }
+    }
+    return si;
   }
 };
 
@@ -210,6 +266,46 @@ struct GroupSrc {
     it.rowblk = d.tb.rowblk + lg.row_off;
     it.N_c = d.g.N_c;
     return it;
+  }
+  __device__ __forceinline__ ScaleItem scale_item(uint32_t item) const {
+    const uint32_t wi = work[item];
+    const TickItem ti = items[wi >> 22];
+    const StreamDev& d = devs[ti.sid];
+    const DetTile tile = d.tb.tiles[wi & 0x3fffffu];
+    ScaleItem si;
+    si.on = d.p.nms_scale != 0;
+    si.layer = tile.layer;
+    si.L = d.g.L;
+    si.th = det_th(d.g.det_shape);
+    si.tx = tile.tx;
+    si.ty = tile.ty;
+    const LayerGeom& lg = d.g.layer[tile.layer];
+    si.h = lg.h;
+    si.S = lg.S;
+    si.bits = d.s.det_bits + lg.bit_off;
+    si.wpr = lg.wpr;
+    si.dscore = d.s.det_score + lg.score_off;
+    si.dpitch = lg.pitch;
+    for (int j = 0; j < 2; ++j) {
+      const int m = tile.layer + (j ? 1 : -1);
+      LayerView& v = si.adj[j];
+      if (m < 0 || m >= d.g.L) {
+        v = LayerView{nullptr, 0, 0, 0, 2};
+        continue;
+      }
+      const LayerGeom& lm = d.g.layer[m];
+      v.w = lm.w;
+      v.h = lm.h;
+      v.S = lm.S;
+      if (m == 0) {
+        v.p = ti.frame;
+        v.pitch = ti.pitch;
+      } else {
+        v.p = d.s.pyr + lm.pyr_off;
+        v.pitch = lm.pitch;
+      }
+    }
+    return si;
   }
 };
 
@@ -517,7 +613,86 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
   cp_async_wait<0>();
 }
 
+// Does the segment test fire at threshold v (>= 1) at pixel (x, y) of the
+// layer, i.e. is its score >= v (Sec. 2)? 0 within 3 px of the layer edge.
+// The bright and dark ring pixels form 16-bit masks; a run of 9 around the
+// ring is found on the mask doubled to 32 bits by shift-and doubling.
+__device__ __forceinline__ bool fires(const LayerView& L, int x, int y, int v) {
+  if (x < 3 || y < 3 || x >= L.w - 3 || y >= L.h - 3) return false;
+  const uint8_t* c = L.p + (long long)y * L.pitch + x;
+  const int ip = c[0];
+  // two adjacent compass points must both be beyond ip +- v (see the prefilter)
+  const int n = c[-3 * L.pitch], e = c[3], so = c[3 * L.pitch], wv = c[-3];
+  const auto far = [&](int q) { return q > ip + v || q < ip - v; };
+  if (!((far(n) || far(so)) && (far(e) || far(wv)))) return false;
+  uint32_t br = 0, dk = 0;
+#define FKD_MASKS(k, dx, dy)                              \
+  {                                                       \
+    const int q = c[(dy) * L.pitch + (dx)];               \
+    br |= (uint32_t)(q > ip + v) << (k);                  \
+    dk |= (uint32_t)(q < ip - v) << (k);                  \
+  }
+  FKD_RING(FKD_MASKS)
+#undef FKD_MASKS
+  auto run9 = [](uint32_t m) {
+    const uint32_t d = m | (m << 16);
+    const uint32_t r2 = d & (d >> 1), r4 = r2 & (r2 >> 2), r8 = r4 & (r4 >> 4);
+    return ((r8 & (d >> 8)) & 0xffffu) != 0u;
+  };
+  return run9(br) || run9(dk);
+}
+
+// Scale-space suppression (Sec. 2, "3x3 scale-space neighbourhood"): a
+// detection of layer l survives only if its score is strictly above every
+// score of the 3x3 window, in the layers l-1 and l+1, around the pixel that
+// contains its centre (x' = floor((2x + 1) * S_l / (2 S_l')), likewise y').
+// Thread -> one bitmap word of one active (frame, tile) item; the window's
+// scores are tested against the detection's score directly on the layers.
+template <class Src>
+__global__ void __launch_bounds__(256) k_scale_nms(Src src) {
+  const uint32_t n_items = src.count();
+  const uint32_t words_per_item = (uint32_t)kDetTH[kDetShapes - 1] * (TW / 32);
+  const unsigned long long total = (unsigned long long)n_items * words_per_item;
+  for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < total;
+       j += (unsigned long long)gridDim.x * blockDim.x) {
+    const uint32_t item = (uint32_t)(j / words_per_item), wi = (uint32_t)(j % words_per_item);
+    const ScaleItem si = src.scale_item(item);
+    if (!si.on || wi >= (uint32_t)si.th * (TW / 32)) continue;
+    const int y = si.ty * si.th + (int)(wi / (TW / 32));
+    const int wx = si.tx * (TW / 32) + (int)(wi % (TW / 32));
+    if (y >= si.h || wx >= si.wpr) continue;
+    uint32_t* wp = si.bits + (long long)y * si.wpr + wx;
+    const uint32_t word = *wp;
+    uint32_t keep = word;
+    for (uint32_t m = word; m; m &= m - 1) {
+      const int x = wx * 32 + (__ffs(m) - 1);
+      const int v = si.dscore[(long long)y * si.dpitch + x];
+      bool dominated = false;
+      for (int a = 0; a < 2 && !dominated; ++a) {
+        const LayerView& L = si.adj[a];
+        if (!L.p) continue;
+        const int cx = (int)(((long long)(2 * x + 1) * si.S) / (2LL * L.S));
+        const int cy = (int)(((long long)(2 * y + 1) * si.S) / (2LL * L.S));
+        for (int dy = -1; dy <= 1 && !dominated; ++dy)
+          for (int dx = -1; dx <= 1 && !dominated; ++dx) dominated = fires(L, cx + dx, cy + dy, v);
+      }
+      if (dominated) keep &= ~(1u << (__ffs(m) - 1));
+    }
+    if (keep != word) *wp = keep;
+  }
+}
+
 }  // namespace
+
+void launch_scale_nms(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
+                      const Params& p, cudaStream_t st) {
+  k_scale_nms<SingleSrc><<<sm_count() * 8, 256, 0, st>>>(SingleSrc{g, b, s, tb, p});
+}
+
+void launch_group_scale_nms(const StreamDev* devs, const TickItem* items, const uint32_t* work,
+                            const uint32_t* work_count, cudaStream_t st) {
+  k_scale_nms<GroupSrc><<<sm_count() * 8, 256, 0, st>>>(GroupSrc{devs, items, work, work_count});
+}
 
 template <int TH>
 int ctas_per_sm(int warps) {

@@ -17,7 +17,7 @@ from . import build as _build
 FKD_OK, FKD_E_ARG, FKD_E_CAPACITY, FKD_E_BUDGET, FKD_E_CUDA, FKD_E_TIMEOUT, FKD_E_STATE = (
     0, -1, -2, -3, -4, -5, -6)
 FKD_MASK_FULL, FKD_MASK_ID, FKD_MASK_KB = 0, 1, 2
-FKD_VERSION = 1
+FKD_VERSION = 2
 FKD_KP_PROPAGATED = 1
 
 KEYPOINT_DTYPE = np.dtype(
@@ -43,7 +43,7 @@ class fkd_params(ctypes.Structure):
     _fields_ = [("version", ctypes.c_uint32)] + [
         (n, ctypes.c_int32) for n in
         ("N_r", "N_c", "T_I", "T_H", "O", "intra", "t", "n", "mask_mode", "mask_layer",
-         "K_max", "T_max")]
+         "K_max", "T_max", "nms_scale")]
 
 
 class fkd_profile(ctypes.Structure):
@@ -177,11 +177,12 @@ class Stream:
     def __init__(self, W: int, H: int, *, N_r: int = 8, N_c: int = 8, T_I: int = 4, T_H: int = 1,
                  O: int = 1, intra: int = 0, t: int = 20, n: int = 9,
                  mask_mode: int = FKD_MASK_ID, mask_layer: int = 0, K_max: int = 65536,
-                 T_max: int = 1, cuda_stream: int | None = None):
+                 T_max: int = 1, cuda_stream: int | None = None, nms_scale: int = 0):
         lib = load()
         p = params_default()
         p.N_r, p.N_c, p.T_I, p.T_H, p.O, p.intra, p.t, p.n = N_r, N_c, T_I, T_H, O, intra, t, n
         p.mask_mode, p.mask_layer, p.K_max, p.T_max = mask_mode, mask_layer, K_max, T_max
+        p.nms_scale = nms_scale
         self.params = p
         self.W, self.H, self.N_r, self.N_c = W, H, N_r, N_c
         h = ctypes.c_void_p()
@@ -329,10 +330,10 @@ class Group:
 
     def add_stream(self, W: int, H: int, *, N_r: int = 8, N_c: int = 8, T_I: int = 4,
                    T_H: int = 1, t: int = 20, mask_mode: int = FKD_MASK_ID, mask_layer: int = 0,
-                   K_max: int = 65536) -> tuple[int, int]:
+                   K_max: int = 65536, nms_scale: int = 0) -> tuple[int, int]:
         p = params_default()
         p.N_r, p.N_c, p.T_I, p.T_H, p.O, p.intra, p.t = N_r, N_c, T_I, T_H, self.O, self.intra, t
-        p.mask_mode, p.mask_layer, p.K_max = mask_mode, mask_layer, K_max
+        p.mask_mode, p.mask_layer, p.K_max, p.nms_scale = mask_mode, mask_layer, K_max, nms_scale
         sid, nbytes = ctypes.c_int(), ctypes.c_size_t()
         _check(_lib.fkd_group_add_stream(self._h, ctypes.byref(p), W, H, ctypes.byref(sid),
                                          ctypes.byref(nbytes)))
@@ -432,10 +433,10 @@ class Server:
 
     def open_stream(self, W: int, H: int, *, N_r: int = 8, N_c: int = 8, T_I: int = 4,
                     T_H: int = 1, t: int = 20, mask_mode: int = FKD_MASK_ID, mask_layer: int = 0,
-                    K_max: int = 16384) -> int:
+                    K_max: int = 16384, nms_scale: int = 0) -> int:
         p = params_default()
         p.N_r, p.N_c, p.T_I, p.T_H, p.O, p.intra, p.t = N_r, N_c, T_I, T_H, self.O, self.intra, t
-        p.mask_mode, p.mask_layer, p.K_max = mask_mode, mask_layer, K_max
+        p.mask_mode, p.mask_layer, p.K_max, p.nms_scale = mask_mode, mask_layer, K_max, nms_scale
         sid = ctypes.c_int()
         _check(_lib.fkd_server_open_stream(self._h, ctypes.byref(p), W, H, ctypes.byref(sid)))
         self.streams[sid.value] = (W, H, K_max)

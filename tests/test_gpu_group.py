@@ -92,3 +92,28 @@ def test_group_equals_solo_streams_and_removal():
     with pytest.raises(fkd.FkdError):
         g.get_keypoints(b)
     g.close()
+
+
+def test_group_mixed_scale_space_suppression():
+    # streams with and without the scale-space suppression in one tick
+    torch = pytest.importorskip("torch")
+    O, intra, m = 3, 1, 5
+    specs = [(320, 240, dict(N_r=8, N_c=8, T_I=4, t=20, nms_scale=1, mask_layer=-1)),
+             (333, 207, dict(N_r=7, N_c=9, T_I=3, t=15, nms_scale=0)),
+             (200, 150, dict(N_r=3, N_c=5, t=12, nms_scale=1, mask_mode=fkd.FKD_MASK_FULL))]
+    stream = torch.cuda.Stream()
+    g = fkd.Group(O, intra, cuda_stream=stream.cuda_stream)
+    refs, clips, ids = [], [], []
+    for i, (W, H, p) in enumerate(specs):
+        clips.append(synth.VideoSource(W, H, seed=70 + i, n_movers=2, mover_size=min(W, H) // 4,
+                                       speed=(2, 4)).frames(m))
+        q = dict(p)
+        mode = q.pop("mask_mode", fkd.FKD_MASK_ID)
+        refs.append(oracle.Stream(W, H, O=O, intra=intra, mask_mode=ORC[mode], **q))
+        ids.append(g.add_stream(W, H, mask_mode=mode, **q)[0])
+    for j in range(m):
+        frames = [torch.from_numpy(np.ascontiguousarray(c[j])).cuda() for c in clips]
+        g.tick(ids, frames)
+        for i, sid in enumerate(ids):
+            refs[i].push(clips[i][j])
+            check(g.get_keypoints(sid), refs[i].keypoints(), f"stream {i} frame {j}")

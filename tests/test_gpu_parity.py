@@ -259,3 +259,30 @@ def test_capacity_errors(clip1):
     exp_kp, _ = run_oracle(frames[:4], **o)
     s2.push_frame(frames[2])
     assert_same_kp(s2.get_keypoints(), exp_kp[2], "frame 2 after overflow")
+
+
+@pytest.mark.parametrize("mode,mask_layer", [("full", 0), ("id", -1), ("id", 0), ("kb", 0)])
+def test_scale_space_suppression(clip2, mode, mask_layer):
+    # nms_scale = 1: detections must also beat the adjacent layers' windows
+    cfg, frames = clip2
+    frames = frames[:12]
+    g, o = both(params(cfg, mask_layer=mask_layer, nms_scale=1), mode)
+    exp_kp, exp_m = run_oracle(frames, **o)
+    s = fkd.Stream(cfg.W, cfg.H, T_max=6, **g)
+    pieces = [1] * 12 if mode == "kb" else [5, 1, 6]
+    push_in_pieces(s, frames, pieces, exp_kp, exp_m)
+    # the suppression removes keypoints on every layer pair
+    g0, o0 = both(params(cfg, mask_layer=mask_layer), mode)
+    plain, _ = run_oracle(frames[:1], **o0)
+    assert len(exp_kp[0]) < len(plain[0])
+
+
+@pytest.mark.parametrize("W,H,O,intra", [(333, 207, 3, 1), (200, 150, 6, 1), (97, 61, 2, 0), (16, 12, 3, 1)])
+def test_scale_space_suppression_ragged(W, H, O, intra):
+    src = synth.VideoSource(W, H, seed=3 * W + H, n_rect=12, n_movers=2, mover_size=max(4, min(W, H) // 3),
+                            speed=(1, 3))
+    frames = src.frames(6)
+    g, o = both(dict(N_r=3, N_c=4, T_I=2, O=O, intra=intra, t=8, nms_scale=1, mask_layer=-1), "id")
+    exp_kp, exp_m = run_oracle(frames, **o)
+    s = fkd.Stream(W, H, T_max=3, **g)
+    push_in_pieces(s, frames, [3, 1, 2], exp_kp, exp_m)
