@@ -605,11 +605,19 @@ def main():
     ms_c0, prof_c0 = timed(masked_c0, max(3, args.steps // 2), 3, profile=True)
     act_c0 = masks.float().mean().item()
 
+    # the masked detection with scale-space suppression (Sec. 2)
+    masked_xs = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_ID, nms_scale=1, **common)
+    masked_xs.set_launch_config(shape_masked)
+    ms_xs, prof_xs = timed(masked_xs, max(3, args.steps // 2), 3, profile=True)
+    off_xs = offsets.cpu().numpy().astype(np.int64)
+    kp_xs = int(off_xs[T] - off_xs[0])
+
     # max over ranks
-    ms, ms_full, ms_c0 = max_over_ranks([ms, ms_full, ms_c0], dist, dev)
+    ms, ms_full, ms_c0, ms_xs = max_over_ranks([ms, ms_full, ms_c0, ms_xs], dist, dev)
     value = whole_job_fps(world, T, args.steps, ms)
     full_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_full)
     c0_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_c0)
+    xs_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_xs)
 
     # frame-by-frame latency (device frames): push_frame + get_keypoints per frame
     lat = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_ID, N_r=cfg.N_r, N_c=cfg.N_c, mask_layer=cfg.mask_layer,
@@ -724,6 +732,11 @@ def main():
                       "what": "the intensity-difference test on c_0 instead of the coarsest octave",
                       "stage_ms_per_step": {k: v / max(1, prof_c0["batches"])
                                             for k, v in prof_c0["ms"].items()}},
+        "masked_nms_scale": {"value": xs_fps, "unit": "frames/s", "keypoints_per_step": kp_xs,
+                             "what": "masked, with scale-space suppression against the adjacent layers "
+                                     "(its pass is timed in the detect stage)",
+                             "stage_ms_per_step": {k: v / max(1, prof_xs["batches"])
+                                                   for k, v in prof_xs["ms"].items()}},
         "active_bin_fraction": act, "keypoints_per_step": kp_masked,
         "stage_ms_per_step": {k: v / max(1, prof["batches"]) for k, v in stage_ms.items()},
         "latency_ms": {"p50": p50, "p99": p99, "frames": len(lat_ms),

@@ -135,10 +135,16 @@ struct Item {
   int N_c;
 };
 
-// One layer of a frame, for the scale-space suppression.
+// One layer of a frame, for the scale-space suppression. Its scale code S
+// is 2^sh or 3 * 2^sh (sh >= 1 or the 3 alone), so n / (2 S) is a shift and
+// at most one division by the constant 3.
 struct LayerView {
   const uint8_t* p;  // null: no such layer
   int pitch, w, h, S;
+  __device__ __forceinline__ int div2S(int n) const {
+    const int q = n >> (__ffs(S) - 1 + 1);  // n / (2 * 2^v2(S))
+    return (S & (S - 1)) ? q / 3 : q;       // S = 3 * 2^k: one more / 3
+  }
 };
 
 // What the scale-space suppression needs of a (frame, tile) work item.
@@ -646,39 +652,73 @@ __device__ __forceinline__ bool fires(const LayerView& L, int x, int y, int v) {
 // detection of layer l survives only if its score is strictly above every
 // score of the 3x3 window, in the layers l-1 and l+1, around the pixel that
 // contains its centre (x' = floor((2x + 1) * S_l / (2 S_l')), likewise y').
-// Thread -> one bitmap word of one active (frame, tile) item; the window's
-// scores are tested against the detection's score directly on the layers.
+// One warp per active (frame, tile) item, 32 bitmap words at a time: every
+// (detection, window pixel) pair of those words becomes one task, the tasks
+// are spread over the lanes, and a window pixel whose segment test fires at
+// the detection's score clears the detection's bit.
+constexpr int kScaleWarps = 8;
 template <class Src>
-__global__ void __launch_bounds__(256) k_scale_nms(Src src) {
+__global__ void __launch_bounds__(kScaleWarps * 32) k_scale_nms(Src src) {
+  __shared__ uint32_t wsm[kScaleWarps][32], pre[kScaleWarps][32], dom[kScaleWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t n_items = src.count();
-  const uint32_t words_per_item = (uint32_t)kDetTH[kDetShapes - 1] * (TW / 32);
-  const unsigned long long total = (unsigned long long)n_items * words_per_item;
-  for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < total;
-       j += (unsigned long long)gridDim.x * blockDim.x) {
-    const uint32_t item = (uint32_t)(j / words_per_item), wi = (uint32_t)(j % words_per_item);
+  for (uint32_t item = blockIdx.x * kScaleWarps + warp; item < n_items; item += gridDim.x * kScaleWarps) {
     const ScaleItem si = src.scale_item(item);
-    if (!si.on || wi >= (uint32_t)si.th * (TW / 32)) continue;
-    const int y = si.ty * si.th + (int)(wi / (TW / 32));
-    const int wx = si.tx * (TW / 32) + (int)(wi % (TW / 32));
-    if (y >= si.h || wx >= si.wpr) continue;
-    uint32_t* wp = si.bits + (long long)y * si.wpr + wx;
-    const uint32_t word = *wp;
-    uint32_t keep = word;
-    for (uint32_t m = word; m; m &= m - 1) {
-      const int x = wx * 32 + (__ffs(m) - 1);
-      const int v = si.dscore[(long long)y * si.dpitch + x];
-      bool dominated = false;
-      for (int a = 0; a < 2 && !dominated; ++a) {
-        const LayerView& L = si.adj[a];
-        if (!L.p) continue;
-        const int cx = (int)(((long long)(2 * x + 1) * si.S) / (2LL * L.S));
-        const int cy = (int)(((long long)(2 * y + 1) * si.S) / (2LL * L.S));
-        for (int dy = -1; dy <= 1 && !dominated; ++dy)
-          for (int dx = -1; dx <= 1 && !dominated; ++dx) dominated = fires(L, cx + dx, cy + dy, v);
+    const int n_adj = (si.adj[0].p ? 1 : 0) + (si.adj[1].p ? 1 : 0);
+    if (!si.on || n_adj == 0) continue;
+    const int nbs = 9 * n_adj;  // window pixels per detection
+    const int words = si.th * (TW / 32);
+    for (int c0 = 0; c0 < words; c0 += 32) {
+      const int wi = c0 + lane;
+      const int y = si.ty * si.th + wi / (TW / 32);
+      const int wx = si.tx * (TW / 32) + wi % (TW / 32);
+      const bool valid = wi < words && y < si.h && wx < si.wpr;
+      uint32_t* wp = si.bits + (long long)y * si.wpr + wx;
+      const uint32_t w = valid ? *wp : 0u;
+      // exclusive prefix of the lanes' task counts
+      const int cnt = __popc(w) * nbs;
+      int incl = cnt;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += o;
       }
-      if (dominated) keep &= ~(1u << (__ffs(m) - 1));
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      if (total == 0) continue;
+      wsm[warp][lane] = w;
+      pre[warp][lane] = (uint32_t)(incl - cnt);
+      dom[warp][lane] = 0u;
+      __syncwarp();
+      for (int t0 = 0; t0 < total; t0 += 32) {
+        const int t = t0 + lane;
+        if (t < total) {
+          // the lane whose tasks hold t: the last with pre <= t
+          int lo = 0, hi = 31;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int)pre[warp][mid] <= t) lo = mid;
+            else hi = mid - 1;
+          }
+          const int owner = lo, local = t - (int)pre[warp][owner];
+          const int bi = local / nbs, nb = local % nbs;
+          uint32_t m = wsm[warp][owner];
+          for (int q = 0; q < bi; ++q) m &= m - 1;
+          const int bit = __ffs(m) - 1;
+          const int owi = c0 + owner;
+          const int oy = si.ty * si.th + owi / (TW / 32);
+          const int ox = (si.tx * (TW / 32) + owi % (TW / 32)) * 32 + bit;
+          const int v = si.dscore[(long long)oy * si.dpitch + ox];
+          const LayerView L = (nb < 9 && si.adj[0].p) ? si.adj[0] : si.adj[1];
+          const int cx = L.div2S((2 * ox + 1) * si.S), cy = L.div2S((2 * oy + 1) * si.S);
+          const int k9 = nb % 9;
+          if (fires(L, cx + k9 % 3 - 1, cy + k9 / 3 - 1, v)) atomicOr(&dom[warp][owner], 1u << bit);
+        }
+      }
+      __syncwarp();
+      const uint32_t d = dom[warp][lane];
+      if (valid && d) *wp = w & ~d;
+      __syncwarp();
     }
-    if (keep != word) *wp = keep;
   }
 }
 
@@ -686,12 +726,12 @@ __global__ void __launch_bounds__(256) k_scale_nms(Src src) {
 
 void launch_scale_nms(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                       const Params& p, cudaStream_t st) {
-  k_scale_nms<SingleSrc><<<sm_count() * 8, 256, 0, st>>>(SingleSrc{g, b, s, tb, p});
+  k_scale_nms<SingleSrc><<<sm_count() * 8, kScaleWarps * 32, 0, st>>>(SingleSrc{g, b, s, tb, p});
 }
 
 void launch_group_scale_nms(const StreamDev* devs, const TickItem* items, const uint32_t* work,
                             const uint32_t* work_count, cudaStream_t st) {
-  k_scale_nms<GroupSrc><<<sm_count() * 8, 256, 0, st>>>(GroupSrc{devs, items, work, work_count});
+  k_scale_nms<GroupSrc><<<sm_count() * 8, kScaleWarps * 32, 0, st>>>(GroupSrc{devs, items, work, work_count});
 }
 
 template <int TH>
