@@ -374,6 +374,74 @@ def run_config5(args):
     return 0
 
 
+def run_sweep(args):
+    """Threshold sweep (the paper's energy-accuracy trade-off, Sec. 4): on the
+    640x480 clip, for each T_I (intensity-difference mask on the coarsest
+    octave) and each T_H (keypoint binning), the active-bin fraction, frames/s
+    and the agreement of D_n with full-frame detection: recall = |D_n and
+    F_n| / |F_n| and precision = |D_n and F_n| / |D_n| over (layer, x, y),
+    averaged over the frames."""
+    import torch
+    from paper_1503_06959_gb300 import fkd
+    cfg = synth.config2()
+    T = args.frames or 120
+    frames = torch.from_numpy(synth.source_for(cfg, 2).frames(T)).cuda()
+    st = torch.cuda.current_stream()
+    base = dict(N_r=cfg.N_r, N_c=cfg.N_c, O=cfg.O, intra=cfg.intra, t=cfg.t, mask_layer=cfg.mask_layer,
+                cuda_stream=st.cuda_stream)
+
+    def run(mode, T_I=cfg.T_I, T_H=1):
+        s = fkd.Stream(cfg.W, cfg.H, mask_mode=mode, T_I=T_I, T_H=T_H, T_max=T, **base)
+        out = torch.empty(T * 65536, dtype=torch.int64, device="cuda")
+        off = torch.empty(T + 1, dtype=torch.int32, device="cuda")
+        msk = torch.empty((T, cfg.N_r, cfg.N_c), dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            s.reset()
+            s.push_frames(frames, out=out, offsets=off, masks=msk)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.reset()
+        s.push_frames(frames, out=out, offsets=off, masks=msk)
+        e1.record(st)
+        s.synchronize()
+        ms = e0.elapsed_time(e1)
+        o = off.cpu().numpy().astype(np.int64)
+        rec = out[:o[T]].cpu().numpy().view(np.uint8).reshape(-1, 8)
+        keys = (rec[:, 4].astype(np.int64) << 32) | (rec[:, 2].astype(np.int64) | rec[:, 3].astype(np.int64) << 8) << 16 \
+            | (rec[:, 0].astype(np.int64) | rec[:, 1].astype(np.int64) << 8)
+        per_frame = [keys[o[k]:o[k + 1]] for k in range(T)]
+        return {"fps": T / (ms / 1e3), "active": float(msk.float().mean().item()), "kp": per_frame}
+
+    full = run(fkd.FKD_MASK_FULL)
+
+    def agree(r):
+        rec_, prec_ = [], []
+        for a, f in zip(r["kp"], full["kp"]):
+            both = np.intersect1d(a, f).size
+            rec_.append(both / max(1, f.size))
+            prec_.append(both / max(1, a.size))
+        return float(np.mean(rec_)), float(np.mean(prec_))
+
+    rows = []
+    for T_I in (1, 2, 4, 8, 16, 32):
+        r = run(fkd.FKD_MASK_ID, T_I=T_I)
+        rc, pc = agree(r)
+        rows.append({"mask": "ID", "T_I": T_I, "active_bin_fraction": r["active"], "frames_per_s": r["fps"],
+                     "time_vs_full": full["fps"] / r["fps"], "recall": rc, "precision": pc})
+    for T_H in (1, 2, 3, 4):
+        r = run(fkd.FKD_MASK_KB, T_H=T_H)
+        rc, pc = agree(r)
+        rows.append({"mask": "KB", "T_H": T_H, "active_bin_fraction": r["active"], "frames_per_s": r["fps"],
+                     "time_vs_full": full["fps"] / r["fps"], "recall": rc, "precision": pc})
+    line = {"metric": "threshold sweep: active bins, frames/s and agreement with full detection",
+            "unit": "frames/s", "n_gpus": 1, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": workload_desc(cfg, T) + "; KB runs frame by frame (its mask needs D_{n-1})"},
+            "full_frame_fps": full["fps"], "rows": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def run_config4(args):
     """Serving: streams of mixed resolution producing frames at 30 fps with
     Poisson jitter, submitted as they arrive; continuous batching."""
@@ -486,6 +554,7 @@ def main():
     ap.add_argument("--latency-frames", type=int, default=300)
     ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5],
                     help="2: the 640x480 clip (default line); 3: stream group; 4: serving; 5: 4K stress")
+    ap.add_argument("--sweep", action="store_true", help="threshold sweep of T_I and T_H on the 640x480 clip")
     ap.add_argument("--streams-per-res", type=int, default=16)
     ap.add_argument("--serve-streams-per-res", type=int, default=64)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
@@ -500,6 +569,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     if args.config == 3:
         return run_config3(args)
     if args.config == 4:
