@@ -30,7 +30,7 @@ KEYPOINT_DTYPE = np.dtype(
     [("x", "<u2"), ("y", "<u2"), ("layer", "u1"), ("score", "u1"), ("flags", "<u2")]
 )
 
-MASK_FULL, MASK_ID, MASK_KB = 0, 1, 2
+MASK_FULL, MASK_ID, MASK_KB, MASK_IDP = 0, 1, 2, 3
 
 
 class _Params(ctypes.Structure):
@@ -143,6 +143,7 @@ class Stream:
                  mask_layer: int = 0, nms_scale: int = 0):
         self.W, self.H, self.N_r, self.N_c = W, H, N_r, N_c
         p = _Params(N_r, N_c, T_I, T_H, O, intra, t, mask_mode, mask_layer, nms_scale)
+        self._O, self._intra = O, intra
         h = ctypes.c_void_p()
         if _load().orc_stream_create(ctypes.byref(p), W, H, ctypes.byref(h)) != 0:
             raise ValueError("invalid oracle stream parameters")
@@ -159,6 +160,16 @@ class Stream:
                                      _ptr(m) if m is not None else None)
         if rc != 0:
             raise RuntimeError("oracle push failed")
+
+    def pixel_mask(self, layer: int) -> np.ndarray:
+        """IDP mode: the last frame's per-pixel mask of a layer (h x w, 0/1)."""
+        lib = _load()
+        W, H = self.W, self.H
+        w, h, _ = layer_geom(W, H, self._O, self._intra, layer)
+        out = np.zeros((h, w), np.uint8)
+        if lib.orc_stream_pixel_mask(self._h, layer, _ptr(out)) != 0:
+            raise ValueError("layer out of range")
+        return out
 
     def keypoints(self) -> np.ndarray:
         lib = _load()

@@ -12,7 +12,8 @@
  * Steps per frame (Sec. 3):
  *   1. pyramid of octaves and intra-octaves (Sec. 2, Sec. 3.1)
  *   2. detection mask M'_n on the N_r x N_c grid: intensity difference
- *      (Eq. 2, Sec. 3.1) or keypoint binning (Eqs. 3-4, Sec. 3.2)
+ *      (Eq. 2, Sec. 3.1) or keypoint binning (Eqs. 3-4, Sec. 3.2); or, per
+ *      pixel of every layer, Eq. 2 itself (mode IDP)
  *   3. segment test with the 16-pixel radius-3 Bresenham ring, corner score,
  *      threshold t and 3x3 non-maximum suppression on every layer (Sec. 2),
  *      optionally over the scale-space neighbourhood (the adjacent layers)
@@ -193,6 +194,7 @@ struct orc_stream {
   size_t nkp, cap;
   uint8_t* mask;     /* M'_n, N_r*N_c */
   uint64_t* bsum;    /* block sums of |L_n - L_{n-1}| (ID) or bin counts (KB) */
+  uint8_t* pmask;    /* IDP: per-pixel masks of every layer (pyramid layout) */
   long frame;        /* index of the last processed frame, -1 before any */
 };
 
@@ -201,7 +203,7 @@ int orc_stream_create(const orc_params* p, int W, int H, orc_stream** out) {
   if (p->N_r < 1 || p->N_c < 1 || p->N_r > H || p->N_c > W) return -1;
   if (p->O < 1 || p->O > 12 || (p->intra != 0 && p->intra != 1)) return -1;
   if (p->t < 1 || p->t > 255 || p->T_I < 0 || p->T_H < 0) return -1;
-  if (p->mask_mode < ORC_MASK_FULL || p->mask_mode > ORC_MASK_KB) return -1;
+  if (p->mask_mode < ORC_MASK_FULL || p->mask_mode > ORC_MASK_IDP) return -1;
   if (p->nms_scale != 0 && p->nms_scale != 1) return -1;
   orc_stream* s = (orc_stream*)calloc(1, sizeof(orc_stream));
   s->p = *p;
@@ -220,6 +222,7 @@ int orc_stream_create(const orc_params* p, int W, int H, orc_stream** out) {
   s->pyr_cur = (uint8_t*)calloc(acc, 1);
   s->mask = (uint8_t*)calloc((size_t)p->N_r * p->N_c, 1);
   s->bsum = (uint64_t*)calloc((size_t)p->N_r * p->N_c, sizeof(uint64_t));
+  s->pmask = (uint8_t*)calloc(acc + 1, 1);
   s->cap = 1024;
   s->kp = (orc_keypoint*)malloc(s->cap * sizeof(orc_keypoint));
   s->nkp = 0;
@@ -230,7 +233,7 @@ int orc_stream_create(const orc_params* p, int W, int H, orc_stream** out) {
 
 void orc_stream_destroy(orc_stream* s) {
   if (!s) return;
-  free(s->pyr_prev); free(s->pyr_cur); free(s->mask); free(s->bsum); free(s->kp);
+  free(s->pyr_prev); free(s->pyr_cur); free(s->mask); free(s->bsum); free(s->kp); free(s->pmask);
   free(s);
 }
 
@@ -270,6 +273,8 @@ int orc_stream_push(orc_stream* s, const uint8_t* frame, size_t pitch, const uin
   } else if (s->frame < 0 || p->mask_mode == ORC_MASK_FULL) {
     /* the first frame has no history: detect everywhere */
     for (int b = 0; b < NB; ++b) s->mask[b] = 1;
+  } else if (p->mask_mode == ORC_MASK_IDP) {
+    /* per pixel, below */
   } else if (p->mask_mode == ORC_MASK_ID) {
     /* Eq. 2 read as "detect where the layer changed": block b is active iff
      * the sum of |L_n - L_{n-1}| over its pixels of the mask layer exceeds
@@ -296,12 +301,27 @@ int orc_stream_push(orc_stream* s, const uint8_t* frame, size_t pitch, const uin
     for (int k = 0; k < NB; ++k) s->mask[k] = s->bsum[k] >= (uint64_t)p->T_H ? 1 : 0;
   }
 
+  /* IDP: Eq. 2 per pixel of every layer, read as "active where the layer
+   * changed by more than T_I" (the mask of layer l decides the pixels of
+   * layer l); every pixel is active on the first frame. The block mask is
+   * then all ones and plays no part. */
+  if (p->mask_mode == ORC_MASK_IDP) {
+    for (int b = 0; b < NB; ++b) s->mask[b] = 1;
+    for (size_t i = 0; i < s->pyr_bytes; ++i) {
+      int dv = (int)s->pyr_cur[i] - (int)s->pyr_prev[i];
+      s->pmask[i] = (s->frame < 0 || (dv < 0 ? -dv : dv) > p->T_I) ? 1 : 0;
+    }
+  }
+#define ORC_ACTIVE(l, x, y)                                                          \
+  (p->mask_mode == ORC_MASK_IDP ? s->pmask[s->loff[l] + (size_t)(y) * s->lw[l] + (x)] \
+                                : s->mask[orc_block_of((x), (y), s->lS[l], W, H, p->N_r, p->N_c)])
+
   /* 3+4. D_n (Eq. 1): keypoints of D_{n-1} in inactive blocks are kept ... */
   orc_keypoint* next = (orc_keypoint*)malloc(1024 * sizeof(orc_keypoint));
   size_t nn = 0, ncap = 1024;
   for (size_t i = 0; i < s->nkp; ++i) {
     orc_keypoint k = s->kp[i];
-    if (!s->mask[orc_block_of(k.x, k.y, s->lS[k.layer], W, H, p->N_r, p->N_c)]) {
+    if (!ORC_ACTIVE(k.layer, k.x, k.y)) {
       k.flags = 1;
       kp_push(&next, &nn, &ncap, k);
     }
@@ -323,7 +343,7 @@ int orc_stream_push(orc_stream* s, const uint8_t* frame, size_t pitch, const uin
       for (int x = 0; x < w; ++x) {
         int v = sc[y * w + x];
         if (v < p->t) continue;
-        if (!s->mask[orc_block_of(x, y, s->lS[l], W, H, p->N_r, p->N_c)]) continue;
+        if (!ORC_ACTIVE(l, x, y)) continue;
         int is_max = 1;
         for (int dy = -1; dy <= 1; ++dy)
           for (int dx = -1; dx <= 1; ++dx) {
@@ -359,6 +379,7 @@ int orc_stream_push(orc_stream* s, const uint8_t* frame, size_t pitch, const uin
       }
   }
   for (int l = 0; l < s->L; ++l) free(scores[l]);
+#undef ORC_ACTIVE
   qsort(next, nn, sizeof(orc_keypoint), kp_cmp);
   free(s->kp);
   s->kp = next; s->nkp = nn; s->cap = ncap;
@@ -374,6 +395,11 @@ void orc_stream_keypoints(const orc_stream* s, orc_keypoint* out) {
 }
 void orc_stream_mask(const orc_stream* s, uint8_t* out) {
   memcpy(out, s->mask, (size_t)s->p.N_r * s->p.N_c);
+}
+int orc_stream_pixel_mask(const orc_stream* s, int l, uint8_t* out) {
+  if (l < 0 || l >= s->L) return -1;
+  memcpy(out, s->pmask + s->loff[l], (size_t)s->lw[l] * s->lh[l]);
+  return 0;
 }
 void orc_stream_block_sums(const orc_stream* s, uint64_t* out) {
   memcpy(out, s->bsum, (size_t)s->p.N_r * s->p.N_c * sizeof(uint64_t));

@@ -33,7 +33,11 @@ typedef struct {
   uint16_t flags;
 } orc_keypoint;
 
-enum { ORC_MASK_FULL = 0, ORC_MASK_ID = 1, ORC_MASK_KB = 2 };
+/* FULL: every pixel active; ID: the block-mean intensity difference (Eq. 2
+ * read per block); KB: keypoint binning (Eqs. 3-4); IDP: Eq. 2 per pixel of
+ * every layer, each layer's mask deciding its own pixels (option (i) of
+ * Sec. 3.1). */
+enum { ORC_MASK_FULL = 0, ORC_MASK_ID = 1, ORC_MASK_KB = 2, ORC_MASK_IDP = 3 };
 
 typedef struct {
   int N_r, N_c;     /* block grid rows, columns (Sec. 3.2)              */
@@ -74,6 +78,8 @@ int orc_stream_push(orc_stream* s, const uint8_t* frame, size_t pitch, const uin
 size_t orc_stream_num_keypoints(const orc_stream* s);
 void orc_stream_keypoints(const orc_stream* s, orc_keypoint* out);
 void orc_stream_mask(const orc_stream* s, uint8_t* out);
+/* IDP mode: the last frame's per-pixel mask of layer l (w*h bytes, 0/1). */
+int orc_stream_pixel_mask(const orc_stream* s, int l, uint8_t* out);
 void orc_stream_block_sums(const orc_stream* s, uint64_t* out);
 long orc_stream_frame_index(const orc_stream* s);
 

@@ -563,3 +563,86 @@ def test_scale_nms_keeps_a_subset_and_removes_only_dominated_points():
                     if 0 <= cy + dy < mh and 0 <= cx + dx < mw and brute_score(layers[m], cx + dx, cy + dy) >= v:
                         found = True
         assert found, (l, y, x, v)
+
+
+# --------------------------------------------------------------------------
+# Eq. 2 per pixel of every layer (mask mode IDP, option (i) of Sec. 3.1)
+
+
+def test_pixel_mask_is_eq2_on_every_layer():
+    rng = np.random.default_rng(21)
+    W, H, O, intra, T_I = 72, 54, 3, 1, 6
+    f0 = np.clip(rng.normal(120, 40, (H, W)), 0, 255).astype(np.uint8)
+    f1 = f0.copy()
+    f1[10:40, 20:60] = np.clip(f1[10:40, 20:60].astype(int) + rng.integers(-30, 31, (30, 40)), 0, 255)
+    s = oracle.Stream(W, H, N_r=2, N_c=3, O=O, intra=intra, t=10, T_I=T_I, mask_mode=oracle.MASK_IDP)
+    s.push(f0)
+    for l in range(oracle.num_layers(O, intra)):
+        assert s.pixel_mask(l).all(), "first frame: every pixel active"
+    s.push(f1)
+    L0, L1 = oracle.pyramid(f0, O, intra), oracle.pyramid(f1, O, intra)
+    for l, (a, b) in enumerate(zip(L0, L1)):
+        exp = (np.abs(b.astype(int) - a.astype(int)) > T_I).astype(np.uint8)
+        np.testing.assert_array_equal(s.pixel_mask(l), exp, err_msg=f"layer {l}")
+    assert 0 < s.pixel_mask(0).mean() < 1
+
+
+def test_pixel_mask_nothing_changes_keeps_everything():
+    rng = np.random.default_rng(22)
+    f = np.clip(rng.normal(120, 50, (40, 48)), 0, 255).astype(np.uint8)
+    s = oracle.Stream(48, 40, N_r=2, N_c=2, O=2, intra=1, t=12, T_I=0, mask_mode=oracle.MASK_IDP)
+    s.push(f)
+    first = kp_tuples(s.keypoints())
+    assert first
+    for _ in range(2):
+        s.push(f)
+        got = kp_tuples(s.keypoints())
+        assert [g[:4] for g in got] == [k[:4] for k in first]
+        assert all(g[4] == 1 for g in got), "all carried over"
+
+
+def test_pixel_mask_everything_changes_redetects_everything():
+    # +1 on every pixel of c_0 (values <= 200) moves every pyramid pixel by
+    # exactly 1: the 2x2 sum grows by 4 and the 3x3 -> 2x2 sum by 9
+    rng = np.random.default_rng(23)
+    f0 = rng.integers(0, 200, (42, 54)).astype(np.uint8)
+    f1 = (f0 + 1).astype(np.uint8)
+    kw = dict(N_r=2, N_c=2, O=2, intra=1, t=10)
+    s = oracle.Stream(54, 42, T_I=0, mask_mode=oracle.MASK_IDP, **kw)
+    s.push(f0)
+    s.push(f1)
+    full = oracle.Stream(54, 42, mask_mode=oracle.MASK_FULL, **kw)
+    full.push(f1)
+    assert kp_tuples(s.keypoints()) == kp_tuples(full.keypoints())
+    for l in range(4):
+        assert s.pixel_mask(l).all()
+
+
+def test_pixel_mask_detection_equals_bruteforce():
+    rng = np.random.default_rng(24)
+    W, H, O, intra, T_I, t = 30, 27, 2, 1, 20, 8
+    big = np.kron(rng.integers(0, 4, (6, 6)), np.ones((6, 6), int))[:H, :W]
+    frames = []
+    for n in range(3):
+        img = big * 60 + rng.integers(0, 3, (H, W)) * 10
+        img[5 + 3 * n:12 + 3 * n, 4:14] = 220 - 30 * n  # a moving plateau
+        frames.append(np.clip(img, 0, 255).astype(np.uint8))
+    s = oracle.Stream(W, H, N_r=1, N_c=1, O=O, intra=intra, t=t, T_I=T_I, mask_mode=oracle.MASK_IDP)
+    prev_layers, prev_kp = None, []
+    for f in frames:
+        s.push(f)
+        layers = oracle.pyramid(f, O, intra)
+        if prev_layers is None:
+            act = [np.ones(L.shape, bool) for L in layers]
+        else:
+            act = [np.abs(L.astype(int) - P.astype(int)) > T_I for L, P in zip(layers, prev_layers)]
+        exp = [(l, y, x, v, 1) for (l, y, x, v, _) in prev_kp if not act[l][y, x]]
+        for l, img in enumerate(layers):
+            for (x, y, v) in brute_detect(img, t):
+                if act[l][y, x]:
+                    exp.append((l, y, x, v, 0))
+        exp.sort()
+        got = kp_tuples(s.keypoints())
+        assert got == exp
+        prev_layers, prev_kp = layers, exp
+    assert any(k[4] == 1 for k in exp) and any(k[4] == 0 for k in exp)
