@@ -57,6 +57,11 @@ extern "C" {
 #define FKD_MASK_FULL 0 /* every bin active: the plain per-frame detector      */
 #define FKD_MASK_ID 1   /* intensity difference detection mask, Eq. 2         */
 #define FKD_MASK_KB 2   /* keypoint binning detection mask, Eqs. 3-4          */
+#define FKD_MASK_IDP 3  /* Eq. 2 per pixel of every layer, option (i) of      */
+                        /* Sec. 3.1: |L_n - L_{n-1}| > T_I at a pixel of      */
+                        /* layer l activates that pixel of layer l; single    */
+                        /* streams only (not groups or servers); the bin mask */
+                        /* of fkd_get_mask is then all ones                   */
 
 /*
  * Parameters, named as the paper names them.
@@ -178,6 +183,11 @@ int fkd_get_keypoints(fkd_stream* s, fkd_keypoint* out, size_t cap, size_t* n_ou
 /* Wait for the last pushed frame and copy its mask M'_n (N_r*N_c bytes, row
  * major, 1 = active bin) to host memory `out`. Errors: FKD_E_STATE, FKD_E_CUDA. */
 int fkd_get_mask(fkd_stream* s, uint8_t* out);
+
+/* FKD_MASK_IDP: the last frame's per-pixel mask of `layer` into host memory
+ * (w*h bytes of 0/1, row-major, w and h as fkd_layer_info gives). Waits.
+ * Errors: FKD_E_ARG (not FKD_MASK_IDP, bad layer), FKD_E_STATE (no frame). */
+int fkd_get_pixel_mask(fkd_stream* s, int layer, uint8_t* out);
 
 /*
  * Process T consecutive frames of the stream in one batched launch sequence

@@ -67,6 +67,7 @@ struct fkd_stream {
   AsmChunk* chunks = nullptr;
   uint32_t* wbins = nullptr;
   uint32_t* wmask = nullptr;
+  int* rowchunk = nullptr;
 
   Scratch s{};
   uint32_t* state_bits[2] = {nullptr, nullptr};
@@ -88,6 +89,7 @@ struct fkd_stream {
   const uint8_t* prev = nullptr;
   int prev_pitch = 0;
   long long frame = 0;
+  long long last_frame_slot = 0;  // batch slot of the last frame pushed
   DetLaunch dl{};
   fkd_launch_config lc{};
   bool have_frame_result = false;
@@ -148,7 +150,7 @@ int validate(const fkd_params* p, int W, int H) {
   if (p->t < 1 || p->t > 255) return fail(FKD_E_ARG, "t=%d outside 1..255", p->t);
   if (p->n != 9) return fail(FKD_E_ARG, "arc length n=%d: only 9 is supported", p->n);
   if (p->T_I < 0 || p->T_H < 0) return fail(FKD_E_ARG, "thresholds must be >= 0");
-  if (p->mask_mode < FKD_MASK_FULL || p->mask_mode > FKD_MASK_KB) return fail(FKD_E_ARG, "bad mask_mode");
+  if (p->mask_mode < FKD_MASK_FULL || p->mask_mode > FKD_MASK_IDP) return fail(FKD_E_ARG, "bad mask_mode");
   const int L = p->intra ? 2 * p->O : p->O;
   if (p->mask_layer < -1 || p->mask_layer >= L) return fail(FKD_E_ARG, "mask_layer %d outside -1..%d", p->mask_layer, L - 1);
   if (p->K_max < 1) return fail(FKD_E_ARG, "K_max must be >= 1");
@@ -188,6 +190,7 @@ int build_geometry(fkd_stream* s, int W, int H) {
   std::vector<DetTile> tiles[kDetShapes];
   std::vector<AsmChunk> chunks;
   std::vector<uint32_t> wbins, wmask;
+  std::vector<int> rowchunk;
   long long pyr = 0, score = 0, bits = 0;
   for (int l = 0; l < g.L; ++l) {
     LayerGeom& lg = g.layer[l];
@@ -230,7 +233,12 @@ int build_geometry(fkd_stream* s, int W, int H) {
     // assembly chunks: bands of whole rows, about kAsmChunkWords words each
     if (lg.wpr > 0) {
       const int rows = std::max(1, kAsmChunkWords / lg.wpr);
-      for (int y0 = 0; y0 < lg.h; y0 += rows) chunks.push_back(AsmChunk{l, y0, std::min(lg.h, y0 + rows)});
+      for (int y0 = 0; y0 < lg.h; y0 += rows) {
+        for (int y = y0; y < std::min(lg.h, y0 + rows); ++y) rowchunk.push_back((int)chunks.size());
+        chunks.push_back(AsmChunk{l, y0, std::min(lg.h, y0 + rows)});
+      }
+    } else {
+      for (int y = 0; y < lg.h; ++y) rowchunk.push_back(0);
     }
     // detection tiles of every shape: kDetTW x TH rectangles, row-major
     for (int k = 0; k < kDetShapes && lg.w > 0 && lg.h > 0; ++k) {
@@ -276,8 +284,11 @@ int build_geometry(fkd_stream* s, int W, int H) {
   if ((rc = s->alloc(&s->colblk, colblk.size())) || (rc = s->alloc(&s->rowblk, rowblk.size())) ||
       (rc = s->alloc(&s->xstart, xstart.size())) || (rc = s->alloc(&s->npix, npix.size())) ||
       (rc = s->alloc(&s->tile_shape[0], all_tiles)) || (rc = s->alloc(&s->chunks, chunks.size())) ||
-      (rc = s->alloc(&s->wbins, wbins.size())) || (rc = s->alloc(&s->wmask, wmask.size())))
+      (rc = s->alloc(&s->wbins, wbins.size())) || (rc = s->alloc(&s->wmask, wmask.size())) ||
+      (rc = s->alloc(&s->rowchunk, rowchunk.size())))
     return rc;
+  if (!rowchunk.empty())
+    CK(cudaMemcpy(s->rowchunk, rowchunk.data(), rowchunk.size() * sizeof(int), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->wmask, wmask.data(), wmask.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->chunks, chunks.data(), chunks.size() * sizeof(AsmChunk), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->wbins, wbins.data(), wbins.size() * 4, cudaMemcpyHostToDevice));
@@ -315,6 +326,12 @@ int allocate_state(fkd_stream* s) {
     return rc;
   CK(cudaMemset(sc.tile_stats, 0, 16));
   CK(cudaMemset(sc.done, 0, 4));
+  sc.pmask = nullptr;
+  sc.pyr_last = nullptr;
+  if (s->p.mask_mode == FKD_MASK_IDP &&
+      ((rc = s->alloc(&sc.pmask, (size_t)(T * std::max(g.bit_words, 1LL)))) ||
+       (rc = s->alloc(&sc.pyr_last, (size_t)g.pyr_bytes))))
+    return rc;
   for (int i = 0; i < 2; ++i) {
     if ((rc = s->alloc(&s->state_bits[i], (size_t)std::max(g.bit_words, 1LL))) ||
         (rc = s->alloc(&s->state_score[i], (size_t)g.score_bytes)) ||
@@ -348,7 +365,7 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   b.prev_pitch = s->prev_pitch;
   b.c0_vec = 0;
   Params pr{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode, s->p.nms_scale};
-  Tables tb{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask};
+  Tables tb{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask, s->rowchunk};
   State stt{};
   stt.bits_in = s->state_bits[s->state_cur];
   stt.score_in = s->state_score[s->state_cur];
@@ -370,16 +387,21 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   launch_pyramid(s->g, tb, b, s->s, pr, s->st);
   mark(1);
   launch_mask(s->g, tb, b, s->s, pr, stt, s->st, reset_base ? base_slot : -1);
+  if (s->s.pmask) launch_pixel_mask(s->g, b, s->s, pr, s->st);
   mark(2);
   launch_worklist(s->g, tb, b, s->s, s->st);
   mark(3);
   launch_detect(s->g, tb, b, s->s, pr, s->dl, s->st);
   if (pr.nms_scale) launch_scale_nms(s->g, tb, b, s->s, pr, s->st);
   mark(4);
-  launch_count(s->g, tb, b, s->s, stt, s->st);  // its last CTA also fills s->s.bases
+  if (s->s.pmask) launch_count_pixel(s->g, tb, b, s->s, stt, s->st);  // its last CTA fills bases
+  else launch_count(s->g, tb, b, s->s, stt, s->st);                   // its last CTA fills s->s.bases
   mark(5);
   launch_emit(s->g, tb, b, s->s, stt, o, s->st);
   mark(6);
+  if (s->s.pmask && s->g.L > 1)  // layers >= 1 of the batch's last frame: L_{n-1} of the next batch
+    CK(cudaMemcpyAsync(s->s.pyr_last, s->s.pyr + (long long)(T - 1) * s->g.pyr_bytes, (size_t)s->g.pyr_bytes,
+                       cudaMemcpyDeviceToDevice, s->st));
   CK(cudaGetLastError());
   if (prof) {
     pd.frames = T;
@@ -391,6 +413,7 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   s->prev_pitch = pitch;
   s->frame += T;
   s->last_mask = s->s.mask + (long long)(T - 1) * s->g.NB;
+  s->last_frame_slot = T - 1;
   return FKD_OK;
 }
 
@@ -685,6 +708,23 @@ int fkd_get_mask(fkd_stream* s, uint8_t* out) {
   return FKD_OK;
 }
 
+int fkd_get_pixel_mask(fkd_stream* s, int layer, uint8_t* out) {
+  if (!s || !out) return fail(FKD_E_ARG, "NULL argument");
+  if (!s->s.pmask) return fail(FKD_E_ARG, "the stream does not use FKD_MASK_IDP");
+  if (layer < 0 || layer >= s->g.L) return fail(FKD_E_ARG, "layer %d outside 0..%d", layer, s->g.L - 1);
+  if (!s->last_mask) return fail(FKD_E_STATE, "no frame pushed yet");
+  const LayerGeom& lg = s->g.layer[layer];
+  std::vector<uint32_t> words((size_t)lg.wpr * lg.h);
+  const long long last = s->last_frame_slot;
+  if (!words.empty())
+    CK(cudaMemcpyAsync(words.data(), s->s.pmask + last * s->g.bit_words + lg.bit_off, words.size() * 4,
+                       cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  for (int y = 0; y < lg.h; ++y)
+    for (int x = 0; x < lg.w; ++x) out[(size_t)y * lg.w + x] = (words[(size_t)y * lg.wpr + x / 32] >> (x % 32)) & 1u;
+  return FKD_OK;
+}
+
 int fkd_synchronize(fkd_stream* s) {
   if (!s) return fail(FKD_E_ARG, "stream is NULL");
   int ov = 0;
@@ -897,7 +937,7 @@ constexpr size_t kTickBytes = kItemsOffset + kMaxTickItems * sizeof(TickItem);
 StreamDev make_dev(const fkd_stream* s, uint8_t* const last[2], fkd_keypoint* rec1, uint32_t* off1) {
   StreamDev d{};
   d.g = s->g;
-  d.tb = Tables{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask};
+  d.tb = Tables{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask, s->rowchunk};
   d.s = s->s;
   d.s.bases = nullptr;  // group ticks (one frame) compute their offsets in place
   d.p = Params{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode, s->p.nms_scale};
@@ -1035,6 +1075,7 @@ int fkd_group_add_stream(fkd_group* G, const fkd_params* p, int W, int H, int* s
   if (!G || !p || !stream_id) return fail(FKD_E_ARG, "NULL argument");
   if (p->O != G->O || p->intra != G->intra)
     return fail(FKD_E_ARG, "stream O/intra (%d/%d) differ from the group's (%d/%d)", p->O, p->intra, G->O, G->intra);
+  if (p->mask_mode == FKD_MASK_IDP) return fail(FKD_E_ARG, "FKD_MASK_IDP is for single streams, not groups");
   CK(cudaStreamSynchronize(G->st));
   fkd_params q = *p;
   q.T_max = 1;

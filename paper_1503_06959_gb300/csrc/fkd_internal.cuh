@@ -113,6 +113,7 @@ struct Tables {
   const AsmChunk* chunks;  // per assembly chunk of a frame
   const uint32_t* wbins;   // per layer, per bitmap word column: first | last bin column << 16
   const uint32_t* wmask;   // per layer, per bitmap word column: bits of the word in its first bin
+  const int* rowchunk;     // per layer, per y: the assembly chunk holding the row
 };
 
 // Arguments of one batch of T consecutive frames of one stream.
@@ -152,6 +153,8 @@ struct Scratch {
   int* overflow;                   // [1]
   unsigned long long* tile_stats;  // [2]: detection tiles and their layer pixels (running totals)
   uint8_t* ml_prev;                // the mask layer of the stream's last frame (mask layers above c_0)
+  uint32_t* pmask;                 // [T_max][bit_words]: per-pixel masks, FKD_MASK_IDP only (else null)
+  uint8_t* pyr_last;               // FKD_MASK_IDP: layers >= 1 of the stream's last frame
 };
 
 // The kept keypoint set D_{n-1} as a per-pixel bitmap + score map, ping-pong.
@@ -266,6 +269,12 @@ void launch_count(const Geometry& g, const Tables& tb, const Batch& b, const Scr
                   const State& state, cudaStream_t st);
 void launch_emit(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                  const State& state, const Output& out, cudaStream_t st);
+// FKD_MASK_IDP: per-pixel masks of every layer of the batch (Eq. 2 per
+// pixel), and D_n of every frame by the per-pixel recurrence of Eq. 1.
+void launch_pixel_mask(const Geometry& g, const Batch& b, const Scratch& s, const Params& p,
+                       cudaStream_t st);
+void launch_count_pixel(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
+                        const State& state, cudaStream_t st);
 // CTAs of the detection kernel resident per SM for a tile shape and warp
 // count (0 when it cannot launch), and the SM count.
 int detect_ctas_per_sm(int shape, int warps);

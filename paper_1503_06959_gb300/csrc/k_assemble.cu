@@ -261,10 +261,20 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
     const int x = (j - yy * wpr_) * 32 + (p & 31);
     const int r = tb.rowblk[lg.row_off + y];
     const int c = colblk[x];
-    const int sf = src_k[r * g.N_c + c];
     const long long so = lg.score_off + (long long)y * lg.pitch + x;
-    const uint8_t score = sf < 0 ? st.score_in[so] : s.det_score[(long long)sf * g.score_bytes + so];
-    const uint32_t flags = sf != k ? FKD_KP_PROPAGATED : 0u;
+    uint8_t score;
+    uint32_t flags;
+    if (s.pmask) {
+      // per-pixel masks: every frame's map holds its keypoints' scores; a
+      // keypoint is carried where its pixel was inactive
+      score = s.det_score[(long long)k * g.score_bytes + so];
+      const uint32_t mw = s.pmask[(long long)k * g.bit_words + word0 + j];
+      flags = ((mw >> (p & 31)) & 1u) ? 0u : FKD_KP_PROPAGATED;
+    } else {
+      const int sf = src_k[r * g.N_c + c];
+      score = sf < 0 ? st.score_in[so] : s.det_score[(long long)sf * g.score_bytes + so];
+      flags = sf != k ? FKD_KP_PROPAGATED : 0u;
+    }
     const unsigned long long idx = base + i;
     if (idx < (unsigned long long)out.cap) {
       uint2 rec;
@@ -301,10 +311,17 @@ __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb
         wv &= wv - 1;
         const int x = wx * 32 + bit;
         const int c = colblk[x];
-        const int sf = srcrow[c];
-        const uint8_t score = sf < 0 ? st.score_in[row_off + x]
-                                     : s.det_score[(long long)sf * g.score_bytes + row_off + x];
-        const uint32_t flags = sf != k ? FKD_KP_PROPAGATED : 0u;
+        uint8_t score;
+        uint32_t flags;
+        if (s.pmask) {  // per-pixel masks: as in the list path of emit_chunk
+          score = s.det_score[(long long)k * g.score_bytes + row_off + x];
+          const uint32_t mw = s.pmask[(long long)k * g.bit_words + lg.bit_off + (long long)y * wpr + wx];
+          flags = ((mw >> bit) & 1u) ? 0u : FKD_KP_PROPAGATED;
+        } else {
+          const int sf = srcrow[c];
+          score = sf < 0 ? st.score_in[row_off + x] : s.det_score[(long long)sf * g.score_bytes + row_off + x];
+          flags = sf != k ? FKD_KP_PROPAGATED : 0u;
+        }
         if (idx < (unsigned long long)out.cap) {
           uint2 rec;
           rec.x = (uint32_t)x | ((uint32_t)y << 16);

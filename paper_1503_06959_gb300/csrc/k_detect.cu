@@ -133,6 +133,7 @@ struct Item {
   const uint16_t* colblk;    // bin column of each layer column
   const uint16_t* rowblk;    // bin row of each layer row
   int N_c;
+  const uint32_t* pmask;     // per-pixel mask of the layer (row 0; FKD_MASK_IDP), else null
 };
 
 // One layer of a frame, for the scale-space suppression. Its scale code S
@@ -193,6 +194,7 @@ struct SingleSrc {
     it.colblk = tb.colblk + lg.col_off;
     it.rowblk = tb.rowblk + lg.row_off;
     it.N_c = g.N_c;
+    it.pmask = s.pmask ? s.pmask + (long long)k * g.bit_words + lg.bit_off : nullptr;
     return it;
   }
   __device__ __forceinline__ ScaleItem scale_item(uint32_t item) const {
@@ -271,6 +273,7 @@ struct GroupSrc {
     it.colblk = d.tb.colblk + lg.col_off;
     it.rowblk = d.tb.rowblk + lg.row_off;
     it.N_c = d.g.N_c;
+    it.pmask = nullptr;  // groups use bin masks
     return it;
   }
   __device__ __forceinline__ ScaleItem scale_item(uint32_t item) const {
@@ -324,6 +327,24 @@ struct GroupSrc {
 template <int TH>
 __device__ __forceinline__ uint32_t active_rows(const Item& it, int lane) {
   constexpr int SC_H = Shape<TH>::SC_H;
+  if (it.pmask) {
+    // per-pixel masks: bit d for layer row y0-2+d when any of the lane's
+    // pixels x .. x+3, or x-1, x+4, is active in it; score row rr then needs
+    // rows rr .. rr+2 of those
+    const int x = it.x0 + 4 * lane, wx = x >> 5, bo = x & 31;
+    uint32_t d = 0;
+    for (int r = 0; r < TH + 4; ++r) {
+      const int yy = it.y0 - 2 + r;
+      if (yy < 0 || yy >= it.h || wx >= it.wpr) continue;
+      const uint32_t* row = it.pmask + (long long)yy * it.wpr;
+      const uint32_t w0 = row[wx];
+      bool any = ((w0 >> bo) & 0xfu) != 0u;
+      any |= bo > 0 ? ((w0 >> (bo - 1)) & 1u) != 0u : (wx > 0 && (row[wx - 1] >> 31));
+      any |= bo < 28 ? ((w0 >> (bo + 4)) & 1u) != 0u : (wx + 1 < it.wpr && (row[wx + 1] & 1u));
+      if (any) d |= 1u << r;
+    }
+    return d | (d >> 1) | (d >> 2);
+  }
   if (!it.mask) return 0xffffffffu;
   const int x = it.x0 + 4 * lane;
   const int xa = max(0, min(it.w - 1, x - 1)), xb = max(0, min(it.w - 1, x + 4));

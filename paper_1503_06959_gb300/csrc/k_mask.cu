@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Ba
     int m = 0;
     if (k < b.T) {
       const long long n = b.first_frame + k;
-      if (n == 0 || p.mask_mode == FKD_MASK_FULL) {
-        m = 1;
+      if (n == 0 || p.mask_mode == FKD_MASK_FULL || p.mask_mode == FKD_MASK_IDP) {
+        m = 1;  // (per-pixel masks decide in the detection and assembly passes)
       } else if (p.mask_mode == FKD_MASK_ID) {
         unsigned long long* sum = s.bsum + (long long)bin * s.bsum_stride + k;
         m = *sum > (unsigned long long)p.T_I * tb.npix[bin];
@@ -174,10 +174,21 @@ __global__ void k_worklist(Geometry g, Tables tb, Batch b, Scratch s) {
   if (i < total) {
     const int k = (int)(i / g.n_tiles), tile = (int)(i % g.n_tiles);
     const DetTile t = tb.tiles[tile];
-    const uint8_t* m = s.mask + (long long)k * g.NB;
-    for (int r = t.rb0; r <= t.rb1 && !act; ++r)
-      for (int c = t.cb0; c <= t.cb1; ++c)
-        if (m[r * g.N_c + c]) { act = true; break; }
+    if (s.pmask) {
+      // per-pixel masks: a tile is active when any of its own pixels is
+      const LayerGeom& lg = g.layer[t.layer];
+      const int th = det_th(g.det_shape), wpt = kDetTW / 32;
+      const uint32_t* pm = s.pmask + (long long)k * g.bit_words + lg.bit_off;
+      const int y1 = min(lg.h, (t.ty + 1) * th), w1 = min(lg.wpr, (t.tx + 1) * wpt);
+      for (int y = t.ty * th; y < y1 && !act; ++y)
+        for (int wx = t.tx * wpt; wx < w1; ++wx)
+          if (pm[(long long)y * lg.wpr + wx]) { act = true; break; }
+    } else {
+      const uint8_t* m = s.mask + (long long)k * g.NB;
+      for (int r = t.rb0; r <= t.rb1 && !act; ++r)
+        for (int c = t.cb0; c <= t.cb1; ++c)
+          if (m[r * g.N_c + c]) { act = true; break; }
+    }
     if (act) area = t.area;
   }
   const unsigned bal = __ballot_sync(0xffffffffu, act);

@@ -16,7 +16,7 @@ from . import build as _build
 
 FKD_OK, FKD_E_ARG, FKD_E_CAPACITY, FKD_E_BUDGET, FKD_E_CUDA, FKD_E_TIMEOUT, FKD_E_STATE = (
     0, -1, -2, -3, -4, -5, -6)
-FKD_MASK_FULL, FKD_MASK_ID, FKD_MASK_KB = 0, 1, 2
+FKD_MASK_FULL, FKD_MASK_ID, FKD_MASK_KB, FKD_MASK_IDP = 0, 1, 2, 3
 FKD_VERSION = 2
 FKD_KP_PROPAGATED = 1
 
@@ -35,6 +35,7 @@ EXPORTS = [
     "fkd_server_close_stream", "fkd_server_submit", "fkd_server_poll", "fkd_server_drain",
     "fkd_server_get_stats", "fkd_get_launch_config", "fkd_set_launch_config", "fkd_autotune",
     "fkd_group_get_launch_config", "fkd_group_set_launch_config", "fkd_group_autotune",
+    "fkd_get_pixel_mask",
 ]
 STAGES = ["pyramid", "mask", "worklist", "detect", "count", "emit"]
 
@@ -132,6 +133,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.fkd_server_poll.argtypes = [vp, c_int, P(ctypes.c_int64), vp, c_size, P(c_size)]
     lib.fkd_server_drain.argtypes = [vp, c_int]
     lib.fkd_server_get_stats.argtypes = [vp, P(fkd_server_stats), c_int]
+    lib.fkd_get_pixel_mask.argtypes = [vp, c_int, vp]
     lib.fkd_get_launch_config.argtypes = [vp, P(fkd_launch_config)]
     lib.fkd_set_launch_config.argtypes = [vp, P(fkd_launch_config)]
     lib.fkd_autotune.argtypes = [vp, vp, c_size, c_size, c_int, c_int, P(fkd_launch_config),
@@ -219,6 +221,13 @@ class Stream:
         n = ctypes.c_size_t()
         _check(_lib.fkd_get_keypoints(self._h, _ptr(out), cap, ctypes.byref(n)))
         return out[:n.value].copy()
+
+    def get_pixel_mask(self, layer: int) -> np.ndarray:
+        """FKD_MASK_IDP: the last frame's per-pixel mask of a layer (h x w, 0/1)."""
+        w, h, _ = self.layer_info(layer)
+        out = np.zeros((h, w), np.uint8)
+        _check(_lib.fkd_get_pixel_mask(self._h, layer, _ptr(out)))
+        return out
 
     def get_mask(self) -> np.ndarray:
         out = np.zeros(self.N_r * self.N_c, np.uint8)

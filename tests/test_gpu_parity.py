@@ -286,3 +286,61 @@ def test_scale_space_suppression_ragged(W, H, O, intra):
     exp_kp, exp_m = run_oracle(frames, **o)
     s = fkd.Stream(W, H, T_max=3, **g)
     push_in_pieces(s, frames, [3, 1, 2], exp_kp, exp_m)
+
+
+def pixel_masks_equal(s, ref, L):
+    for l in range(L):
+        np.testing.assert_array_equal(s.get_pixel_mask(l), ref.pixel_mask(l), err_msg=f"layer {l}")
+
+
+@pytest.mark.parametrize("T_I,mask_nms", [(8, 0), (4, 1), (20, 0)])
+def test_per_pixel_mask(clip2, T_I, mask_nms):
+    # Eq. 2 per pixel of every layer; batches, single pushes, the camera step
+    cfg, frames = clip2
+    frames = frames[:34]
+    kw = dict(N_r=cfg.N_r, N_c=cfg.N_c, T_I=T_I, O=cfg.O, intra=cfg.intra, t=cfg.t, nms_scale=mask_nms)
+    ref = oracle.Stream(cfg.W, cfg.H, mask_mode=oracle.MASK_IDP, **kw)
+    exp = []
+    for f in frames:
+        ref.push(f)
+        exp.append(ref.keypoints())
+    s = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_IDP, T_max=12, **kw)
+    n = 0
+    for T in [10, 1, 1, 12, 10]:
+        if T == 1:
+            s.push_frame(frames[n])
+            assert_same_kp(s.get_keypoints(), exp[n], f"frame {n}")
+        else:
+            rec, off, _ = s.push_frames(frames[n:n + T], want_masks=False)
+            for k, kp in enumerate(fkd.split_frames(rec, off)):
+                assert_same_kp(kp, exp[n + k], f"frame {n + k}")
+        n += T
+    pixel_masks_equal(s, ref, 8)
+    assert any((k["flags"] == 1).any() for k in exp[1:]) and any((k["flags"] == 0).any() for k in exp[1:])
+
+
+@pytest.mark.parametrize("W,H,O,intra", [(333, 207, 3, 1), (97, 61, 2, 0), (16, 12, 3, 1), (200, 150, 6, 1)])
+def test_per_pixel_mask_ragged(W, H, O, intra):
+    src = synth.VideoSource(W, H, seed=5 * W + H, n_rect=12, n_movers=2, mover_size=max(4, min(W, H) // 3),
+                            speed=(1, 3))
+    frames = src.frames(7)
+    kw = dict(N_r=3, N_c=4, T_I=5, O=O, intra=intra, t=8)
+    ref = oracle.Stream(W, H, mask_mode=oracle.MASK_IDP, **kw)
+    exp = []
+    for f in frames:
+        ref.push(f)
+        exp.append(ref.keypoints())
+    s = fkd.Stream(W, H, mask_mode=fkd.FKD_MASK_IDP, T_max=3, **kw)
+    n = 0
+    for T in [3, 1, 3]:
+        rec, off, _ = s.push_frames(frames[n:n + T], want_masks=False)
+        for k, kp in enumerate(fkd.split_frames(rec, off)):
+            assert_same_kp(kp, exp[n + k], f"frame {n + k}")
+        n += T
+    pixel_masks_equal(s, ref, oracle.num_layers(O, intra))
+
+
+def test_per_pixel_mask_rejected_in_groups():
+    g = fkd.Group(2, 1)
+    with pytest.raises(fkd.FkdError):
+        g.add_stream(64, 48, mask_mode=fkd.FKD_MASK_IDP)
