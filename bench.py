@@ -704,6 +704,12 @@ def main():
     ms_c0, prof_c0 = timed(masked_c0, max(3, args.steps // 2), 3, profile=True)
     act_c0 = masks.float().mean().item()
 
+    # Eq. 2 per pixel of every layer (option (i) of Sec. 3.1)
+    masked_px = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_IDP, **common)
+    masked_px.set_launch_config(shape_masked)
+    ms_px, prof_px = timed(masked_px, max(3, args.steps // 2), 3, profile=True)
+    px_tiles = prof_px["tile_pixels"] / max(1, prof_px["batches"])
+
     # the masked detection with scale-space suppression (Sec. 2)
     masked_xs = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_ID, nms_scale=1, **common)
     masked_xs.set_launch_config(shape_masked)
@@ -712,11 +718,12 @@ def main():
     kp_xs = int(off_xs[T] - off_xs[0])
 
     # max over ranks
-    ms, ms_full, ms_c0, ms_xs = max_over_ranks([ms, ms_full, ms_c0, ms_xs], dist, dev)
+    ms, ms_full, ms_c0, ms_xs, ms_px = max_over_ranks([ms, ms_full, ms_c0, ms_xs, ms_px], dist, dev)
     value = whole_job_fps(world, T, args.steps, ms)
     full_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_full)
     c0_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_c0)
     xs_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_xs)
+    px_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_px)
 
     # frame-by-frame latency (device frames): push_frame + get_keypoints per frame
     lat = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_ID, N_r=cfg.N_r, N_c=cfg.N_c, mask_layer=cfg.mask_layer,
@@ -831,6 +838,11 @@ def main():
                       "what": "the intensity-difference test on c_0 instead of the coarsest octave",
                       "stage_ms_per_step": {k: v / max(1, prof_c0["batches"])
                                             for k, v in prof_c0["ms"].items()}},
+        "masked_pixel": {"value": px_fps, "unit": "frames/s", "masked_over_full": px_fps / full_fps,
+                         "tile_pixels_per_step": px_tiles,
+                         "what": "Eq. 2 per pixel of every layer (each layer's own mask), T_I as above",
+                         "stage_ms_per_step": {k: v / max(1, prof_px["batches"])
+                                               for k, v in prof_px["ms"].items()}},
         "masked_nms_scale": {"value": xs_fps, "unit": "frames/s", "keypoints_per_step": kp_xs,
                              "what": "masked, with scale-space suppression against the adjacent layers "
                                      "(its pass is timed in the detect stage)",

@@ -91,8 +91,13 @@ __device__ __forceinline__ void count_chunk(const Geometry& g, const Tables& tb,
       if ((yy + 1) * wpr <= j) ++yy;
       const int wx = j - yy * wpr;
       const int* srcrow = src_k + tb.rowblk[lg.row_off + ch.y0 + yy] * g.N_c;
-      const uint32_t word = merge_word(g, tb, s, st, lg, xst, srcrow, word0, j, wx);
-      out[j] = word;
+      uint32_t word;
+      if (s.pmask) {
+        word = out[j];  // per-pixel masks: merged by the per-pixel recurrence
+      } else {
+        word = merge_word(g, tb, s, st, lg, xst, srcrow, word0, j, wx);
+        out[j] = word;
+      }
       cnt += __popc(word);
     }
   }

@@ -328,22 +328,37 @@ template <int TH>
 __device__ __forceinline__ uint32_t active_rows(const Item& it, int lane) {
   constexpr int SC_H = Shape<TH>::SC_H;
   if (it.pmask) {
-    // per-pixel masks: bit d for layer row y0-2+d when any of the lane's
-    // pixels x .. x+3, or x-1, x+4, is active in it; score row rr then needs
-    // rows rr .. rr+2 of those
-    const int x = it.x0 + 4 * lane, wx = x >> 5, bo = x & 31;
-    uint32_t d = 0;
-    for (int r = 0; r < TH + 4; ++r) {
-      const int yy = it.y0 - 2 + r;
-      if (yy < 0 || yy >= it.h || wx >= it.wpr) continue;
-      const uint32_t* row = it.pmask + (long long)yy * it.wpr;
-      const uint32_t w0 = row[wx];
-      bool any = ((w0 >> bo) & 0xfu) != 0u;
-      any |= bo > 0 ? ((w0 >> (bo - 1)) & 1u) != 0u : (wx > 0 && (row[wx - 1] >> 31));
-      any |= bo < 28 ? ((w0 >> (bo + 4)) & 1u) != 0u : (wx + 1 < it.wpr && (row[wx + 1] & 1u));
-      if (any) d |= 1u << r;
+    // per-pixel masks, bit-parallel: lane r loads mask row y0-2+r (words
+    // x0-32 .. x0+159), dilates it by one pixel left and right; rows r .. r+2
+    // are OR-ed (the vertical dilation) for score row r; the 128 bits of a
+    // score row shrink to one bit per 4-pixel word; a 32 x 32 bit transpose
+    // gives each lane its word's rows
+    const int yy = it.y0 - 2 + lane, wb = it.x0 >> 5;
+    const bool row_ok = lane < TH + 4 && yy >= 0 && yy < it.h;
+    uint32_t W[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const int wx = wb - 1 + i;
+      W[i] = (row_ok && wx >= 0 && wx < it.wpr) ? it.pmask[(long long)yy * it.wpr + wx] : 0u;
     }
-    return d | (d >> 1) | (d >> 2);
+    uint32_t act32 = 0u;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t c = W[i + 1];
+      const uint32_t dh = c | (c << 1) | (c >> 1) | (W[i] >> 31) | (W[i + 2] << 31);
+      const uint32_t dv = dh | __shfl_down_sync(0xffffffffu, dh, 1) | __shfl_down_sync(0xffffffffu, dh, 2);
+      // any bit of each 4-bit group -> bits 0, 4, ..., 28 -> bits 0 .. 7
+      uint32_t n = (dv | (dv >> 1) | (dv >> 2) | (dv >> 3)) & 0x11111111u;
+      n = (n | (n >> 3)) & 0x03030303u;
+      n = (n | (n >> 6)) & 0x000f000fu;
+      n = (n | (n >> 12)) & 0xffu;
+      act32 |= n << (8 * i);
+    }
+    if (lane >= SC_H) act32 = 0u;
+    uint32_t rows = 0u;
+#pragma unroll
+    for (int rr = 0; rr < SC_H; ++rr) rows |= ((__shfl_sync(0xffffffffu, act32, rr) >> lane) & 1u) << rr;
+    return rows;
   }
   if (!it.mask) return 0xffffffffu;
   const int x = it.x0 + 4 * lane;

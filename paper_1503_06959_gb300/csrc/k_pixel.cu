@@ -5,13 +5,13 @@
 //   k_pixel_mask:  bit of pixel p of layer l in frame k = |L_k,l(p) - L_{k-1},l(p)|
 //                  > T_I (every pixel on the stream's first frame), stored in
 //                  the layout of the keypoint bitmaps;
-//   k_count_pixel: D_k = (detections of frame k & M_k) | (D_{k-1} & ~M_k),
-//                  word by word, the frames of the batch in order (each word
-//                  position is one thread). The score of a carried keypoint
-//                  is copied into frame k's score map, so that the records
-//                  of every frame read their scores from their own frame.
-//                  Counts per chunk and frame feed the same emission pass as
-//                  the bin masks.
+//   k_merge_pixel: D_k = (detections of frame k & M_k) | (D_{k-1} & ~M_k),
+//                  pixel by pixel, the frames of the batch in order (each
+//                  pixel is one lane). The score of a carried keypoint is
+//                  copied into frame k's score map, so that the records of
+//                  every frame read their scores from their own frame. The
+//                  bin-mask count pass then counts the merged words, and
+//                  the same emission pass writes the records.
 #include <algorithm>
 
 #include "fkd_internal.cuh"
@@ -69,111 +69,82 @@ __global__ void __launch_bounds__(256) k_pixel_mask(Geometry g, Batch b, Scratch
               (long long)y * lg.pitch;
       }
       m = 0u;
+      uint32_t a[8], c[8];
+      const bool vec = nx == 32 && (((reinterpret_cast<uintptr_t>(cur + x0)) | reinterpret_cast<uintptr_t>(prv + x0)) & 15) == 0;
+      if (vec) {  // 32 aligned bytes of each: two 16-byte loads
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int x = x0 + 4 * q;
-        if (x >= lg.w) break;
-        uint32_t a = 0u, c = 0u;
+        for (int h = 0; h < 2; ++h) {
+          const uint4 va = reinterpret_cast<const uint4*>(cur + x0)[h], vc = reinterpret_cast<const uint4*>(prv + x0)[h];
+          a[4 * h] = va.x; a[4 * h + 1] = va.y; a[4 * h + 2] = va.z; a[4 * h + 3] = va.w;
+          c[4 * h] = vc.x; c[4 * h + 1] = vc.y; c[4 * h + 2] = vc.z; c[4 * h + 3] = vc.w;
+        }
+      } else {
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (x + e < lg.w) {
-            a |= (uint32_t)cur[x + e] << (8 * e);
-            c |= (uint32_t)prv[x + e] << (8 * e);
-          }
-        m |= gather_bits(bytes_gt(__vabsdiffu4(a, c), t1_low7, t1_high)) << (4 * q);
+        for (int q = 0; q < 8; ++q) {
+          a[q] = c[q] = 0u;
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (4 * q + e < nx) {
+              a[q] |= (uint32_t)cur[x0 + 4 * q + e] << (8 * e);
+              c[q] |= (uint32_t)prv[x0 + 4 * q + e] << (8 * e);
+            }
+        }
       }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) m |= gather_bits(bytes_gt(__vabsdiffu4(a[q], c[q]), t1_low7, t1_high)) << (4 * q);
       m &= valid;
     }
     s.pmask[i] = m;
   }
 }
 
-// Last-CTA scan of the frame totals into record offsets (as the bin-mask
-// count pass does).
-__device__ __forceinline__ void scan_bases(const Scratch& s, int T) {
-  const int lane = threadIdx.x & 31;
-  __threadfence();
-  uint32_t carry = 0;
-  for (int e0 = 0; e0 < T; e0 += 32) {
-    const int e = e0 + lane;
-    const uint32_t c = e < T ? __ldcg(&s.frame_totals[e]) : 0u;
-    uint32_t incl = c;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += v;
-    }
-    if (e < T) s.bases[e] = carry + incl - c;
-    carry += __shfl_sync(0xffffffffu, incl, 31);
-  }
-  if (lane == 0) {
-    s.bases[T] = carry;
-    *s.done = 0u;
-  }
-}
+// One warp per bitmap word, one lane per pixel of it: each lane runs the
+// recurrence of its own pixel over the frames of the batch (keeping the
+// pixel's keypoint score in a register while it is carried), and a ballot
+// forms each frame's word. The counting pass then reads the merged words.
+constexpr int kMergeWarps = 8;
 
-constexpr int kCountThreads = 256;
-
-__global__ void __launch_bounds__(kCountThreads) k_count_pixel(Geometry g, Tables tb, Batch b, Scratch s,
-                                                               State st) {
-  __shared__ int last_cta;
-  const int lane = threadIdx.x & 31;
-  const long long j = blockIdx.x * (long long)kCountThreads + threadIdx.x;
-  const bool valid = j < g.bit_words;
-  int l = 0, y = 0, wx = 0, chunk = -1;
-  if (valid) {
-    l = layer_of_word(g, j);
-    const LayerGeom& lg = g.layer[l];
-    y = (int)((j - lg.bit_off) / lg.wpr);
-    wx = (int)((j - lg.bit_off) % lg.wpr);
-    chunk = tb.rowchunk[lg.row_off + y];
-  }
+__global__ void __launch_bounds__(kMergeWarps * 32) k_merge_pixel(Geometry g, Batch b, Scratch s, State st) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long j = blockIdx.x * (long long)kMergeWarps + warp;
+  if (j >= g.bit_words) return;  // whole warps leave together
+  const int l = layer_of_word(g, j);
   const LayerGeom& lg = g.layer[l];
-  // all lanes in one chunk: one atomic per warp, else one per lane
-  const int chunk0 = __shfl_sync(0xffffffffu, chunk, 0);
-  const bool one_chunk = __all_sync(0xffffffffu, !valid || chunk == chunk0);
-  uint32_t prev = valid ? st.bits_in[j] : 0u;
+  const int y = (int)((j - lg.bit_off) / lg.wpr), wx = (int)((j - lg.bit_off) % lg.wpr);
+  const long long so = lg.score_off + (long long)y * lg.pitch + wx * 32 + lane;  // this lane's pixel
+  uint32_t bit = (st.bits_in[j] >> lane) & 1u;
+  // the keypoint's score is read only when it is first carried: from the
+  // frame that detected it (src >= 0) or from the kept set (src = -1)
+  int src = -1;
+  bool have = false;
+  uint8_t score = 0;
+  // the mask and detection words of the next frames are loaded ahead (lane
+  // q < AHEAD holds frame k + q's; the warp reads them by shuffles)
+  constexpr int AHEAD = 16;
+  uint32_t pm = 0u, pd = 0u;
   for (int k = 0; k < b.T; ++k) {
-    uint32_t merged = 0u;
-    if (valid) {
-      const uint32_t m = s.pmask[(long long)k * g.bit_words + j];
-      const uint32_t d = s.det_bits[(long long)k * g.bit_words + j];
-      const uint32_t carried = prev & ~m;
-      merged = (d & m) | carried;
-      s.merged[(long long)k * g.bit_words + j] = merged;
-      if (carried) {
-        // a carried keypoint keeps its score: copy it into frame k's map
-        uint8_t* dst = s.det_score + (long long)k * g.score_bytes + lg.score_off + (long long)y * lg.pitch;
-        const uint8_t* src = k > 0 ? s.det_score + (long long)(k - 1) * g.score_bytes + lg.score_off +
-                                         (long long)y * lg.pitch
-                                   : st.score_in + lg.score_off + (long long)y * lg.pitch;
-        for (uint32_t c = carried; c; c &= c - 1) {
-          const int x = wx * 32 + __ffs(c) - 1;
-          dst[x] = src[x];
-        }
-      }
-      prev = merged;
+    if ((k % AHEAD) == 0) {
+      const int kk = k + lane;
+      pm = lane < AHEAD && kk < b.T ? s.pmask[(long long)kk * g.bit_words + j] : 0u;
+      pd = lane < AHEAD && kk < b.T ? s.det_bits[(long long)kk * g.bit_words + j] : 0u;
     }
-    const uint32_t cnt = __popc(merged);
-    if (one_chunk) {
-      const uint32_t sum = __reduce_add_sync(0xffffffffu, cnt);
-      if (lane == 0 && sum) {
-        atomicAdd(&s.chunk_counts[(long long)k * g.n_chunks + chunk0], sum);
-        atomicAdd(&s.frame_totals[k], sum);
+    const uint32_t m = (__shfl_sync(0xffffffffu, pm, k % AHEAD) >> lane) & 1u;
+    const uint32_t d = (__shfl_sync(0xffffffffu, pd, k % AHEAD) >> lane) & 1u;
+    if (m) {
+      bit = d;  // detected anew, or nothing
+      src = k;
+      have = false;
+    } else if (bit) {
+      // carried: its score goes into frame k's map
+      if (!have) {
+        score = src < 0 ? st.score_in[so] : s.det_score[(long long)src * g.score_bytes + so];
+        have = true;
       }
-    } else if (cnt) {
-      atomicAdd(&s.chunk_counts[(long long)k * g.n_chunks + chunk], cnt);
-      atomicAdd(&s.frame_totals[k], cnt);
+      s.det_score[(long long)k * g.score_bytes + so] = score;
     }
+    const uint32_t word = __ballot_sync(0xffffffffu, bit != 0u);
+    if (lane == 0) s.merged[(long long)k * g.bit_words + j] = word;
   }
-  // the CTA that finishes last turns the frame totals into offsets
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last_cta = atomicAdd(s.done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (last_cta && threadIdx.x < 32) scan_bases(s, b.T);
 }
 
 }  // namespace
@@ -187,8 +158,9 @@ void launch_pixel_mask(const Geometry& g, const Batch& b, const Scratch& s, cons
 
 void launch_count_pixel(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                         const State& state, cudaStream_t st) {
-  const int blocks = (int)((g.bit_words + kCountThreads - 1) / kCountThreads);
-  k_count_pixel<<<std::max(blocks, 1), kCountThreads, 0, st>>>(g, tb, b, s, state);
+  const int blocks = (int)((g.bit_words + kMergeWarps - 1) / kMergeWarps);
+  k_merge_pixel<<<std::max(blocks, 1), kMergeWarps * 32, 0, st>>>(g, b, s, state);
+  launch_count(g, tb, b, s, state, st);  // counts the merged words (and fills the offsets)
 }
 
 }  // namespace fkd
