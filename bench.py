@@ -559,9 +559,40 @@ def run_config4(args):
                      "frames_refused_queue_full": refused[0], "results_truncated": truncated[0],
                      "device_bytes": st["bytes_in_use"]}
         srv.close()
+    # admission under a small budget: streams of the mix, round robin, until
+    # the budget refuses them; closing one frees room for the next
+    small = args.small_budget_mb << 20
+    srv = fkd.Server(4, 1, budget_bytes=small, max_tick_keypoints=1 << 20)
+    admitted = {f"{W}x{H}": 0 for W, H in res_list}
+    refused = {f"{W}x{H}": 0 for W, H in res_list}
+    open_ids = []
+    for j in range(per_res):
+        for W, H in res_list:
+            try:
+                open_ids.append((srv.open_stream(W, H, N_r=12, N_c=16, T_I=4, t=30, mask_mode=fkd.FKD_MASK_ID,
+                                                 mask_layer=-1, K_max=1 << 17), W, H))
+                admitted[f"{W}x{H}"] += 1
+            except fkd.FkdError as e:
+                if e.code != fkd.FKD_E_BUDGET:
+                    raise
+                refused[f"{W}x{H}"] += 1
+    in_use = srv.stats()["bytes_in_use"]
+    readmit = None
+    big = [sid for sid, W, H in open_ids if W == 1920]
+    if big:
+        srv.close_stream(big[0])
+        try:
+            srv.open_stream(1920, 1080, N_r=12, N_c=16, T_I=4, t=30, mask_mode=fkd.FKD_MASK_ID,
+                            mask_layer=-1, K_max=1 << 17)
+            readmit = True
+        except fkd.FkdError:
+            readmit = False
+    srv.close()
+    admission = {"budget_bytes": small, "admitted": admitted, "refused": refused,
+                 "bytes_in_use": in_use, "readmitted_after_close": readmit}
     line = {"metric": "frames/s and p99 latency (serving, continuous batching)",
             "value": out["masked"]["fps"], "unit": "frames/s", "n_gpus": 1, "dtype": "u8",
-            "data": "synthetic",
+            "data": "synthetic", "admission_small_budget": admission,
             "config": {"workload": f"{4 * per_res} streams ({per_res} each of 320x240 .. 1920x1080), "
                                    f"30 fps Poisson arrivals for {seconds} s, O=4 + intra-octaves, "
                                    f"budget {args.budget_gb} GB"},
@@ -588,6 +619,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--pool", type=int, default=12)
     ap.add_argument("--budget-gb", type=int, default=8)
+    ap.add_argument("--small-budget-mb", type=int, default=256)
     ap.add_argument("--segment", type=int, default=20)
     ap.add_argument("--streams-5", type=int, default=8)
     ap.add_argument("--shape", default="",
