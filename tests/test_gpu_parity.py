@@ -344,3 +344,21 @@ def test_per_pixel_mask_rejected_in_groups():
     g = fkd.Group(2, 1)
     with pytest.raises(fkd.FkdError):
         g.add_stream(64, 48, mask_mode=fkd.FKD_MASK_IDP)
+
+
+@pytest.mark.parametrize("mode,T", [("id", 36), ("kb", 33), ("full", 32)])
+def test_host_batches_uploaded_in_parts(clip2, mode, T):
+    # host frames of a large batch are uploaded in parts that overlap the
+    # kernels; the records must not change, nor must later single pushes
+    cfg, frames = clip2
+    g, o = both(params(cfg, mask_layer=-1), mode)
+    exp_kp, exp_m = run_oracle(frames[:T], **o)
+    s = fkd.Stream(cfg.W, cfg.H, T_max=T, **g)
+    push_in_pieces(s, frames[:T], [T - 2, 1, 1] if T > 33 else [T], exp_kp, exp_m)
+    # a strided (not back-to-back) host batch takes the frame-by-frame copies
+    big = np.zeros((T, cfg.H, cfg.W + 8), np.uint8)
+    big[:, :, :cfg.W] = frames[:T]
+    s.reset()
+    rec, off, _ = s.push_frames(big[:, :, :cfg.W])
+    for k, kp in enumerate(fkd.split_frames(rec, off)):
+        assert_same_kp(kp, exp_kp[k], f"strided frame {k}")
