@@ -250,8 +250,10 @@ class Stream:
             pitch, stride = frames.stride(1), frames.stride(0)
             on_device = 1
         else:
-            frames = np.ascontiguousarray(frames, dtype=np.uint8)
-            pitch, stride = frames.strides[1], frames.strides[0]
+            frames = np.asarray(frames)
+            if frames.dtype != np.uint8 or frames.strides[2] != 1 or min(frames.strides[:2]) <= 0:
+                frames = np.ascontiguousarray(frames, dtype=np.uint8)
+            pitch, stride = frames.strides[1], frames.strides[0]  # row pitch and frame stride kept
             on_device = 0
         if out is not None and _is_torch_cuda(out):
             cap = out.numel() * out.element_size() // 8 if cap is None else cap

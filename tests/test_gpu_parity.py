@@ -355,10 +355,14 @@ def test_host_batches_uploaded_in_parts(clip2, mode, T):
     exp_kp, exp_m = run_oracle(frames[:T], **o)
     s = fkd.Stream(cfg.W, cfg.H, T_max=T, **g)
     push_in_pieces(s, frames[:T], [T - 2, 1, 1] if T > 33 else [T], exp_kp, exp_m)
-    # a strided (not back-to-back) host batch takes the frame-by-frame copies
-    big = np.zeros((T, cfg.H, cfg.W + 8), np.uint8)
-    big[:, :, :cfg.W] = frames[:T]
-    s.reset()
-    rec, off, _ = s.push_frames(big[:, :, :cfg.W])
-    for k, kp in enumerate(fkd.split_frames(rec, off)):
-        assert_same_kp(kp, exp_kp[k], f"strided frame {k}")
+    # rows of pitch W + 8 (frames still back to back), then frames with gaps
+    # between them (frame by frame copies)
+    wide = np.zeros((T, cfg.H, cfg.W + 8), np.uint8)
+    wide[:, :, :cfg.W] = frames[:T]
+    gaps = np.zeros((T, cfg.H + 3, cfg.W), np.uint8)
+    gaps[:, :cfg.H] = frames[:T]
+    for view in (wide[:, :, :cfg.W], gaps[:, :cfg.H]):
+        s.reset()
+        rec, off, _ = s.push_frames(view)
+        for k, kp in enumerate(fkd.split_frames(rec, off)):
+            assert_same_kp(kp, exp_kp[k], f"strided frame {k}")
