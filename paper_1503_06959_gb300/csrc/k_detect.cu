@@ -1,28 +1,34 @@
 // k_detect.cu -- masked segment test, corner score and 3x3 non-maximum
-// suppression (Sec. 2) over the active detection tiles of a batch.
+// suppression (Sec. 2) over the active detection tiles of a batch, and the
+// optional scale-space suppression against the adjacent layers.
 //
-// Every warp works alone on one 128 x 16 tile of one layer at a time (no
+// Every warp works alone on one 128 x tile_h tile of one layer at a time (no
 // block-wide barriers; each warp owns a slice of shared memory), pulling
-// (frame, tile) items from the compacted list of active tiles. Per tile:
+// (frame, tile) items from the compacted list of active tiles; tile_h (8, 16
+// or 24), warps per CTA and CTAs per SM are the launch shape the caller sets
+// or the autotuner picks. Per tile:
 //   A. stage the tile plus a 4-pixel halo (3 for the ring, 1 for the
-//      suppression neighbours), widened to 16 bytes left and right: 24 rows
-//      x 160 bytes, copied with cp.async (zero-filled outside the layer) into
-//      one of two buffers while the warp works on the previous tile;
-//   B. prefilter the 130 x 18 pixels whose score the tile needs, one 32-bit
-//      word (4 pixels) per lane per row, with packed byte arithmetic: a pixel
-//      can pass the segment test at threshold t only if two adjacent compass
-//      points of its ring (12, 3, 6, 9 o'clock) differ from it by more than t,
-//      because every 9-pixel arc of the 16-pixel ring holds two adjacent
-//      compass points; survivors are compacted per row with a warp scan;
-//   C. score the survivors exactly, two per lane in 16-bit lanes: with I_k the
-//      ring values, the bright score is max over arcs of (min over the arc of
-//      I_k) - I_p and the dark one I_p - min over arcs of (max over the arc);
-//      arc extrema are 3-input extrema of 3-input extrema;
-//   D. scan the score map: a pixel of the tile is kept when its score is >= t
-//      and strictly above its 8 neighbours' (scores below t count as 0, which
-//      never changes the outcome); write the tile's bitmap words and scores.
-// Bins are not consulted here: assembly takes each pixel from the frame its
-// bin points to, so the kernel only has to be right on the tiles it runs.
+//      suppression neighbours), widened to 16 bytes left and right:
+//      (tile_h + 8) rows x 160 bytes, copied with cp.async, zero-filled
+//      outside the layer;
+//   B. for each 4-pixel word and score row, decide from the bin mask (or the
+//      per-pixel mask) whether any pixel there, or one of its neighbours, is
+//      in an active region; prefilter the words that are, one word per lane
+//      per row, with packed byte arithmetic: a pixel can pass the segment
+//      test at threshold t only if two adjacent compass points of its ring
+//      (12, 3, 6, 9 o'clock) differ from it by more than t, because every
+//      9-pixel arc of the 16-pixel ring holds two adjacent compass points;
+//      words with survivors are compacted with one ballot per row;
+//   C. expand those words into candidate pixels (four bit-position ballots
+//      per 32 words) and score them exactly, two per lane in 16-bit lanes:
+//      with I_k the ring values, the bright score is max over arcs of (min
+//      over the arc of I_k) - I_p and the dark one I_p - min over arcs of
+//      (max over the arc); arc extrema are 3-input extrema of 3-input extrema;
+//   D. a pixel of the tile is kept when its score is >= t and strictly above
+//      its 8 neighbours' (scores below t count as 0, which never changes the
+//      outcome); write the tile's bitmap words and the kept scores.
+// Bins are not consulted beyond B: assembly takes each pixel from the frame
+// its bin points to, so the kernel only has to be right on the tiles it runs.
 #include <algorithm>
 
 #include "fkd_internal.cuh"
