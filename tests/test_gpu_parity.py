@@ -347,9 +347,10 @@ def test_per_pixel_mask_rejected_in_groups():
 
 
 @pytest.mark.parametrize("mode,T", [("id", 36), ("kb", 33), ("full", 32)])
-def test_host_batches_uploaded_in_parts(clip2, mode, T):
-    # host frames of a large batch are uploaded in parts that overlap the
-    # kernels; the records must not change, nor must later single pushes
+def test_host_batch_layouts(clip2, mode, T):
+    # host frames of a batch are uploaded with one copy when back to back,
+    # else frame by frame; the records must not change, nor must later
+    # single pushes
     cfg, frames = clip2
     g, o = both(params(cfg, mask_layer=-1), mode)
     exp_kp, exp_m = run_oracle(frames[:T], **o)
