@@ -8,7 +8,8 @@ with the CUDA library and never imports it.
 
 Pinned by ``tests/test_oracle_pins.py`` against what the paper and the
 mathematics fix (brute-force segment tests, closed forms, symmetries, Eq. 1
-special cases, hand-computed pyramids and bins). The whole-pipeline keypoint
+special cases, hand-computed pyramids and bins, descriptor bits against a
+library box filter, a hand-computed edge and rotations). The whole-pipeline keypoint
 sets are not pinned to any value the paper prints: the paper prints none.
 """
 from __future__ import annotations
@@ -77,6 +78,9 @@ def _load():
     lib.orc_stream_num_keypoints.argtypes = [vp]
     lib.orc_stream_num_keypoints.restype = c_size
     lib.orc_stream_keypoints.argtypes = [vp, vp]
+    lib.orc_describe.argtypes = [vp, c_int, c_int, c_int, c_int, vp, c_int, vp]
+    lib.orc_stream_set_descriptor.argtypes = [vp, vp, c_int]
+    lib.orc_stream_descriptors.argtypes = [vp, vp]
     lib.orc_stream_mask.argtypes = [vp, vp]
     lib.orc_stream_block_sums.argtypes = [vp, vp]
     lib.orc_stream_frame_index.argtypes = [vp]
@@ -131,6 +135,19 @@ def score_image(img: np.ndarray) -> np.ndarray:
     return out
 
 
+def describe(img: np.ndarray, x: int, y: int, pattern: np.ndarray) -> np.ndarray:
+    """Binary descriptor of pixel (x, y) of a layer: D/8 bytes, bit i in byte
+    i // 8 at bit i % 8 (pattern: D x 4 int8 rows (ax, ay, bx, by))."""
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    pat = np.ascontiguousarray(pattern, dtype=np.int8)
+    h, w = img.shape
+    D = pat.shape[0]
+    out = np.zeros(D // 8, np.uint8)
+    if _load().orc_describe(_ptr(img), w, h, x, y, _ptr(pat), D, _ptr(out)) != 0:
+        raise ValueError("invalid descriptor arguments")
+    return out
+
+
 def block_of(x: int, y: int, S: int, W: int, H: int, N_r: int, N_c: int) -> int:
     return _load().orc_block_of(x, y, S, W, H, N_r, N_c)
 
@@ -140,7 +157,7 @@ class Stream:
 
     def __init__(self, W: int, H: int, *, N_r: int, N_c: int, T_I: int = 4, T_H: int = 1,
                  O: int = 1, intra: int = 0, t: int = 20, mask_mode: int = MASK_ID,
-                 mask_layer: int = 0, nms_scale: int = 0):
+                 mask_layer: int = 0, nms_scale: int = 0, pattern: np.ndarray | None = None):
         self.W, self.H, self.N_r, self.N_c = W, H, N_r, N_c
         p = _Params(N_r, N_c, T_I, T_H, O, intra, t, mask_mode, mask_layer, nms_scale)
         self._O, self._intra = O, intra
@@ -148,6 +165,12 @@ class Stream:
         if _load().orc_stream_create(ctypes.byref(p), W, H, ctypes.byref(h)) != 0:
             raise ValueError("invalid oracle stream parameters")
         self._h = h
+        self._D = 0
+        if pattern is not None:
+            pat = np.ascontiguousarray(pattern, dtype=np.int8)
+            if _load().orc_stream_set_descriptor(h, _ptr(pat), pat.shape[0]) != 0:
+                raise ValueError("invalid descriptor pattern")
+            self._D = pat.shape[0]
 
     def push(self, frame: np.ndarray, mask_override: np.ndarray | None = None):
         frame = np.ascontiguousarray(frame, dtype=np.uint8)
@@ -177,6 +200,15 @@ class Stream:
         out = np.zeros(n, KEYPOINT_DTYPE)
         if n:
             lib.orc_stream_keypoints(self._h, _ptr(out))
+        return out
+
+    def descriptors(self) -> np.ndarray:
+        """Descriptors of the last frame's keypoints (n x D/8 uint8, their order)."""
+        lib = _load()
+        n = lib.orc_stream_num_keypoints(self._h)
+        out = np.zeros((n, self._D // 8), np.uint8)
+        if not self._D or lib.orc_stream_descriptors(self._h, _ptr(out)) != 0:
+            raise ValueError("description is off")
         return out
 
     def mask(self) -> np.ndarray:

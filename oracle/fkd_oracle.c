@@ -196,7 +196,40 @@ struct orc_stream {
   uint64_t* bsum;    /* block sums of |L_n - L_{n-1}| (ID) or bin counts (KB) */
   uint8_t* pmask;    /* IDP: per-pixel masks of every layer (pyramid layout) */
   long frame;        /* index of the last processed frame, -1 before any */
+  int8_t* pattern;   /* description: D pairs (ax, ay, bx, by), or NULL */
+  int D;             /* descriptor bits (0: no description) */
+  uint8_t* desc;     /* descriptors of D_n, D/8 bytes each, in D_n's order */
 };
+
+/* Binary descriptor of pixel (x, y) of a w*h layer (Sec. 2: every bit
+ * compares the smoothed intensities of one pair of pixels sampled around the
+ * keypoint). The smoothed intensity at q is the sum of the 5x5 pixels around
+ * q, coordinates clamped to the layer; bit i is set iff the sum at
+ * (x + ax_i, y + ay_i) is below the sum at (x + bx_i, y + by_i), and lands
+ * in byte i / 8 at bit i % 8. No orientation: the pattern is upright. */
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+static int box5(const uint8_t* img, int w, int h, int qx, int qy) {
+  int sum = 0;
+  for (int dy = -2; dy <= 2; ++dy)
+    for (int dx = -2; dx <= 2; ++dx)
+      sum += img[(size_t)clampi(qy + dy, 0, h - 1) * w + clampi(qx + dx, 0, w - 1)];
+  return sum;
+}
+
+int orc_describe(const uint8_t* img, int w, int h, int x, int y, const int8_t* pattern, int D,
+                 uint8_t* out) {
+  if (!img || !pattern || !out || w < 1 || h < 1 || x < 0 || y < 0 || x >= w || y >= h) return -1;
+  if (D < 8 || (D & 7)) return -1;
+  memset(out, 0, (size_t)D / 8);
+  for (int i = 0; i < D; ++i) {
+    const int8_t* q = pattern + 4 * i;
+    int a = box5(img, w, h, x + q[0], y + q[1]);
+    int b = box5(img, w, h, x + q[2], y + q[3]);
+    if (a < b) out[i >> 3] |= (uint8_t)(1u << (i & 7));
+  }
+  return 0;
+}
 
 int orc_stream_create(const orc_params* p, int W, int H, orc_stream** out) {
   if (!p || !out || W < 1 || H < 1 || W > 16384 || H > 16384) return -1;
@@ -234,7 +267,21 @@ int orc_stream_create(const orc_params* p, int W, int H, orc_stream** out) {
 void orc_stream_destroy(orc_stream* s) {
   if (!s) return;
   free(s->pyr_prev); free(s->pyr_cur); free(s->mask); free(s->bsum); free(s->kp); free(s->pmask);
+  free(s->pattern); free(s->desc);
   free(s);
+}
+
+int orc_stream_set_descriptor(orc_stream* s, const int8_t* pattern, int D) {
+  if (!s || s->frame >= 0) return -1;  /* before the first frame only */
+  if (D != 0 && (!pattern || D < 8 || (D & 7))) return -1;
+  free(s->pattern);
+  s->pattern = NULL;
+  s->D = D;
+  if (D) {
+    s->pattern = (int8_t*)malloc((size_t)D * 4);
+    memcpy(s->pattern, pattern, (size_t)D * 4);
+  }
+  return 0;
 }
 
 static void kp_push(orc_keypoint** arr, size_t* n, size_t* cap, orc_keypoint k) {
@@ -381,6 +428,27 @@ int orc_stream_push(orc_stream* s, const uint8_t* frame, size_t pitch, const uin
   for (int l = 0; l < s->L; ++l) free(scores[l]);
 #undef ORC_ACTIVE
   qsort(next, nn, sizeof(orc_keypoint), kp_cmp);
+
+  /* Description (Sec. 3): only the keypoints detected in this frame are
+   * described, on their own layer of L_n; a carried keypoint keeps the
+   * descriptor it had in D_{n-1} (found by its position, unique in D_{n-1}). */
+  if (s->D) {
+    const size_t DB = (size_t)s->D / 8;
+    uint8_t* nd = (uint8_t*)malloc(nn * DB + 1);
+    for (size_t i = 0; i < nn; ++i) {
+      const orc_keypoint* k = &next[i];
+      if (!(k->flags & 1)) {
+        const int l = k->layer;
+        orc_describe(s->pyr_cur + s->loff[l], s->lw[l], s->lh[l], k->x, k->y, s->pattern, s->D, nd + i * DB);
+      } else {
+        const orc_keypoint* o = (const orc_keypoint*)bsearch(k, s->kp, s->nkp, sizeof(orc_keypoint), kp_cmp);
+        if (!o) { free(nd); free(next); return -1; }
+        memcpy(nd + i * DB, s->desc + (size_t)(o - s->kp) * DB, DB);
+      }
+    }
+    free(s->desc);
+    s->desc = nd;
+  }
   free(s->kp);
   s->kp = next; s->nkp = nn; s->cap = ncap;
 
@@ -392,6 +460,11 @@ int orc_stream_push(orc_stream* s, const uint8_t* frame, size_t pitch, const uin
 size_t orc_stream_num_keypoints(const orc_stream* s) { return s->nkp; }
 void orc_stream_keypoints(const orc_stream* s, orc_keypoint* out) {
   memcpy(out, s->kp, s->nkp * sizeof(orc_keypoint));
+}
+int orc_stream_descriptors(const orc_stream* s, uint8_t* out) {
+  if (!s->D) return -1;
+  memcpy(out, s->desc, s->nkp * ((size_t)s->D / 8));
+  return 0;
 }
 void orc_stream_mask(const orc_stream* s, uint8_t* out) {
   memcpy(out, s->mask, (size_t)s->p.N_r * s->p.N_c);

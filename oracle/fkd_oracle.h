@@ -65,6 +65,13 @@ void orc_build_pyramid(const uint8_t* frame, int W, int H, int O, int intra, uin
 int orc_score(const uint8_t* img, int w, int h, int x, int y);
 void orc_score_image(const uint8_t* img, int w, int h, uint8_t* out);
 
+/* Binary descriptor of pixel (x, y) of a w*h layer: D bits (D % 8 == 0),
+ * bit i set iff the 5x5 sum around (x+ax_i, y+ay_i) is below the 5x5 sum
+ * around (x+bx_i, y+by_i) (coordinates clamped to the layer); pattern holds
+ * D rows (ax, ay, bx, by); bit i lands in out[i/8] at bit i%8. */
+int orc_describe(const uint8_t* img, int w, int h, int x, int y, const int8_t* pattern, int D,
+                 uint8_t* out);
+
 /* Block index r*N_c + c of pixel (x, y) of a layer with scale code S. */
 int orc_block_of(int x, int y, int S, int W, int H, int N_r, int N_c);
 
@@ -75,6 +82,12 @@ void orc_stream_destroy(orc_stream* s);
 /* Process one frame.  mask_override: NULL, or N_r*N_c bytes used as M'_n in
  * place of the configured test (a hook for the mask properties of Eq. 1). */
 int orc_stream_push(orc_stream* s, const uint8_t* frame, size_t pitch, const uint8_t* mask_override);
+/* Masked description: before the first frame, a D-bit pattern (NULL, 0:
+ * off). Each frame then describes its newly detected keypoints and carries
+ * the descriptors of carried ones; orc_stream_descriptors writes D/8 bytes
+ * per keypoint of D_n, in D_n's order (-1 if description is off). */
+int orc_stream_set_descriptor(orc_stream* s, const int8_t* pattern, int D);
+int orc_stream_descriptors(const orc_stream* s, uint8_t* out);
 size_t orc_stream_num_keypoints(const orc_stream* s);
 void orc_stream_keypoints(const orc_stream* s, orc_keypoint* out);
 void orc_stream_mask(const orc_stream* s, uint8_t* out);

@@ -1,7 +1,8 @@
 """Seeded synthetic video shaped like the paper's hand-held VGA-class clips.
 
-This module only makes input frames. It holds none of the detector's
-arithmetic, and both the CUDA path and the CPU oracle read the same bytes.
+This module only makes inputs: frames and the descriptor's sample pattern.
+It holds none of the detector's arithmetic, and both the CUDA path and the
+CPU oracle read the same bytes.
 
 Scene recipe (one stream):
   * background: a mid-grey field with 40 rectangles, position and size
@@ -170,3 +171,20 @@ def config5() -> StreamConfig:
 
 def source_for(cfg: StreamConfig, config_id: int, stream: int = 0) -> VideoSource:
     return VideoSource(cfg.W, cfg.H, seed=1000 + 100 * config_id + stream, **cfg.source)
+
+
+DESC_RADIUS = 13  # largest |offset| of a descriptor sample the library accepts
+
+
+def descriptor_pattern(D: int = 256, seed: int = 7) -> np.ndarray:
+    """D sample pairs (ax, ay, bx, by) for the binary descriptor, int8 D x 4.
+
+    The paper names no pattern. This draws each coordinate from an isotropic
+    Gaussian of standard deviation (2 * DESC_RADIUS + 1) / 5, rounded and
+    clipped to +-DESC_RADIUS (the usual choice for BRIEF-style pair tests).
+    These are inputs of the method, drawn once and passed to both sides.
+    """
+    rng = np.random.default_rng(seed)
+    sigma = (2 * DESC_RADIUS + 1) / 5.0
+    p = np.rint(rng.normal(0.0, sigma, size=(D, 4)))
+    return np.clip(p, -DESC_RADIUS, DESC_RADIUS).astype(np.int8)

@@ -646,3 +646,131 @@ def test_pixel_mask_detection_equals_bruteforce():
         assert got == exp
         prev_layers, prev_kp = layers, exp
     assert any(k[4] == 1 for k in exp) and any(k[4] == 0 for k in exp)
+
+
+# --------------------------------------------------------------------------
+# masked description (Sec. 2: bits from intensity comparisons of sampled
+# pixel pairs; Sec. 3: only detected keypoints are described, carried ones
+# keep their descriptors)
+
+
+def box_sums_padded(img, pad):
+    """5x5 sums around every pixel of the replicate-padded image, computed by
+    scipy's correlation (an independent routine), exact in int64."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    p = np.pad(img.astype(np.int64), pad, mode="edge")
+    return ndimage.correlate(p, np.ones((5, 5), np.int64), mode="constant", cval=0)
+
+
+def library_descriptor(img, x, y, pattern):
+    pad = 16
+    box = box_sums_padded(img, pad)
+    bits = np.zeros(len(pattern), np.uint8)
+    for i, (ax, ay, bx, by) in enumerate(pattern.astype(int)):
+        bits[i] = box[y + ay + pad, x + ax + pad] < box[y + by + pad, x + bx + pad]
+    return np.packbits(bits, bitorder="little")
+
+
+def test_descriptor_matches_library_box_filter_everywhere():
+    rng = np.random.default_rng(11)
+    from paper_1503_06959_gb300 import synth
+    pattern = np.concatenate([synth.descriptor_pattern(32, seed=5),
+                              rng.integers(-13, 14, (32, 4)).astype(np.int8)])
+    for h, w in ((29, 37), (7, 5), (40, 33)):
+        img = rng.integers(0, 256, (h, w), dtype=np.uint8)
+        pts = [(0, 0), (w - 1, h - 1), (w - 1, 0), (0, h - 1), (w // 2, h // 2)]
+        pts += [(int(rng.integers(0, w)), int(rng.integers(0, h))) for _ in range(10)]
+        for x, y in pts:
+            np.testing.assert_array_equal(oracle.describe(img, x, y, pattern),
+                                          library_descriptor(img, x, y, pattern), err_msg=f"{w}x{h} at {x},{y}")
+
+
+def test_descriptor_step_edge_hand_computed():
+    img = np.full((40, 40), 10, np.uint8)
+    img[:, 20:] = 200
+    pattern = np.array([[-6, 0, 6, 0],    # dark left vs bright right: 1
+                        [6, 0, -6, 0],    # reversed: 0
+                        [0, -6, 0, 6],    # same column, equal sums: 0 (strict)
+                        [-1, 0, 0, 0],    # 3 dark + 2 bright columns vs 2 dark + 3 bright: 1
+                        [0, 0, -1, 0],    # reversed: 0
+                        [3, 3, 3, 3],     # a pair with itself: 0
+                        [-13, 13, 13, -13],  # far left vs far right: 1
+                        [2, 0, 3, 0]],    # both boxes wholly bright: 0
+                       np.int8)
+    assert oracle.describe(img, 20, 20, pattern).tolist() == [0b01001001]
+
+
+def test_descriptor_constant_image_is_all_zeros():
+    from paper_1503_06959_gb300 import synth
+    img = np.full((30, 30), 77, np.uint8)
+    assert not oracle.describe(img, 3, 25, synth.descriptor_pattern(256)).any()
+
+
+def test_descriptor_rotation_by_90_degrees():
+    """Rotating the image, the point and every offset by 90 degrees leaves
+    every bit unchanged (the 5x5 boxes and the clamping to the image
+    rectangle are symmetric); a swapped or sign-flipped coordinate fails."""
+    rng = np.random.default_rng(12)
+    img = rng.integers(0, 256, (31, 45), dtype=np.uint8)
+    pattern = rng.integers(-13, 14, (64, 4)).astype(np.int8)
+    H, W = img.shape
+    rot = np.rot90(img)  # rot[r, c] = img[c, W - 1 - r]: (x, y) -> (y, W - 1 - x)
+    rpat = np.stack([pattern[:, 1], -pattern[:, 0], pattern[:, 3], -pattern[:, 2]], axis=1).astype(np.int8)
+    for x, y in ((0, 0), (44, 30), (10, 3), (22, 15), (40, 28)):
+        np.testing.assert_array_equal(oracle.describe(rot, y, W - 1 - x, rpat),
+                                      oracle.describe(img, x, y, pattern))
+
+
+def _describe_all(frame, kp, O, intra, pattern):
+    layers = oracle.pyramid(frame, O, intra)
+    return np.array([oracle.describe(layers[k["layer"]], int(k["x"]), int(k["y"]), pattern) for k in kp]
+                    ).reshape(len(kp), -1)
+
+
+@pytest.mark.parametrize("mode", ["ID", "IDP"])
+def test_masked_description_describes_new_and_carries_old(mode):
+    from paper_1503_06959_gb300 import synth
+    src = synth.VideoSource(96, 96, seed=23, n_movers=3, mover_size=24, speed=(3, 4))
+    frames = src.frames(4)
+    pattern = synth.descriptor_pattern(128, seed=3)
+    kw = dict(N_r=3, N_c=3, O=2, intra=1, T_I=4, t=12, pattern=pattern)
+    if mode == "ID":
+        s = oracle.Stream(96, 96, mask_mode=oracle.MASK_ID, **kw)
+    else:
+        s = oracle.Stream(96, 96, mask_mode=oracle.MASK_IDP, **kw)
+    one = np.zeros((3, 3), np.uint8)
+    one[1, 1] = 1
+    prev_kp, prev_d = None, None
+    seen_carried_changed = False
+    for n, f in enumerate(frames):
+        s.push(f, mask_override=one if (mode == "ID" and n > 0) else None)
+        kp, d = s.keypoints(), s.descriptors()
+        assert d.shape == (len(kp), 16)
+        here = _describe_all(f, kp, 2, 1, pattern)
+        new = kp["flags"] == 0
+        np.testing.assert_array_equal(d[new], here[new])
+        if n == 0:
+            assert new.all()
+        else:
+            assert (~new).any() and new.any()
+            index = {(int(k["layer"]), int(k["y"]), int(k["x"])): i for i, k in enumerate(prev_kp)}
+            for i in np.flatnonzero(~new):
+                k = kp[i]
+                j = index[(int(k["layer"]), int(k["y"]), int(k["x"]))]
+                np.testing.assert_array_equal(d[i], prev_d[j])
+                seen_carried_changed |= not np.array_equal(d[i], here[i])
+        prev_kp, prev_d = kp, d
+    # the carried descriptors come from the frame that detected them, not
+    # from the current pixels (which moved under some of them)
+    assert seen_carried_changed
+
+
+def test_description_is_set_before_the_first_frame_only():
+    from paper_1503_06959_gb300 import synth
+    s = oracle.Stream(64, 48, N_r=2, N_c=2, O=1, t=15)
+    s.push(synth.VideoSource(64, 48, seed=1).frame(0))
+    lib = oracle._load()
+    pat = synth.descriptor_pattern(64)
+    assert lib.orc_stream_set_descriptor(s._h, oracle._ptr(pat), 64) == -1
+    with pytest.raises(ValueError):
+        s.descriptors()
