@@ -235,6 +235,43 @@ int fkd_device_keypoints(fkd_stream* s, const fkd_keypoint** records, const uint
 int fkd_reset_stream(fkd_stream* s);
 
 /*
+ * Masked description (Sec. 3: the mask decides where keypoints are detected
+ * and described, and a carried keypoint keeps its descriptor; Sec. 2: each
+ * bit of a binary descriptor compares the smoothed intensities of one pair of
+ * pixels sampled around the keypoint). The paper gives no sampling pattern,
+ * so the caller supplies one.
+ *   pattern: D rows of four int8 (ax, ay, bx, by), offsets in pixels of the
+ *     keypoint's layer, each within +-FKD_DESC_RADIUS; host memory, copied.
+ *     NULL with D = 0 turns description off.
+ *   D: descriptor bits, a multiple of 32 in 32 .. FKD_DESC_MAX_BITS.
+ * Bit i of the descriptor of keypoint (x, y) of layer l is set iff the sum of
+ * the 5x5 pixels of layer l around (x + ax_i, y + ay_i) is below the sum
+ * around (x + bx_i, y + by_i), pixel coordinates clamped to the layer; it is
+ * bit i % 8 of byte i / 8. The pattern is upright (no orientation). Only
+ * keypoints detected in a frame are described, on that frame's layer; a
+ * carried keypoint (FKD_KP_PROPAGATED) keeps the descriptor it had in the
+ * previous frame. Resets the stream (waits for its pending work). Streams of
+ * groups and servers do not describe.
+ * Errors: FKD_E_ARG (D or an offset out of range), FKD_E_CUDA.
+ */
+#define FKD_DESC_RADIUS 13
+#define FKD_DESC_MAX_BITS 512
+int fkd_set_descriptor(fkd_stream* s, const int8_t* pattern, int D);
+
+/*
+ * Descriptors of the records of the last fkd_push_frame (the set
+ * fkd_get_keypoints returns) or fkd_push_frames call (one per record its
+ * `out` received, in that order), D/8 bytes each, into `out`: host memory,
+ * or device memory with out_on_device = 1. *n_out = the number of those
+ * records; at most `cap` descriptors are copied (out = NULL with cap = 0
+ * only reports the count). Waits for the stream.
+ * Errors: FKD_E_STATE (description off, or no frame pushed since it was
+ * set), FKD_E_CAPACITY (more than cap: the first cap are copied),
+ * FKD_E_ARG, FKD_E_CUDA.
+ */
+int fkd_get_descriptors(fkd_stream* s, uint8_t* out, size_t cap, size_t* n_out, int out_on_device);
+
+/*
  * Per-stage timing of the launch sequence, for profiling. While enabled,
  * every batch records CUDA events around each of its kernels on the stream's
  * CUDA stream. fkd_profile_read waits for the stream, adds the elapsed times

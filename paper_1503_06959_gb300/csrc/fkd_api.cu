@@ -86,6 +86,17 @@ struct fkd_stream {
   uint32_t* host_offsets = nullptr;  // [T_max + 1]
   uint8_t* last_mask = nullptr;      // device pointer to the last frame's mask
 
+  // masked description (off while desc_D == 0)
+  int desc_D = 0;
+  int8_t* desc_pattern = nullptr;          // [D][4]
+  uint32_t* desc = nullptr;                // per output record, D / 32 words
+  long long desc_cap = 0;                  // records desc holds
+  fkd_keypoint* keep_rec[2] = {nullptr, nullptr};  // the last frame's records and descriptors, ping-pong
+  uint32_t* keep_desc[2] = {nullptr, nullptr};     //   with the kept keypoint set (state_cur)
+  uint32_t* keep_n = nullptr;              // [2]
+  uint32_t* desc_count = nullptr;          // [1]: end index of the last call's described records
+  bool desc_ready = false;                 // a frame was described since description was set
+
   const uint8_t* prev = nullptr;
   int prev_pitch = 0;
   long long frame = 0;
@@ -125,6 +136,15 @@ struct fkd_stream {
     bytes_held += std::max<size_t>(count, 1) * sizeof(T);
     *p = static_cast<T*>(d);
     return FKD_OK;
+  }
+  // free one allocation made by alloc()
+  template <class T>
+  void free_one(T*& p) {
+    if (!p) return;
+    auto it = std::find(allocs.begin(), allocs.end(), (void*)p);
+    if (it != allocs.end()) allocs.erase(it);
+    cudaFree(p);
+    p = nullptr;
   }
   void release() {
     for (void* d : allocs) cudaFree(d);
@@ -398,6 +418,24 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   else launch_count(s->g, tb, b, s->s, stt, s->st);                   // its last CTA fills s->s.bases
   mark(5);
   launch_emit(s->g, tb, b, s->s, stt, o, s->st);
+  if (s->desc_D) {
+    // descriptors of the detected records, carried ones copied (Sec. 3)
+    Describe d{};
+    d.pattern = s->desc_pattern;
+    d.D = s->desc_D;
+    d.desc = s->desc;
+    d.keep_rec_in = s->keep_rec[s->state_cur];
+    d.keep_desc_in = s->keep_desc[s->state_cur];
+    d.keep_n_in = s->keep_n + s->state_cur;
+    d.keep_rec_out = s->keep_rec[s->state_cur ^ 1];
+    d.keep_desc_out = s->keep_desc[s->state_cur ^ 1];
+    d.keep_n_out = s->keep_n + (s->state_cur ^ 1);
+    d.keep_cap = s->p.K_max;
+    d.count = s->desc_count;
+    d.missing = s->s.overflow;
+    launch_describe(s->g, tb, b, s->s, o, d, s->st);
+    s->desc_ready = true;
+  }
   mark(6);
   if (s->s.pmask && s->g.L > 1)  // layers >= 1 of the batch's last frame: L_{n-1} of the next batch
     CK(cudaMemcpyAsync(s->s.pyr_last, s->s.pyr + (long long)(T - 1) * s->g.pyr_bytes, (size_t)s->g.pyr_bytes,
@@ -645,6 +683,16 @@ int fkd_push_frames(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t f
     doff = s->host_offsets;
   }
 
+  // descriptors: one per record the call can write
+  if (s->desc_D && (long long)cap > s->desc_cap) {
+    CK(cudaStreamSynchronize(s->st));
+    s->free_one(s->desc);
+    s->desc_cap = 0;
+    int rc = s->alloc(&s->desc, cap * (size_t)(s->desc_D / 32));
+    if (rc) return rc;
+    s->desc_cap = (long long)cap;
+  }
+
   // 3. the batch (frame by frame for keypoint binning)
   int rc = run_frames(s, dframes, dpitch, dstride, T, drec, (long long)cap, doff, masks,
                       out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
@@ -753,6 +801,63 @@ int fkd_reset_stream(fkd_stream* s) {
   if (!s) return fail(FKD_E_ARG, "stream is NULL");
   CK(cudaStreamSynchronize(s->st));
   reset_history(s);
+  return FKD_OK;
+}
+
+int fkd_set_descriptor(fkd_stream* s, const int8_t* pattern, int D) {
+  if (!s) return fail(FKD_E_ARG, "stream is NULL");
+  if (D != 0) {
+    if (!pattern) return fail(FKD_E_ARG, "pattern is NULL");
+    if (D < 32 || D > FKD_DESC_MAX_BITS || D % 32)
+      return fail(FKD_E_ARG, "D=%d: a multiple of 32 in 32..%d", D, FKD_DESC_MAX_BITS);
+    for (int i = 0; i < 4 * D; ++i)
+      if (pattern[i] < -FKD_DESC_RADIUS || pattern[i] > FKD_DESC_RADIUS)
+        return fail(FKD_E_ARG, "pattern offset %d of pair %d outside +-%d", pattern[i], i / 4, FKD_DESC_RADIUS);
+  }
+  CK(cudaStreamSynchronize(s->st));
+  reset_history(s);
+  s->desc_ready = false;
+  s->desc_D = 0;
+  s->free_one(s->desc_pattern);
+  s->free_one(s->desc);
+  s->desc_cap = 0;
+  for (int i = 0; i < 2; ++i) {
+    s->free_one(s->keep_rec[i]);
+    s->free_one(s->keep_desc[i]);
+  }
+  s->free_one(s->keep_n);
+  s->free_one(s->desc_count);
+  if (D == 0) return FKD_OK;
+  const size_t words = (size_t)D / 32, K = (size_t)s->p.K_max;
+  int rc;
+  if ((rc = s->alloc(&s->desc_pattern, (size_t)D * 4)) || (rc = s->alloc(&s->desc, K * words)) ||
+      (rc = s->alloc(&s->keep_n, 2)) || (rc = s->alloc(&s->desc_count, 1)))
+    return rc;
+  for (int i = 0; i < 2; ++i)
+    if ((rc = s->alloc(&s->keep_rec[i], K)) || (rc = s->alloc(&s->keep_desc[i], K * words))) return rc;
+  s->desc_cap = (long long)K;
+  CK(cudaMemcpy(s->desc_pattern, pattern, (size_t)D * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemset(s->keep_n, 0, 8));
+  CK(cudaMemset(s->desc_count, 0, 4));
+  s->desc_D = D;
+  return FKD_OK;
+}
+
+int fkd_get_descriptors(fkd_stream* s, uint8_t* out, size_t cap, size_t* n_out, int out_on_device) {
+  if (!s || !n_out || (!out && cap > 0)) return fail(FKD_E_ARG, "NULL argument");
+  if (!s->desc_D) return fail(FKD_E_STATE, "description is off (fkd_set_descriptor)");
+  if (!s->desc_ready) return fail(FKD_E_STATE, "no frame pushed since fkd_set_descriptor");
+  uint32_t n = 0;
+  CK(cudaMemcpyAsync(&n, s->desc_count, 4, cudaMemcpyDeviceToHost, s->st));
+  CK(cudaStreamSynchronize(s->st));
+  *n_out = n;
+  const size_t bytes = (size_t)s->desc_D / 8;
+  const size_t ncopy = std::min<size_t>(n, cap);
+  if (ncopy)
+    CK(cudaMemcpyAsync(out, s->desc, ncopy * bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       s->st));
+  CK(cudaStreamSynchronize(s->st));
+  if (n > cap && out) return fail(FKD_E_CAPACITY, "%u descriptors > cap %zu", n, cap);
   return FKD_OK;
 }
 

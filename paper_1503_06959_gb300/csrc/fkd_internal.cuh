@@ -174,6 +174,26 @@ struct Output {
   int base_slot;                   // out_base slot read; the other one is written
 };
 
+// Masked description: binary descriptors of D bits (D / 32 words per record,
+// bit i in word i / 32 at bit i % 32) over a caller-given pattern of pairs
+// with offsets within +-kDescR.
+constexpr int kDescR = FKD_DESC_RADIUS;
+constexpr int kDescMaxBits = FKD_DESC_MAX_BITS;
+struct Describe {
+  const int8_t* pattern;           // [D][4]: ax, ay, bx, by
+  int D;
+  uint32_t* desc;                  // descriptor of output record i at desc + i * D / 32
+  const fkd_keypoint* keep_rec_in; // the kept set: the previous batch's last frame, canonical order
+  const uint32_t* keep_desc_in;
+  const uint32_t* keep_n_in;
+  fkd_keypoint* keep_rec_out;      // this batch's last frame, for the next batch
+  uint32_t* keep_desc_out;
+  uint32_t* keep_n_out;
+  long long keep_cap;              // records the kept set holds (K_max)
+  uint32_t* count;                 // end index of the described records (device word)
+  int* missing;                    // set when a carried record's origin is absent (after an overflow)
+};
+
 // ---------------------------------------------------------------- groups
 // A group runs one frame of each of many streams (any mix of sizes) per
 // tick, with one launch per kernel for the whole tick. Each stream's static
@@ -285,6 +305,10 @@ void launch_scale_nms(const Geometry& g, const Tables& tb, const Batch& b, const
                       const Params& p, cudaStream_t st);
 void launch_group_scale_nms(const StreamDev* devs, const TickItem* items, const uint32_t* work,
                             const uint32_t* work_count, cudaStream_t st);
+
+// Descriptors of a batch's records (after the emission kernel).
+void launch_describe(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s, const Output& out,
+                     const Describe& d, cudaStream_t st);
 
 // Record a message for fkd_last_error (printf format) and return `code`.
 int set_error(int code, const char* fmt, ...);

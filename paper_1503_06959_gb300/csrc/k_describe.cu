@@ -1,0 +1,241 @@
+// k_describe.cu -- masked description (Sec. 3): binary descriptors for the
+// keypoints a batch detected, carried descriptors for the ones it kept.
+//
+// Descriptor of keypoint (x, y) of layer l (Sec. 2: one bit per pair of
+// sampled pixels, comparing smoothed intensities): bit i is set iff the sum
+// of the 5x5 layer pixels around (x + ax_i, y + ay_i) is below the sum around
+// (x + bx_i, y + by_i), coordinates clamped to the layer, for a caller-given
+// pattern of D pairs with offsets within +-kDescR.
+//
+//   k_describe_new:     one warp per newly detected record. The warp stages
+//                       the 31 x 31 window around the keypoint (clamped) in
+//                       shared memory, forms 5-pixel row sums (lane per row)
+//                       and then the 27 x 27 box sums (lane per column), and
+//                       evaluates 32 pairs per ballot.
+//   k_describe_carried: one thread per carried record. Eq. 1 makes a carried
+//                       record a copy of the record with the same position in
+//                       the frame that last detected there: src(k, bin) for
+//                       the block masks, the last frame whose per-pixel mask
+//                       bit was set for FKD_MASK_IDP, or the kept set of the
+//                       batch before. A binary search in that frame's
+//                       records (canonical order) finds it; its descriptor is
+//                       copied. The carried pass runs after the new pass, so
+//                       every source descriptor is final.
+// Both passes also copy the batch's last frame (records and descriptors)
+// into the kept set of the next batch.
+#include "fkd_internal.cuh"
+
+namespace fkd {
+namespace {
+
+constexpr int kDescWin = 2 * kDescR + 5;  // staged window: 31 x 31 pixels
+constexpr int kDescBox = 2 * kDescR + 1;  // box centres: 27 x 27
+constexpr int kWinPitch = 36;             // bytes; 9 words per row: lanes on distinct rows hit distinct banks
+constexpr int kHsPitch = 29;              // words; odd, so a lane per row is conflict-free
+constexpr int kNewWarps = 8;
+constexpr int kCarriedThreads = 256;
+static_assert(kDescWin <= 32, "one lane per window row and column");
+
+__device__ __forceinline__ unsigned long long rec_key(uint2 r) {
+  return ((unsigned long long)(r.y & 0xffu) << 32) | r.x;  // (layer, y, x)
+}
+
+// Index of the record with `key` in recs[lo, hi) (canonical order), or -1.
+__device__ __forceinline__ long long find_record(const uint2* recs, long long lo, long long hi,
+                                                 unsigned long long key) {
+  while (lo < hi) {
+    const long long mid = (lo + hi) >> 1;
+    const unsigned long long k = rec_key(recs[mid]);
+    if (k == key) return mid;
+    if (k < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return -1;
+}
+
+// Pixels of layer l of batch frame k.
+__device__ __forceinline__ const uint8_t* layer_base(const Geometry& g, const Batch& b, const Scratch& s,
+                                                     int k, int l, int* pitch) {
+  if (l == 0) {
+    *pitch = b.pitch;
+    return b.frames + (long long)k * b.frame_stride;
+  }
+  *pitch = g.layer[l].pitch;
+  return s.pyr + (long long)k * g.pyr_bytes + g.layer[l].pyr_off;
+}
+
+__global__ void __launch_bounds__(kNewWarps * 32) k_describe_new(Geometry g, Batch b, Scratch s, Output out,
+                                                                 Describe d) {
+  __shared__ uint32_t pat[kDescMaxBits];  // pair i: ax, ay, bx, by as bytes (offsets + kDescR)
+  __shared__ __align__(16) uint8_t win[kNewWarps][kDescWin * kWinPitch];
+  __shared__ uint32_t hs[kNewWarps][kDescWin * kHsPitch];  // row sums, then box sums in place
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < d.D; i += blockDim.x) {
+    const char4 q = reinterpret_cast<const char4*>(d.pattern)[i];
+    pat[i] = (uint32_t)(q.x + kDescR) | (uint32_t)(q.y + kDescR) << 8 | (uint32_t)(q.z + kDescR) << 16 |
+             (uint32_t)(q.w + kDescR) << 24;
+  }
+  __syncthreads();
+
+  const int T = b.T;
+  const uint32_t* off = out.offsets;
+  const long long first = off[0];
+  const long long end = min((long long)off[T], out.cap);
+  const long long last_first = off[T - 1];
+  const int DW = d.D >> 5;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *d.count = (uint32_t)max(end, 0LL);
+    const long long n_last = (long long)off[T] - last_first;
+    const long long kept = max(0LL, end - last_first);
+    *d.keep_n_out = (uint32_t)min(kept, d.keep_cap);
+    if (kept < n_last || kept > d.keep_cap) *s.overflow = 1;
+  }
+  const uint2* recs = reinterpret_cast<const uint2*>(out.rec);
+  uint8_t* w = win[warp];
+  uint32_t* h = hs[warp];
+  const long long gw = (long long)blockIdx.x * kNewWarps + warp, nw = (long long)gridDim.x * kNewWarps;
+  for (long long base = first + gw * 32; base < end; base += nw * 32) {
+    const long long idx = base + lane;
+    uint2 r = make_uint2(0u, 0u);
+    bool is_new = false;
+    int k = 0;
+    if (idx < end) {
+      r = recs[idx];
+      is_new = ((r.y >> 16) & FKD_KP_PROPAGATED) == 0u;
+      if (is_new) k = find_item(T, (int)(idx - first), [&](int q) { return (int)(off[q] - first); });
+    }
+    uint32_t todo = __ballot_sync(0xffffffffu, is_new);
+    while (todo) {
+      const int src_lane = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint32_t rx = __shfl_sync(0xffffffffu, r.x, src_lane);
+      const uint32_t ry = __shfl_sync(0xffffffffu, r.y, src_lane);
+      const int kk = __shfl_sync(0xffffffffu, k, src_lane);
+      const long long ridx = base + src_lane;
+      const int x = (int)(rx & 0xffffu), y = (int)(rx >> 16), l = (int)(ry & 0xffu);
+      const LayerGeom& lg = g.layer[l];
+      int pitch;
+      const uint8_t* img = layer_base(g, b, s, kk, l, &pitch);
+      // 1. the clamped window: lane c takes column c of every row (each
+      //    row is one contiguous read across the warp)
+      if (lane < kDescWin) {
+        const int gx = min(max(x - kDescR - 2 + lane, 0), lg.w - 1);
+#pragma unroll 8
+        for (int rr = 0; rr < kDescWin; ++rr) {
+          const int gy = min(max(y - kDescR - 2 + rr, 0), lg.h - 1);
+          w[rr * kWinPitch + lane] = img[(long long)gy * pitch + gx];
+        }
+      }
+      __syncwarp();
+      // 2. 5-pixel row sums, lane per row
+      if (lane < kDescWin) {
+        const uint8_t* row = w + lane * kWinPitch;
+        uint32_t sum = row[0] + row[1] + row[2] + row[3] + row[4];
+        uint32_t* hr = h + lane * kHsPitch;
+        hr[0] = sum;
+#pragma unroll
+        for (int c = 1; c < kDescBox; ++c) {
+          sum += (uint32_t)row[c + 4] - (uint32_t)row[c - 1];
+          hr[c] = sum;
+        }
+      }
+      __syncwarp();
+      // 3. 5-row sums of those, lane per column, in place
+      if (lane < kDescBox) {
+        uint32_t v[kDescWin];
+#pragma unroll
+        for (int rr = 0; rr < kDescWin; ++rr) v[rr] = h[rr * kHsPitch + lane];
+        uint32_t sum = v[0] + v[1] + v[2] + v[3] + v[4];
+        h[lane] = sum;
+#pragma unroll
+        for (int rr = 1; rr < kDescBox; ++rr) {
+          sum += v[rr + 4] - v[rr - 1];
+          h[rr * kHsPitch + lane] = sum;
+        }
+      }
+      __syncwarp();
+      // 4. 32 pairs per ballot; lane j keeps word j
+      uint32_t mine = 0u;
+      for (int j = 0; j < DW; ++j) {
+        const uint32_t q = pat[j * 32 + lane];
+        const uint32_t a = h[((q >> 8) & 0xffu) * kHsPitch + (q & 0xffu)];
+        const uint32_t c = h[(q >> 24) * kHsPitch + ((q >> 16) & 0xffu)];
+        const uint32_t word = __ballot_sync(0xffffffffu, a < c);
+        if (lane == j) mine = word;
+      }
+      if (lane < DW) d.desc[ridx * DW + lane] = mine;
+      if (ridx >= last_first && ridx - last_first < d.keep_cap) {
+        const long long kidx = ridx - last_first;
+        if (lane < DW) d.keep_desc_out[kidx * DW + lane] = mine;
+        if (lane == 0) reinterpret_cast<uint2*>(d.keep_rec_out)[kidx] = make_uint2(rx, ry);
+      }
+      __syncwarp();  // the window and sums are reused by the next record
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kCarriedThreads) k_describe_carried(Geometry g, Tables tb, Batch b, Scratch s,
+                                                                      Output out, Describe d) {
+  const int T = b.T;
+  const uint32_t* off = out.offsets;
+  const long long first = off[0];
+  const long long end = min((long long)off[T], out.cap);
+  const long long last_first = off[T - 1];
+  const int DW = d.D >> 5;
+  const uint2* recs = reinterpret_cast<const uint2*>(out.rec);
+  const uint2* keep = reinterpret_cast<const uint2*>(d.keep_rec_in);
+  const long long n_keep = *d.keep_n_in;
+  for (long long idx = first + blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < end;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const uint2 r = recs[idx];
+    if (((r.y >> 16) & FKD_KP_PROPAGATED) == 0u) continue;
+    const int k = find_item(T, (int)(idx - first), [&](int q) { return (int)(off[q] - first); });
+    const int x = (int)(r.x & 0xffffu), y = (int)(r.x >> 16), l = (int)(r.y & 0xffu);
+    const LayerGeom& lg = g.layer[l];
+    int sf = -1;  // the batch frame holding the record's origin, -1 = the kept set
+    if (s.pmask) {
+      const long long word = lg.bit_off + (long long)y * lg.wpr + (x >> 5);
+      for (int q = k - 1; q >= 0; --q)
+        if ((s.pmask[(long long)q * g.bit_words + word] >> (x & 31)) & 1u) {
+          sf = q;
+          break;
+        }
+    } else {
+      const int bin = tb.rowblk[lg.row_off + y] * g.N_c + tb.colblk[lg.col_off + x];
+      sf = s.src[(long long)k * g.NB + bin];
+    }
+    const unsigned long long key = rec_key(r);
+    const uint32_t* from = nullptr;
+    if (sf >= 0) {
+      const long long j = find_record(recs, off[sf], min((long long)off[sf + 1], out.cap), key);
+      if (j >= 0) from = d.desc + j * DW;
+    } else {
+      const long long j = find_record(keep, 0, n_keep, key);
+      if (j >= 0) from = d.keep_desc_in + j * DW;
+    }
+    if (!from) {
+      *d.missing = 1;  // only after an overflow dropped the origin record
+      continue;
+    }
+    uint32_t* to = d.desc + idx * DW;
+    const bool keep_it = idx >= last_first && idx - last_first < d.keep_cap;
+    uint32_t* kto = keep_it ? d.keep_desc_out + (idx - last_first) * DW : nullptr;
+    for (int q = 0; q < DW; ++q) {
+      const uint32_t v = from[q];
+      to[q] = v;
+      if (kto) kto[q] = v;
+    }
+    if (keep_it) reinterpret_cast<uint2*>(d.keep_rec_out)[idx - last_first] = r;
+  }
+}
+
+}  // namespace
+
+void launch_describe(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s, const Output& out,
+                     const Describe& d, cudaStream_t st) {
+  const int sms = sm_count();
+  k_describe_new<<<sms * 4, kNewWarps * 32, 0, st>>>(g, b, s, out, d);
+  k_describe_carried<<<sms * 8, kCarriedThreads, 0, st>>>(g, tb, b, s, out, d);
+}
+
+}  // namespace fkd

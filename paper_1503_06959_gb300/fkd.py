@@ -35,7 +35,7 @@ EXPORTS = [
     "fkd_server_close_stream", "fkd_server_submit", "fkd_server_poll", "fkd_server_drain",
     "fkd_server_get_stats", "fkd_get_launch_config", "fkd_set_launch_config", "fkd_autotune",
     "fkd_group_get_launch_config", "fkd_group_set_launch_config", "fkd_group_autotune",
-    "fkd_get_pixel_mask",
+    "fkd_get_pixel_mask", "fkd_set_descriptor", "fkd_get_descriptors",
 ]
 STAGES = ["pyramid", "mask", "worklist", "detect", "count", "emit"]
 
@@ -134,6 +134,8 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.fkd_server_drain.argtypes = [vp, c_int]
     lib.fkd_server_get_stats.argtypes = [vp, P(fkd_server_stats), c_int]
     lib.fkd_get_pixel_mask.argtypes = [vp, c_int, vp]
+    lib.fkd_set_descriptor.argtypes = [vp, vp, c_int]
+    lib.fkd_get_descriptors.argtypes = [vp, vp, c_size, P(c_size), c_int]
     lib.fkd_get_launch_config.argtypes = [vp, P(fkd_launch_config)]
     lib.fkd_set_launch_config.argtypes = [vp, P(fkd_launch_config)]
     lib.fkd_autotune.argtypes = [vp, vp, c_size, c_size, c_int, c_int, P(fkd_launch_config),
@@ -179,7 +181,8 @@ class Stream:
     def __init__(self, W: int, H: int, *, N_r: int = 8, N_c: int = 8, T_I: int = 4, T_H: int = 1,
                  O: int = 1, intra: int = 0, t: int = 20, n: int = 9,
                  mask_mode: int = FKD_MASK_ID, mask_layer: int = 0, K_max: int = 65536,
-                 T_max: int = 1, cuda_stream: int | None = None, nms_scale: int = 0):
+                 T_max: int = 1, cuda_stream: int | None = None, nms_scale: int = 0,
+                 pattern=None):
         lib = load()
         p = params_default()
         p.N_r, p.N_c, p.T_I, p.T_H, p.O, p.intra, p.t, p.n = N_r, N_c, T_I, T_H, O, intra, t, n
@@ -191,6 +194,9 @@ class Stream:
         _check(lib.fkd_create_stream(ctypes.byref(p), W, H, ctypes.c_void_p(cuda_stream or 0),
                                      ctypes.byref(h)))
         self._h = h
+        self._D = 0
+        if pattern is not None:
+            self.set_descriptor(pattern)
 
     # -- geometry
     def num_layers(self) -> int:
@@ -277,6 +283,33 @@ class Stream:
 
     def synchronize(self):
         _check(_lib.fkd_synchronize(self._h))
+
+    # -- masked description
+    def set_descriptor(self, pattern):
+        """Describe keypoints with a D x 4 int8 pattern of pairs (ax, ay, bx, by);
+        None turns description off. Resets the stream."""
+        if pattern is None:
+            _check(_lib.fkd_set_descriptor(self._h, None, 0))
+            self._D = 0
+            return
+        pat = np.ascontiguousarray(pattern, dtype=np.int8)
+        assert pat.ndim == 2 and pat.shape[1] == 4
+        _check(_lib.fkd_set_descriptor(self._h, _ptr(pat), pat.shape[0]))
+        self._D = pat.shape[0]
+
+    def get_descriptors(self, out=None):
+        """Descriptors of the records of the last push (n x D/8 uint8, in record
+        order). With a torch CUDA ``out`` (uint8, rows of D/8 bytes) they are
+        copied there on the device and ``out[:n]`` is returned."""
+        n = ctypes.c_size_t()
+        if out is not None and _is_torch_cuda(out):
+            _check(_lib.fkd_get_descriptors(self._h, _ptr(out), out.shape[0], ctypes.byref(n), 1))
+            return out[:n.value]
+        _check(_lib.fkd_get_descriptors(self._h, None, 0, ctypes.byref(n), 0))
+        res = np.zeros((n.value, self._D // 8), np.uint8)
+        if n.value:
+            _check(_lib.fkd_get_descriptors(self._h, _ptr(res), n.value, ctypes.byref(n), 0))
+        return res
 
     def frame_count(self) -> int:
         n = ctypes.c_int64()

@@ -1,0 +1,147 @@
+"""Masked description on the GPU against the oracle (through the C ABI).
+
+Descriptors are integer results (bits of comparisons of integer box sums):
+the bar is bit-exact equality for every record, new and carried, on top of
+bit-exact keypoints.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1503_06959_gb300 import fkd, synth
+
+pytestmark = pytest.mark.gpu
+
+MODES = {"full": (fkd.FKD_MASK_FULL, oracle.MASK_FULL), "id": (fkd.FKD_MASK_ID, oracle.MASK_ID),
+         "kb": (fkd.FKD_MASK_KB, oracle.MASK_KB), "idp": (fkd.FKD_MASK_IDP, oracle.MASK_IDP)}
+
+
+def run_oracle(frames, pattern, **kw):
+    s = oracle.Stream(frames.shape[2], frames.shape[1], pattern=pattern, **kw)
+    kps, descs = [], []
+    for f in frames:
+        s.push(f)
+        kps.append(s.keypoints())
+        descs.append(s.descriptors())
+    return kps, descs
+
+
+def check(rec, desc, exp_kp, exp_desc, where):
+    assert len(rec) == len(exp_kp), f"{where}: {len(rec)} vs {len(exp_kp)} keypoints"
+    for f in ("layer", "y", "x", "score", "flags"):
+        np.testing.assert_array_equal(rec[f], exp_kp[f], err_msg=f"{where}: {f}")
+    assert desc.shape == exp_desc.shape, where
+    bad = np.flatnonzero((desc != exp_desc).any(axis=1))
+    assert bad.size == 0, (f"{where}: {bad.size} of {len(desc)} descriptors differ, first at record "
+                           f"{bad[0]} {rec[bad[0]]}")
+
+
+def streams(W, H, mode, pattern, T_max, **p):
+    g = fkd.Stream(W, H, mask_mode=MODES[mode][0], T_max=T_max, pattern=pattern, **p)
+    o = dict(p, mask_mode=MODES[mode][1])
+    return g, o
+
+
+@pytest.mark.parametrize("mode,mask_layer,D", [("id", -1, 256), ("id", 0, 32), ("kb", 0, 128),
+                                               ("idp", 0, 512), ("full", 0, 64)])
+def test_batches_match_oracle(mode, mask_layer, D):
+    W, H = 333, 250
+    src = synth.VideoSource(W, H, seed=41, n_movers=3, mover_size=60, speed=(2, 4), jitter_every=7)
+    frames = src.frames(17)
+    pattern = synth.descriptor_pattern(D, seed=D)
+    p = dict(N_r=7, N_c=9, T_I=4, T_H=2, O=3, intra=1, t=18, mask_layer=mask_layer)
+    g, o = streams(W, H, mode, pattern, 8, **p)
+    exp_kp, exp_d = run_oracle(frames, pattern, **o)
+    carried = sum(int((k["flags"] == 1).sum()) for k in exp_kp)
+    if mode != "full":
+        assert carried > 0, "the clip must carry keypoints"
+    # batches of 8, 1 and 8: carried descriptors cross batch boundaries
+    n0 = 0
+    for T in (8, 1, 8):
+        rec, off, _ = g.push_frames(frames[n0:n0 + T])
+        desc = g.get_descriptors()
+        assert len(desc) == off[T]
+        for k in range(T):
+            check(rec[off[k]:off[k + 1]], desc[off[k]:off[k + 1]], exp_kp[n0 + k], exp_d[n0 + k],
+                  f"{mode} frame {n0 + k}")
+        n0 += T
+
+
+@pytest.mark.parametrize("mode", ["id", "idp"])
+def test_frame_by_frame_and_device_output(mode):
+    torch = pytest.importorskip("torch")
+    W, H = 200, 150
+    frames = synth.VideoSource(W, H, seed=5, n_movers=2, mover_size=40, speed=(2, 3)).frames(9)
+    pattern = synth.descriptor_pattern(256, seed=9)
+    p = dict(N_r=5, N_c=6, T_I=4, O=2, intra=1, t=15, mask_layer=0)
+    g, o = streams(W, H, mode, pattern, 4, **p)
+    exp_kp, exp_d = run_oracle(frames, pattern, **o)
+    dev = torch.from_numpy(frames).cuda()
+    for n in range(5):  # single frames, host then device input
+        g.push_frame(frames[n] if n % 2 else dev[n])
+        check(g.get_keypoints(), g.get_descriptors(), exp_kp[n], exp_d[n], f"frame {n}")
+    # then a device batch with device outputs
+    cap = 4 * 20000
+    out = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    offs = torch.zeros(5, dtype=torch.int32, device="cuda")
+    g.push_frames(dev[5:9], out=out, offsets=offs)
+    g.synchronize()
+    dbuf = torch.zeros((cap, 32), dtype=torch.uint8, device="cuda")
+    d = g.get_descriptors(out=dbuf).cpu().numpy()
+    off = offs.cpu().numpy()
+    rec = out[:int(off[4])].cpu().numpy().view(fkd.KEYPOINT_DTYPE)
+    assert len(d) == off[4]
+    for k in range(4):
+        check(rec[off[k]:off[k + 1]], d[off[k]:off[k + 1]], exp_kp[5 + k], exp_d[5 + k], f"frame {5 + k}")
+
+
+def test_config2_batch_matches_oracle():
+    """640x480, four octaves with intra-octaves, coarse-layer mask: 32 frames
+    in one batch (including the camera step at frame 30), every descriptor."""
+    cfg = synth.config2()
+    frames = synth.source_for(cfg, 2).frames(32)
+    pattern = synth.descriptor_pattern(256)
+    p = dict(N_r=cfg.N_r, N_c=cfg.N_c, T_I=cfg.T_I, O=cfg.O, intra=cfg.intra, t=cfg.t,
+             mask_layer=cfg.mask_layer)
+    g, o = streams(cfg.W, cfg.H, "id", pattern, 32, **p)
+    exp_kp, exp_d = run_oracle(frames, pattern, **o)
+    rec, off, _ = g.push_frames(frames)
+    desc = g.get_descriptors()
+    for k in range(32):
+        check(rec[off[k]:off[k + 1]], desc[off[k]:off[k + 1]], exp_kp[k], exp_d[k], f"config 2 frame {k}")
+
+
+def test_pattern_validation_and_state():
+    W, H = 64, 48
+    s = fkd.Stream(W, H, N_r=2, N_c=2, O=1, t=15)
+    frame = synth.VideoSource(W, H, seed=2).frame(0)
+    with pytest.raises(fkd.FkdError):
+        s.get_descriptors()  # description off
+    for bad in (np.zeros((31, 4), np.int8), np.zeros((544, 4), np.int8), np.full((32, 4), 14, np.int8),
+                np.full((32, 4), -14, np.int8)):
+        with pytest.raises(fkd.FkdError):
+            s.set_descriptor(bad)
+    s.set_descriptor(np.full((32, 4), 13, np.int8))
+    with pytest.raises(fkd.FkdError):
+        s.get_descriptors()  # nothing pushed since
+    s.push_frame(frame)
+    d = s.get_descriptors()
+    assert d.shape == (len(s.get_keypoints()), 4)
+    assert not d.any()  # every pair compares a box with itself
+    s.set_descriptor(None)
+    with pytest.raises(fkd.FkdError):
+        s.get_descriptors()
+
+
+def test_described_detection_equals_undescribed():
+    """Description adds kernels after the emission; keypoints stay the same."""
+    cfg = synth.config1()
+    frames = synth.source_for(cfg, 1).frames(12)
+    p = dict(N_r=cfg.N_r, N_c=cfg.N_c, T_I=cfg.T_I, O=2, intra=1, t=cfg.t, T_max=12)
+    a = fkd.Stream(cfg.W, cfg.H, pattern=synth.descriptor_pattern(128), **p)
+    b = fkd.Stream(cfg.W, cfg.H, **p)
+    ra, oa, ma = a.push_frames(frames)
+    rb, ob, mb = b.push_frames(frames)
+    np.testing.assert_array_equal(oa, ob)
+    np.testing.assert_array_equal(ra, rb)
+    np.testing.assert_array_equal(ma, mb)
