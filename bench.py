@@ -749,13 +749,30 @@ def main():
     off_xs = offsets.cpu().numpy().astype(np.int64)
     kp_xs = int(off_xs[T] - off_xs[0])
 
+    # detection and description (Sec. 3): masked (descriptors only for new
+    # keypoints, carried ones copied) against full-frame (every keypoint
+    # described every frame), 256-bit descriptors
+    pattern = synth.descriptor_pattern(256)
+    desc_m = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_ID, pattern=pattern, **common)
+    desc_m.set_launch_config(shape_masked)
+    ms_dm, prof_dm = timed(desc_m, max(3, args.steps // 2), 3, profile=True)
+    off_dm = offsets.cpu().numpy().astype(np.int64)
+    rec_dm = out[:int(off_dm[T])].cpu().numpy().view(fkd.KEYPOINT_DTYPE)
+    new_dm = int(((rec_dm["flags"] & fkd.FKD_KP_PROPAGATED) == 0).sum())
+    desc_f = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_FULL, pattern=pattern, **common)
+    desc_f.set_launch_config(shape_full)
+    ms_df, prof_df = timed(desc_f, max(3, args.steps // 2), 3, profile=True)
+
     # max over ranks
-    ms, ms_full, ms_c0, ms_xs, ms_px = max_over_ranks([ms, ms_full, ms_c0, ms_xs, ms_px], dist, dev)
+    ms, ms_full, ms_c0, ms_xs, ms_px, ms_dm, ms_df = max_over_ranks(
+        [ms, ms_full, ms_c0, ms_xs, ms_px, ms_dm, ms_df], dist, dev)
     value = whole_job_fps(world, T, args.steps, ms)
     full_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_full)
     c0_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_c0)
     xs_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_xs)
     px_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_px)
+    dm_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_dm)
+    df_fps = whole_job_fps(world, T, max(3, args.steps // 2), ms_df)
 
     # frame-by-frame latency (device frames): push_frame + get_keypoints per frame
     lat = fkd.Stream(cfg.W, cfg.H, mask_mode=fkd.FKD_MASK_ID, N_r=cfg.N_r, N_c=cfg.N_c, mask_layer=cfg.mask_layer,
@@ -880,6 +897,15 @@ def main():
                                      "(its pass is timed in the detect stage)",
                              "stage_ms_per_step": {k: v / max(1, prof_xs["batches"])
                                                    for k, v in prof_xs["ms"].items()}},
+        "describe": {"masked": dm_fps, "full": df_fps, "unit": "frames/s", "masked_over_full": dm_fps / df_fps,
+                     "bits": 256, "described_per_step": {"masked": new_dm, "full": kp_full},
+                     "records_per_step": {"masked": int(off_dm[T]), "full": kp_full},
+                     "what": "detection + masked description (descriptors for new keypoints, carried "
+                             "ones copied) against full-frame detection + description of every keypoint",
+                     "stage_ms_per_step": {"masked": {k: v / max(1, prof_dm["batches"])
+                                                      for k, v in prof_dm["ms"].items()},
+                                           "full": {k: v / max(1, prof_df["batches"])
+                                                    for k, v in prof_df["ms"].items()}}},
         "active_bin_fraction": act, "keypoints_per_step": kp_masked,
         "stage_ms_per_step": {k: v / max(1, prof["batches"]) for k, v in stage_ms.items()},
         "latency_ms": {"p50": p50, "p99": p99, "frames": len(lat_ms),

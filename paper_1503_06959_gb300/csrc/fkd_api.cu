@@ -94,7 +94,7 @@ struct fkd_stream {
   fkd_keypoint* keep_rec[2] = {nullptr, nullptr};  // the last frame's records and descriptors, ping-pong
   uint32_t* keep_desc[2] = {nullptr, nullptr};     //   with the kept keypoint set (state_cur)
   uint32_t* keep_n = nullptr;              // [2]
-  uint32_t* desc_count = nullptr;          // [1]: end index of the last call's described records
+  uint32_t* desc_count = nullptr;          // [2]: end index of the last call's described records, work counter
   bool desc_ready = false;                 // a frame was described since description was set
 
   const uint8_t* prev = nullptr;
@@ -110,6 +110,7 @@ struct fkd_stream {
   struct Pending {
     cudaEvent_t ev[FKD_NUM_STAGES + 1];
     int frames;
+    bool described;
   };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
@@ -418,6 +419,8 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   else launch_count(s->g, tb, b, s->s, stt, s->st);                   // its last CTA fills s->s.bases
   mark(5);
   launch_emit(s->g, tb, b, s->s, stt, o, s->st);
+  mark(6);
+  pd.described = s->desc_D != 0;
   if (s->desc_D) {
     // descriptors of the detected records, carried ones copied (Sec. 3)
     Describe d{};
@@ -432,11 +435,12 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
     d.keep_n_out = s->keep_n + (s->state_cur ^ 1);
     d.keep_cap = s->p.K_max;
     d.count = s->desc_count;
+    d.next_group = s->desc_count + 1;
     d.missing = s->s.overflow;
     launch_describe(s->g, tb, b, s->s, o, d, s->st);
     s->desc_ready = true;
   }
-  mark(6);
+  mark(7);
   if (s->s.pmask && s->g.L > 1)  // layers >= 1 of the batch's last frame: L_{n-1} of the next batch
     CK(cudaMemcpyAsync(s->s.pyr_last, s->s.pyr + (long long)(T - 1) * s->g.pyr_bytes, (size_t)s->g.pyr_bytes,
                        cudaMemcpyDeviceToDevice, s->st));
@@ -831,14 +835,14 @@ int fkd_set_descriptor(fkd_stream* s, const int8_t* pattern, int D) {
   const size_t words = (size_t)D / 32, K = (size_t)s->p.K_max;
   int rc;
   if ((rc = s->alloc(&s->desc_pattern, (size_t)D * 4)) || (rc = s->alloc(&s->desc, K * words)) ||
-      (rc = s->alloc(&s->keep_n, 2)) || (rc = s->alloc(&s->desc_count, 1)))
+      (rc = s->alloc(&s->keep_n, 2)) || (rc = s->alloc(&s->desc_count, 2)))
     return rc;
   for (int i = 0; i < 2; ++i)
     if ((rc = s->alloc(&s->keep_rec[i], K)) || (rc = s->alloc(&s->keep_desc[i], K * words))) return rc;
   s->desc_cap = (long long)K;
   CK(cudaMemcpy(s->desc_pattern, pattern, (size_t)D * 4, cudaMemcpyHostToDevice));
   CK(cudaMemset(s->keep_n, 0, 8));
-  CK(cudaMemset(s->desc_count, 0, 4));
+  CK(cudaMemset(s->desc_count, 0, 8));
   s->desc_D = D;
   return FKD_OK;
 }
@@ -948,7 +952,7 @@ int fkd_profile_read(fkd_stream* s, fkd_profile* out, int reset) {
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, pd.ev[i], pd.ev[i + 1]));
       s->prof.ms[i] += ms;
-      s->prof.launches[i] += 1;
+      if (i != FKD_STAGE_DESCRIBE || pd.described) s->prof.launches[i] += 1;
     }
     s->prof.batches += 1;
     s->prof.frames += (uint64_t)pd.frames;
@@ -1094,6 +1098,7 @@ int group_launch(fkd_group* G, int b, int n_items, fkd_stream::Pending* pd) {
   mark(5);
   launch_group_emit(G->d_devs, G->d_hdr, G->d_items, G->grid_asm, G->st);
   mark(6);
+  mark(7);  // no description stage in groups
   CK(cudaGetLastError());
   return FKD_OK;
 }
@@ -1412,7 +1417,7 @@ int fkd_group_profile_read(fkd_group* G, fkd_profile* out, int reset) {
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, pd.ev[i], pd.ev[i + 1]));
       G->prof.ms[i] += ms;
-      G->prof.launches[i] += 1;
+      if (i != FKD_STAGE_DESCRIBE) G->prof.launches[i] += 1;  // groups do not describe
     }
     G->prof.batches += 1;
     G->prof.frames += (uint64_t)pd.frames;

@@ -191,6 +191,7 @@ struct Describe {
   uint32_t* keep_n_out;
   long long keep_cap;              // records the kept set holds (K_max)
   uint32_t* count;                 // end index of the described records (device word)
+  uint32_t* next_group;            // work counter of the new-record pass (zero between batches)
   int* missing;                    // set when a carried record's origin is absent (after an overflow)
 };
 

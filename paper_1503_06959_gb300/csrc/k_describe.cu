@@ -7,11 +7,14 @@
 // (x + bx_i, y + by_i), coordinates clamped to the layer, for a caller-given
 // pattern of D pairs with offsets within +-kDescR.
 //
-//   k_describe_new:     one warp per newly detected record. The warp stages
-//                       the 31 x 31 window around the keypoint (clamped) in
-//                       shared memory, forms 5-pixel row sums (lane per row)
-//                       and then the 27 x 27 box sums (lane per column), and
-//                       evaluates 32 pairs per ballot.
+//   k_describe_new:     one warp per newly detected record (warps take
+//                       groups of 32 records from a counter). Lane c loads
+//                       column c of the 32 x 32 window around the keypoint
+//                       (one coalesced read per row, clamped to the layer),
+//                       sums 5 rows in registers (two rows per register as
+//                       16-bit halves), adds 5 columns with shuffles, and
+//                       stores the 27 x 27 box sums to shared memory, where
+//                       32 pairs are compared per ballot.
 //   k_describe_carried: one thread per carried record. Eq. 1 makes a carried
 //                       record a copy of the record with the same position in
 //                       the frame that last detected there: src(k, bin) for
@@ -28,13 +31,18 @@
 namespace fkd {
 namespace {
 
-constexpr int kDescWin = 2 * kDescR + 5;  // staged window: 31 x 31 pixels
-constexpr int kDescBox = 2 * kDescR + 1;  // box centres: 27 x 27
-constexpr int kWinPitch = 36;             // bytes; 9 words per row: lanes on distinct rows hit distinct banks
-constexpr int kHsPitch = 29;              // words; odd, so a lane per row is conflict-free
+constexpr int kDescBox = 2 * kDescR + 1;  // 27: box centres per row and column
+constexpr int kHalfRows = 14;             // box rows r and r + 14 share a word
 constexpr int kNewWarps = 8;
+constexpr int kNewMinBlocks = 4;
 constexpr int kCarriedThreads = 256;
-static_assert(kDescWin <= 32, "one lane per window row and column");
+static_assert(kDescBox == 27 && 2 * kHalfRows >= kDescBox, "window of 32 rows and columns");
+
+// 16-bit index of the box sum of row r, column c in a warp's box array:
+// word (r % 14) * 32 + c, low half for r < 14, high half for r >= 14.
+__host__ __device__ constexpr int box_half(int r, int c) {
+  return 2 * ((r % kHalfRows) * 32 + c) + r / kHalfRows;
+}
 
 __device__ __forceinline__ unsigned long long rec_key(uint2 r) {
   return ((unsigned long long)(r.y & 0xffu) << 32) | r.x;  // (layer, y, x)
@@ -64,16 +72,15 @@ __device__ __forceinline__ const uint8_t* layer_base(const Geometry& g, const Ba
   return s.pyr + (long long)k * g.pyr_bytes + g.layer[l].pyr_off;
 }
 
-__global__ void __launch_bounds__(kNewWarps * 32) k_describe_new(Geometry g, Batch b, Scratch s, Output out,
-                                                                 Describe d) {
-  __shared__ uint32_t pat[kDescMaxBits];  // pair i: ax, ay, bx, by as bytes (offsets + kDescR)
-  __shared__ __align__(16) uint8_t win[kNewWarps][kDescWin * kWinPitch];
-  __shared__ uint32_t hs[kNewWarps][kDescWin * kHsPitch];  // row sums, then box sums in place
+__global__ void __launch_bounds__(kNewWarps * 32, kNewMinBlocks)
+    k_describe_new(Geometry g, Batch b, Scratch s, Output out, Describe d) {
+  __shared__ uint32_t pat[kDescMaxBits];                  // pair i: 16-bit indices of its two box sums
+  __shared__ uint32_t boxes[kNewWarps][kHalfRows * 32];   // 5 x 5 sums, two rows per word
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < d.D; i += blockDim.x) {
     const char4 q = reinterpret_cast<const char4*>(d.pattern)[i];
-    pat[i] = (uint32_t)(q.x + kDescR) | (uint32_t)(q.y + kDescR) << 8 | (uint32_t)(q.z + kDescR) << 16 |
-             (uint32_t)(q.w + kDescR) << 24;
+    pat[i] = (uint32_t)box_half(q.y + kDescR, q.x + kDescR) |
+             (uint32_t)box_half(q.w + kDescR, q.z + kDescR) << 16;
   }
   __syncthreads();
 
@@ -90,11 +97,16 @@ __global__ void __launch_bounds__(kNewWarps * 32) k_describe_new(Geometry g, Bat
     *d.keep_n_out = (uint32_t)min(kept, d.keep_cap);
     if (kept < n_last || kept > d.keep_cap) *s.overflow = 1;
   }
+  const long long groups = end > first ? (end - first + 31) / 32 : 0;
   const uint2* recs = reinterpret_cast<const uint2*>(out.rec);
-  uint8_t* w = win[warp];
-  uint32_t* h = hs[warp];
-  const long long gw = (long long)blockIdx.x * kNewWarps + warp, nw = (long long)gridDim.x * kNewWarps;
-  for (long long base = first + gw * 32; base < end; base += nw * 32) {
+  uint32_t* bw = boxes[warp];
+  const uint16_t* box16 = reinterpret_cast<const uint16_t*>(bw);
+  for (;;) {
+    unsigned long long gi = 0;
+    if (lane == 0) gi = atomicAdd(d.next_group, 1u);
+    gi = __shfl_sync(0xffffffffu, gi, 0);
+    if ((long long)gi >= groups) break;
+    const long long base = first + (long long)gi * 32;
     const long long idx = base + lane;
     uint2 r = make_uint2(0u, 0u);
     bool is_new = false;
@@ -116,51 +128,46 @@ __global__ void __launch_bounds__(kNewWarps * 32) k_describe_new(Geometry g, Bat
       const LayerGeom& lg = g.layer[l];
       int pitch;
       const uint8_t* img = layer_base(g, b, s, kk, l, &pitch);
-      // 1. the clamped window: lane c takes column c of every row (each
-      //    row is one contiguous read across the warp)
-      if (lane < kDescWin) {
-        const int gx = min(max(x - kDescR - 2 + lane, 0), lg.w - 1);
-#pragma unroll 8
-        for (int rr = 0; rr < kDescWin; ++rr) {
-          const int gy = min(max(y - kDescR - 2 + rr, 0), lg.h - 1);
-          w[rr * kWinPitch + lane] = img[(long long)gy * pitch + gx];
-        }
+
+      // 1. lane c: column x - 15 + c of rows y - 15 .. y + 16, clamped
+      const uint8_t* col = img + min(max(x - kDescR - 2 + lane, 0), lg.w - 1);
+      uint32_t px[32];
+      if (y >= kDescR + 2 && y + kDescR + 4 <= lg.h) {
+        const uint8_t* p = col + (long long)(y - kDescR - 2) * pitch;
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr) px[rr] = p[(long long)rr * pitch];
+      } else {
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr)
+          px[rr] = col[(long long)min(max(y - kDescR - 2 + rr, 0), lg.h - 1) * pitch];
+      }
+      // 2. 5-row sums of the column: P[m] = (sum of rows m..m+4, sum of rows
+      //    m+14..m+18) as 16-bit halves, sliding down
+      uint32_t P[kHalfRows];
+      {
+        uint32_t q[kHalfRows + 4];
+#pragma unroll
+        for (int m = 0; m < kHalfRows + 4; ++m) q[m] = px[m] | (px[m + kHalfRows] << 16);
+        P[0] = q[0] + q[1] + q[2] + q[3] + q[4];
+#pragma unroll
+        for (int m = 1; m < kHalfRows; ++m) P[m] = P[m - 1] + q[m + 4] - q[m - 1];
+      }
+      // 3. 5-column sums across lanes (lane c: columns c..c+4, valid for
+      //    c < 27), stored for the pair tests
+      __syncwarp();  // the previous record's tests are done with the array
+#pragma unroll
+      for (int m = 0; m < kHalfRows; ++m) {
+        const uint32_t a2 = P[m] + __shfl_down_sync(0xffffffffu, P[m], 1);
+        const uint32_t a4 = a2 + __shfl_down_sync(0xffffffffu, a2, 2);
+        bw[m * 32 + lane] = a4 + __shfl_down_sync(0xffffffffu, P[m], 4);
       }
       __syncwarp();
-      // 2. 5-pixel row sums, lane per row
-      if (lane < kDescWin) {
-        const uint8_t* row = w + lane * kWinPitch;
-        uint32_t sum = row[0] + row[1] + row[2] + row[3] + row[4];
-        uint32_t* hr = h + lane * kHsPitch;
-        hr[0] = sum;
-#pragma unroll
-        for (int c = 1; c < kDescBox; ++c) {
-          sum += (uint32_t)row[c + 4] - (uint32_t)row[c - 1];
-          hr[c] = sum;
-        }
-      }
-      __syncwarp();
-      // 3. 5-row sums of those, lane per column, in place
-      if (lane < kDescBox) {
-        uint32_t v[kDescWin];
-#pragma unroll
-        for (int rr = 0; rr < kDescWin; ++rr) v[rr] = h[rr * kHsPitch + lane];
-        uint32_t sum = v[0] + v[1] + v[2] + v[3] + v[4];
-        h[lane] = sum;
-#pragma unroll
-        for (int rr = 1; rr < kDescBox; ++rr) {
-          sum += v[rr + 4] - v[rr - 1];
-          h[rr * kHsPitch + lane] = sum;
-        }
-      }
-      __syncwarp();
+
       // 4. 32 pairs per ballot; lane j keeps word j
       uint32_t mine = 0u;
       for (int j = 0; j < DW; ++j) {
         const uint32_t q = pat[j * 32 + lane];
-        const uint32_t a = h[((q >> 8) & 0xffu) * kHsPitch + (q & 0xffu)];
-        const uint32_t c = h[(q >> 24) * kHsPitch + ((q >> 16) & 0xffu)];
-        const uint32_t word = __ballot_sync(0xffffffffu, a < c);
+        const uint32_t word = __ballot_sync(0xffffffffu, box16[q & 0xffffu] < box16[q >> 16]);
         if (lane == j) mine = word;
       }
       if (lane < DW) d.desc[ridx * DW + lane] = mine;
@@ -169,7 +176,6 @@ __global__ void __launch_bounds__(kNewWarps * 32) k_describe_new(Geometry g, Bat
         if (lane < DW) d.keep_desc_out[kidx * DW + lane] = mine;
         if (lane == 0) reinterpret_cast<uint2*>(d.keep_rec_out)[kidx] = make_uint2(rx, ry);
       }
-      __syncwarp();  // the window and sums are reused by the next record
     }
   }
 }
@@ -185,6 +191,7 @@ __global__ void __launch_bounds__(kCarriedThreads) k_describe_carried(Geometry g
   const uint2* recs = reinterpret_cast<const uint2*>(out.rec);
   const uint2* keep = reinterpret_cast<const uint2*>(d.keep_rec_in);
   const long long n_keep = *d.keep_n_in;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *d.next_group = 0u;  // the new pass is done with it
   for (long long idx = first + blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < end;
        idx += (long long)gridDim.x * blockDim.x) {
     const uint2 r = recs[idx];
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(kCarriedThreads) k_describe_carried(Geometry g
 void launch_describe(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s, const Output& out,
                      const Describe& d, cudaStream_t st) {
   const int sms = sm_count();
-  k_describe_new<<<sms * 4, kNewWarps * 32, 0, st>>>(g, b, s, out, d);
+  k_describe_new<<<sms * kNewMinBlocks, kNewWarps * 32, 0, st>>>(g, b, s, out, d);
   k_describe_carried<<<sms * 8, kCarriedThreads, 0, st>>>(g, tb, b, s, out, d);
 }
 

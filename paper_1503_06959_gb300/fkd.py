@@ -17,7 +17,7 @@ from . import build as _build
 FKD_OK, FKD_E_ARG, FKD_E_CAPACITY, FKD_E_BUDGET, FKD_E_CUDA, FKD_E_TIMEOUT, FKD_E_STATE = (
     0, -1, -2, -3, -4, -5, -6)
 FKD_MASK_FULL, FKD_MASK_ID, FKD_MASK_KB, FKD_MASK_IDP = 0, 1, 2, 3
-FKD_VERSION = 2
+FKD_VERSION = 3
 FKD_KP_PROPAGATED = 1
 
 KEYPOINT_DTYPE = np.dtype(
@@ -37,7 +37,7 @@ EXPORTS = [
     "fkd_group_get_launch_config", "fkd_group_set_launch_config", "fkd_group_autotune",
     "fkd_get_pixel_mask", "fkd_set_descriptor", "fkd_get_descriptors",
 ]
-STAGES = ["pyramid", "mask", "worklist", "detect", "count", "emit"]
+STAGES = ["pyramid", "mask", "worklist", "detect", "count", "emit", "describe"]
 
 
 class fkd_params(ctypes.Structure):
@@ -48,7 +48,7 @@ class fkd_params(ctypes.Structure):
 
 
 class fkd_profile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_uint64 * 6),
+    _fields_ = [("ms", ctypes.c_double * 7), ("launches", ctypes.c_uint64 * 7),
                 ("batches", ctypes.c_uint64), ("frames", ctypes.c_uint64),
                 ("tiles", ctypes.c_uint64), ("tile_pixels", ctypes.c_uint64)]
 
@@ -344,8 +344,8 @@ class Stream:
     def profile_read(self, reset: bool = True) -> dict:
         p = fkd_profile()
         _check(_lib.fkd_profile_read(self._h, ctypes.byref(p), int(reset)))
-        return {"ms": {STAGES[i]: p.ms[i] for i in range(6)},
-                "launches": {STAGES[i]: int(p.launches[i]) for i in range(6)},
+        return {"ms": {STAGES[i]: p.ms[i] for i in range(len(STAGES))},
+                "launches": {STAGES[i]: int(p.launches[i]) for i in range(len(STAGES))},
                 "batches": int(p.batches), "frames": int(p.frames), "tiles": int(p.tiles),
                 "tile_pixels": int(p.tile_pixels)}
 
@@ -446,8 +446,8 @@ class Group:
     def profile_read(self, reset: bool = True) -> dict:
         p = fkd_profile()
         _check(_lib.fkd_group_profile_read(self._h, ctypes.byref(p), int(reset)))
-        return {"ms": {STAGES[i]: p.ms[i] for i in range(6)},
-                "launches": {STAGES[i]: int(p.launches[i]) for i in range(6)},
+        return {"ms": {STAGES[i]: p.ms[i] for i in range(len(STAGES))},
+                "launches": {STAGES[i]: int(p.launches[i]) for i in range(len(STAGES))},
                 "batches": int(p.batches), "frames": int(p.frames), "tiles": int(p.tiles),
                 "tile_pixels": int(p.tile_pixels)}
 

@@ -30,11 +30,11 @@ def test_library_exports_every_declared_symbol():
 def test_params_default_and_validation_without_gpu():
     lib = fkd.load()
     p = fkd.params_default()
-    assert (p.version, p.N_r, p.N_c, p.t, p.n, p.O, p.mask_mode, p.T_max) == (2, 8, 8, 20, 9, 1, 1, 1)
+    assert (p.version, p.N_r, p.N_c, p.t, p.n, p.O, p.mask_mode, p.T_max) == (3, 8, 8, 20, 9, 1, 1, 1)
     h = ctypes.c_void_p()
     bad = [dict(n=8), dict(t=0), dict(t=256), dict(O=7), dict(N_r=0), dict(N_c=700),
            dict(mask_mode=4), dict(mask_layer=1), dict(K_max=0), dict(T_max=0), dict(intra=2),
-           dict(version=1), dict(T_I=-1), dict(nms_scale=2)]
+           dict(version=1), dict(version=2), dict(T_I=-1), dict(nms_scale=2)]
     for over in bad:
         q = fkd.params_default()
         for k, v in over.items():
