@@ -95,6 +95,9 @@ struct fkd_stream {
   uint32_t* keep_desc[2] = {nullptr, nullptr};     //   with the kept keypoint set (state_cur)
   uint32_t* keep_n = nullptr;              // [2]
   uint32_t* desc_count = nullptr;          // [2]: end index of the last call's described records, work counter
+  uint32_t* desc_rows = nullptr;           // [T_max][rows]: first record of each layer row of each frame
+  uint32_t* keep_row[2] = {nullptr, nullptr};  // [rows + 1]: the kept set's row starts, ping-pong
+  int rows = 0;                            // layer rows per frame
   bool desc_ready = false;                 // a frame was described since description was set
 
   const uint8_t* prev = nullptr;
@@ -395,6 +398,10 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   stt.score_out = s->state_score[s->state_cur ^ 1];
   stt.cnt_out = s->state_cnt[s->state_cur ^ 1];
   Output o{out, cap, offsets, base_slot};
+  if (s->desc_D) {
+    o.row_base = s->desc_rows;
+    o.rows = s->rows;
+  }
 
   fkd_stream::Pending pd{};
   const bool prof = s->profiling;
@@ -434,6 +441,8 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
     d.keep_desc_out = s->keep_desc[s->state_cur ^ 1];
     d.keep_n_out = s->keep_n + (s->state_cur ^ 1);
     d.keep_cap = s->p.K_max;
+    d.keep_row_in = s->keep_row[s->state_cur];
+    d.keep_row_out = s->keep_row[s->state_cur ^ 1];
     d.count = s->desc_count;
     d.next_group = s->desc_count + 1;
     d.missing = s->s.overflow;
@@ -828,7 +837,9 @@ int fkd_set_descriptor(fkd_stream* s, const int8_t* pattern, int D) {
   for (int i = 0; i < 2; ++i) {
     s->free_one(s->keep_rec[i]);
     s->free_one(s->keep_desc[i]);
+    s->free_one(s->keep_row[i]);
   }
+  s->free_one(s->desc_rows);
   s->free_one(s->keep_n);
   s->free_one(s->desc_count);
   if (D == 0) return FKD_OK;
@@ -837,8 +848,15 @@ int fkd_set_descriptor(fkd_stream* s, const int8_t* pattern, int D) {
   if ((rc = s->alloc(&s->desc_pattern, (size_t)D * 4)) || (rc = s->alloc(&s->desc, K * words)) ||
       (rc = s->alloc(&s->keep_n, 2)) || (rc = s->alloc(&s->desc_count, 2)))
     return rc;
-  for (int i = 0; i < 2; ++i)
-    if ((rc = s->alloc(&s->keep_rec[i], K)) || (rc = s->alloc(&s->keep_desc[i], K * words))) return rc;
+  const LayerGeom& top = s->g.layer[s->g.L - 1];
+  s->rows = top.row_off + top.h;
+  for (int i = 0; i < 2; ++i) {
+    if ((rc = s->alloc(&s->keep_rec[i], K)) || (rc = s->alloc(&s->keep_desc[i], K * words)) ||
+        (rc = s->alloc(&s->keep_row[i], (size_t)s->rows + 1)))
+      return rc;
+    CK(cudaMemset(s->keep_row[i], 0, ((size_t)s->rows + 1) * 4));
+  }
+  if ((rc = s->alloc(&s->desc_rows, (size_t)s->p.T_max * s->rows))) return rc;
   s->desc_cap = (long long)K;
   CK(cudaMemcpy(s->desc_pattern, pattern, (size_t)D * 4, cudaMemcpyHostToDevice));
   CK(cudaMemset(s->keep_n, 0, 8));

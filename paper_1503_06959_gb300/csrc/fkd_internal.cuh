@@ -172,6 +172,8 @@ struct Output {
   long long cap;
   uint32_t* offsets;               // T + 1 entries
   int base_slot;                   // out_base slot read; the other one is written
+  uint32_t* row_base;              // null, or [T][rows]: index of the first record of each layer row
+  int rows;                        // layer rows per frame (all layers)
 };
 
 // Masked description: binary descriptors of D bits (D / 32 words per record,
@@ -190,6 +192,8 @@ struct Describe {
   uint32_t* keep_desc_out;
   uint32_t* keep_n_out;
   long long keep_cap;              // records the kept set holds (K_max)
+  const uint32_t* keep_row_in;     // [rows + 1]: first kept record of each layer row, then the count
+  uint32_t* keep_row_out;
   uint32_t* count;                 // end index of the described records (device word)
   uint32_t* next_group;            // work counter of the new-record pass (zero between batches)
   int* missing;                    // set when a carried record's origin is absent (after an overflow)

@@ -233,6 +233,24 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
     total += wsum[q];
   }
   const unsigned long long base = call_base + frame_base + chunk_base;
+  if (out.row_base) {
+    // index of the first record of every row starting in this thread's words
+    // (the descriptor pass looks keypoints up by row)
+    uint32_t* rb = out.row_base + (long long)k * out.rows + lg.row_off + ch.y0;
+    const int nrows = ch.y1 - ch.y0;
+    int row = (j0 + wpr - 1) / wpr;
+    int next = row * wpr;
+    unsigned long long at = base + before + incl - cnt;
+#pragma unroll
+    for (int jj = 0; jj < kAsmWordsPerThread; ++jj) {
+      if (j0 + jj == next && row < nrows) {
+        rb[row] = (uint32_t)at;
+        ++row;
+        next += wpr;
+      }
+      at += __popc(words[jj]);
+    }
+  }
   if (total > (uint32_t)kEmitList) {
     // a dense chunk: every thread emits its own words' records
     if (cnt) emit_records(g, tb, s, st, out, k, last, ch, lg, j0, words, base + before + incl - cnt);

@@ -33,15 +33,16 @@ namespace {
 
 constexpr int kDescBox = 2 * kDescR + 1;  // 27: box centres per row and column
 constexpr int kHalfRows = 14;             // box rows r and r + 14 share a word
+constexpr int kBoxPitch = 27;             // words per row pair: banks (c - 5 r) % 32 spread the pattern's lookups
 constexpr int kNewWarps = 8;
 constexpr int kNewMinBlocks = 4;
 constexpr int kCarriedThreads = 256;
 static_assert(kDescBox == 27 && 2 * kHalfRows >= kDescBox, "window of 32 rows and columns");
 
 // 16-bit index of the box sum of row r, column c in a warp's box array:
-// word (r % 14) * 32 + c, low half for r < 14, high half for r >= 14.
+// word (r % 14) * 27 + c, low half for r < 14, high half for r >= 14.
 __host__ __device__ constexpr int box_half(int r, int c) {
-  return 2 * ((r % kHalfRows) * 32 + c) + r / kHalfRows;
+  return 2 * ((r % kHalfRows) * kBoxPitch + c) + r / kHalfRows;
 }
 
 __device__ __forceinline__ unsigned long long rec_key(uint2 r) {
@@ -75,7 +76,7 @@ __device__ __forceinline__ const uint8_t* layer_base(const Geometry& g, const Ba
 __global__ void __launch_bounds__(kNewWarps * 32, kNewMinBlocks)
     k_describe_new(Geometry g, Batch b, Scratch s, Output out, Describe d) {
   __shared__ uint32_t pat[kDescMaxBits];                  // pair i: 16-bit indices of its two box sums
-  __shared__ uint32_t boxes[kNewWarps][kHalfRows * 32];   // 5 x 5 sums, two rows per word
+  __shared__ uint32_t boxes[kNewWarps][kHalfRows * kBoxPitch];  // 5 x 5 sums, two rows per word
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < d.D; i += blockDim.x) {
     const char4 q = reinterpret_cast<const char4*>(d.pattern)[i];
@@ -159,7 +160,8 @@ __global__ void __launch_bounds__(kNewWarps * 32, kNewMinBlocks)
       for (int m = 0; m < kHalfRows; ++m) {
         const uint32_t a2 = P[m] + __shfl_down_sync(0xffffffffu, P[m], 1);
         const uint32_t a4 = a2 + __shfl_down_sync(0xffffffffu, a2, 2);
-        bw[m * 32 + lane] = a4 + __shfl_down_sync(0xffffffffu, P[m], 4);
+        const uint32_t box = a4 + __shfl_down_sync(0xffffffffu, P[m], 4);
+        if (lane < kDescBox) bw[m * kBoxPitch + lane] = box;
       }
       __syncwarp();
 
@@ -192,6 +194,16 @@ __global__ void __launch_bounds__(kCarriedThreads) k_describe_carried(Geometry g
   const uint2* keep = reinterpret_cast<const uint2*>(d.keep_rec_in);
   const long long n_keep = *d.keep_n_in;
   if (blockIdx.x == 0 && threadIdx.x == 0) *d.next_group = 0u;  // the new pass is done with it
+  {
+    // row starts of the last frame, relative to its first record: the kept
+    // set's row index for the next batch
+    const long long kept_end = min(end, last_first + d.keep_cap);
+    const uint32_t* rb = out.row_base + (long long)(T - 1) * out.rows;
+    for (int gr = blockIdx.x * blockDim.x + threadIdx.x; gr <= out.rows; gr += gridDim.x * blockDim.x) {
+      const long long v = gr < out.rows ? (long long)rb[gr] : (long long)off[T];
+      d.keep_row_out[gr] = (uint32_t)(min(max(v, last_first), max(kept_end, last_first)) - last_first);
+    }
+  }
   for (long long idx = first + blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < end;
        idx += (long long)gridDim.x * blockDim.x) {
     const uint2 r = recs[idx];
@@ -211,13 +223,17 @@ __global__ void __launch_bounds__(kCarriedThreads) k_describe_carried(Geometry g
       const int bin = tb.rowblk[lg.row_off + y] * g.N_c + tb.colblk[lg.col_off + x];
       sf = s.src[(long long)k * g.NB + bin];
     }
+    // the origin is in the same layer row of its frame: search that row only
     const unsigned long long key = rec_key(r);
+    const int gr = lg.row_off + y;
     const uint32_t* from = nullptr;
     if (sf >= 0) {
-      const long long j = find_record(recs, off[sf], min((long long)off[sf + 1], out.cap), key);
+      const uint32_t* rb = out.row_base + (long long)sf * out.rows;
+      const long long lo = rb[gr], hi = gr + 1 < out.rows ? rb[gr + 1] : off[sf + 1];
+      const long long j = find_record(recs, lo, min(hi, out.cap), key);
       if (j >= 0) from = d.desc + j * DW;
     } else {
-      const long long j = find_record(keep, 0, n_keep, key);
+      const long long j = find_record(keep, d.keep_row_in[gr], min((long long)d.keep_row_in[gr + 1], n_keep), key);
       if (j >= 0) from = d.keep_desc_in + j * DW;
     }
     if (!from) {
