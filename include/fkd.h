@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define FKD_VERSION 2u
+#define FKD_VERSION 3u
 
 /* status codes */
 #define FKD_OK 0
@@ -278,7 +278,8 @@ int fkd_get_descriptors(fkd_stream* s, uint8_t* out, size_t cap, size_t* n_out, 
  * of all batches since the last read (reset != 0 clears them afterwards).
  * Stages: FKD_STAGE_PYRAMID (pyramid + per-bin change sums), _MASK (mask and
  * source frames), _WORKLIST (active-tile compaction), _DETECT (segment test,
- * score, suppression), _COUNT and _EMIT (assembly of D_n).
+ * score, suppression), _COUNT and _EMIT (assembly of D_n), _DESCRIBE (masked
+ * description; its launches count only batches that described).
  * tile_pixels counts the layer pixels inside the detection tiles processed
  * (each is one input byte the detection kernel must read), tiles the tiles.
  */
@@ -288,7 +289,8 @@ int fkd_get_descriptors(fkd_stream* s, uint8_t* out, size_t cap, size_t* n_out, 
 #define FKD_STAGE_DETECT 3
 #define FKD_STAGE_COUNT 4
 #define FKD_STAGE_EMIT 5
-#define FKD_NUM_STAGES 6
+#define FKD_STAGE_DESCRIBE 6
+#define FKD_NUM_STAGES 7
 typedef struct {
   double ms[FKD_NUM_STAGES];       /* summed kernel time per stage            */
   uint64_t launches[FKD_NUM_STAGES];

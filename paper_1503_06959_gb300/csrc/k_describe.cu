@@ -243,10 +243,18 @@ __global__ void __launch_bounds__(kCarriedThreads) k_describe_carried(Geometry g
     uint32_t* to = d.desc + idx * DW;
     const bool keep_it = idx >= last_first && idx - last_first < d.keep_cap;
     uint32_t* kto = keep_it ? d.keep_desc_out + (idx - last_first) * DW : nullptr;
-    for (int q = 0; q < DW; ++q) {
-      const uint32_t v = from[q];
-      to[q] = v;
-      if (kto) kto[q] = v;
+    if ((DW & 3) == 0) {  // rows of 16-byte multiples: vector copies
+      for (int q = 0; q < DW; q += 4) {
+        const uint4 v = *reinterpret_cast<const uint4*>(from + q);
+        *reinterpret_cast<uint4*>(to + q) = v;
+        if (kto) *reinterpret_cast<uint4*>(kto + q) = v;
+      }
+    } else {
+      for (int q = 0; q < DW; ++q) {
+        const uint32_t v = from[q];
+        to[q] = v;
+        if (kto) kto[q] = v;
+      }
     }
     if (keep_it) reinterpret_cast<uint2*>(d.keep_rec_out)[idx - last_first] = r;
   }
