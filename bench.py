@@ -470,6 +470,66 @@ def run_sweep(args):
     return 0
 
 
+def run_describe(args):
+    """Detection + masked description alone on the 640x480 clip (Sec. 3:
+    descriptors only for newly detected keypoints, carried ones copied),
+    against full-frame detection + description of every keypoint; 256-bit
+    descriptors. One JSON line; also the case the describe profiles use."""
+    import torch
+    from paper_1503_06959_gb300 import fkd
+    cfg = synth.config2()
+    T = args.frames or cfg.frames
+    frames = torch.from_numpy(synth.source_for(cfg, 2).frames(T)).cuda()
+    st = torch.cuda.current_stream()
+    base = dict(N_r=cfg.N_r, N_c=cfg.N_c, T_I=cfg.T_I, O=cfg.O, intra=cfg.intra, t=cfg.t,
+                mask_layer=cfg.mask_layer, T_max=T, cuda_stream=st.cuda_stream,
+                pattern=synth.descriptor_pattern(256))
+    cap = T * 32768
+    out = torch.empty(cap, dtype=torch.int64, device="cuda")
+    off = torch.empty(T + 1, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    res = {}
+    modes = {"masked": fkd.FKD_MASK_ID, "full": fkd.FKD_MASK_FULL}
+    for name in (modes if args.describe == "both" else [args.describe]):
+        s = fkd.Stream(cfg.W, cfg.H, mask_mode=modes[name], **base)
+        if args.shape:
+            th, wp, cp = (int(v) for v in args.shape.split(","))
+            s.set_launch_config(dict(tile_h=th, warps_per_cta=wp, ctas_per_sm=cp))
+        for _ in range(args.warmup):
+            s.reset()
+            s.push_frames(frames, out=out, offsets=off)
+        s.synchronize()
+        s.profile_read(reset=True)
+        s.profile_enable(True)
+        ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            s.reset()
+            s.push_frames(frames, out=out, offsets=off)
+            e1.record(st)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        s.synchronize()
+        prof = s.profile_read(reset=True)
+        o = off.cpu().numpy().astype(np.int64)
+        rec = out[:int(o[T])].cpu().numpy().view(fkd.KEYPOINT_DTYPE)
+        res[name] = {"value": T * args.steps / (ms / 1e3), "unit": "frames/s", "records_per_step": int(o[T]),
+                     "described_per_step": int(((rec["flags"] & fkd.FKD_KP_PROPAGATED) == 0).sum()),
+                     "stage_ms_per_step": {k: v / max(1, prof["batches"]) for k, v in prof["ms"].items()}}
+        s.close()
+    line = {"metric": "frames/s (detection + masked description, bit-exact)", "unit": "frames/s",
+            "steps": args.steps, "warmup": args.warmup, "bits": 256,
+            "config": {"workload": workload_desc(cfg, T), "frames_per_step": T,
+                       "l2": "flushed between steps (256 MB write outside the timed events)"},
+            **res}
+    if "masked" in res and "full" in res:
+        line["masked_over_full"] = res["masked"]["value"] / res["full"]["value"]
+    print(json.dumps(line))
+    return 0
+
+
 def run_config4(args):
     """Serving: streams of mixed resolution producing frames at 30 fps with
     Poisson jitter, submitted as they arrive; continuous batching."""
@@ -622,6 +682,8 @@ def main():
     ap.add_argument("--small-budget-mb", type=int, default=256)
     ap.add_argument("--segment", type=int, default=20)
     ap.add_argument("--streams-5", type=int, default=8)
+    ap.add_argument("--describe", default="", choices=["", "masked", "full", "both"],
+                    help="detection + description on the 640x480 clip only (masked, full or both)")
     ap.add_argument("--shape", default="",
                     help="detection launch shape tile_h,warps_per_cta,ctas_per_sm (default: autotune)")
     args = ap.parse_args()
@@ -631,6 +693,8 @@ def main():
         return run_reference(args)
     if args.sweep:
         return run_sweep(args)
+    if args.describe:
+        return run_describe(args)
     if args.config == 3:
         return run_config3(args)
     if args.config == 4:
