@@ -145,3 +145,32 @@ def test_described_detection_equals_undescribed():
     np.testing.assert_array_equal(oa, ob)
     np.testing.assert_array_equal(ra, rb)
     np.testing.assert_array_equal(ma, mb)
+
+
+def test_capacity_overflow_then_reset():
+    """Records past `cap` are dropped and reported; the descriptors of the
+    records that fit are still right, and after a reset the stream describes
+    bit-exactly again."""
+    cfg = synth.config1()
+    frames = synth.source_for(cfg, 1).frames(8)
+    pattern = synth.descriptor_pattern(64, seed=4)
+    p = dict(N_r=cfg.N_r, N_c=cfg.N_c, T_I=cfg.T_I, O=2, intra=1, t=cfg.t)
+    g, o = streams(cfg.W, cfg.H, "id", pattern, 4, **p)
+    exp_kp, exp_d = run_oracle(frames, pattern, **o)
+    total = sum(len(k) for k in exp_kp[:4])
+    cap = total // 2
+    out = np.zeros(cap, fkd.KEYPOINT_DTYPE)
+    off = np.zeros(5, np.uint32)
+    with pytest.raises(fkd.FkdError):
+        g.push_frames(frames[:4], out=out, offsets=off)
+    d = g.get_descriptors()
+    assert len(d) == cap
+    n0 = len(exp_kp[0])
+    np.testing.assert_array_equal(d[:min(n0, cap)], exp_d[0][:min(n0, cap)])
+    g.reset()
+    for n0 in (0, 4):
+        rec, off2, _ = g.push_frames(frames[n0:n0 + 4])
+        desc = g.get_descriptors()
+        for k in range(4):
+            check(rec[off2[k]:off2[k + 1]], desc[off2[k]:off2[k + 1]], exp_kp[n0 + k], exp_d[n0 + k],
+                  f"after reset, frame {n0 + k}")
