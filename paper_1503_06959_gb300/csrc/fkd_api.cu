@@ -2,6 +2,7 @@
 // and the launch sequence of one batch (pyramid -> mask -> active tiles ->
 // detection -> assembly).
 #include <algorithm>
+#include <utility>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -53,7 +54,7 @@ struct fkd_stream {
   fkd_params p{};
   Geometry g{};
   cudaStream_t st = nullptr;
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> allocs;  // device allocations and their sizes
   size_t bytes_held = 0;  // device bytes this stream allocated
 
   uint16_t* colblk = nullptr;
@@ -136,8 +137,8 @@ struct fkd_stream {
     void* d = nullptr;
     cudaError_t e = cudaMalloc(&d, std::max<size_t>(count, 1) * sizeof(T));
     if (e != cudaSuccess) return fail(FKD_E_CUDA, "cudaMalloc(%zu) failed: %s", count * sizeof(T), cudaGetErrorString(e));
-    allocs.push_back(d);
-    bytes_held += std::max<size_t>(count, 1) * sizeof(T);
+    allocs.emplace_back(d, std::max<size_t>(count, 1) * sizeof(T));
+    bytes_held += allocs.back().second;
     *p = static_cast<T*>(d);
     return FKD_OK;
   }
@@ -145,14 +146,18 @@ struct fkd_stream {
   template <class T>
   void free_one(T*& p) {
     if (!p) return;
-    auto it = std::find(allocs.begin(), allocs.end(), (void*)p);
-    if (it != allocs.end()) allocs.erase(it);
+    auto it = std::find_if(allocs.begin(), allocs.end(), [&](const auto& a) { return a.first == (void*)p; });
+    if (it != allocs.end()) {
+      bytes_held -= it->second;
+      allocs.erase(it);
+    }
     cudaFree(p);
     p = nullptr;
   }
   void release() {
-    for (void* d : allocs) cudaFree(d);
+    for (auto& a : allocs) cudaFree(a.first);
     allocs.clear();
+    bytes_held = 0;
     for (auto& pd : pending)
       for (cudaEvent_t e : pd.ev) cudaEventDestroy(e);
     pending.clear();
@@ -681,9 +686,7 @@ int fkd_push_frames(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t f
     if ((long long)cap > s->host_out_cap) {
       if (s->host_out) {
         CK(cudaStreamSynchronize(s->st));
-        cudaFree(s->host_out);
-        s->allocs.erase(std::find(s->allocs.begin(), s->allocs.end(), (void*)s->host_out));
-        s->host_out = nullptr;
+        s->free_one(s->host_out);
         s->host_out_cap = 0;
       }
       fkd_keypoint* nb = nullptr;
