@@ -54,6 +54,10 @@ struct fkd_stream {
   fkd_params p{};
   Geometry g{};
   cudaStream_t st = nullptr;
+  cudaStream_t copy_st = nullptr;  // host-frame uploads, overlapped with the previous part's kernels
+  static constexpr int kParts = 2;
+  cudaEvent_t part_done[kParts] = {};  // upload of part i finished
+  cudaEvent_t staging_free = nullptr;  // earlier work on the stream no longer needs the staging buffer
   std::vector<std::pair<void*, size_t>> allocs;  // device allocations and their sizes
   size_t bytes_held = 0;  // device bytes this stream allocated
 
@@ -163,6 +167,10 @@ struct fkd_stream {
     pending.clear();
     for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
     event_pool.clear();
+    for (cudaEvent_t& e : part_done)
+      if (e) cudaEventDestroy(e), e = nullptr;
+    if (staging_free) cudaEventDestroy(staging_free), staging_free = nullptr;
+    if (copy_st) cudaStreamDestroy(copy_st), copy_st = nullptr;
   }
 };
 
@@ -476,12 +484,21 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
 // T frames in device memory as one batch (frame by frame for keypoint
 // binning, whose mask needs the previous frame's keypoints); masks, if not
 // NULL, receive each frame's mask.
+// With `parts` > 1 the frames arrive in that many equal parts (the last one
+// shorter), part i ready once s->part_done[i] has fired; each part is then
+// its own batch (exactly the same results), so its kernels start while the
+// later parts are still uploading.
 int run_frames(fkd_stream* s, const uint8_t* dframes, int dpitch, long long dstride, int T, fkd_keypoint* drec,
-               long long cap, uint32_t* doff, uint8_t* masks, cudaMemcpyKind mask_kind) {
+               long long cap, uint32_t* doff, uint8_t* masks, cudaMemcpyKind mask_kind, int parts = 1) {
   const bool serial = s->p.mask_mode == FKD_MASK_KB;
-  int slot = 0;
+  const int per_part = (T + parts - 1) / parts;
+  int slot = 0, next_part = 0;
   for (int k0 = 0; k0 < T;) {
-    const int n = serial ? 1 : T;
+    if (parts > 1 && k0 == next_part * per_part) {
+      CK(cudaStreamWaitEvent(s->st, s->part_done[next_part], 0));
+      ++next_part;
+    }
+    const int n = serial ? 1 : (parts > 1 ? std::min(per_part, T - k0) : T);
     int rc = run_batch(s, dframes + (long long)k0 * dstride, dpitch, dstride, n, drec, cap, doff + k0, slot, k0 == 0);
     if (rc) return rc;
     if (masks)
@@ -652,6 +669,7 @@ int fkd_push_frames(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t f
   if (cap > 0xffffffffull) return fail(FKD_E_ARG, "cap must fit in 32 bits");
 
   // 1. frames to device memory
+  int parts = 1;
   const uint8_t* dframes = frames;
   int dpitch = (int)pitch;
   long long dstride = (long long)frame_stride;
@@ -662,9 +680,32 @@ int fkd_push_frames(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t f
       if (rc) return rc;
     }
     const bool back_to_back = T == 1 || frame_stride == pitch * (size_t)g.H;
-    if (back_to_back) {
-      // the frames' rows follow one another: one copy of T * H rows (one
-      // large copy runs far faster than one per frame)
+    if (back_to_back && T >= 32 && !s->copy_st) {
+      // first large host batch: a stream for the uploads, so that they
+      // overlap the kernels of the frames before them
+      cudaError_t e = cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking);
+      for (int i = 0; i < fkd_stream::kParts && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&s->part_done[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->staging_free, cudaEventDisableTiming);
+      if (e != cudaSuccess) return fail(FKD_E_CUDA, "upload stream setup failed: %s", cudaGetErrorString(e));
+    }
+    if (back_to_back && T >= 32) {
+      // upload in parts on the copy stream, each part's kernels starting as
+      // soon as it has arrived (after earlier work is done with the buffer)
+      parts = fkd_stream::kParts;
+      const int per_part = (T + parts - 1) / parts;
+      CK(cudaEventRecord(s->staging_free, s->st));
+      CK(cudaStreamWaitEvent(s->copy_st, s->staging_free, 0));
+      for (int i = 0; i < parts; ++i) {
+        const int k0 = i * per_part, k1 = std::min(T, k0 + per_part);
+        if (k1 > k0)
+          CK(cudaMemcpy2DAsync(buf + (long long)k0 * s->staging_pitch * g.H, s->staging_pitch,
+                               frames + (size_t)k0 * frame_stride, pitch, g.W, (size_t)(k1 - k0) * g.H,
+                               cudaMemcpyHostToDevice, s->copy_st));
+        CK(cudaEventRecord(s->part_done[i], s->copy_st));
+      }
+    } else if (back_to_back) {
+      // the frames' rows follow one another: one copy of T * H rows
       CK(cudaMemcpy2DAsync(buf, s->staging_pitch, frames, pitch, g.W, (size_t)T * g.H, cudaMemcpyHostToDevice,
                            s->st));
     } else {
@@ -711,7 +752,7 @@ int fkd_push_frames(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t f
 
   // 3. the batch (frame by frame for keypoint binning)
   int rc = run_frames(s, dframes, dpitch, dstride, T, drec, (long long)cap, doff, masks,
-                      out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+                      out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, parts);
   if (rc) return rc;
 
   if (out_on_device) return FKD_OK;
