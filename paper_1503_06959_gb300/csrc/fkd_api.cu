@@ -1051,6 +1051,8 @@ struct GroupStream {
   uint8_t* last[2] = {nullptr, nullptr};
   fkd_keypoint* rec1 = nullptr;  // results of odd frames (even frames use the stream's own)
   uint32_t* off1 = nullptr;
+  uint32_t* desc1 = nullptr;      // descriptors of odd frames (even frames: the stream's own)
+  uint32_t* rows1 = nullptr;      // row starts of odd frames
   size_t bytes = 0;
 };
 
@@ -1073,6 +1075,7 @@ struct fkd_group {
   fkd_launch_config lc{};            // detection launch shape of every stream
   DetLaunch dl{};
   bool any_nms_scale = false;        // some stream asked for scale-space suppression
+  bool any_describe = false;         // some stream describes its keypoints
   bool use_graph = true;
   bool graph_valid = false;
   int graph_items = 0;               // items copied per tick by the captured graphs
@@ -1113,7 +1116,8 @@ static_assert(sizeof(TickHeader) <= kItemsOffset, "tick header fits before the i
 static_assert(alignof(TickItem) <= 64 && sizeof(TickItem) % alignof(TickItem) == 0, "aligned items");
 constexpr size_t kTickBytes = kItemsOffset + kMaxTickItems * sizeof(TickItem);
 
-StreamDev make_dev(const fkd_stream* s, uint8_t* const last[2], fkd_keypoint* rec1, uint32_t* off1) {
+StreamDev make_dev(const fkd_stream* s, const GroupStream& gs) {
+  uint8_t* const* last = gs.last;
   StreamDev d{};
   d.g = s->g;
   d.tb = Tables{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask, s->rowchunk};
@@ -1128,9 +1132,16 @@ StreamDev make_dev(const fkd_stream* s, uint8_t* const last[2], fkd_keypoint* re
   }
   d.rec[0] = s->rec;
   d.rec_offsets[0] = s->rec_offsets;
-  d.rec[1] = rec1;
-  d.rec_offsets[1] = off1;
+  d.rec[1] = gs.rec1;
+  d.rec_offsets[1] = gs.off1;
   d.K_max = s->p.K_max;
+  d.D = s->desc_D;
+  d.pattern = s->desc_pattern;
+  d.desc[0] = s->desc;
+  d.desc[1] = gs.desc1;
+  d.row_base[0] = s->desc_rows;
+  d.row_base[1] = gs.rows1;
+  d.rows = s->rows;
   return d;
 }
 
@@ -1160,7 +1171,9 @@ int group_launch(fkd_group* G, int b, int n_items, fkd_stream::Pending* pd) {
   mark(5);
   launch_group_emit(G->d_devs, G->d_hdr, G->d_items, G->grid_asm, G->st);
   mark(6);
-  mark(7);  // no description stage in groups
+  // streams that do not describe skip their items inside
+  if (G->any_describe) launch_group_describe(G->d_devs, G->d_hdr, G->d_items, G->st);
+  mark(7);
   CK(cudaGetLastError());
   return FKD_OK;
 }
@@ -1301,7 +1314,7 @@ int fkd_group_add_stream(fkd_group* G, const fkd_params* p, int W, int H, int* s
     G->devs_cap = cap;
     G->drop_graphs();
   }
-  const StreamDev d = make_dev(s, gs.last, gs.rec1, gs.off1);
+  const StreamDev d = make_dev(s, gs);
   CK(cudaMemcpy(G->d_devs + id, &d, sizeof d, cudaMemcpyHostToDevice));
   // the tick's active-tile list holds at most the tiles of all live streams
   long long need = 0;
@@ -1465,6 +1478,54 @@ int fkd_group_device_keypoints(fkd_group* G, int id, const fkd_keypoint** record
   return FKD_OK;
 }
 
+int fkd_group_set_descriptor(fkd_group* G, int id, const int8_t* pattern, int D) {
+  fkd_stream* s = group_member(G, id);
+  if (!s) return fail(FKD_E_ARG, "unknown stream id %d", id);
+  if (s->frame != 0) return fail(FKD_E_STATE, "set the descriptor of stream %d before its first tick", id);
+  CK(cudaStreamSynchronize(G->st));
+  GroupStream& gs = G->streams[id];
+  s->free_one(gs.desc1);
+  s->free_one(gs.rows1);
+  int rc = fkd_set_descriptor(s, pattern, D);  // validates, allocates the even frames' buffers
+  if (rc) return rc;
+  if (D) {
+    if ((rc = s->alloc(&gs.desc1, (size_t)s->p.K_max * (size_t)(D / 32))) ||
+        (rc = s->alloc(&gs.rows1, (size_t)s->rows + 1)))
+      return rc;
+    if (!G->any_describe) {
+      G->any_describe = true;
+      G->drop_graphs();  // the captured ticks lack the description pass
+    }
+  }
+  gs.bytes = s->bytes_held;
+  const StreamDev d = make_dev(s, gs);
+  CK(cudaMemcpy(G->d_devs + id, &d, sizeof d, cudaMemcpyHostToDevice));
+  return FKD_OK;
+}
+
+int fkd_group_get_descriptors(fkd_group* G, int id, uint8_t* out, size_t cap, size_t* n_out, int out_on_device) {
+  if (!n_out || (!out && cap > 0)) return fail(FKD_E_ARG, "NULL argument");
+  fkd_stream* s;
+  const fkd_keypoint* rec;
+  const uint32_t* off;
+  int rc = group_last_result(G, id, &s, &rec, &off);
+  if (rc) return rc;
+  if (!s->desc_D) return fail(FKD_E_STATE, "stream %d does not describe (fkd_group_set_descriptor)", id);
+  uint32_t o[2];
+  CK(cudaMemcpyAsync(o, off, 8, cudaMemcpyDeviceToHost, G->st));
+  CK(cudaStreamSynchronize(G->st));
+  const size_t n = std::min<size_t>(o[1] - o[0], (size_t)s->p.K_max);
+  *n_out = n;
+  const size_t words = (size_t)s->desc_D / 32;
+  const bool odd = ((s->frame - 1) & 1) != 0;
+  const uint32_t* src = (odd ? G->streams[id].desc1 : s->desc) + (size_t)o[0] * words;
+  const size_t ncopy = std::min(n, cap);
+  if (ncopy)
+    CK(cudaMemcpy(out, src, ncopy * words * 4, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  if (n > cap && out) return fail(FKD_E_CAPACITY, "%zu descriptors > cap %zu", n, cap);
+  return FKD_OK;
+}
+
 int fkd_group_profile_enable(fkd_group* G, int on) {
   if (!G) return fail(FKD_E_ARG, "group is NULL");
   G->profiling = on != 0;
@@ -1479,7 +1540,7 @@ int fkd_group_profile_read(fkd_group* G, fkd_profile* out, int reset) {
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, pd.ev[i], pd.ev[i + 1]));
       G->prof.ms[i] += ms;
-      if (i != FKD_STAGE_DESCRIBE) G->prof.launches[i] += 1;  // groups do not describe
+      if (i != FKD_STAGE_DESCRIBE || G->any_describe) G->prof.launches[i] += 1;
     }
     G->prof.batches += 1;
     G->prof.frames += (uint64_t)pd.frames;
@@ -1521,7 +1582,7 @@ int fkd_group_set_launch_config(fkd_group* G, const fkd_launch_config* c) {
     GroupStream& gs = G->streams[id];
     if (!gs.s) continue;
     apply_launch(gs.s, *c, dl);
-    const StreamDev d = make_dev(gs.s, gs.last, gs.rec1, gs.off1);
+    const StreamDev d = make_dev(gs.s, gs);
     CK(cudaMemcpy(G->d_devs + id, &d, sizeof d, cudaMemcpyHostToDevice));
   }
   G->drop_graphs();

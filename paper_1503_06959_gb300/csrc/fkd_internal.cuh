@@ -220,6 +220,13 @@ struct StreamDev {
   fkd_keypoint* rec[2];      // D_n of frame n in rec[n & 1] (K_max records each)
   uint32_t* rec_offsets[2];  // [2] each: 0 and |D_n|
   long long K_max;
+  // masked description (D == 0: off): descriptors of rec[n & 1] in
+  // desc[n & 1], and the first record of every layer row in row_base[n & 1]
+  int D;
+  const int8_t* pattern;
+  uint32_t* desc[2];
+  uint32_t* row_base[2];
+  int rows;
 };
 
 // One participating stream of a tick.
@@ -311,9 +318,11 @@ void launch_scale_nms(const Geometry& g, const Tables& tb, const Batch& b, const
 void launch_group_scale_nms(const StreamDev* devs, const TickItem* items, const uint32_t* work,
                             const uint32_t* work_count, cudaStream_t st);
 
-// Descriptors of a batch's records (after the emission kernel).
+// Descriptors of a batch's records (after the emission kernel), and of a
+// group tick's records for the streams that describe.
 void launch_describe(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s, const Output& out,
                      const Describe& d, cudaStream_t st);
+void launch_group_describe(const StreamDev* devs, const TickHeader* hdr, const TickItem* items, cudaStream_t st);
 
 // Record a message for fkd_last_error (printf format) and return `code`.
 int set_error(int code, const char* fmt, ...);

@@ -408,6 +408,10 @@ __global__ void __launch_bounds__(kAsmThreads) k_group_emit(const StreamDev* dev
     const StreamDev& d = devs[it.sid];
     const int par = (int)(it.frame_index & 1);
     Output o{d.rec[par], d.K_max, d.rec_offsets[par], 0};
+    if (d.D) {  // row starts for the descriptor pass
+      o.row_base = d.row_base[par];
+      o.rows = d.rows;
+    }
     emit_chunk(d.g, d.tb, d.s, state_of(d, it.state_cur), o, 0, 1, j - it.chunk_base);
   }
 }

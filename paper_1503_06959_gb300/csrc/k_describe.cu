@@ -73,6 +73,57 @@ __device__ __forceinline__ const uint8_t* layer_base(const Geometry& g, const Ba
   return s.pyr + (long long)k * g.pyr_bytes + g.layer[l].pyr_off;
 }
 
+// Descriptor of the keypoint at (x, y) of a w x h layer (pixels at img,
+// row pitch `pitch`) by one warp: pat holds the D / 32 words' pairs as
+// 16-bit box indices, bw the warp's box array. Returns word j in lane j.
+__device__ __forceinline__ uint32_t describe_record(const uint8_t* img, int pitch, int w, int h, int x, int y,
+                                                   const uint32_t* pat, uint32_t* bw, int DW, int lane) {
+  const uint16_t* box16 = reinterpret_cast<const uint16_t*>(bw);
+  // 1. lane c: column x - 15 + c of rows y - 15 .. y + 16, clamped
+  const uint8_t* col = img + min(max(x - kDescR - 2 + lane, 0), w - 1);
+  uint32_t px[32];
+  if (y >= kDescR + 2 && y + kDescR + 4 <= h) {
+    const uint8_t* p = col + (long long)(y - kDescR - 2) * pitch;
+#pragma unroll
+    for (int rr = 0; rr < 32; ++rr) px[rr] = p[(long long)rr * pitch];
+  } else {
+#pragma unroll
+    for (int rr = 0; rr < 32; ++rr)
+      px[rr] = col[(long long)min(max(y - kDescR - 2 + rr, 0), h - 1) * pitch];
+  }
+  // 2. 5-row sums of the column: P[m] = (sum of rows m..m+4, sum of rows
+  //    m+14..m+18) as 16-bit halves, sliding down
+  uint32_t P[kHalfRows];
+  {
+    uint32_t q[kHalfRows + 4];
+#pragma unroll
+    for (int m = 0; m < kHalfRows + 4; ++m) q[m] = px[m] | (px[m + kHalfRows] << 16);
+    P[0] = q[0] + q[1] + q[2] + q[3] + q[4];
+#pragma unroll
+    for (int m = 1; m < kHalfRows; ++m) P[m] = P[m - 1] + q[m + 4] - q[m - 1];
+  }
+  // 3. 5-column sums across lanes (lane c: columns c..c+4, valid for
+  //    c < 27), stored for the pair tests
+  __syncwarp();  // the previous record's tests are done with the array
+#pragma unroll
+  for (int m = 0; m < kHalfRows; ++m) {
+    const uint32_t a2 = P[m] + __shfl_down_sync(0xffffffffu, P[m], 1);
+    const uint32_t a4 = a2 + __shfl_down_sync(0xffffffffu, a2, 2);
+    const uint32_t box = a4 + __shfl_down_sync(0xffffffffu, P[m], 4);
+    if (lane < kDescBox) bw[m * kBoxPitch + lane] = box;
+  }
+  __syncwarp();
+
+  // 4. 32 pairs per ballot; lane j keeps word j
+  uint32_t mine = 0u;
+  for (int j = 0; j < DW; ++j) {
+    const uint32_t q = pat[j * 32 + lane];
+    const uint32_t word = __ballot_sync(0xffffffffu, box16[q & 0xffffu] < box16[q >> 16]);
+    if (lane == j) mine = word;
+  }
+  return mine;
+}
+
 __global__ void __launch_bounds__(kNewWarps * 32, kNewMinBlocks)
     k_describe_new(Geometry g, Batch b, Scratch s, Output out, Describe d) {
   __shared__ uint32_t pat[kDescMaxBits];                  // pair i: 16-bit indices of its two box sums
@@ -101,7 +152,6 @@ __global__ void __launch_bounds__(kNewWarps * 32, kNewMinBlocks)
   const long long groups = end > first ? (end - first + 31) / 32 : 0;
   const uint2* recs = reinterpret_cast<const uint2*>(out.rec);
   uint32_t* bw = boxes[warp];
-  const uint16_t* box16 = reinterpret_cast<const uint16_t*>(bw);
   for (;;) {
     unsigned long long gi = 0;
     if (lane == 0) gi = atomicAdd(d.next_group, 1u);
@@ -130,48 +180,7 @@ __global__ void __launch_bounds__(kNewWarps * 32, kNewMinBlocks)
       int pitch;
       const uint8_t* img = layer_base(g, b, s, kk, l, &pitch);
 
-      // 1. lane c: column x - 15 + c of rows y - 15 .. y + 16, clamped
-      const uint8_t* col = img + min(max(x - kDescR - 2 + lane, 0), lg.w - 1);
-      uint32_t px[32];
-      if (y >= kDescR + 2 && y + kDescR + 4 <= lg.h) {
-        const uint8_t* p = col + (long long)(y - kDescR - 2) * pitch;
-#pragma unroll
-        for (int rr = 0; rr < 32; ++rr) px[rr] = p[(long long)rr * pitch];
-      } else {
-#pragma unroll
-        for (int rr = 0; rr < 32; ++rr)
-          px[rr] = col[(long long)min(max(y - kDescR - 2 + rr, 0), lg.h - 1) * pitch];
-      }
-      // 2. 5-row sums of the column: P[m] = (sum of rows m..m+4, sum of rows
-      //    m+14..m+18) as 16-bit halves, sliding down
-      uint32_t P[kHalfRows];
-      {
-        uint32_t q[kHalfRows + 4];
-#pragma unroll
-        for (int m = 0; m < kHalfRows + 4; ++m) q[m] = px[m] | (px[m + kHalfRows] << 16);
-        P[0] = q[0] + q[1] + q[2] + q[3] + q[4];
-#pragma unroll
-        for (int m = 1; m < kHalfRows; ++m) P[m] = P[m - 1] + q[m + 4] - q[m - 1];
-      }
-      // 3. 5-column sums across lanes (lane c: columns c..c+4, valid for
-      //    c < 27), stored for the pair tests
-      __syncwarp();  // the previous record's tests are done with the array
-#pragma unroll
-      for (int m = 0; m < kHalfRows; ++m) {
-        const uint32_t a2 = P[m] + __shfl_down_sync(0xffffffffu, P[m], 1);
-        const uint32_t a4 = a2 + __shfl_down_sync(0xffffffffu, a2, 2);
-        const uint32_t box = a4 + __shfl_down_sync(0xffffffffu, P[m], 4);
-        if (lane < kDescBox) bw[m * kBoxPitch + lane] = box;
-      }
-      __syncwarp();
-
-      // 4. 32 pairs per ballot; lane j keeps word j
-      uint32_t mine = 0u;
-      for (int j = 0; j < DW; ++j) {
-        const uint32_t q = pat[j * 32 + lane];
-        const uint32_t word = __ballot_sync(0xffffffffu, box16[q & 0xffffu] < box16[q >> 16]);
-        if (lane == j) mine = word;
-      }
+      const uint32_t mine = describe_record(img, pitch, lg.w, lg.h, x, y, pat, bw, DW, lane);
       if (lane < DW) d.desc[ridx * DW + lane] = mine;
       if (ridx >= last_first && ridx - last_first < d.keep_cap) {
         const long long kidx = ridx - last_first;
@@ -260,6 +269,124 @@ __global__ void __launch_bounds__(kCarriedThreads) k_describe_carried(Geometry g
   }
 }
 
+// Group tick: one frame of each participating stream; a stream describes if
+// its StreamDev has D > 0. The previous frame's records (rec[(n-1) & 1]) are
+// the kept set, and its row starts index them. The tick's records, taken
+// stream by stream, are numbered in a running sum that each warp (thread)
+// keeps as it walks the items, so work is spread over all warps (threads)
+// whatever the mix of streams.
+__device__ __forceinline__ const uint8_t* group_layer(const StreamDev& d, const TickItem& ti, int l, int* pitch) {
+  if (l == 0) {
+    *pitch = ti.pitch;
+    return ti.frame;
+  }
+  *pitch = d.g.layer[l].pitch;
+  return d.s.pyr + d.g.layer[l].pyr_off;
+}
+
+constexpr int kGroupNewBlocks = 2;  // CTAs per SM of the group pass (its grid)
+
+__global__ void __launch_bounds__(kNewWarps * 32, kGroupNewBlocks)
+    k_group_describe_new(const StreamDev* devs, const TickHeader* hdr, const TickItem* items) {
+  __shared__ uint32_t pat[kNewWarps][kDescMaxBits];       // the current stream's pairs, per warp
+  __shared__ uint32_t boxes[kNewWarps][kHalfRows * kBoxPitch];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long gw = (long long)blockIdx.x * kNewWarps + warp, nw = (long long)gridDim.x * kNewWarps;
+  uint32_t* bw = boxes[warp];
+  uint32_t* pw = pat[warp];
+  const int n_items = hdr->n_items;
+  long long acc = 0;  // 32-record groups of the items before this one
+  int loaded = -1;    // stream whose pairs are in pw
+  for (int i = 0; i < n_items; ++i) {
+    const TickItem ti = items[i];
+    const StreamDev& d = devs[ti.sid];
+    if (!d.D) continue;
+    const int par = (int)(ti.frame_index & 1);
+    const long long first = d.rec_offsets[par][0];
+    const long long end = min((long long)d.rec_offsets[par][1], d.K_max);
+    const long long groups = end > first ? (end - first + 31) / 32 : 0;
+    // this warp takes the groups whose tick-wide number is gw modulo nw
+    long long g0 = (gw - acc) % nw;
+    if (g0 < 0) g0 += nw;
+    acc += groups;
+    if (g0 >= groups) continue;
+    const int DW = d.D >> 5;
+    if (loaded != ti.sid) {
+      __syncwarp();  // the previous stream's tests are done with pw
+      for (int q = lane; q < d.D; q += 32) {
+        const char4 c = reinterpret_cast<const char4*>(d.pattern)[q];
+        pw[q] = (uint32_t)box_half(c.y + kDescR, c.x + kDescR) | (uint32_t)box_half(c.w + kDescR, c.z + kDescR) << 16;
+      }
+      __syncwarp();
+      loaded = ti.sid;
+    }
+    const uint2* recs = reinterpret_cast<const uint2*>(d.rec[par]);
+    for (long long gi = g0; gi < groups; gi += nw) {
+      const long long base = first + gi * 32, idx = base + lane;
+      uint2 r = make_uint2(0u, 0u);
+      bool is_new = false;
+      if (idx < end) {
+        r = recs[idx];
+        is_new = ((r.y >> 16) & FKD_KP_PROPAGATED) == 0u;
+      }
+      uint32_t todo = __ballot_sync(0xffffffffu, is_new);
+      while (todo) {
+        const int src_lane = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint32_t rx = __shfl_sync(0xffffffffu, r.x, src_lane);
+        const uint32_t ry = __shfl_sync(0xffffffffu, r.y, src_lane);
+        const int x = (int)(rx & 0xffffu), y = (int)(rx >> 16), l = (int)(ry & 0xffu);
+        const LayerGeom& lg = d.g.layer[l];
+        int pitch;
+        const uint8_t* img = group_layer(d, ti, l, &pitch);
+        const uint32_t mine = describe_record(img, pitch, lg.w, lg.h, x, y, pw, bw, DW, lane);
+        if (lane < DW) d.desc[par][(base + src_lane) * DW + lane] = mine;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kCarriedThreads)
+    k_group_describe_carried(const StreamDev* devs, const TickHeader* hdr, const TickItem* items) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+  const int n_items = hdr->n_items;
+  long long acc = 0;  // records of the items before this one
+  for (int i = 0; i < n_items; ++i) {
+    const TickItem ti = items[i];
+    const StreamDev& d = devs[ti.sid];
+    if (!d.D) continue;
+    const int par = (int)(ti.frame_index & 1), pp = par ^ 1;
+    const long long first = d.rec_offsets[par][0];
+    const long long end = min((long long)d.rec_offsets[par][1], d.K_max);
+    const long long n = max(0LL, end - first);
+    long long j0 = (tid - acc) % nt;
+    if (j0 < 0) j0 += nt;
+    acc += n;
+    if (j0 >= n || ti.frame_index == 0) continue;
+    const int DW = d.D >> 5;
+    const uint2* recs = reinterpret_cast<const uint2*>(d.rec[par]);
+    const uint2* prev = reinterpret_cast<const uint2*>(d.rec[pp]);
+    const long long prev_end = min((long long)d.rec_offsets[pp][1], d.K_max);
+    for (long long j = j0; j < n; j += nt) {
+      const long long idx = first + j;
+      const uint2 r = recs[idx];
+      if (((r.y >> 16) & FKD_KP_PROPAGATED) == 0u) continue;
+      const int y = (int)(r.x >> 16), l = (int)(r.y & 0xffu);
+      const int gr = d.g.layer[l].row_off + y;
+      const long long lo = d.row_base[pp][gr];
+      const long long hi = gr + 1 < d.rows ? (long long)d.row_base[pp][gr + 1] : prev_end;
+      const long long o = find_record(prev, lo, min(hi, prev_end), rec_key(r));
+      if (o < 0) {
+        *d.s.overflow = 1;  // only after an overflow dropped the origin record
+        continue;
+      }
+      const uint32_t* from = d.desc[pp] + o * DW;
+      uint32_t* to = d.desc[par] + idx * DW;
+      for (int q = 0; q < DW; ++q) to[q] = from[q];
+    }
+  }
+}
+
 }  // namespace
 
 void launch_describe(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s, const Output& out,
@@ -267,6 +394,12 @@ void launch_describe(const Geometry& g, const Tables& tb, const Batch& b, const 
   const int sms = sm_count();
   k_describe_new<<<sms * kNewMinBlocks, kNewWarps * 32, 0, st>>>(g, b, s, out, d);
   k_describe_carried<<<sms * 8, kCarriedThreads, 0, st>>>(g, tb, b, s, out, d);
+}
+
+void launch_group_describe(const StreamDev* devs, const TickHeader* hdr, const TickItem* items, cudaStream_t st) {
+  const int sms = sm_count();
+  k_group_describe_new<<<sms * kGroupNewBlocks, kNewWarps * 32, 0, st>>>(devs, hdr, items);
+  k_group_describe_carried<<<sms * 4, kCarriedThreads, 0, st>>>(devs, hdr, items);
 }
 
 }  // namespace fkd

@@ -35,7 +35,8 @@ EXPORTS = [
     "fkd_server_close_stream", "fkd_server_submit", "fkd_server_poll", "fkd_server_drain",
     "fkd_server_get_stats", "fkd_get_launch_config", "fkd_set_launch_config", "fkd_autotune",
     "fkd_group_get_launch_config", "fkd_group_set_launch_config", "fkd_group_autotune",
-    "fkd_get_pixel_mask", "fkd_set_descriptor", "fkd_get_descriptors",
+    "fkd_get_pixel_mask", "fkd_set_descriptor", "fkd_get_descriptors", "fkd_group_set_descriptor",
+    "fkd_group_get_descriptors",
 ]
 STAGES = ["pyramid", "mask", "worklist", "detect", "count", "emit", "describe"]
 
@@ -136,6 +137,8 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.fkd_get_pixel_mask.argtypes = [vp, c_int, vp]
     lib.fkd_set_descriptor.argtypes = [vp, vp, c_int]
     lib.fkd_get_descriptors.argtypes = [vp, vp, c_size, P(c_size), c_int]
+    lib.fkd_group_set_descriptor.argtypes = [vp, c_int, vp, c_int]
+    lib.fkd_group_get_descriptors.argtypes = [vp, c_int, vp, c_size, P(c_size), c_int]
     lib.fkd_get_launch_config.argtypes = [vp, P(fkd_launch_config)]
     lib.fkd_set_launch_config.argtypes = [vp, P(fkd_launch_config)]
     lib.fkd_autotune.argtypes = [vp, vp, c_size, c_size, c_int, c_int, P(fkd_launch_config),
@@ -371,6 +374,7 @@ class Group:
         self._h = h
         self.O, self.intra = O, intra
         self.streams = {}
+        self._desc_bits = {}
 
     def add_stream(self, W: int, H: int, *, N_r: int = 8, N_c: int = 8, T_I: int = 4,
                    T_H: int = 1, t: int = 20, mask_mode: int = FKD_MASK_ID, mask_layer: int = 0,
@@ -433,6 +437,27 @@ class Group:
         n = ctypes.c_size_t()
         _check(_lib.fkd_group_get_keypoints(self._h, sid, _ptr(out), cap, ctypes.byref(n)))
         return out[:n.value].copy()
+
+    def set_descriptor(self, sid: int, pattern):
+        """Masked description for stream `sid` (before its first tick): a D x 4
+        int8 pattern of pairs (ax, ay, bx, by); None turns it off."""
+        if pattern is None:
+            _check(_lib.fkd_group_set_descriptor(self._h, sid, None, 0))
+            self._desc_bits.pop(sid, None)
+            return
+        pat = np.ascontiguousarray(pattern, dtype=np.int8)
+        assert pat.ndim == 2 and pat.shape[1] == 4
+        _check(_lib.fkd_group_set_descriptor(self._h, sid, _ptr(pat), pat.shape[0]))
+        self._desc_bits[sid] = pat.shape[0]
+
+    def get_descriptors(self, sid: int) -> np.ndarray:
+        """Descriptors of the stream's last frame (n x D/8 uint8, record order)."""
+        n = ctypes.c_size_t()
+        _check(_lib.fkd_group_get_descriptors(self._h, sid, None, 0, ctypes.byref(n), 0))
+        res = np.zeros((n.value, self._desc_bits.get(sid, 0) // 8), np.uint8)
+        if n.value:
+            _check(_lib.fkd_group_get_descriptors(self._h, sid, _ptr(res), n.value, ctypes.byref(n), 0))
+        return res
 
     def get_mask(self, sid: int) -> np.ndarray:
         W, H, N_r, N_c, _ = self.streams[sid]

@@ -174,3 +174,53 @@ def test_capacity_overflow_then_reset():
         for k in range(4):
             check(rec[off2[k]:off2[k + 1]], desc[off2[k]:off2[k + 1]], exp_kp[n0 + k], exp_d[n0 + k],
                   f"after reset, frame {n0 + k}")
+
+
+def test_group_description_matches_oracle():
+    """Streams of a group describe in their ticks (with and without the
+    captured graphs), each bit-exact with the oracle; a stream that does not
+    describe is unaffected."""
+    torch = pytest.importorskip("torch")
+    O, intra, m = 2, 1, 7
+    specs = [(320, 240, dict(N_r=8, N_c=8, T_I=4, t=20), "id", 256),
+             (333, 207, dict(N_r=7, N_c=9, T_I=4, t=15, mask_layer=-1), "id", 128),
+             (200, 150, dict(N_r=3, N_c=5, T_H=2, t=12), "kb", 64),
+             (256, 192, dict(N_r=4, N_c=4, T_I=4, t=18), "id", 0)]
+    clips, exp_kp, exp_d = [], [], []
+    for i, (w, h, p, mode, D) in enumerate(specs):
+        clips.append(synth.VideoSource(w, h, seed=60 + i, n_movers=2, mover_size=min(w, h) // 4,
+                                       speed=(2, 4)).frames(m))
+        pat = synth.descriptor_pattern(D, seed=D) if D else None
+        ref = oracle.Stream(w, h, O=O, intra=intra, mask_mode=MODES[mode][1], pattern=pat, **p)
+        ek, ed = [], []
+        for f in clips[-1]:
+            ref.push(f)
+            ek.append(ref.keypoints())
+            ed.append(ref.descriptors() if D else None)
+        exp_kp.append(ek)
+        exp_d.append(ed)
+    dev = [[torch.from_numpy(np.ascontiguousarray(c[j])).cuda() for c in clips] for j in range(m)]
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()  # graphs need a stream of their own
+    for graph in (True, False):
+        g = fkd.Group(O, intra, cuda_stream=stream.cuda_stream)
+        g.use_graph(graph)
+        ids = []
+        for (w, h, p, mode, D) in specs:
+            sid = g.add_stream(w, h, mask_mode=MODES[mode][0], **p)[0]
+            if D:
+                g.set_descriptor(sid, synth.descriptor_pattern(D, seed=D))
+            ids.append(sid)
+        for j in range(m):
+            g.tick(ids, dev[j])
+            for i, sid in enumerate(ids):
+                kp = g.get_keypoints(sid)
+                if specs[i][4]:
+                    check(kp, g.get_descriptors(sid), exp_kp[i][j], exp_d[i][j], f"graph {graph} stream {i} frame {j}")
+                else:
+                    assert len(kp) == len(exp_kp[i][j])
+                    with pytest.raises(fkd.FkdError):
+                        g.get_descriptors(sid)
+        with pytest.raises(fkd.FkdError):  # after the first tick
+            g.set_descriptor(ids[3], synth.descriptor_pattern(64))
+        g.close()
