@@ -71,16 +71,19 @@ def profile_counters(kernel: str, shape: dict | None = None):
     m = hashlib.sha256()
     for f in KERNEL_SOURCES[kernel]:
         m.update(open(os.path.join(ROOT, "paper_1503_06959_gb300", "csrc", f), "rb").read())
-    got = {k: re.search(k + r": (\S+)", text) for k in
-           ("source_sha256", "traffic_bytes_per_launch", "alu_warp_inst_per_launch", "launch_shape")}
-    if not got["source_sha256"] or got["source_sha256"].group(1) != m.hexdigest()[:16]:
+    sha = re.search(r"source_sha256: (\S+)", text)
+    if not sha or sha.group(1) != m.hexdigest()[:16]:
         return None
     if kernel == "detect" and shape is not None:
+        # one line of counters per captured launch shape
         want = f"{shape['tile_h']},{shape['warps_per_cta']},{shape['ctas_per_sm']}"
-        if not got["launch_shape"] or got["launch_shape"].group(1) != want:
+        c = re.search(r"counters " + re.escape(want) +
+                      r": traffic_bytes_per_launch (\d+) alu_warp_inst_per_launch (\d+)", text)
+        if not c:
             return None
-    got.pop("launch_shape")
-    return {k: float(v.group(1)) for k, v in got.items() if v and k != "source_sha256"}
+        return {"traffic_bytes_per_launch": float(c.group(1)), "alu_warp_inst_per_launch": float(c.group(2))}
+    got = {k: re.search(k + r": (\S+)", text) for k in ("traffic_bytes_per_launch", "alu_warp_inst_per_launch")}
+    return {k: float(v.group(1)) for k, v in got.items() if v}
 
 
 # --- multi-GPU plumbing: one independent stream per rank, timings max-reduced
