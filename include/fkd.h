@@ -251,7 +251,8 @@ int fkd_reset_stream(fkd_stream* s);
  * keypoints detected in a frame are described, on that frame's layer; a
  * carried keypoint (FKD_KP_PROPAGATED) keeps the descriptor it had in the
  * previous frame. Resets the stream (waits for its pending work). Streams of
- * a group describe through fkd_group_set_descriptor; servers do not describe.
+ * a group or a server describe through fkd_group_set_descriptor and
+ * fkd_server_set_descriptor.
  * Errors: FKD_E_ARG (D or an offset out of range), FKD_E_CUDA.
  */
 #define FKD_DESC_RADIUS 13
@@ -499,6 +500,18 @@ int fkd_server_submit(fkd_server* s, int id, const uint8_t* frame, size_t pitch,
  * is dropped), FKD_E_ARG. */
 int fkd_server_poll(fkd_server* s, int id, int64_t* frame_index, fkd_keypoint* out, size_t cap,
                     size_t* n_out);
+
+/* Masked description for stream `id` (as fkd_set_descriptor), before its
+ * first frame; the descriptor buffers count against the budget. Errors:
+ * FKD_E_ARG, FKD_E_STATE (frames already submitted), FKD_E_BUDGET, FKD_E_CUDA. */
+int fkd_server_set_descriptor(fkd_server* s, int id, const int8_t* pattern, int D);
+
+/* Descriptors of the result the last fkd_server_poll of stream `id` returned
+ * (one per keypoint, in its order), D/8 bytes each, into host memory, at most
+ * `cap`; out = NULL with cap = 0 only reports the count. Errors: FKD_E_ARG,
+ * FKD_E_STATE (the stream does not describe, or nothing polled yet),
+ * FKD_E_CAPACITY. */
+int fkd_server_get_descriptors(fkd_server* s, int id, uint8_t* out, size_t cap, size_t* n_out);
 
 /* Wait until no frame is waiting or on the GPU. Errors: FKD_E_TIMEOUT. */
 int fkd_server_drain(fkd_server* s, int timeout_ms);

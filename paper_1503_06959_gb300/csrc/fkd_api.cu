@@ -1662,6 +1662,18 @@ int group_result_ref(fkd_group* G, int id, long long frame_index, ResultRef* ref
   return FKD_OK;
 }
 
+int group_desc_ref(fkd_group* G, int id, long long frame_index, const uint32_t** desc, int* D) {
+  fkd_stream* s = group_member(G, id);
+  if (!s) return fail(FKD_E_ARG, "unknown stream id %d", id);
+  *D = s->desc_D;
+  *desc = (frame_index & 1) ? G->streams[id].desc1 : s->desc;
+  return FKD_OK;
+}
+
+size_t group_stream_bytes(fkd_group* G, int id) {
+  return group_member(G, id) ? G->streams[id].bytes : 0;
+}
+
 long long group_stream_frames(fkd_group* G, int id) {
   fkd_stream* s = group_member(G, id);
   return s ? s->frame : -1;

@@ -24,6 +24,12 @@
 
 #include "fkd_internal.cuh"
 
+namespace fkd {
+// Group internals for the description of served streams (fkd_api.cu).
+int group_desc_ref(fkd_group* G, int id, long long frame_index, const uint32_t** desc, int* D);
+size_t group_stream_bytes(fkd_group* G, int id);
+}  // namespace fkd
+
 using namespace fkd;
 
 namespace {
@@ -40,6 +46,7 @@ struct Result {
   int64_t index;
   bool truncated;
   std::vector<fkd_keypoint> kp;
+  std::vector<uint8_t> desc;  // D/8 bytes per keypoint, if the stream describes
 };
 
 struct SStream {
@@ -53,6 +60,9 @@ struct SStream {
   int64_t taken = 0;           // frames handed to ticks so far
   uint8_t* dstage[2] = {nullptr, nullptr};  // device copies, by frame parity
   std::deque<Result> results;
+  int D = 0;                       // descriptor bits (0: the stream does not describe)
+  std::vector<uint8_t> last_desc;  // descriptors of the result the last poll returned
+  bool have_last = false;
 };
 
 struct TickRec {
@@ -176,6 +186,21 @@ void fkd_server::collect(const TickRec& t) {
     const long long keep = std::max(0LL, std::min(c, cap - o));
     r.truncated = keep < raw;
     r.kp.assign(h_out[b] + o, h_out[b] + o + keep);
+    if (s.D && !r.truncated && keep > 0) {
+      // the frame's descriptors stay in the group's buffers of its parity
+      // until the tick after next, which is launched after this collection
+      const uint32_t* desc = nullptr;
+      int D = 0;
+      cudaError_t ed = cudaErrorInvalidValue;
+      if (group_desc_ref(G, t.ids[i], t.index[i], &desc, &D) == FKD_OK && desc) {
+        r.desc.resize((size_t)keep * (size_t)(D / 8));
+        ed = cudaMemcpy(r.desc.data(), desc, r.desc.size(), cudaMemcpyDeviceToHost);
+      }
+      if (ed != cudaSuccess) {
+        error = FKD_E_CUDA;
+        err_msg = std::string("descriptor copy failed: ") + cudaGetErrorString(ed);
+      }
+    }
     s.results.push_back(std::move(r));
     s.head = (s.head + 1) % kRingSlots;
     s.count -= 1;
@@ -406,7 +431,51 @@ int fkd_server_poll(fkd_server* S, int id, int64_t* frame_index, fkd_keypoint* o
   }
   if (r.kp.size() > cap) return set_error(FKD_E_CAPACITY, "%zu keypoints > cap %zu", r.kp.size(), cap);
   if (!r.kp.empty()) std::memcpy(out, r.kp.data(), r.kp.size() * sizeof(fkd_keypoint));
+  if (s.D) {
+    s.last_desc = std::move(r.desc);
+    s.have_last = true;
+  }
   s.results.pop_front();
+  return FKD_OK;
+}
+
+int fkd_server_set_descriptor(fkd_server* S, int id, const int8_t* pattern, int D) {
+  if (!S) return set_error(FKD_E_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (S->error) return worker_error(S);
+  if (id < 0 || id >= (int)S->streams.size() || !S->streams[id].open)
+    return set_error(FKD_E_ARG, "unknown stream id %d", id);
+  SStream& s = S->streams[id];
+  if (s.taken > 0 || s.count > 0) return set_error(FKD_E_STATE, "set the descriptor of stream %d before its first frame", id);
+  int rc = fkd_group_set_descriptor(S->G, id, pattern, D);
+  if (rc) return rc;
+  const size_t bytes = group_stream_bytes(S->G, id) + 2 * (size_t)s.pitch * s.H;
+  if (S->used - s.bytes + bytes > S->budget) {
+    fkd_group_set_descriptor(S->G, id, nullptr, 0);
+    return set_error(FKD_E_BUDGET, "description needs %zu more bytes, %zu of %zu in use", bytes - s.bytes, S->used,
+                     S->budget);
+  }
+  S->used = S->used - s.bytes + bytes;
+  s.bytes = bytes;
+  s.D = D;
+  s.last_desc.clear();
+  s.have_last = false;
+  return FKD_OK;
+}
+
+int fkd_server_get_descriptors(fkd_server* S, int id, uint8_t* out, size_t cap, size_t* n_out) {
+  if (!S || !n_out || (!out && cap > 0)) return set_error(FKD_E_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (id < 0 || id >= (int)S->streams.size() || !S->streams[id].open)
+    return set_error(FKD_E_ARG, "unknown stream id %d", id);
+  SStream& s = S->streams[id];
+  if (!s.D) return set_error(FKD_E_STATE, "stream %d does not describe (fkd_server_set_descriptor)", id);
+  if (!s.have_last) return set_error(FKD_E_STATE, "no result of stream %d polled yet", id);
+  const size_t bytes = (size_t)s.D / 8, n = s.last_desc.size() / bytes;
+  *n_out = n;
+  const size_t ncopy = std::min(n, cap);
+  if (ncopy) std::memcpy(out, s.last_desc.data(), ncopy * bytes);
+  if (n > cap && out) return set_error(FKD_E_CAPACITY, "%zu descriptors > cap %zu", n, cap);
   return FKD_OK;
 }
 

@@ -36,7 +36,7 @@ EXPORTS = [
     "fkd_server_get_stats", "fkd_get_launch_config", "fkd_set_launch_config", "fkd_autotune",
     "fkd_group_get_launch_config", "fkd_group_set_launch_config", "fkd_group_autotune",
     "fkd_get_pixel_mask", "fkd_set_descriptor", "fkd_get_descriptors", "fkd_group_set_descriptor",
-    "fkd_group_get_descriptors",
+    "fkd_group_get_descriptors", "fkd_server_set_descriptor", "fkd_server_get_descriptors",
 ]
 STAGES = ["pyramid", "mask", "worklist", "detect", "count", "emit", "describe"]
 
@@ -139,6 +139,8 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.fkd_get_descriptors.argtypes = [vp, vp, c_size, P(c_size), c_int]
     lib.fkd_group_set_descriptor.argtypes = [vp, c_int, vp, c_int]
     lib.fkd_group_get_descriptors.argtypes = [vp, c_int, vp, c_size, P(c_size), c_int]
+    lib.fkd_server_set_descriptor.argtypes = [vp, c_int, vp, c_int]
+    lib.fkd_server_get_descriptors.argtypes = [vp, c_int, vp, c_size, P(c_size)]
     lib.fkd_get_launch_config.argtypes = [vp, P(fkd_launch_config)]
     lib.fkd_set_launch_config.argtypes = [vp, P(fkd_launch_config)]
     lib.fkd_autotune.argtypes = [vp, vp, c_size, c_size, c_int, c_int, P(fkd_launch_config),
@@ -499,6 +501,7 @@ class Server:
         self._h = h
         self.O, self.intra = O, intra
         self.streams = {}
+        self._desc_bits = {}
 
     def open_stream(self, W: int, H: int, *, N_r: int = 8, N_c: int = 8, T_I: int = 4,
                     T_H: int = 1, t: int = 20, mask_mode: int = FKD_MASK_ID, mask_layer: int = 0,
@@ -529,6 +532,27 @@ class Server:
             return None
         _check(rc)
         return idx.value, out[:n.value].copy()
+
+    def set_descriptor(self, sid: int, pattern):
+        """Masked description for stream `sid` (before its first frame): a
+        D x 4 int8 pattern of pairs (ax, ay, bx, by); None turns it off."""
+        if pattern is None:
+            _check(_lib.fkd_server_set_descriptor(self._h, sid, None, 0))
+            self._desc_bits.pop(sid, None)
+            return
+        pat = np.ascontiguousarray(pattern, dtype=np.int8)
+        assert pat.ndim == 2 and pat.shape[1] == 4
+        _check(_lib.fkd_server_set_descriptor(self._h, sid, _ptr(pat), pat.shape[0]))
+        self._desc_bits[sid] = pat.shape[0]
+
+    def get_descriptors(self, sid: int) -> np.ndarray:
+        """Descriptors of the result the last poll of `sid` returned (n x D/8)."""
+        n = ctypes.c_size_t()
+        _check(_lib.fkd_server_get_descriptors(self._h, sid, None, 0, ctypes.byref(n)))
+        res = np.zeros((n.value, self._desc_bits.get(sid, 0) // 8), np.uint8)
+        if n.value:
+            _check(_lib.fkd_server_get_descriptors(self._h, sid, _ptr(res), n.value, ctypes.byref(n)))
+        return res
 
     def drain(self, timeout_ms: int = 60000):
         _check(_lib.fkd_server_drain(self._h, timeout_ms))

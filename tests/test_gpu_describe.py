@@ -224,3 +224,49 @@ def test_group_description_matches_oracle():
         with pytest.raises(fkd.FkdError):  # after the first tick
             g.set_descriptor(ids[3], synth.descriptor_pattern(64))
         g.close()
+
+
+def test_server_description_matches_oracle():
+    """A served stream that describes hands out each polled frame's
+    descriptors, bit-exact with the oracle; a stream beside it that does not
+    describe is unaffected."""
+    O, intra, m = 2, 1, 8
+    specs = [(320, 240, dict(N_r=8, N_c=8, T_I=4, t=20), 256), (200, 150, dict(N_r=3, N_c=5, T_I=4, t=12), 0)]
+    clips, exp_kp, exp_d = [], [], []
+    for i, (w, h, p, D) in enumerate(specs):
+        clips.append(synth.VideoSource(w, h, seed=70 + i, n_movers=2, mover_size=min(w, h) // 4,
+                                       speed=(2, 4)).frames(m))
+        pat = synth.descriptor_pattern(D, seed=11) if D else None
+        ref = oracle.Stream(w, h, O=O, intra=intra, mask_mode=oracle.MASK_ID, pattern=pat, **p)
+        ek, ed = [], []
+        for f in clips[-1]:
+            ref.push(f)
+            ek.append(ref.keypoints())
+            ed.append(ref.descriptors() if D else None)
+        exp_kp.append(ek)
+        exp_d.append(ed)
+    srv = fkd.Server(O, intra, budget_bytes=2 << 30)
+    ids = [srv.open_stream(w, h, **p) for (w, h, p, D) in specs]
+    srv.set_descriptor(ids[0], synth.descriptor_pattern(256, seed=11))
+    got = {sid: [] for sid in ids}
+    for j in range(m):
+        for i, sid in enumerate(ids):
+            srv.submit(sid, clips[i][j])
+        srv.drain()
+        for i, sid in enumerate(ids):
+            while True:
+                r = srv.poll(sid)
+                if r is None:
+                    break
+                idx, kp = r
+                got[sid].append((idx, kp, srv.get_descriptors(sid) if specs[i][3] else None))
+    with pytest.raises(fkd.FkdError):  # frames were submitted already
+        srv.set_descriptor(ids[1], synth.descriptor_pattern(64))
+    for i, sid in enumerate(ids):
+        assert [g[0] for g in got[sid]] == list(range(m))
+        for idx, kp, d in got[sid]:
+            if specs[i][3]:
+                check(kp, d, exp_kp[i][idx], exp_d[i][idx], f"served stream {i} frame {idx}")
+            else:
+                assert len(kp) == len(exp_kp[i][idx])
+    srv.close()
