@@ -223,7 +223,8 @@ def run_reference(args):
     return 0
 
 
-def _group_run(streams, frames_dev, mode, warm, ticks_timed, fkd, torch, tune_ticks=3, mask_layer=None):
+def _group_run(streams, frames_dev, mode, warm, ticks_timed, fkd, torch, tune_ticks=3, mask_layer=None,
+               pattern=None):
     """Tick every stream once per tick through one group, after tuning the
     detection launch shape on the first `tune_ticks` ticks; returns (seconds
     for the timed ticks, profile, keypoints per tick, chosen shape)."""
@@ -232,6 +233,9 @@ def _group_run(streams, frames_dev, mode, warm, ticks_timed, fkd, torch, tune_ti
     ids = [g.add_stream(c.W, c.H, N_r=c.N_r, N_c=c.N_c, T_I=c.T_I, t=c.t, mask_mode=mode,
                         mask_layer=c.mask_layer if mask_layer is None else mask_layer,
                         K_max=1 << 17)[0] for c in streams]
+    if pattern is not None:  # every stream describes its keypoints
+        for i in ids:
+            g.set_descriptor(i, pattern)
     n_frames = frames_dev[0].shape[0]
     shape, tune_ms = g.autotune(ids, [[f[n] for f in frames_dev] for n in range(tune_ticks)], reps=2)
     shape["tuned_ms_for_ticks"] = [tune_ticks, tune_ms]
@@ -272,10 +276,13 @@ def run_config3(args):
         frames_dev.append(torch.from_numpy(clip).cuda())
     warm = 3
     res = {}
-    for name, mode, ml in (("masked", fkd.FKD_MASK_ID, None), ("masked_c0", fkd.FKD_MASK_ID, 0),
-                           ("full", fkd.FKD_MASK_FULL, None)):
+    pattern = synth.descriptor_pattern(256)
+    for name, mode, ml, pat in (("masked", fkd.FKD_MASK_ID, None, None), ("masked_c0", fkd.FKD_MASK_ID, 0, None),
+                                ("full", fkd.FKD_MASK_FULL, None, None),
+                                ("masked_describe", fkd.FKD_MASK_ID, None, pattern),
+                                ("full_describe", fkd.FKD_MASK_FULL, None, pattern)):
         sec, prof, kps, shape = _group_run(streams, frames_dev, mode, warm, F - warm, fkd, torch,
-                                           mask_layer=ml)
+                                           mask_layer=ml, pattern=pat)
         ticks = F - warm
         res[name] = {"frames_per_s": len(streams) * ticks / sec, "ms_per_tick": sec / ticks * 1e3,
                      "launch_shape": shape,
@@ -293,7 +300,12 @@ def run_config3(args):
             "mpix_per_s": res["masked"]["frames_per_s"] / len(streams) * mpix,
             "masked": res["masked"], "full_frame": res["full"],
             "masked_c0": dict(res["masked_c0"], what="the intensity-difference test on c_0"),
-            "masked_over_full": res["masked"]["frames_per_s"] / res["full"]["frames_per_s"]}
+            "masked_over_full": res["masked"]["frames_per_s"] / res["full"]["frames_per_s"],
+            "describe": {"masked": res["masked_describe"], "full": res["full_describe"], "bits": 256,
+                         "masked_over_full": res["masked_describe"]["frames_per_s"] /
+                         res["full_describe"]["frames_per_s"],
+                         "what": "detection + description in the group (masked: new keypoints described, "
+                                 "carried ones copied; full: every keypoint described)"}}
     if not args.no_cpu_baseline:
         # the oracle on the first frames of one stream per resolution (about
         # 3 s each); the mix has equal counts per resolution

@@ -284,32 +284,68 @@ __device__ __forceinline__ const uint8_t* group_layer(const StreamDev& d, const 
   return d.s.pyr + d.g.layer[l].pyr_off;
 }
 
-constexpr int kGroupNewBlocks = 2;  // CTAs per SM of the group pass (its grid)
+constexpr int kGroupNewBlocks = 3;  // CTAs per SM of the group pass (its grid)
+
+// Units of work of every tick item in shared memory: pre[i] = units of the
+// items before item i, pre[n] = the tick's total. A unit is a group of 32
+// records (`groups`) or one record of a frame with a previous frame; items of
+// streams that do not describe have none. Ends with a barrier.
+__device__ __forceinline__ void tick_prefix(const StreamDev* devs, const TickItem* items, int n, bool groups,
+                                            uint32_t* pre) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const TickItem& ti = items[i];
+    const StreamDev& d = devs[ti.sid];
+    uint32_t u = 0;
+    if (d.D && (groups || ti.frame_index > 0)) {
+      const int par = (int)(ti.frame_index & 1);
+      const long long first = d.rec_offsets[par][0];
+      const long long end = min((long long)d.rec_offsets[par][1], d.K_max);
+      const long long m = max(0LL, end - first);
+      u = (uint32_t)(groups ? (m + 31) / 32 : m);
+    }
+    pre[i] = u;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {  // exclusive scan, 32 items at a time
+    const int lane = threadIdx.x;
+    uint32_t carry = 0;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      const int i = c0 + lane;
+      const uint32_t v = i < n ? pre[i] : 0u;
+      uint32_t incl = v;
+#pragma unroll
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, incl, dd);
+        if (lane >= dd) incl += o;
+      }
+      if (i < n) pre[i] = carry + incl - v;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) pre[n] = carry;
+  }
+  __syncthreads();
+}
 
 __global__ void __launch_bounds__(kNewWarps * 32, kGroupNewBlocks)
     k_group_describe_new(const StreamDev* devs, const TickHeader* hdr, const TickItem* items) {
   __shared__ uint32_t pat[kNewWarps][kDescMaxBits];       // the current stream's pairs, per warp
   __shared__ uint32_t boxes[kNewWarps][kHalfRows * kBoxPitch];
+  __shared__ uint32_t pre[kMaxTickItems + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long gw = (long long)blockIdx.x * kNewWarps + warp, nw = (long long)gridDim.x * kNewWarps;
+  const int n_items = hdr->n_items;
+  tick_prefix(devs, items, n_items, true, pre);
+  const uint32_t total = pre[n_items];
   uint32_t* bw = boxes[warp];
   uint32_t* pw = pat[warp];
-  const int n_items = hdr->n_items;
-  long long acc = 0;  // 32-record groups of the items before this one
-  int loaded = -1;    // stream whose pairs are in pw
-  for (int i = 0; i < n_items; ++i) {
+  int loaded = -1;  // stream whose pairs are in pw
+  // the tick's 32-record groups, numbered item after item, spread over the warps
+  for (uint32_t g = blockIdx.x * kNewWarps + warp; g < total; g += gridDim.x * kNewWarps) {
+    const int i = find_item(n_items, (int)g, [&](int q) { return (int)pre[q]; });
     const TickItem ti = items[i];
     const StreamDev& d = devs[ti.sid];
-    if (!d.D) continue;
     const int par = (int)(ti.frame_index & 1);
     const long long first = d.rec_offsets[par][0];
     const long long end = min((long long)d.rec_offsets[par][1], d.K_max);
-    const long long groups = end > first ? (end - first + 31) / 32 : 0;
-    // this warp takes the groups whose tick-wide number is gw modulo nw
-    long long g0 = (gw - acc) % nw;
-    if (g0 < 0) g0 += nw;
-    acc += groups;
-    if (g0 >= groups) continue;
     const int DW = d.D >> 5;
     if (loaded != ti.sid) {
       __syncwarp();  // the previous stream's tests are done with pw
@@ -321,69 +357,59 @@ __global__ void __launch_bounds__(kNewWarps * 32, kGroupNewBlocks)
       loaded = ti.sid;
     }
     const uint2* recs = reinterpret_cast<const uint2*>(d.rec[par]);
-    for (long long gi = g0; gi < groups; gi += nw) {
-      const long long base = first + gi * 32, idx = base + lane;
-      uint2 r = make_uint2(0u, 0u);
-      bool is_new = false;
-      if (idx < end) {
-        r = recs[idx];
-        is_new = ((r.y >> 16) & FKD_KP_PROPAGATED) == 0u;
-      }
-      uint32_t todo = __ballot_sync(0xffffffffu, is_new);
-      while (todo) {
-        const int src_lane = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const uint32_t rx = __shfl_sync(0xffffffffu, r.x, src_lane);
-        const uint32_t ry = __shfl_sync(0xffffffffu, r.y, src_lane);
-        const int x = (int)(rx & 0xffffu), y = (int)(rx >> 16), l = (int)(ry & 0xffu);
-        const LayerGeom& lg = d.g.layer[l];
-        int pitch;
-        const uint8_t* img = group_layer(d, ti, l, &pitch);
-        const uint32_t mine = describe_record(img, pitch, lg.w, lg.h, x, y, pw, bw, DW, lane);
-        if (lane < DW) d.desc[par][(base + src_lane) * DW + lane] = mine;
-      }
+    const long long base = first + (long long)(g - pre[i]) * 32, idx = base + lane;
+    uint2 r = make_uint2(0u, 0u);
+    bool is_new = false;
+    if (idx < end) {
+      r = recs[idx];
+      is_new = ((r.y >> 16) & FKD_KP_PROPAGATED) == 0u;
+    }
+    uint32_t todo = __ballot_sync(0xffffffffu, is_new);
+    while (todo) {
+      const int src_lane = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint32_t rx = __shfl_sync(0xffffffffu, r.x, src_lane);
+      const uint32_t ry = __shfl_sync(0xffffffffu, r.y, src_lane);
+      const int x = (int)(rx & 0xffffu), y = (int)(rx >> 16), l = (int)(ry & 0xffu);
+      const LayerGeom& lg = d.g.layer[l];
+      int pitch;
+      const uint8_t* img = group_layer(d, ti, l, &pitch);
+      const uint32_t mine = describe_record(img, pitch, lg.w, lg.h, x, y, pw, bw, DW, lane);
+      if (lane < DW) d.desc[par][(base + src_lane) * DW + lane] = mine;
     }
   }
 }
 
 __global__ void __launch_bounds__(kCarriedThreads)
     k_group_describe_carried(const StreamDev* devs, const TickHeader* hdr, const TickItem* items) {
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+  __shared__ uint32_t pre[kMaxTickItems + 1];
   const int n_items = hdr->n_items;
-  long long acc = 0;  // records of the items before this one
-  for (int i = 0; i < n_items; ++i) {
+  tick_prefix(devs, items, n_items, false, pre);
+  const uint32_t total = pre[n_items];
+  // the tick's records (of frames with a previous frame), one per thread
+  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
+    const int i = find_item(n_items, (int)u, [&](int q) { return (int)pre[q]; });
     const TickItem ti = items[i];
     const StreamDev& d = devs[ti.sid];
-    if (!d.D) continue;
     const int par = (int)(ti.frame_index & 1), pp = par ^ 1;
-    const long long first = d.rec_offsets[par][0];
-    const long long end = min((long long)d.rec_offsets[par][1], d.K_max);
-    const long long n = max(0LL, end - first);
-    long long j0 = (tid - acc) % nt;
-    if (j0 < 0) j0 += nt;
-    acc += n;
-    if (j0 >= n || ti.frame_index == 0) continue;
+    const long long idx = d.rec_offsets[par][0] + (long long)(u - pre[i]);
+    const uint2 r = reinterpret_cast<const uint2*>(d.rec[par])[idx];
+    if (((r.y >> 16) & FKD_KP_PROPAGATED) == 0u) continue;
     const int DW = d.D >> 5;
-    const uint2* recs = reinterpret_cast<const uint2*>(d.rec[par]);
     const uint2* prev = reinterpret_cast<const uint2*>(d.rec[pp]);
     const long long prev_end = min((long long)d.rec_offsets[pp][1], d.K_max);
-    for (long long j = j0; j < n; j += nt) {
-      const long long idx = first + j;
-      const uint2 r = recs[idx];
-      if (((r.y >> 16) & FKD_KP_PROPAGATED) == 0u) continue;
-      const int y = (int)(r.x >> 16), l = (int)(r.y & 0xffu);
-      const int gr = d.g.layer[l].row_off + y;
-      const long long lo = d.row_base[pp][gr];
-      const long long hi = gr + 1 < d.rows ? (long long)d.row_base[pp][gr + 1] : prev_end;
-      const long long o = find_record(prev, lo, min(hi, prev_end), rec_key(r));
-      if (o < 0) {
-        *d.s.overflow = 1;  // only after an overflow dropped the origin record
-        continue;
-      }
-      const uint32_t* from = d.desc[pp] + o * DW;
-      uint32_t* to = d.desc[par] + idx * DW;
-      for (int q = 0; q < DW; ++q) to[q] = from[q];
+    const int y = (int)(r.x >> 16), l = (int)(r.y & 0xffu);
+    const int gr = d.g.layer[l].row_off + y;
+    const long long lo = d.row_base[pp][gr];
+    const long long hi = gr + 1 < d.rows ? (long long)d.row_base[pp][gr + 1] : prev_end;
+    const long long o = find_record(prev, lo, min(hi, prev_end), rec_key(r));
+    if (o < 0) {
+      *d.s.overflow = 1;  // only after an overflow dropped the origin record
+      continue;
     }
+    const uint32_t* from = d.desc[pp] + o * DW;
+    uint32_t* to = d.desc[par] + idx * DW;
+    for (int q = 0; q < DW; ++q) to[q] = from[q];
   }
 }
 
