@@ -49,3 +49,51 @@ def test_params_default_and_validation_without_gpu():
     assert lib.fkd_destroy_stream(None) == fkd.FKD_OK
     assert lib.fkd_push_frame(None, None, 0, 0) == fkd.FKD_E_ARG
     assert lib.fkd_synchronize(None) == fkd.FKD_E_ARG
+
+
+def test_descriptor_entry_points_reject_bad_arguments_without_gpu():
+    """Argument checks that run before any device work."""
+    lib = fkd.load()
+    n = ctypes.c_size_t()
+    assert lib.fkd_set_descriptor(None, None, 0) == fkd.FKD_E_ARG
+    assert lib.fkd_get_descriptors(None, None, 0, ctypes.byref(n), 0) == fkd.FKD_E_ARG
+    assert lib.fkd_group_set_descriptor(None, 0, None, 0) == fkd.FKD_E_ARG
+    assert lib.fkd_group_get_descriptors(None, 0, None, 0, None, 0) == fkd.FKD_E_ARG
+    assert lib.fkd_server_set_descriptor(None, 0, None, 0) == fkd.FKD_E_ARG
+    assert lib.fkd_server_get_descriptors(None, 0, None, 0, ctypes.byref(n)) == fkd.FKD_E_ARG
+
+
+def test_descriptor_pattern_generator():
+    """The seeded pattern: deterministic, D x 4 int8 within the library's
+    offset bound, not degenerate."""
+    import numpy as np
+
+    from paper_1503_06959_gb300 import synth
+    a, b = synth.descriptor_pattern(256, seed=3), synth.descriptor_pattern(256, seed=3)
+    np.testing.assert_array_equal(a, b)
+    assert a.shape == (256, 4) and a.dtype == np.int8
+    assert np.abs(a).max() <= synth.DESC_RADIUS == 13
+    assert not np.array_equal(a, synth.descriptor_pattern(256, seed=4))
+    assert (a[:, :2] != a[:, 2:]).any(axis=1).mean() > 0.95  # pairs of two distinct points
+
+
+def test_bench_reads_profile_counters_per_launch_shape(tmp_path, monkeypatch):
+    """The bench takes the dominant kernel's traffic and ALU counts from the
+    committed profile only for the launch shape in use and unchanged sources."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    got = bench.profile_counters("detect", dict(tile_h=16, warps_per_cta=8, ctas_per_sm=2))
+    assert got and got["traffic_bytes_per_launch"] > 0 and got["alu_warp_inst_per_launch"] > 0
+    assert bench.profile_counters("detect", dict(tile_h=8, warps_per_cta=4, ctas_per_sm=1)) is None
+    # a changed source no longer matches the recorded hash
+    csrc = tmp_path / "paper_1503_06959_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    for f in bench.KERNEL_SOURCES["detect"]:
+        data = open(os.path.join(ROOT, "paper_1503_06959_gb300", "csrc", f), "rb").read()
+        (csrc / f).write_bytes(data + (b"\n" if f.endswith(".cu") else b""))
+    prof = open(os.path.join(ROOT, "profiles", "k_detect_masked_clip_640x480x300.md")).read()
+    (tmp_path / "profiles" / "k_detect_masked_clip_640x480x300.md").write_text(prof)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profile_counters("detect", dict(tile_h=16, warps_per_cta=8, ctas_per_sm=2)) is None

@@ -727,17 +727,15 @@ def _describe_all(frame, kp, O, intra, pattern):
                     ).reshape(len(kp), -1)
 
 
-@pytest.mark.parametrize("mode", ["ID", "IDP"])
+@pytest.mark.parametrize("mode", ["ID", "IDP", "KB"])
 def test_masked_description_describes_new_and_carries_old(mode):
     from paper_1503_06959_gb300 import synth
     src = synth.VideoSource(96, 96, seed=23, n_movers=3, mover_size=24, speed=(3, 4))
     frames = src.frames(4)
     pattern = synth.descriptor_pattern(128, seed=3)
     kw = dict(N_r=3, N_c=3, O=2, intra=1, T_I=4, t=12, pattern=pattern)
-    if mode == "ID":
-        s = oracle.Stream(96, 96, mask_mode=oracle.MASK_ID, **kw)
-    else:
-        s = oracle.Stream(96, 96, mask_mode=oracle.MASK_IDP, **kw)
+    modes = {"ID": oracle.MASK_ID, "IDP": oracle.MASK_IDP, "KB": oracle.MASK_KB}
+    s = oracle.Stream(96, 96, mask_mode=modes[mode], T_H=2, **kw)
     one = np.zeros((3, 3), np.uint8)
     one[1, 1] = 1
     prev_kp, prev_d = None, None
@@ -752,7 +750,8 @@ def test_masked_description_describes_new_and_carries_old(mode):
         if n == 0:
             assert new.all()
         else:
-            assert (~new).any() and new.any()
+            if mode != "KB":
+                assert (~new).any() and new.any()
             index = {(int(k["layer"]), int(k["y"]), int(k["x"])): i for i, k in enumerate(prev_kp)}
             for i in np.flatnonzero(~new):
                 k = kp[i]
@@ -761,8 +760,9 @@ def test_masked_description_describes_new_and_carries_old(mode):
                 seen_carried_changed |= not np.array_equal(d[i], here[i])
         prev_kp, prev_d = kp, d
     # the carried descriptors come from the frame that detected them, not
-    # from the current pixels (which moved under some of them)
-    assert seen_carried_changed
+    # from the current pixels (which moved under some of them; keypoint
+    # binning carries only sparse, mostly static bins)
+    assert seen_carried_changed or mode == "KB"
 
 
 def test_description_is_set_before_the_first_frame_only():
