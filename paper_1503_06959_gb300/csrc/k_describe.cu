@@ -20,12 +20,15 @@
 //                       the frame that last detected there: src(k, bin) for
 //                       the block masks, the last frame whose per-pixel mask
 //                       bit was set for FKD_MASK_IDP, or the kept set of the
-//                       batch before. A binary search in that frame's
-//                       records (canonical order) finds it; its descriptor is
-//                       copied. The carried pass runs after the new pass, so
-//                       every source descriptor is final.
-// Both passes also copy the batch's last frame (records and descriptors)
-// into the kept set of the next batch.
+//                       batch before. A binary search within its layer row of
+//                       that frame's records (canonical order; the emission
+//                       pass records where every row starts) finds it; its
+//                       descriptor is copied. The carried pass runs after
+//                       the new pass, so every source descriptor is final.
+// Both passes also copy the batch's last frame (records, descriptors, row
+// starts) into the kept set of the next batch. The group passes do the same
+// for one frame of each describing stream of a tick, the previous frame's
+// records being the kept set.
 #include "fkd_internal.cuh"
 
 namespace fkd {
