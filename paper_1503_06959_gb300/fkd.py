@@ -181,7 +181,10 @@ def params_default() -> fkd_params:
 
 
 class Stream:
-    """One video stream: fkd_create_stream ... fkd_destroy_stream."""
+    """One video stream: fkd_create_stream ... fkd_destroy_stream.
+
+    Keyword arguments are the fields of fkd_params (paper names); `pattern`
+    (D x 4 int8 pairs) turns on masked description (fkd_set_descriptor)."""
 
     def __init__(self, W: int, H: int, *, N_r: int = 8, N_c: int = 8, T_I: int = 4, T_H: int = 1,
                  O: int = 1, intra: int = 0, t: int = 20, n: int = 9,
