@@ -403,21 +403,22 @@ int fkd_group_get_mask(fkd_group* g, int id, uint8_t* out);
 int fkd_group_device_keypoints(fkd_group* g, int id, const fkd_keypoint** records,
                                const uint32_t** count_dev);
 
-/* Summed CUDA-event times of the group's kernels over the ticks since the
- * last read (same stages and semantics as fkd_profile_read; `frames` counts
- * the frames of those ticks). */
 /* Masked description for a stream of the group (as fkd_set_descriptor),
  * before its first tick; the description pass then runs in the stream's ticks.
  * Errors: FKD_E_ARG, FKD_E_STATE (the stream has ticked), FKD_E_CUDA. */
 int fkd_group_set_descriptor(fkd_group* G, int stream_id, const int8_t* pattern, int D);
 
 /* Descriptors of the stream's last frame (the records fkd_group_get_keypoints
- * returns, in their order), D/8 bytes each, at most `cap`; out = NULL with
- * cap = 0 only reports the count. Waits. Errors: FKD_E_ARG, FKD_E_STATE (no
+ * returns, in their order), D/8 bytes each, at most `cap`, into host memory
+ * (device memory with out_on_device = 1); out = NULL with cap = 0 only
+ * reports the count. Waits. Errors: FKD_E_ARG, FKD_E_STATE (no
  * frame yet, or the stream does not describe), FKD_E_CAPACITY, FKD_E_CUDA. */
 int fkd_group_get_descriptors(fkd_group* G, int stream_id, uint8_t* out, size_t cap, size_t* n_out,
                               int out_on_device);
 
+/* Summed CUDA-event times of the group's kernels over the ticks since the
+ * last read (same stages and semantics as fkd_profile_read; `frames` counts
+ * the frames of those ticks). */
 int fkd_group_profile_enable(fkd_group* g, int on);
 int fkd_group_profile_read(fkd_group* g, fkd_profile* out, int reset);
 
