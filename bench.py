@@ -12,9 +12,16 @@ active), per-frame latency of frame-by-frame pushes (p50 / p99), an
 end-to-end figure through the C ABI with pinned host buffers (host->device
 copies of the frames and device->host copies of the keypoints inside the
 timed region), the roofline of the dominant kernel from CUDA events recorded
-around each kernel on the launching stream, the SM clocks sampled during the
-timed region, and the CPU oracle timed on a bounded sample on this host.
+around each kernel on the launching stream (in further steps after the timed
+ones, so that the timed steps run plain launches), the SM clocks sampled
+during the timed region, variants (mask on c_0, per-pixel masks, scale-space
+suppression, detection + masked description), and the CPU oracle timed on a
+bounded sample on this host.
 
+--config 3|4|5: a group of 64 mixed-resolution streams, the serving loop
+(256 streams at 30 fps), 8 streams of 3840x2160. --sweep: the T_I / T_H
+trade-off against full-frame detection. --describe masked|full|both:
+detection + description alone on the 640x480 clip.
 --impl reference times the CPU oracle (single-threaded C, the correctness
 reference) on the same workload, a bounded number of frames per step.
 """
