@@ -19,6 +19,9 @@
  *      optionally over the scale-space neighbourhood (the adjacent layers)
  *   4. D_n = detections in active blocks united with the keypoints of
  *      D_{n-1} that lie in inactive blocks (Eq. 1).
+ *   5. optionally, masked description: a binary pair-test descriptor for
+ *      every keypoint detected in the frame, carried keypoints keeping
+ *      theirs (Sec. 2, Sec. 3).
  */
 #include "fkd_oracle.h"
 
