@@ -538,15 +538,20 @@ int fkd_server_get_stats(fkd_server* s, fkd_server_stats* out, int reset);
  *
  * Its per-bin sums live in a fixed array of FKD_NOALLOC_MAX_BINS 64-bit
  * counters (32 KiB) in this library's device memory, present on every GPU
- * that loads the library until the process exits. The first call made while
- * a given device is current looks the array's address up on that device
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call clears the counters it uses and then reuses the same array, so
- * calls that overlap on the GPU (on different streams, or different host
- * threads) race and give wrong masks: serialise them.
+ * that loads the library until the process exits. The first call made in a
+ * given CUDA context (normally a device's primary context) looks the array's
+ * address up in that context (cudaGetSymbolAddress) and remembers it for
+ * the context; make that first call outside stream capture: a first call
+ * whose stream is being captured fails with FKD_E_STATE and launches
+ * nothing. Every call clears the counters it uses and then reuses the same
+ * array, so calls that overlap on the GPU (on different streams, or
+ * different host threads) race and give wrong masks: serialise them.
  * Errors: FKD_E_ARG (NULL buffer, sizes outside 1..16384, pitch < W, a bin
  * grid that does not fit the frame, N_r*N_c > FKD_NOALLOC_MAX_BINS, T_I < 0),
- * FKD_E_CUDA. Calls no cudaMalloc, cudaFree or other allocating routine.
+ * FKD_E_STATE (see above), FKD_E_CUDA (also when a CUDA error from earlier
+ * work on the calling thread is still pending: it is reported, left pending
+ * for the caller, and nothing is launched). Calls no cudaMalloc, cudaFree or
+ * other allocating routine.
  */
 #define FKD_NOALLOC_MAX_BINS 4096
 int fkd_id_mask_noalloc(const uint8_t* cur, const uint8_t* prev, int W, int H, size_t pitch, int N_r,

@@ -11,7 +11,9 @@
 // the same test fkd_push_frames applies with mask_layer 0) using only the
 // caller's buffers and a fixed scratch array that lives in this library's
 // device memory for as long as the library is loaded.
-#include <atomic>
+#include <mutex>
+
+#include <cuda.h>
 
 #include "fkd_internal.cuh"
 
@@ -75,10 +77,46 @@ int noalloc_fail(int code, const char* msg, cudaError_t e = cudaSuccess) {
                         e != cudaSuccess ? cudaGetErrorString(e) : "");
 }
 
-// Device address of the scratch array on each device, looked up on the
-// first call made while that device is current.
-constexpr int kMaxDevices = 64;
-std::atomic<unsigned long long*> g_scratch_ptr[kMaxDevices] = {};
+// Device address of the scratch array in each CUDA context that has called
+// this entry point, keyed by the driver's context ID (unique for the life of
+// the process, so a context destroyed and created again at the same handle
+// never finds a stale address). The address is looked up once per context,
+// on its first call made outside stream capture.
+constexpr int kMaxContexts = 64;
+struct ScratchSlot {
+  unsigned long long ctx_id;
+  unsigned long long* ptr;
+};
+std::mutex g_scratch_mu;
+ScratchSlot g_scratch[kMaxContexts] = {};
+int g_scratch_n = 0;
+
+// The driver's cuCtxGetCurrent and cuCtxGetId, fetched through the runtime
+// (no link-time dependency on the driver library).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+int current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+  });
+  if (!get_current || !get_id) return noalloc_fail(FKD_E_CUDA, "driver context queries unavailable");
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return noalloc_fail(FKD_E_CUDA, "no current CUDA context");
+  if (get_id(ctx, id) != CUDA_SUCCESS) return noalloc_fail(FKD_E_CUDA, "cuCtxGetId failed");
+  return FKD_OK;
+}
 
 }  // namespace
 
@@ -91,25 +129,40 @@ extern "C" int fkd_id_mask_noalloc(const uint8_t* cur, const uint8_t* prev, int 
   if (N_r * N_c > kNoAllocMaxBins)
     return noalloc_fail(FKD_E_ARG, "N_r * N_c exceeds FKD_NOALLOC_MAX_BINS (4096)");
   if (T_I < 0) return noalloc_fail(FKD_E_ARG, "T_I must be >= 0");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return noalloc_fail(FKD_E_CUDA, "cudaGetDevice failed", e);
-  if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(FKD_E_ARG, "device index out of range");
-  unsigned long long* bsum = g_scratch_ptr[dev].load();
-  if (!bsum) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_bsum);
-    if (e != cudaSuccess) return noalloc_fail(FKD_E_CUDA, "cudaGetSymbolAddress failed", e);
-    bsum = static_cast<unsigned long long*>(p);
-    g_scratch_ptr[dev].store(bsum);
-  }
+  // an error left pending by earlier work on this thread belongs to the
+  // caller: report it without clearing it, and launch nothing
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) return noalloc_fail(FKD_E_CUDA, "a CUDA error was already pending", e);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) return noalloc_fail(FKD_E_CUDA, "cudaStreamIsCapturing failed", e);
+  unsigned long long ctx_id = 0;
+  if (int rc = current_context_id(&ctx_id)) return rc;
+  unsigned long long* bsum = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    for (int i = 0; i < g_scratch_n; ++i)
+      if (g_scratch[i].ctx_id == ctx_id) bsum = g_scratch[i].ptr;
+    if (!bsum) {
+      if (cap != cudaStreamCaptureStatusNone)
+        return noalloc_fail(FKD_E_STATE,
+                            "first call on this CUDA context made during stream capture; call once before capturing");
+      if (g_scratch_n == kMaxContexts) return noalloc_fail(FKD_E_CUDA, "more than 64 CUDA contexts");
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_bsum);
+      if (e != cudaSuccess) return noalloc_fail(FKD_E_CUDA, "cudaGetSymbolAddress failed", e);
+      bsum = static_cast<unsigned long long*>(p);
+      g_scratch[g_scratch_n++] = ScratchSlot{ctx_id, bsum};
+    }
+  }
   const int nb = N_r * N_c;
   k_noalloc_clear<<<(nb + kThreads - 1) / kThreads, kThreads, 0, st>>>(bsum, nb);
+  if ((e = cudaGetLastError()) != cudaSuccess) return noalloc_fail(FKD_E_CUDA, "clear kernel launch failed", e);
   dim3 grid((W + kThreads - 1) / kThreads, (H + kRowsPerBlock - 1) / kRowsPerBlock);
   k_noalloc_sums<<<grid, kThreads, 0, st>>>(cur, prev, W, H, (long long)pitch, N_r, N_c, bsum);
+  if ((e = cudaGetLastError()) != cudaSuccess) return noalloc_fail(FKD_E_CUDA, "sums kernel launch failed", e);
   k_noalloc_mask<<<(nb + kThreads - 1) / kThreads, kThreads, 0, st>>>(bsum, W, H, N_r, N_c, T_I, mask_out);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return noalloc_fail(FKD_E_CUDA, "kernel launch failed", e);
+  if ((e = cudaGetLastError()) != cudaSuccess) return noalloc_fail(FKD_E_CUDA, "mask kernel launch failed", e);
   return FKD_OK;
 }

@@ -583,10 +583,21 @@ def id_mask_noalloc(cur, prev, N_r: int, N_c: int, T_I: int, mask_out, cuda_stre
     device memory themselves). cur, prev: torch CUDA uint8 H x W frames with
     the same row stride; mask_out: torch CUDA uint8 tensor of N_r*N_c bytes.
     Asynchronous on `cuda_stream` (default: the legacy default stream)."""
+    import torch
     lib = load()
+    dev = torch.cuda.current_device()
+    for name, t in (("cur", cur), ("prev", prev), ("mask_out", mask_out)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.uint8):
+            raise TypeError(f"{name} must be a torch CUDA uint8 tensor")
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
     H, W = cur.shape
-    assert tuple(prev.shape) == (H, W) and cur.stride(0) == prev.stride(0)
-    assert cur.stride(1) == 1 and prev.stride(1) == 1 and mask_out.numel() == N_r * N_c
+    if tuple(prev.shape) != (H, W) or cur.stride(0) != prev.stride(0):
+        raise ValueError("cur and prev must have the same shape and row stride")
+    if cur.stride(1) != 1 or prev.stride(1) != 1:
+        raise ValueError("frame rows must be contiguous")
+    if not mask_out.is_contiguous() or mask_out.numel() != N_r * N_c:
+        raise ValueError("mask_out must be a contiguous tensor of N_r * N_c bytes")
     _check(lib.fkd_id_mask_noalloc(_ptr(cur), _ptr(prev), W, H, cur.stride(0), N_r, N_c, T_I,
                                    _ptr(mask_out), ctypes.c_void_p(cuda_stream or 0)))
 
