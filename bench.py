@@ -18,8 +18,15 @@ during the timed region, variants (mask on c_0, per-pixel masks, scale-space
 suppression, detection + masked description), and the CPU oracle timed on a
 bounded sample on this host.
 
---config 3|4|5: a group of 64 mixed-resolution streams, the serving loop
-(256 streams at 30 fps), 8 streams of 3840x2160. --sweep: the T_I / T_H
+The default line also carries "config3" (64 mixed-resolution streams, 120
+frames each, one group tick per frame) and "config5" (8 streams of
+3840x2160, 100 moving then 100 static frames) at their stated sizes: masked
+against full-frame frames/s, Mpixel/s, tick latency p50 / p99, the
+detection kernel's roofline on active bytes and their own clock records
+(--no-groups leaves them out).
+
+--config 3|4|5: one of those alone, or the serving loop (256 streams at 30
+fps for 20 s, 600 frames each) with its clocks. --sweep: the T_I / T_H
 trade-off against full-frame detection. --describe masked|full|both:
 detection + description alone on the 640x480 clip.
 --impl reference times the CPU oracle (single-threaded C, the correctness
@@ -82,14 +89,15 @@ def profile_counters(kernel: str, shape: dict | None = None):
     if not sha or sha.group(1) != m.hexdigest()[:16]:
         return None
     if kernel == "detect" and shape is not None:
-        # one line of counters per captured launch shape
+        # one line of counters per captured launch shape: "counters th,w,c: key value key value ..."
         want = f"{shape['tile_h']},{shape['warps_per_cta']},{shape['ctas_per_sm']}"
-        c = re.search(r"counters " + re.escape(want) +
-                      r": traffic_bytes_per_launch (\d+) alu_warp_inst_per_launch (\d+)", text)
+        c = re.search(r"counters " + re.escape(want) + r": ([^\n]+)", text)
         if not c:
             return None
-        return {"traffic_bytes_per_launch": float(c.group(1)), "alu_warp_inst_per_launch": float(c.group(2))}
-    got = {k: re.search(k + r": (\S+)", text) for k in ("traffic_bytes_per_launch", "alu_warp_inst_per_launch")}
+        toks = c.group(1).split()
+        return {k: float(v) for k, v in zip(toks[0::2], toks[1::2])}
+    got = {k: re.search(k + r": (\S+)", text)
+           for k in ("traffic_bytes_per_launch", "alu_warp_inst_per_launch", "alu_peak_warp_inst_per_sm_cycle")}
     return {k: float(v.group(1)) for k, v in got.items() if v}
 
 
@@ -230,179 +238,320 @@ def run_reference(args):
     return 0
 
 
-def _group_run(streams, frames_dev, mode, warm, ticks_timed, fkd, torch, tune_ticks=3, mask_layer=None,
-               pattern=None):
-    """Tick every stream once per tick through one group, after tuning the
-    detection launch shape on the first `tune_ticks` ticks; returns (seconds
-    for the timed ticks, profile, keypoints per tick, chosen shape)."""
-    st = torch.cuda.Stream()
-    g = fkd.Group(streams[0].O, streams[0].intra, cuda_stream=st.cuda_stream)
-    ids = [g.add_stream(c.W, c.H, N_r=c.N_r, N_c=c.N_c, T_I=c.T_I, t=c.t, mask_mode=mode,
-                        mask_layer=c.mask_layer if mask_layer is None else mask_layer,
-                        K_max=1 << 17)[0] for c in streams]
-    if pattern is not None:  # every stream describes its keypoints
-        for i in ids:
-            g.set_descriptor(i, pattern)
-    n_frames = frames_dev[0].shape[0]
-    shape, tune_ms = g.autotune(ids, [[f[n] for f in frames_dev] for n in range(tune_ticks)], reps=2)
-    shape["tuned_ms_for_ticks"] = [tune_ticks, tune_ms]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+# --- synthetic clips generated in parallel (spawned processes write into
+# shared memory; the generator is sequential within a stream)
+def gen_clips(jobs, torch, device):
+    """jobs: (count, W, H, seed, source kwargs). Returns one device tensor
+    (count x H x W uint8) per job and the first frames of each on the host."""
+    import concurrent.futures
+    import multiprocessing
+    from multiprocessing import shared_memory
+    shms = [shared_memory.SharedMemory(create=True, size=max(1, c * W * H)) for c, W, H, _, _ in jobs]
+    try:
+        workers = max(1, min(len(jobs), os.cpu_count() or 1))
+        with concurrent.futures.ProcessPoolExecutor(workers, mp_context=multiprocessing.get_context("spawn")) as ex:
+            futs = [ex.submit(synth.fill_shared, s.name, *j) for s, j in zip(shms, jobs)]
+            for f in futs:
+                f.result()
+        dev, heads = [], []
+        for s, (c, W, H, _, _) in zip(shms, jobs):
+            arr = np.ndarray((c, H, W), np.uint8, buffer=s.buf)
+            dev.append(torch.from_numpy(arr).to(device, copy=True))
+            heads.append(arr[:4].copy())
+            del arr
+        if torch.device(device).type == "cuda":
+            torch.cuda.synchronize()
+        return dev, heads
+    finally:
+        for s in shms:
+            s.close()
+            s.unlink()
+
+
+# --- the active bytes of the detection step (the pixels that must be read:
+# every pixel within 4 px -- the ring radius 3 plus the suppression
+# neighbour -- of a pixel whose bin is active, on every layer)
+def layer_dims(W, H, O, intra):
+    """(w, h, S) of every layer: c_0 = W x H, c_{i+1} = c_i halved (floor),
+    d_0 = 2 floor(W/3) x 2 floor(H/3), d_{i+1} = d_i halved; S = 2 sigma."""
+    out = []
+    for i in range(O):
+        out.append((W >> i, H >> i, 2 << i))
+        if intra:
+            out.append(((W // 3) * 2 >> i, (H // 3) * 2 >> i, 3 << i))
+    return out
+
+
+class ActiveBytes:
+    """Active layer pixels plus a `halo`-pixel border, per frame mask: the
+    bytes the masked detection must read at least once. A layer pixel (x, y)
+    of scale code S lies in bin (floor(floor(y S/2) N_r / H), floor(floor(x
+    S/2) N_c / W)) (Eq. 3); it must be read when a bin of a pixel within
+    `halo` of it (Chebyshev distance, inside the layer) is active. Because the
+    bin index is monotone in x and y, the bins within reach of a pixel form a
+    rectangle of bins, and pixels with the same rectangle are counted
+    together through a prefix sum of the mask."""
+
+    def __init__(self, W, H, O, intra, N_r, N_c, halo=4):
+        self.N_r, self.N_c = N_r, N_c
+        self.classes = []
+        for w, h, S in layer_dims(W, H, O, intra):
+            if w < 1 or h < 1:
+                continue
+            cb = ((np.arange(w) * S) // 2) * N_c // W
+            rb = ((np.arange(h) * S) // 2) * N_r // H
+            xs, ys = np.arange(w), np.arange(h)
+            cu, cc = np.unique(cb[np.maximum(0, xs - halo)] * 65536 + cb[np.minimum(w - 1, xs + halo)],
+                               return_counts=True)
+            ru, rc = np.unique(rb[np.maximum(0, ys - halo)] * 65536 + rb[np.minimum(h - 1, ys + halo)],
+                               return_counts=True)
+            self.classes.append((ru >> 16, ru & 0xffff, rc, cu >> 16, cu & 0xffff, cc))
+
+    def __call__(self, mask) -> int:
+        m = np.asarray(mask, np.int64).reshape(self.N_r, self.N_c)
+        P = np.zeros((self.N_r + 1, self.N_c + 1), np.int64)
+        P[1:, 1:] = m.cumsum(0).cumsum(1)
+        total = 0
+        for r0, r1, rc, c0, c1, cc in self.classes:
+            rect = (P[r1 + 1][:, c1 + 1] - P[r0][:, c1 + 1] - P[r1 + 1][:, c0] + P[r0][:, c0])
+            total += int(((rect > 0) * rc[:, None] * cc[None, :]).sum())
+        return total
+
+
+def keypoint_keys(rec):
+    """(layer, y, x) of records as one int64 each."""
+    return (rec["layer"].astype(np.int64) << 32) | (rec["y"].astype(np.int64) << 16) | rec["x"].astype(np.int64)
+
+
+def recall_precision(masked_frames, full_frames):
+    """Mean over frames of |D_n and F_n| / |F_n| and |D_n and F_n| / |D_n|,
+    D_n the masked set and F_n full-frame detection, over (layer, y, x)."""
+    rec, prec = [], []
+    for a, f in zip(masked_frames, full_frames):
+        ka, kf = keypoint_keys(a), keypoint_keys(f)
+        both = np.intersect1d(ka, kf).size
+        rec.append(both / max(1, kf.size))
+        prec.append(both / max(1, ka.size))
+    return float(np.mean(rec)), float(np.mean(prec))
+
+
+def group_workload(cfgs, clips, segments, warm, mode, fkd, torch, mask_layer=None, pattern=None,
+                   with_latency=True, with_profile=True, profile_ticks=12):
+    """One group of streams (cfgs[i] fed clips[i], device frames), one frame of
+    every stream per tick. The detection launch shape is autotuned on the
+    first ticks. Per segment (name, tick range; the ticks before the first
+    segment are warm-up): frames/s from back-to-back graph replays between two
+    CUDA events; then, in a second group, the tick latency (tick + wait, host
+    clock) of the same ticks; then, in a third, stage times from CUDA events
+    around every kernel and the masks (for the detection step's active bytes)."""
+    O, intra = cfgs[0].O, cfgs[0].intra
+    mpix = sum(c.W * c.H for c in cfgs) / 1e6
+
+    def make():
+        st = torch.cuda.Stream()
+        g = fkd.Group(O, intra, cuda_stream=st.cuda_stream)
+        ids = [g.add_stream(c.W, c.H, N_r=c.N_r, N_c=c.N_c, T_I=c.T_I, t=c.t, mask_mode=mode,
+                            mask_layer=c.mask_layer if mask_layer is None else mask_layer,
+                            K_max=1 << 20 if c.W * c.H > 4_000_000 else 1 << 17)[0] for c in cfgs]
+        if pattern is not None:
+            for i in ids:
+                g.set_descriptor(i, pattern)
+        return st, g, ids
+
+    def tick(g, ids, n):
+        g.tick(ids, [f[n] for f in clips])
+
+    st, g, ids = make()
+    shape, tune_ms = g.autotune(ids, [[f[n] for f in clips] for n in range(min(3, warm))], reps=2)
+    res = {"launch_shape": dict(shape, tuned_ms_for_ticks=[min(3, warm), tune_ms]), "segments": {}}
     for n in range(warm):
-        g.tick(ids, [f[n] for f in frames_dev])
-    g.synchronize()
-    # timed ticks: graph replays, no events between the kernels
-    e0.record(st)
-    for n in range(warm, warm + ticks_timed):
-        g.tick(ids, [f[n % n_frames] for f in frames_dev])
-    e1.record(st)
-    e1.synchronize()
-    kps = sum(len(g.get_keypoints(i)) for i in ids)
-    # stage times from a few more ticks with CUDA events around every kernel
-    g.profile_read()
-    g.profile_enable(True)
-    for n in range(warm + ticks_timed, warm + ticks_timed + 4):
-        g.tick(ids, [f[n % n_frames] for f in frames_dev])
-    g.synchronize()
-    prof = g.profile_read()
+        tick(g, ids, n)
+    for name, rng in segments:
+        g.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for n in rng:
+            tick(g, ids, n)
+        e1.record(st)
+        e1.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        fps = len(cfgs) * len(rng) / sec
+        res["segments"][name] = {"frames_per_s": fps, "mpix_per_s": fps / len(cfgs) * mpix,
+                                 "ms_per_tick": sec / len(rng) * 1e3, "ticks": len(rng)}
     g.close()
-    return e0.elapsed_time(e1) / 1e3, prof, kps, shape
+    if with_latency:
+        st, g, ids = make()
+        g.set_launch_config(shape)
+        for n in range(warm):
+            tick(g, ids, n)
+        g.synchronize()
+        for name, rng in segments:
+            lat = []
+            for n in rng:
+                t0 = time.perf_counter()
+                tick(g, ids, n)
+                g.synchronize()
+                lat.append((time.perf_counter() - t0) * 1e3)
+            res["segments"][name]["tick_latency_ms"] = {
+                "p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                "what": "fkd_group_tick of every stream + fkd_group_synchronize, host clock, one tick at a time"}
+        g.close()
+    if with_profile:
+        pk, pk_kind = peaks()
+        st, g, ids = make()
+        g.set_launch_config(shape)
+        counters = [ActiveBytes(c.W, c.H, c.O, c.intra, c.N_r, c.N_c) for c in cfgs]
+        for n in range(warm):
+            tick(g, ids, n)
+        g.synchronize()
+        g.profile_enable(True)
+        for name, rng in segments:
+            g.profile_read()
+            sampled = set(list(rng)[::max(1, len(rng) // profile_ticks)])
+            ms = {}
+            act_bytes, act_bins, nb, tiles_px, nt = 0, 0, 0, 0, 0
+            for n in rng:
+                tick(g, ids, n)
+                g.synchronize()
+                prof = g.profile_read()
+                if n not in sampled:
+                    continue
+                nt += 1
+                for k, v in prof["ms"].items():
+                    ms[k] = ms.get(k, 0.0) + v
+                tiles_px += prof["tile_pixels"]
+                for i, cnt in zip(ids, counters):
+                    m = g.get_mask(i)
+                    act_bytes += cnt(m)
+                    act_bins += int(m.sum())
+                    nb += m.size
+            det_ms = ms.get("detect", 0.0) / max(1, nt)
+            ab = act_bytes / max(1, nt)
+            ach = ab / (det_ms / 1e3) / 1e9 if det_ms else None
+            seg = res["segments"][name]
+            seg["stage_ms_per_tick"] = {k: v / max(1, nt) for k, v in ms.items()}
+            seg["active_bin_fraction"] = act_bins / max(1, nb)
+            seg["detect_roofline"] = {
+                "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"] if ach else None, "peak_source": f"{pk_kind} hbm_gbs",
+                "active_bytes_per_tick": ab, "launch_ms": det_ms, "ticks_sampled": nt,
+                "processed_tile_pixels_per_tick": tiles_px / max(1, nt),
+                "bytes": "layer pixels within 4 px of an active bin's pixels, every layer of every stream "
+                         "(1 byte read each), from the sampled ticks' masks; launch_ms from CUDA events "
+                         "around the detection kernel of the same ticks"}
+        g.close()
+    return res
+
+
+def config3_workload(torch, fkd, device, F=120, per_res=16):
+    """64 streams (16 of each of 320x240 .. 1920x1080), F frames each, moving
+    area U[5 %, 60 %] per stream: masked (intensity difference on the
+    coarsest octave) against full-frame detection, one group tick per frame."""
+    cfgs = synth.config3_streams(per_res)
+    jobs = [(F, c.W, c.H, 1000 + 300 + j, c.source) for j, c in enumerate(cfgs)]
+    t0 = time.perf_counter()
+    clips, heads = gen_clips(jobs, torch, device)
+    gen_s = time.perf_counter() - t0
+    warm = 3
+    segs = [("all", range(warm, F))]
+    clocks = ClockSampler(torch.cuda.current_device())
+    masked = group_workload(cfgs, clips, segs, warm, fkd.FKD_MASK_ID, fkd, torch)
+    full = group_workload(cfgs, clips, segs, warm, fkd.FKD_MASK_FULL, fkd, torch)
+    clk = clocks.stop()
+    mpix = sum(c.W * c.H for c in cfgs) / 1e6
+    out = {"workload": f"{len(cfgs)} streams ({per_res} each of 320x240, 640x480, 1280x720, 1920x1080), "
+                       f"{F} frames each resident in HBM, O=4 + intra-octaves, 16x12 bins, t=30, T_I=4, "
+                       f"moving area U[5%,60%]; one group tick = one frame of every stream "
+                       f"({mpix:.1f} Mpixel of c_0); {warm} warm-up ticks, {F - warm} timed",
+           "l2": f"inputs larger than L2 ({(F - warm) * mpix:.0f} MB of distinct frames over the timed ticks)",
+           "masked": dict(masked["segments"]["all"], launch_shape=masked["launch_shape"]),
+           "full_frame": dict(full["segments"]["all"], launch_shape=full["launch_shape"]),
+           "clocks": clk, "frame_generation_s": gen_s}
+    out["masked_over_full"] = out["masked"]["frames_per_s"] / out["full_frame"]["frames_per_s"]
+    del clips
+    return out, cfgs, heads
+
+
+def config5_workload(torch, fkd, device, seg=100, n_streams=8):
+    """8 streams of 3840x2160, 2 * seg frames: seg frames of motion (12
+    movers of 700x700) then seg static frames (sensor noise only), O=5 +
+    intra-octaves: masked against full-frame detection per segment."""
+    cfg = synth.config5()
+    F = 2 * seg
+    src = dict(cfg.source, static_segments=(seg, 0))
+    jobs = [(F, cfg.W, cfg.H, 1000 + 500 + j, src) for j in range(n_streams)]
+    t0 = time.perf_counter()
+    clips, heads = gen_clips(jobs, torch, device)
+    gen_s = time.perf_counter() - t0
+    warm = 2
+    segs = [("moving", range(warm, seg)), ("static", range(seg, F))]
+    cfgs = [cfg] * n_streams
+    clocks = ClockSampler(torch.cuda.current_device())
+    masked = group_workload(cfgs, clips, segs, warm, fkd.FKD_MASK_ID, fkd, torch)
+    full = group_workload(cfgs, clips, segs, warm, fkd.FKD_MASK_FULL, fkd, torch)
+    clk = clocks.stop()
+    out = {"workload": f"{n_streams} streams of 3840x2160, {F} frames each resident in HBM: {seg} moving "
+                       f"(12 movers of 700x700 at 2-6 px/frame) then {seg} static, N(0,2) noise, O=5 + "
+                       f"intra-octaves (10 layers), 16x12 bins, t=30, T_I=4; one tick = one frame of every "
+                       f"stream; ticks 0-{warm - 1} warm-up",
+           "l2": "inputs larger than L2 (66 MB of c_0 per tick, distinct frames every tick)",
+           "masked": dict(masked["segments"], launch_shape=masked["launch_shape"]),
+           "full_frame": dict(full["segments"], launch_shape=full["launch_shape"]),
+           "clocks": clk, "frame_generation_s": gen_s}
+    out["masked_over_full"] = {p: out["masked"][p]["frames_per_s"] / out["full_frame"][p]["frames_per_s"]
+                               for p in ("moving", "static")}
+    del clips
+    return out, cfg, heads
 
 
 def run_config3(args):
-    """64 streams of mixed resolution, one frame of each per tick in one
-    persistent launch sequence (group), frames resident in HBM."""
+    """The 64-stream group alone, as one JSON line (plus the describe variants)."""
     import torch
     from paper_1503_06959_gb300 import fkd
-    per_res = args.streams_per_res
-    streams = synth.config3_streams(per_res)
-    F = args.frames or 24
-    frames_dev, first_of_res = [], {}
-    for j, c in enumerate(streams):
-        clip = synth.source_for(c, 3, j).frames(F)
-        first_of_res.setdefault((c.W, c.H), (c, clip[:6]))
-        frames_dev.append(torch.from_numpy(clip).cuda())
-    warm = 3
-    res = {}
-    pattern = synth.descriptor_pattern(256)
-    for name, mode, ml, pat in (("masked", fkd.FKD_MASK_ID, None, None), ("masked_c0", fkd.FKD_MASK_ID, 0, None),
-                                ("full", fkd.FKD_MASK_FULL, None, None),
-                                ("masked_describe", fkd.FKD_MASK_ID, None, pattern),
-                                ("full_describe", fkd.FKD_MASK_FULL, None, pattern)):
-        sec, prof, kps, shape = _group_run(streams, frames_dev, mode, warm, F - warm, fkd, torch,
-                                           mask_layer=ml, pattern=pat)
-        ticks = F - warm
-        res[name] = {"frames_per_s": len(streams) * ticks / sec, "ms_per_tick": sec / ticks * 1e3,
-                     "launch_shape": shape,
-                     "stage_ms_per_tick": {k: v / max(1, prof["batches"]) for k, v in prof["ms"].items()},
-                     "keypoints_last_tick": kps, "tile_pixels_per_tick": prof["tile_pixels"] / max(1, prof["batches"])}
-    mpix = sum(c.W * c.H for c in streams) / 1e6
+    dev = torch.device("cuda", 0)
+    F = args.frames or 120
+    sub, cfgs, heads = config3_workload(torch, fkd, dev, F=F, per_res=args.streams_per_res)
     line = {"metric": "frames/s (group of mixed-resolution streams, bit-exact keypoints)",
-            "value": res["masked"]["frames_per_s"], "unit": "frames/s", "n_gpus": 1,
-            "steps": F - warm, "warmup": warm, "ms_per_step": res["masked"]["ms_per_tick"],
-            "higher_is_better": True, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": f"{len(streams)} streams ({per_res} each of 320x240, 640x480, "
-                                   f"1280x720, 1920x1080), O=4 + intra-octaves, one frame of each per tick, "
-                                   f"moving area U[5%,60%], {F} frames per stream resident in HBM",
-                       "mpix_per_tick": mpix},
-            "mpix_per_s": res["masked"]["frames_per_s"] / len(streams) * mpix,
-            "masked": res["masked"], "full_frame": res["full"],
-            "masked_c0": dict(res["masked_c0"], what="the intensity-difference test on c_0"),
-            "masked_over_full": res["masked"]["frames_per_s"] / res["full"]["frames_per_s"],
-            "describe": {"masked": res["masked_describe"], "full": res["full_describe"], "bits": 256,
-                         "masked_over_full": res["masked_describe"]["frames_per_s"] /
-                         res["full_describe"]["frames_per_s"],
-                         "what": "detection + description in the group (masked: new keypoints described, "
-                                 "carried ones copied; full: every keypoint described)"}}
+            "value": sub["masked"]["frames_per_s"], "unit": "frames/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "u8", "data": "synthetic", **sub}
+    if args.describe_groups:
+        clips, _ = gen_clips([(F, c.W, c.H, 1000 + 300 + j, c.source) for j, c in enumerate(cfgs)], torch, dev)
+        pattern = synth.descriptor_pattern(256)
+        segs = [("all", range(3, F))]
+        dm = group_workload(cfgs, clips, segs, 3, fkd.FKD_MASK_ID, fkd, torch, pattern=pattern, with_latency=False)
+        df = group_workload(cfgs, clips, segs, 3, fkd.FKD_MASK_FULL, fkd, torch, pattern=pattern, with_latency=False)
+        line["describe"] = {"masked": dm["segments"]["all"], "full": df["segments"]["all"], "bits": 256,
+                            "masked_over_full": dm["segments"]["all"]["frames_per_s"] /
+                            df["segments"]["all"]["frames_per_s"]}
     if not args.no_cpu_baseline:
-        # the oracle on the first frames of one stream per resolution (about
-        # 3 s each); the mix has equal counts per resolution
-        per_frame = []
-        for (W, H), (c, clip) in first_of_res.items():
-            fps_r, n_r, dt_r = cpu_oracle_fps(clip, c, seconds=3.0)
-            per_frame.append(1.0 / fps_r)
-        line["cpu_baseline"] = {"value": 1.0 / (sum(per_frame) / len(per_frame)), "unit": "frames/s",
-                                "cores": 1, "kind": "oracle",
-                                "sample": "first frames (about 3 s each) of one stream per resolution, "
-                                          "masked, one thread; frames/s of the equal-count mix"}
+        line["cpu_baseline"] = group_cpu_baseline(cfgs, heads, per_res=args.streams_per_res)
     print(json.dumps(line))
     return 0
 
 
+def group_cpu_baseline(cfgs, heads, per_res=16, seconds=3.0):
+    """The oracle on the first frames of one stream per resolution (about
+    `seconds` each): frames/s of the equal-count mix, one thread."""
+    per_frame = []
+    for j in range(0, len(cfgs), per_res):
+        fps_r, _, _ = cpu_oracle_fps(heads[j], cfgs[j], seconds=seconds)
+        per_frame.append(1.0 / fps_r)
+    return {"value": 1.0 / (sum(per_frame) / len(per_frame)), "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": "first frames (about 3 s each) of one stream per resolution, masked, one thread; "
+                      "frames/s of the equal-count mix"}
+
+
 def run_config5(args):
-    """8 streams of 3840x2160, 5 octaves: moving and static segments."""
+    """8 streams of 3840x2160 alone, as one JSON line."""
     import torch
     from paper_1503_06959_gb300 import fkd
-    cfg = synth.config5()
-    seg = args.segment
-    F = 2 * seg
-    n_streams = args.streams_5
-    frames_dev, clip0 = [], None
-    for j in range(n_streams):
-        src = synth.VideoSource(cfg.W, cfg.H, seed=1000 + 500 + j,
-                                **dict(cfg.source, static_segments=(seg, 0)))
-        clip = src.frames(F)
-        if j == 0:
-            clip0 = clip[:4]
-        frames_dev.append(torch.from_numpy(clip).cuda())
-    def run_pass(mode, ml, profile):
-        """One group through both segments: per segment the frames/s and tick
-        latencies (graph replays, no events) or, with `profile`, the stage
-        times (CUDA events around every kernel)."""
-        st = torch.cuda.Stream()
-        g = fkd.Group(cfg.O, cfg.intra, cuda_stream=st.cuda_stream)
-        ids = [g.add_stream(cfg.W, cfg.H, N_r=cfg.N_r, N_c=cfg.N_c, T_I=cfg.T_I, t=cfg.t,
-                            mask_mode=mode, mask_layer=ml, K_max=1 << 20)[0]
-               for _ in range(n_streams)]
-        g.profile_enable(profile)
-        segs = {}
-        for part, rng in (("moving", range(0, seg)), ("static", range(seg, F))):
-            g.synchronize()
-            g.profile_read()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            lat = []
-            first = rng[0] + (2 if part == "moving" else 0)
-            for n in rng:
-                if n == first:
-                    g.synchronize()
-                    g.profile_read()
-                    e0.record(st)
-                t0 = time.perf_counter()
-                g.tick(ids, [f[n] for f in frames_dev])
-                g.synchronize()
-                if n >= first:
-                    lat.append((time.perf_counter() - t0) * 1e3)
-            e1.record(st)
-            e1.synchronize()
-            prof = g.profile_read()
-            ticks = len(rng) - (first - rng[0])
-            if profile:
-                det_ms = prof["ms"]["detect"] / max(1, prof["batches"])
-                det_bytes = prof["tile_pixels"] / max(1, prof["batches"]) * 1.125
-                segs[part] = {"stage_ms_per_tick": {k: v / max(1, prof["batches"]) for k, v in prof["ms"].items()},
-                              "detect_hbm_gbs": det_bytes / (det_ms / 1e3) / 1e9 if det_ms else None,
-                              "tile_pixels_per_tick": prof["tile_pixels"] / max(1, prof["batches"])}
-            else:
-                sec = e0.elapsed_time(e1) / 1e3
-                segs[part] = {"frames_per_s": n_streams * ticks / sec,
-                              "tick_latency_ms_p50": float(np.percentile(lat, 50)),
-                              "tick_latency_ms_p99": float(np.percentile(lat, 99))}
-        g.close()
-        return segs
-
-    out = {}
-    for name, mode, ml in (("masked", fkd.FKD_MASK_ID, cfg.mask_layer), ("masked_c0", fkd.FKD_MASK_ID, 0),
-                           ("full", fkd.FKD_MASK_FULL, cfg.mask_layer)):
-        timed_segs, prof_segs = run_pass(mode, ml, False), run_pass(mode, ml, True)
-        out[name] = {part: dict(timed_segs[part], **prof_segs[part]) for part in timed_segs}
+    sub, cfg, heads = config5_workload(torch, fkd, torch.device("cuda", 0), seg=args.segment,
+                                       n_streams=args.streams_5)
     line = {"metric": "frames/s and tick latency (3840x2160 stress: moving vs static segments)",
-            "value": out["masked"]["moving"]["frames_per_s"], "unit": "frames/s", "n_gpus": 1,
-            "dtype": "u8", "data": "synthetic",
-            "config": {"workload": f"{n_streams} streams of 3840x2160, O=5 + intra-octaves, "
-                                   f"{seg} moving then {seg} static frames, N(0,2) noise"},
-            "masked": out["masked"], "full_frame": out["full"],
-            "masked_c0": dict(out["masked_c0"], what="the intensity-difference test on c_0")}
+            "value": sub["masked"]["moving"]["frames_per_s"], "unit": "frames/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "u8", "data": "synthetic", **sub}
     if not args.no_cpu_baseline:
-        fps_o, n_o, dt_o = cpu_oracle_fps(clip0, cfg, seconds=10.0)
+        fps_o, n_o, dt_o = cpu_oracle_fps(heads[0], cfg, seconds=10.0)
         line["cpu_baseline"] = {"value": fps_o, "unit": "frames/s", "cores": 1, "kind": "oracle",
                                 "sample": f"first {n_o} frames of stream 0 (moving segment), masked, "
                                           f"one thread, {dt_o:.1f} s"}
@@ -586,6 +735,7 @@ def run_config4(args):
         pool[(W, H)] = src.frames(args.pool)
     out = {}
     for name, mode in (("masked", fkd.FKD_MASK_ID), ("full", fkd.FKD_MASK_FULL)):
+        clocks = ClockSampler(0)
         srv = fkd.Server(4, 1, budget_bytes=args.budget_gb << 30, max_tick_keypoints=1 << 23)
         streams = []
         rejected = 0
@@ -658,7 +808,7 @@ def run_config4(args):
                      "frames_done": st["frames_done"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                      "max_ms": st["max_ms"], "mean_batch": st["mean_batch"], "ticks": st["ticks"],
                      "frames_refused_queue_full": refused[0], "results_truncated": truncated[0],
-                     "device_bytes": st["bytes_in_use"]}
+                     "device_bytes": st["bytes_in_use"], "clocks": clocks.stop()}
         srv.close()
     # admission under a small budget: streams of the mix, round robin, until
     # the budget refuses them; closing one frees room for the next
@@ -717,11 +867,15 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="threshold sweep of T_I and T_H on the 640x480 clip")
     ap.add_argument("--streams-per-res", type=int, default=16)
     ap.add_argument("--serve-streams-per-res", type=int, default=64)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window: 600 frames per stream at 30 fps")
     ap.add_argument("--pool", type=int, default=12)
     ap.add_argument("--budget-gb", type=int, default=8)
     ap.add_argument("--small-budget-mb", type=int, default=256)
-    ap.add_argument("--segment", type=int, default=20)
+    ap.add_argument("--segment", type=int, default=100)
+    ap.add_argument("--no-groups", action="store_true",
+                    help="default run: leave out the config 3 and config 5 sub-objects")
+    ap.add_argument("--describe-groups", action="store_true",
+                    help="--config 3: add detection + description in the group")
     ap.add_argument("--streams-5", type=int, default=8)
     ap.add_argument("--describe", default="", choices=["", "masked", "full", "both"],
                     help="detection + description on the 640x480 clip only (masked, full or both)")
@@ -831,12 +985,22 @@ def main():
     clk = clocks.stop() if clocks else None
     off_masked = offsets.cpu().numpy().astype(np.int64)
     kp_masked = int(off_masked[T] - off_masked[0])
-    act = masks.float().mean().item()
+    rec_masked = out[:kp_masked].cpu().numpy().view(fkd.KEYPOINT_DTYPE)
+    masks_np = masks.cpu().numpy()
+    act = float(masks_np.mean())
+    act_counter = ActiveBytes(cfg.W, cfg.H, cfg.O, cfg.intra, cfg.N_r, cfg.N_c)
+    act_bytes = sum(act_counter(m) for m in masks_np)  # per step (one launch of each kernel)
     _, prof = timed(masked, 0, 0, profile=True)
 
     ms_full, prof_full = timed(full, max(3, args.steps // 2), 3, profile=True)
     off_full = offsets.cpu().numpy().astype(np.int64)
     kp_full = int(off_full[T] - off_full[0])
+    rec_full = out[:kp_full].cpu().numpy().view(fkd.KEYPOINT_DTYPE)
+    # how much of full-frame detection the masked sets keep (a statistic of
+    # the method, not parity: each mode is bit-exact with its own oracle mode)
+    m_recall, m_precision = recall_precision(fkd.split_frames(rec_masked, off_masked),
+                                             fkd.split_frames(rec_full, off_full))
+    del rec_masked, rec_full
 
     # the same masked detection with the intensity test on c_0 (the library's
     # default layer) beside the coarsest octave (the paper's experiments)
@@ -933,7 +1097,8 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel (CUDA events around each launch)
+    # roofline of the dominant kernel (CUDA events around each launch, in the
+    # steps run with events after the timed ones; one launch per step)
     pk, pk_kind = peaks()
     stage_ms = prof["ms"]
     dom = max(stage_ms, key=stage_ms.get)
@@ -942,38 +1107,38 @@ def main():
     layer_px = sum(masked.layer_info(l)[0] * masked.layer_info(l)[1]
                    for l in range(masked.num_layers()))
     if dom == "detect":
-        # one input byte per pixel of each processed tile, one bitmap bit out
-        bytes_per_launch = prof["tile_pixels"] / launches * (1 + 1 / 8)
-        bytes_desc = "layer pixels of the processed detection tiles x (1 B read + 1/8 B bitmap)"
+        bytes_per_launch = act_bytes
+        bytes_desc = ("active bytes: layer pixels within 4 px (ring radius 3 + the suppression neighbour) "
+                      "of a pixel of an active bin, every layer of every frame of the step, 1 byte read each; "
+                      "counted from the step's masks")
     elif dom == "pyramid":
-        bytes_per_launch = prof["frames"] / launches * (2 * cfg.W * cfg.H + (layer_px - cfg.W * cfg.H))
-        bytes_desc = "per frame: c0 of I_n and I_{n-1} read, layers >= 1 written"
+        bytes_per_launch = prof["frames"] / launches * (cfg.W * cfg.H + (layer_px - cfg.W * cfg.H))
+        bytes_desc = "per frame: c_0 read, layers >= 1 written"
     else:
         bytes_per_launch = prof["frames"] / launches * layer_px / 8 * 2
         bytes_desc = "per frame: keypoint bitmap words read and written"
     achieved = bytes_per_launch / dur_s / 1e9
     counters = profile_counters(dom, shape_masked) if T == cfg.frames else None
-    hbm = {"achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-           "frac": achieved / pk["hbm_gbs"], "peak_source": f"{pk_kind} hbm_gbs",
-           "bytes_per_launch": bytes_per_launch, "bytes": bytes_desc}
-    traffic = counters.get("traffic_bytes_per_launch") if counters else None
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "peak_source": f"{pk_kind} hbm_gbs",
+            "traffic": counters.get("traffic_bytes_per_launch") if counters else None,
+            "bytes_per_launch": bytes_per_launch, "bytes": bytes_desc, "launch_ms": dur_s * 1e3,
+            "processed_tile_pixels_per_launch": prof["tile_pixels"] / launches if dom == "detect" else None}
     alu_inst = counters.get("alu_warp_inst_per_launch") if counters else None
-    if alu_inst:
-        # integer ALU pipe: 2 warp instructions per clock per SM (measured with a
-        # throughput probe of IADD3 / PRMT / 16-bit min-max), 152 SMs, max SM clock
-        sm_clk = pk.get("sm_max_mhz", 2070.0) * 1e6
-        peak_alu = 152 * 2 * sm_clk / 1e9
+    alu_rate = counters.get("alu_peak_warp_inst_per_sm_cycle") if counters else None
+    if alu_inst and alu_rate and clk and clk.get("sm_mhz"):
+        # the integer ALU pipe: warp instructions the kernel issued to it
+        # (ncu smsp__inst_executed_pipe_alu.sum) per launch duration, against
+        # the pipe's issue rate per SM and cycle (ncu
+        # sm__inst_executed_pipe_alu.avg.peak_sustained) x SMs x the median SM
+        # clock sampled during the timed steps
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_alu = n_sm * alu_rate * clk["sm_mhz"] * 1e6 / 1e9
         ach_alu = alu_inst / dur_s / 1e9
-        roof = {"kernel": dom, "bound": "alu", "achieved": ach_alu, "peak": peak_alu,
-                "unit": "G warp-instructions/s (integer ALU pipe)", "frac": ach_alu / peak_alu,
-                "traffic": traffic, "alu_warp_inst_per_launch": alu_inst,
-                "peak_source": "152 SMs x 2 ALU warp-instructions/clk x sm_max_mhz",
-                "launch_ms": dur_s * 1e3, "hbm": hbm}
-    else:
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-                "peak_source": f"{pk_kind} hbm_gbs", "bytes_per_launch": bytes_per_launch,
-                "bytes": bytes_desc, "launch_ms": dur_s * 1e3}
+        roof["alu"] = {"achieved": ach_alu, "peak": peak_alu, "unit": "G warp-instructions/s (integer ALU pipe)",
+                       "frac": ach_alu / peak_alu, "alu_warp_inst_per_launch": alu_inst,
+                       "peak_source": f"{n_sm} SMs x {alu_rate} ALU warp-instructions/cycle/SM (ncu peak_sustained) "
+                                      f"x {clk['sm_mhz']:.0f} MHz (median sampled)"}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -996,6 +1161,10 @@ def main():
                        "stage_ms_per_step": {k: v / max(1, prof_full["batches"])
                                              for k, v in prof_full["ms"].items()}},
         "masked_over_full": value / full_fps,
+        "masked_recall": {"recall": m_recall, "precision": m_precision,
+                          "what": "mean over frames of |D_n and F_n| / |F_n| (recall) and / |D_n| (precision), "
+                                  "D_n masked, F_n full-frame detection, over (layer, y, x)"},
+        "active_bytes_per_step": act_bytes,
         "masked_c0": {"value": c0_fps, "unit": "frames/s", "active_bin_fraction": act_c0,
                       "masked_over_full": c0_fps / full_fps, "launch_shape": shape_c0,
                       "what": "the intensity-difference test on c_0 instead of the coarsest octave",
@@ -1034,6 +1203,11 @@ def main():
         "cpu_baseline": cpu,
         "wall_s_timed_region": t_wall,
     }
+    if world == 1 and not args.no_groups:
+        # the batched and the stress workloads at their stated sizes, each with
+        # its own clock record (one GPU: under torchrun only the clip runs)
+        line["config3"], _, _ = config3_workload(torch, fkd, dev)
+        line["config5"], _, _ = config5_workload(torch, fkd, dev)
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

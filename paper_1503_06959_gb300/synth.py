@@ -173,6 +173,20 @@ def source_for(cfg: StreamConfig, config_id: int, stream: int = 0) -> VideoSourc
     return VideoSource(cfg.W, cfg.H, seed=1000 + 100 * config_id + stream, **cfg.source)
 
 
+def fill_shared(name: str, count: int, W: int, H: int, seed: int, source: dict) -> None:
+    """Write the first `count` frames of the stream VideoSource(W, H, seed,
+    **source) into the existing shared-memory block `name` (count x H x W
+    uint8), so that several processes can generate streams in parallel."""
+    from multiprocessing import shared_memory
+    shm = shared_memory.SharedMemory(name=name)  # the creating process unlinks it
+    arr = np.ndarray((count, H, W), np.uint8, buffer=shm.buf)
+    src = VideoSource(W, H, seed=seed, **source)
+    for n in range(count):
+        arr[n] = src.frame(n)
+    del arr
+    shm.close()
+
+
 DESC_RADIUS = 13  # largest |offset| of a descriptor sample the library accepts
 
 
