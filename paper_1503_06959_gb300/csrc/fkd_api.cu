@@ -73,11 +73,13 @@ struct fkd_stream {
   uint32_t* wbins = nullptr;
   uint32_t* wmask = nullptr;
   int* rowchunk = nullptr;
+  int* rowcell = nullptr;
 
   Scratch s{};
   uint32_t* state_bits[2] = {nullptr, nullptr};
   uint8_t* state_score[2] = {nullptr, nullptr};
   uint32_t* state_cnt[2] = {nullptr, nullptr};
+  uint32_t* state_kcnt[2] = {nullptr, nullptr};  // keypoints of the kept set per cell
   int state_cur = 0;
 
   uint8_t* staging[2] = {nullptr, nullptr};
@@ -227,8 +229,9 @@ int build_geometry(fkd_stream* s, int W, int H) {
   std::vector<DetTile> tiles[kDetShapes];
   std::vector<AsmChunk> chunks;
   std::vector<uint32_t> wbins, wmask;
-  std::vector<int> rowchunk;
+  std::vector<int> rowchunk, rowcell;
   long long pyr = 0, score = 0, bits = 0;
+  int cells = 0;
   for (int l = 0; l < g.L; ++l) {
     LayerGeom& lg = g.layer[l];
     layer_dims(W, H, p.intra, l, &lg.w, &lg.h, &lg.S);
@@ -267,15 +270,25 @@ int build_geometry(fkd_stream* s, int W, int H) {
         if (colblk[lg.col_off + x] == c0) m |= 1u << (x - 32 * wx);
       wmask.push_back(m);
     }
-    // assembly chunks: bands of whole rows, about kAsmChunkWords words each
+    // assembly chunks: bands of whole rows, about kAsmChunkWords words each;
+    // a chunk's cells are its parts in the bins of the bin rows it spans
     if (lg.wpr > 0) {
       const int rows = std::max(1, kAsmChunkWords / lg.wpr);
       for (int y0 = 0; y0 < lg.h; y0 += rows) {
-        for (int y = y0; y < std::min(lg.h, y0 + rows); ++y) rowchunk.push_back((int)chunks.size());
-        chunks.push_back(AsmChunk{l, y0, std::min(lg.h, y0 + rows)});
+        const int y1 = std::min(lg.h, y0 + rows);
+        const int rb0 = rowblk[lg.row_off + y0], rb1 = rowblk[lg.row_off + y1 - 1];
+        for (int y = y0; y < y1; ++y) {
+          rowchunk.push_back((int)chunks.size());
+          rowcell.push_back(cells + (rowblk[lg.row_off + y] - rb0) * p.N_c);
+        }
+        chunks.push_back(AsmChunk{l, y0, y1, cells, rb0, rb1});
+        cells += (rb1 - rb0 + 1) * p.N_c;
       }
     } else {
-      for (int y = 0; y < lg.h; ++y) rowchunk.push_back(0);
+      for (int y = 0; y < lg.h; ++y) {
+        rowchunk.push_back(0);
+        rowcell.push_back(0);
+      }
     }
     // detection tiles of every shape: kDetTW x TH rectangles, row-major
     for (int k = 0; k < kDetShapes && lg.w > 0 && lg.h > 0; ++k) {
@@ -308,6 +321,7 @@ int build_geometry(fkd_stream* s, int W, int H) {
   g.det_shape = kDetDefaultShape;
   g.n_tiles = s->n_tiles_shape[g.det_shape];
   g.n_chunks = (int)chunks.size();
+  g.n_cells = cells;
   g.pyr_tiles_x = (W + kPyrTile - 1) / kPyrTile;
   g.pyr_tiles_y = (H + kPyrTile - 1) / kPyrTile;
 
@@ -322,8 +336,10 @@ int build_geometry(fkd_stream* s, int W, int H) {
       (rc = s->alloc(&s->xstart, xstart.size())) || (rc = s->alloc(&s->npix, npix.size())) ||
       (rc = s->alloc(&s->tile_shape[0], all_tiles)) || (rc = s->alloc(&s->chunks, chunks.size())) ||
       (rc = s->alloc(&s->wbins, wbins.size())) || (rc = s->alloc(&s->wmask, wmask.size())) ||
-      (rc = s->alloc(&s->rowchunk, rowchunk.size())))
+      (rc = s->alloc(&s->rowchunk, rowchunk.size())) || (rc = s->alloc(&s->rowcell, rowcell.size())))
     return rc;
+  if (!rowcell.empty())
+    CK(cudaMemcpy(s->rowcell, rowcell.data(), rowcell.size() * sizeof(int), cudaMemcpyHostToDevice));
   if (!rowchunk.empty())
     CK(cudaMemcpy(s->rowchunk, rowchunk.data(), rowchunk.size() * sizeof(int), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->wmask, wmask.data(), wmask.size() * 4, cudaMemcpyHostToDevice));
@@ -355,6 +371,7 @@ int allocate_state(fkd_stream* s) {
       (rc = s->alloc(&sc.det_bits, (size_t)(T * std::max(g.bit_words, 1LL)))) ||
       (rc = s->alloc(&sc.det_score, (size_t)(T * g.score_bytes))) ||
       (rc = s->alloc(&sc.chunk_counts, (size_t)(T * std::max(g.n_chunks, 1)))) ||
+      (rc = s->alloc(&sc.dcnt, (size_t)(T * std::max(g.n_cells, 1)))) ||
       (rc = s->alloc(&sc.merged, (size_t)(T * std::max(g.bit_words, 1LL)))) ||
       (rc = s->alloc(&sc.bases, (size_t)(T + 1))) || (rc = s->alloc(&sc.done, 1)) ||
       (rc = s->alloc(&sc.frame_totals, (size_t)T)) || (rc = s->alloc(&sc.out_base, 2)) ||
@@ -372,10 +389,12 @@ int allocate_state(fkd_stream* s) {
   for (int i = 0; i < 2; ++i) {
     if ((rc = s->alloc(&s->state_bits[i], (size_t)std::max(g.bit_words, 1LL))) ||
         (rc = s->alloc(&s->state_score[i], (size_t)g.score_bytes)) ||
-        (rc = s->alloc(&s->state_cnt[i], (size_t)g.NB)))
+        (rc = s->alloc(&s->state_cnt[i], (size_t)g.NB)) ||
+        (rc = s->alloc(&s->state_kcnt[i], (size_t)std::max(g.n_cells, 1))))
       return rc;
     CK(cudaMemset(s->state_bits[i], 0, (size_t)std::max(g.bit_words, 1LL) * 4));
     CK(cudaMemset(s->state_cnt[i], 0, (size_t)g.NB * 4));
+    CK(cudaMemset(s->state_kcnt[i], 0, (size_t)std::max(g.n_cells, 1) * 4));
   }
   CK(cudaMemset(sc.bsum, 0, (size_t)(T * g.NB) * 8));
   sc.bsum_stride = (int)T;
@@ -402,7 +421,8 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   b.prev_pitch = s->prev_pitch;
   b.c0_vec = 0;
   Params pr{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode, s->p.nms_scale};
-  Tables tb{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask, s->rowchunk};
+  Tables tb{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask, s->rowchunk,
+            s->rowcell};
   State stt{};
   stt.bits_in = s->state_bits[s->state_cur];
   stt.score_in = s->state_score[s->state_cur];
@@ -410,6 +430,8 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   stt.bits_out = s->state_bits[s->state_cur ^ 1];
   stt.score_out = s->state_score[s->state_cur ^ 1];
   stt.cnt_out = s->state_cnt[s->state_cur ^ 1];
+  stt.kcnt_in = s->state_kcnt[s->state_cur];
+  stt.kcnt_out = s->state_kcnt[s->state_cur ^ 1];
   Output o{out, cap, offsets, base_slot};
   if (s->desc_D) {
     o.row_base = s->desc_rows;
@@ -436,7 +458,7 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   if (pr.nms_scale) launch_scale_nms(s->g, tb, b, s->s, pr, s->st);
   mark(4);
   if (s->s.pmask) launch_count_pixel(s->g, tb, b, s->s, stt, s->st);  // its last CTA fills bases
-  else launch_count(s->g, tb, b, s->s, stt, s->st);                   // its last CTA fills s->s.bases
+  else launch_offsets(s->g, tb, b, s->s, stt, s->st);                 // its last CTA fills s->s.bases
   mark(5);
   launch_emit(s->g, tb, b, s->s, stt, o, s->st);
   mark(6);
@@ -1120,7 +1142,8 @@ StreamDev make_dev(const fkd_stream* s, const GroupStream& gs) {
   uint8_t* const* last = gs.last;
   StreamDev d{};
   d.g = s->g;
-  d.tb = Tables{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask, s->rowchunk};
+  d.tb = Tables{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask, s->rowchunk,
+                s->rowcell};
   d.s = s->s;
   d.s.bases = nullptr;  // group ticks (one frame) compute their offsets in place
   d.p = Params{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode, s->p.nms_scale};
@@ -1128,6 +1151,7 @@ StreamDev make_dev(const fkd_stream* s, const GroupStream& gs) {
     d.state_bits[i] = s->state_bits[i];
     d.state_score[i] = s->state_score[i];
     d.state_cnt[i] = s->state_cnt[i];
+    d.state_kcnt[i] = s->state_kcnt[i];
     d.last[i] = last[i];
   }
   d.rec[0] = s->rec;
@@ -1167,7 +1191,7 @@ int group_launch(fkd_group* G, int b, int n_items, fkd_stream::Pending* pd) {
   if (G->any_nms_scale)
     launch_group_scale_nms(G->d_devs, G->d_items, G->d_work, G->d_work_count, G->st);
   mark(4);
-  launch_group_count(G->d_devs, G->d_hdr, G->d_items, G->grid_asm, G->st);
+  launch_group_offsets(G->d_devs, G->d_hdr, G->d_items, G->grid_small, G->st);
   mark(5);
   launch_group_emit(G->d_devs, G->d_hdr, G->d_items, G->grid_asm, G->st);
   mark(6);

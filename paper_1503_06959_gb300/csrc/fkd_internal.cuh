@@ -87,12 +87,16 @@ struct Geometry {
   int n_tiles;            // detection tiles per frame (current tile shape)
   int det_shape;          // current tile shape (index into kDetTH)
   int n_chunks;           // assembly chunks per frame
+  int n_cells;            // (chunk, bin) cells per frame
   int pyr_tiles_x, pyr_tiles_y;
 };
 
-// One assembly chunk: rows y0 .. y1-1 of one layer.
+// One assembly chunk: rows y0 .. y1-1 of one layer, spanning bin rows
+// rb0 .. rb1. Its cells -- the parts of the chunk inside one bin each --
+// are numbered cell0 + (r - rb0) * N_c + c for bin (r, c).
 struct AsmChunk {
   int layer, y0, y1;
+  int cell0, rb0, rb1;
 };
 
 // One detection tile: a kDetTW x kDetTH[shape] rectangle of one layer, its
@@ -114,6 +118,7 @@ struct Tables {
   const uint32_t* wbins;   // per layer, per bitmap word column: first | last bin column << 16
   const uint32_t* wmask;   // per layer, per bitmap word column: bits of the word in its first bin
   const int* rowchunk;     // per layer, per y: the assembly chunk holding the row
+  const int* rowcell;      // per layer, per y: cell of (the row's chunk, bin row, bin column 0)
 };
 
 // Arguments of one batch of T consecutive frames of one stream.
@@ -144,7 +149,9 @@ struct Scratch {
   uint32_t* work_count;            // [1]
   uint32_t* det_bits;              // [T_max][bit_words]
   uint8_t* det_score;              // [T_max][score_bytes]
-  uint32_t* chunk_counts;          // [T_max][n_chunks]
+  uint32_t* chunk_counts;          // [T_max][n_chunks]: records of each chunk (per-pixel masks), or
+                                   //   records of the frame before the chunk (bin masks)
+  uint32_t* dcnt;                  // [T_max][n_cells]: detections of each frame in each cell
   uint32_t* merged;                // [T_max][bit_words]: D_n bitmap of every frame of the batch
   uint32_t* bases;                 // [T_max + 1]: records of the batch before each frame, then the total
   uint32_t* done;                  // [1]: chunks counted (last-CTA scan)
@@ -162,9 +169,11 @@ struct State {
   const uint32_t* bits_in;
   const uint8_t* score_in;
   const uint32_t* cnt_in;          // keypoints per bin (for keypoint binning)
+  const uint32_t* kcnt_in;         // keypoints per cell
   uint32_t* bits_out;
   uint8_t* score_out;
   uint32_t* cnt_out;
+  uint32_t* kcnt_out;
 };
 
 struct Output {
@@ -216,6 +225,7 @@ struct StreamDev {
   uint32_t* state_bits[2];
   uint8_t* state_score[2];
   uint32_t* state_cnt[2];
+  uint32_t* state_kcnt[2];
   uint8_t* last[2];          // copies of the stream's last two frames (c_0, pitch layer[0].pitch)
   fkd_keypoint* rec[2];      // D_n of frame n in rec[n & 1] (K_max records each)
   uint32_t* rec_offsets[2];  // [2] each: 0 and |D_n|
@@ -256,8 +266,8 @@ void launch_group_worklist(const StreamDev* devs, const TickHeader* hdr, const T
                            uint32_t* work, uint32_t* work_count, int grid, cudaStream_t st);
 void launch_group_detect(const StreamDev* devs, const TickItem* items, const uint32_t* work,
                          const uint32_t* work_count, const DetLaunch& dl, cudaStream_t st);
-void launch_group_count(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
-                        int grid, cudaStream_t st);
+void launch_group_offsets(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
+                          int grid, cudaStream_t st);
 void launch_group_emit(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
                        int grid, cudaStream_t st);
 
@@ -299,6 +309,11 @@ void launch_detect(const Geometry& g, const Tables& tb, const Batch& b, const Sc
                    const Params& p, const DetLaunch& dl, cudaStream_t st);
 void launch_count(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                   const State& state, cudaStream_t st);
+// Bin masks: the records of every (frame, chunk) from the detection counts
+// per cell, the source frames and the kept set's counts (no pass over the
+// bitmaps); also the kept counts of the batch's last frame.
+void launch_offsets(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
+                    const State& state, cudaStream_t st);
 void launch_emit(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                  const State& state, const Output& out, cudaStream_t st);
 // FKD_MASK_IDP: per-pixel masks of every layer of the batch (Eq. 2 per

@@ -7,13 +7,19 @@
 // the frame src(k, bin) -- the last frame up to k in which the bin was active
 // -- or from the kept set D_{n0-1} when the bin was inactive since the batch
 // began. Work is cut into chunks of whole rows of one layer, so a CTA knows
-// its layer and each row's bin row up front.
-//   k_count: merge each word from its sources, store it, and sum the
-//            popcounts per chunk and per frame;
-//   k_emit:  turn chunk counts and frame totals into output offsets, scan the
-//            chunk's stored words, and write one record per set bit, in order.
+// its layer and each row's bin row up front. A chunk's parts inside one bin
+// each are its cells.
+//   k_offsets (bin masks): the records of cell c of frame k are the detections
+//            the detection pass counted in cell c of frame src(k, bin(c)), or
+//            the kept set's count of cell c; their sums give every chunk's
+//            first record and every frame's total without reading a bitmap;
+//            the last frame's counts become the kept set's;
+//   k_count  (per-pixel masks): merge each word from its sources, store it,
+//            and sum the popcounts per chunk and per frame;
+//   k_emit:  merge (or load) the chunk's words, scan their popcounts, and
+//            write one record per set bit, in order.
 // The last frame of the batch also becomes the new kept set (bitmap, scores,
-// keypoints per bin).
+// keypoints per bin and per cell).
 #include "fkd_internal.cuh"
 
 namespace fkd {
@@ -140,6 +146,101 @@ __device__ __forceinline__ void count_chunk(const Geometry& g, const Tables& tb,
   __syncthreads();  // red and last_cta are reused by the next chunk of this CTA
 }
 
+// Records of every chunk of frame k (bin masks) from the per-cell counts:
+// cell c of bin b holds the detections of frame src(k, b) there, or the kept
+// set's when src < 0. The CTA writes, in chunk_counts, the frame's records
+// before each chunk (exclusive scan) and its total in frame_totals[k]; for the
+// batch's last frame (`last`) it also stores the counts as the new kept
+// set's and adds them up per bin for keypoint binning (Eqs. 3-4). With
+// s.bases, the CTA that finishes last of `total_ctas` turns the frame totals
+// into record offsets. Ends with a barrier.
+__device__ __forceinline__ void offsets_frame(const Geometry& g, const Tables& tb, const Scratch& s, const State& st,
+                                              int k, bool last, int T, int total_ctas) {
+  __shared__ uint32_t wsum[kAsmThreads / 32];
+  __shared__ uint32_t carry_sh;
+  __shared__ int last_cta;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int* src_k = s.src + (long long)k * g.NB;
+  uint32_t* cc = s.chunk_counts + (long long)k * g.n_chunks;
+  // one warp per chunk: the sum of its cells
+  for (int c = wid; c < g.n_chunks; c += kAsmThreads / 32) {
+    const AsmChunk ch = tb.chunks[c];
+    const int ncell = (ch.rb1 - ch.rb0 + 1) * g.N_c;
+    uint32_t sum = 0;
+    for (int i = lane; i < ncell; i += 32) {
+      const int r = ch.rb0 + i / g.N_c, col = i - (i / g.N_c) * g.N_c;
+      const int bin = r * g.N_c + col, cell = ch.cell0 + i;
+      const int sf = src_k[bin];
+      const uint32_t v = sf < 0 ? st.kcnt_in[cell] : s.dcnt[(long long)sf * g.n_cells + cell];
+      if (last) {
+        st.kcnt_out[cell] = v;
+        if (v) atomicAdd(&st.cnt_out[bin], v);
+      }
+      sum += v;
+    }
+    sum = __reduce_add_sync(0xffffffffu, sum);
+    if (lane == 0) cc[c] = sum;
+  }
+  __syncthreads();
+  // exclusive scan of the chunk counts in place, 256 at a time
+  if (threadIdx.x == 0) carry_sh = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < g.n_chunks; c0 += kAsmThreads) {
+    const int c = c0 + threadIdx.x;
+    const uint32_t v = c < g.n_chunks ? cc[c] : 0u;
+    uint32_t incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += o;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    uint32_t before = carry_sh, total = 0;
+#pragma unroll
+    for (int q = 0; q < kAsmThreads / 32; ++q) {
+      before += q < wid ? wsum[q] : 0u;
+      total += wsum[q];
+    }
+    if (c < g.n_chunks) cc[c] = before + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_sh += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    s.frame_totals[k] = carry_sh;
+    bool lastc = false;
+    if (s.bases) {
+      __threadfence();
+      lastc = atomicAdd(s.done, 1u) == (unsigned)(total_ctas - 1);
+    }
+    last_cta = lastc;
+  }
+  __syncthreads();
+  if (last_cta && threadIdx.x < 32) {
+    // exclusive scan of the frame totals, 32 at a time
+    __threadfence();
+    uint32_t carry = 0;
+    for (int e0 = 0; e0 < T; e0 += 32) {
+      const int e = e0 + lane;
+      const uint32_t c = e < T ? __ldcg(&s.frame_totals[e]) : 0u;
+      uint32_t incl = c;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+      }
+      if (e < T) s.bases[e] = carry + incl - c;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) {
+      s.bases[T] = carry;
+      *s.done = 0u;
+    }
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb, const Scratch& s,
                                              const State& st, const Output& out, int k, bool last,
                                              const AsmChunk& ch, const LayerGeom& lg, int j0,
@@ -163,7 +264,17 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
 
   // offsets: base of this call + earlier frames + earlier chunks of this frame
   uint32_t frame_base, chunk_base;
-  if (s.bases) {
+  if (!s.pmask) {
+    // bin masks: the offsets pass stored the records before the chunk
+    chunk_base = s.chunk_counts[(long long)k * g.n_chunks + chunk];
+    if (s.bases) {
+      frame_base = s.bases[k];
+    } else {
+      uint32_t part = 0;
+      for (int q = threadIdx.x; q < k; q += kAsmThreads) part += s.frame_totals[q];
+      frame_base = block_sum(part, red);
+    }
+  } else if (s.bases) {
     // warp 0 sums the earlier chunks of this frame (few) and shares it
     if (threadIdx.x < 32) {
       uint32_t part = 0;
@@ -192,13 +303,29 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
     }
   }
 
-  // the chunk's words, loaded coalesced into shared memory; each thread then
-  // takes 8 contiguous ones, so the scan order is the canonical order
+  // the chunk's words -- merged here from their source frames (bin masks)
+  // or loaded (per-pixel masks: merged by the per-pixel recurrence) -- into
+  // shared memory, coalesced; each thread then takes 8 contiguous ones, so
+  // the scan order is the canonical order
   const uint32_t* merged = s.merged + (long long)k * g.bit_words + word0;
+  const int* src_kw = s.src + (long long)k * g.NB;
+  const int* xst = tb.xstart + lg.xs_off;
+  const float inv_wpr_m = 1.0f / (float)wpr;
 #pragma unroll
   for (int jj = 0; jj < kAsmWordsPerThread; ++jj) {
     const int j = threadIdx.x + jj * kAsmThreads;
-    const uint32_t v = j < nwords ? merged[j] : 0u;
+    uint32_t v = 0u;
+    if (j < nwords) {
+      if (s.pmask) {
+        v = merged[j];
+      } else {
+        int yy = __float2int_rz((float)j * inv_wpr_m);  // j / wpr, fixed up below
+        if (yy * wpr > j) --yy;
+        if ((yy + 1) * wpr <= j) ++yy;
+        const int* srcrow = src_kw + tb.rowblk[lg.row_off + ch.y0 + yy] * g.N_c;
+        v = merge_word(g, tb, s, st, lg, xst, srcrow, word0, j, j - yy * wpr);
+      }
+    }
     stage_words[j] = v;
     if (last && j < nwords) st.bits_out[word0 + j] = v;
   }
@@ -309,7 +436,7 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
     }
     if (last) {
       st.score_out[so] = score;
-      atomicAdd(&st.cnt_out[r * g.N_c + c], 1u);
+      if (s.pmask) atomicAdd(&st.cnt_out[r * g.N_c + c], 1u);  // bin masks: counted by the offsets pass
     }
   }
   __syncthreads();  // red, wsum and pos are reused by the next chunk of this CTA
@@ -356,7 +483,7 @@ __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb
         ++idx;
         if (last) {
           st.score_out[row_off + x] = score;
-          atomicAdd(&st.cnt_out[r * g.N_c + c], 1u);
+          if (s.pmask) atomicAdd(&st.cnt_out[r * g.N_c + c], 1u);  // bin masks: counted by the offsets pass
         }
       }
     }
@@ -369,6 +496,10 @@ __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb
 
 __global__ void __launch_bounds__(kAsmThreads) k_count(Geometry g, Tables tb, Scratch s, State st, int T) {
   count_chunk(g, tb, s, st, blockIdx.y, blockIdx.x, T, gridDim.x * gridDim.y);
+}
+
+__global__ void __launch_bounds__(kAsmThreads) k_offsets(Geometry g, Tables tb, Scratch s, State st, int T) {
+  offsets_frame(g, tb, s, st, blockIdx.x, blockIdx.x == T - 1, T, gridDim.x);
 }
 
 __global__ void __launch_bounds__(kAsmThreads) k_emit(Geometry g, Tables tb, Batch b, Scratch s,
@@ -384,18 +515,20 @@ __device__ __forceinline__ State state_of(const StreamDev& d, int cur) {
   st.bits_out = d.state_bits[cur ^ 1];
   st.score_out = d.state_score[cur ^ 1];
   st.cnt_out = d.state_cnt[cur ^ 1];
+  st.kcnt_in = d.state_kcnt[cur];
+  st.kcnt_out = d.state_kcnt[cur ^ 1];
   return st;
 }
 
-// Group tick: persistent CTAs over the chunks of every participating frame.
-__global__ void __launch_bounds__(kAsmThreads) k_group_count(const StreamDev* devs, const TickHeader* hdr,
-                                                             const TickItem* items) {
-  const int n = hdr->n_items, total = hdr->total_chunks;
-  for (int j = blockIdx.x; j < total; j += gridDim.x) {
-    const int i = find_item(n, j, [&](int q) { return items[q].chunk_base; });
+// Group tick: persistent CTAs over the participating frames (one frame of
+// each stream): the records of each chunk from the per-cell counts.
+__global__ void __launch_bounds__(kAsmThreads) k_group_offsets(const StreamDev* devs, const TickHeader* hdr,
+                                                               const TickItem* items) {
+  const int n = hdr->n_items;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const TickItem it = items[i];
     const StreamDev& d = devs[it.sid];
-    count_chunk(d.g, d.tb, d.s, state_of(d, it.state_cur), 0, j - it.chunk_base, 1, 0);
+    offsets_frame(d.g, d.tb, d.s, state_of(d, it.state_cur), 0, true, 1, 0);
   }
 }
 
@@ -418,9 +551,9 @@ __global__ void __launch_bounds__(kAsmThreads) k_group_emit(const StreamDev* dev
 
 }  // namespace
 
-void launch_group_count(const StreamDev* devs, const TickHeader* hdr, const TickItem* items, int grid,
-                        cudaStream_t st) {
-  k_group_count<<<grid, kAsmThreads, 0, st>>>(devs, hdr, items);
+void launch_group_offsets(const StreamDev* devs, const TickHeader* hdr, const TickItem* items, int grid,
+                          cudaStream_t st) {
+  k_group_offsets<<<grid, kAsmThreads, 0, st>>>(devs, hdr, items);
 }
 
 void launch_group_emit(const StreamDev* devs, const TickHeader* hdr, const TickItem* items, int grid,
@@ -431,6 +564,11 @@ void launch_group_emit(const StreamDev* devs, const TickHeader* hdr, const TickI
 void launch_count(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                   const State& state, cudaStream_t st) {
   k_count<<<dim3(g.n_chunks, b.T), kAsmThreads, 0, st>>>(g, tb, s, state, b.T);
+}
+
+void launch_offsets(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
+                    const State& state, cudaStream_t st) {
+  k_offsets<<<b.T, kAsmThreads, 0, st>>>(g, tb, s, state, b.T);
 }
 
 void launch_emit(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,

@@ -41,7 +41,6 @@ constexpr int IN_W = TW + 32;  // input row: x in [x0-16, x0+TW+16)
 constexpr int SC_P = TW + 8;   // score row pitch; column = x - x0 + 4
 constexpr int RING = 256;      // candidate pixels waiting to be scored, per warp (power of two)
 constexpr int PASS = 256;      // passing-pixel list per warp (entries); beyond it the pass bitmap is scanned
-constexpr int NBUF = 1;        // input buffers per warp (2: the next tile loads during this one; no gain measured)
 constexpr int MIN_BLOCKS = 2;  // 256-thread CTAs resident per SM the register budget is sized for
 static_assert(TW == 32 * 4, "one 4-pixel word per lane per row");
 static_assert(RING >= 64 + 128 && (RING & (RING - 1)) == 0, "a round leaves < 64, an expansion adds <= 128");
@@ -57,8 +56,7 @@ struct Shape {
   static constexpr int WLIST = (SC_H * 34 + 7) / 8 * 8;  // candidate words: 32 per score row + 2 edge words
   // input buffer(s), score map, keypoint and pass bitmaps, candidate words,
   // candidate ring and pass list
-  static constexpr int WARP_SMEM =
-      NBUF * IN_BYTES + SC_BYTES + 2 * DET_WORDS * 4 + WLIST * 4 + RING * 2 + PASS * 2;
+  static constexpr int WARP_SMEM = IN_BYTES + SC_BYTES + 2 * DET_WORDS * 4 + WLIST * 4 + RING * 2 + PASS * 2;
   static_assert(TH % 8 == 0 && TH + 4 <= 32, "one lane per dilated score row; whole 32-word rounds");
   static_assert(IN_BYTES % 16 == 0 && SC_BYTES % 16 == 0, "16-byte aligned slices");
 };
@@ -140,7 +138,37 @@ struct Item {
   const uint16_t* rowblk;    // bin row of each layer row
   int N_c;
   const uint32_t* pmask;     // per-pixel mask of the layer (row 0; FKD_MASK_IDP), else null
+  uint32_t* dcnt;            // the frame's detections per cell (bin masks), else null
+  const int* rowcell;        // the layer's first cell of each row
+  const uint32_t* wbins;     // the layer's bin columns of each bitmap word column
+  const uint32_t* wmask;     // the layer's bits of each word column in its first bin
+  const int* xstart;         // the layer's first column of each bin column
 };
+
+// Add (sign = 1) or remove (sign = -1) the detections of bitmap word `word`,
+// word column wx of a row whose cells start at `cells`, to the counts of the
+// cells its pixels lie in: words inside one or two bin columns split by the
+// precomputed mask, wider ones (coarse layers, narrow bins) walk their bins.
+__device__ __forceinline__ void count_word(uint32_t* cells, uint32_t word, int wx, int w, const uint32_t* wbins,
+                                           const uint32_t* wmask, const int* xstart, int sign) {
+  const uint32_t wb = wbins[wx];
+  const int c_lo = wb & 0xffffu, c_hi = wb >> 16;
+  if (c_hi - c_lo <= 1) {
+    const uint32_t m = wmask[wx];
+    const int n0 = __popc(word & m), n1 = __popc(word & ~m);
+    if (n0) atomicAdd(cells + c_lo, (uint32_t)(sign * n0));
+    if (n1) atomicAdd(cells + c_hi, (uint32_t)(sign * n1));
+    return;
+  }
+  const int xlo = wx * 32, xhi = min(xlo + 32, w);
+  for (int c = c_lo; c <= c_hi; ++c) {
+    const int a = max(xstart[c], xlo) - xlo, e = min(xstart[c + 1], xhi) - xlo;
+    if (e <= a) continue;
+    const uint32_t m = (e - a == 32) ? 0xffffffffu : (((1u << (e - a)) - 1u) << a);
+    const int n = __popc(word & m);
+    if (n) atomicAdd(cells + c, (uint32_t)(sign * n));
+  }
+}
 
 // One layer of a frame, for the scale-space suppression. Its scale code S
 // is 2^sh or 3 * 2^sh (sh >= 1 or the 3 alone), so n / (2 S) is a shift and
@@ -163,6 +191,12 @@ struct ScaleItem {
   const uint8_t* dscore;
   int dpitch;
   LayerView adj[2];     // the layers just below and above in scale
+  int w;                // layer width
+  uint32_t* dcnt;       // as Item: the cell counts of the detections (null: none kept)
+  const int* rowcell;
+  const uint32_t* wbins;
+  const uint32_t* wmask;
+  const int* xstart;
 };
 
 // Work items of one stream's batch of T frames.
@@ -201,6 +235,11 @@ struct SingleSrc {
     it.rowblk = tb.rowblk + lg.row_off;
     it.N_c = g.N_c;
     it.pmask = s.pmask ? s.pmask + (long long)k * g.bit_words + lg.bit_off : nullptr;
+    it.dcnt = s.pmask ? nullptr : s.dcnt + (long long)k * g.n_cells;
+    it.rowcell = tb.rowcell + lg.row_off;
+    it.wbins = tb.wbins + lg.wb_off;
+    it.wmask = tb.wmask + lg.wb_off;
+    it.xstart = tb.xstart + lg.xs_off;
     return it;
   }
   __device__ __forceinline__ ScaleItem scale_item(uint32_t item) const {
@@ -221,6 +260,12 @@ struct SingleSrc {
     si.wpr = lg.wpr;
     si.dscore = s.det_score + (long long)k * g.score_bytes + lg.score_off;
     si.dpitch = lg.pitch;
+    si.w = lg.w;
+    si.dcnt = s.pmask ? nullptr : s.dcnt + (long long)k * g.n_cells;
+    si.rowcell = tb.rowcell + lg.row_off;
+    si.wbins = tb.wbins + lg.wb_off;
+    si.wmask = tb.wmask + lg.wb_off;
+    si.xstart = tb.xstart + lg.xs_off;
     for (int j = 0; j < 2; ++j) {
       const int m = tile.layer + (j ? 1 : -1);
       LayerView& v = si.adj[j];
@@ -280,6 +325,11 @@ struct GroupSrc {
     it.rowblk = d.tb.rowblk + lg.row_off;
     it.N_c = d.g.N_c;
     it.pmask = nullptr;  // groups use bin masks
+    it.dcnt = d.s.dcnt;
+    it.rowcell = d.tb.rowcell + lg.row_off;
+    it.wbins = d.tb.wbins + lg.wb_off;
+    it.wmask = d.tb.wmask + lg.wb_off;
+    it.xstart = d.tb.xstart + lg.xs_off;
     return it;
   }
   __device__ __forceinline__ ScaleItem scale_item(uint32_t item) const {
@@ -301,6 +351,12 @@ struct GroupSrc {
     si.wpr = lg.wpr;
     si.dscore = d.s.det_score + lg.score_off;
     si.dpitch = lg.pitch;
+    si.w = lg.w;
+    si.dcnt = d.s.dcnt;
+    si.rowcell = d.tb.rowcell + lg.row_off;
+    si.wbins = d.tb.wbins + lg.wb_off;
+    si.wmask = d.tb.wmask + lg.wb_off;
+    si.xstart = d.tb.xstart + lg.xs_off;
     for (int j = 0; j < 2; ++j) {
       const int m = tile.layer + (j ? 1 : -1);
       LayerView& v = si.adj[j];
@@ -393,28 +449,31 @@ __device__ __forceinline__ uint32_t active_rows(const Item& it, int lane) {
   return rows;
 }
 
-// A. stage input rows y0-4 .. y0+TH+3, columns x0-16 .. x0+TW+15, zeros
-// outside the layer. x0 is a multiple of 128, so each 16-byte chunk is either
-// wholly left of the layer or starts inside it.
+// A. stage input rows r_lo .. r_hi (input row r is layer row y0-4+r) and the
+// 16-byte chunks c_lo .. c_hi of each (chunk c covers columns
+// x0-16+16c .. +15), zeros outside the layer: the part of the tile plus halo
+// that the active words need. x0 is a multiple of 128, so each chunk is
+// either wholly left of the layer or starts inside it.
 template <int TH>
-__device__ __forceinline__ void stage(uint8_t* in, const Item& it, int lane) {
-  constexpr int IN_H = Shape<TH>::IN_H;
+__device__ __forceinline__ void stage(uint8_t* in, const Item& it, int lane, int r_lo, int r_hi, int c_lo,
+                                      int c_hi) {
   const bool vec = ((reinterpret_cast<uintptr_t>(it.src) | (uintptr_t)it.pitch) & 15) == 0;
-  if (vec && it.x0 >= 16 && it.x0 + TW + 16 <= it.w && it.y0 >= 4 && it.y0 + TH + 4 <= it.h) {
+  const int nch = c_hi - c_lo + 1, n = (r_hi - r_lo + 1) * nch;
+  const float inv = 1.0f / (float)nch;
+  const int gy0 = it.y0 - 4 + r_lo, gx0 = it.x0 - 16 + 16 * c_lo;
+  if (vec && gx0 >= 0 && it.x0 - 16 + 16 * c_hi + 16 <= it.w && gy0 >= 0 && it.y0 - 4 + r_hi < it.h) {
     // the whole staged rectangle lies inside the layer: no checks, no zero fill
-    const uint8_t* base = it.src + (long long)(it.y0 - 4) * it.pitch + (it.x0 - 16);
-#pragma unroll
-    for (int q0 = 0; q0 < IN_H * (IN_W / 16); q0 += 32) {
-      const int q = q0 + lane;
-      if ((IN_H * (IN_W / 16)) % 32 == 0 || q < IN_H * (IN_W / 16)) {
-        const int r = q / (IN_W / 16), c = (q % (IN_W / 16)) * 16;
-        cp_async16(in + r * IN_W + c, base + (long long)r * it.pitch + c, 16);
-      }
+    const uint8_t* base = it.src + (long long)gy0 * it.pitch + gx0;
+    uint8_t* dst = in + r_lo * IN_W + 16 * c_lo;
+    for (int q = lane; q < n; q += 32) {
+      const int r = __float2int_rz(((float)q + 0.5f) * inv), c = q - r * nch;
+      cp_async16(dst + r * IN_W + 16 * c, base + (long long)r * it.pitch + 16 * c, 16);
     }
     return;
   }
-  for (int q = lane; q < IN_H * (IN_W / 16); q += 32) {
-    const int r = q / (IN_W / 16), c = (q % (IN_W / 16)) * 16;
+  for (int q = lane; q < n; q += 32) {
+    const int rq = __float2int_rz(((float)q + 0.5f) * inv);
+    const int r = r_lo + rq, c = (c_lo + q - rq * nch) * 16;
     const int gy = it.y0 - 4 + r, gx = it.x0 - 16 + c;
     uint8_t* d = in + r * IN_W + c;
     const bool row_ok = gy >= 0 && gy < it.h;
@@ -444,7 +503,7 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
   extern __shared__ __align__(16) uint8_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
   uint8_t* inbuf = smem + warp * Sh::WARP_SMEM;
-  uint8_t* sc = inbuf + NBUF * IN_BYTES;
+  uint8_t* sc = inbuf + IN_BYTES;
   uint32_t* detw = reinterpret_cast<uint32_t*>(sc + SC_BYTES);
   uint32_t* passw = detw + DET_WORDS;
   uint32_t* wlist = passw + DET_WORDS;
@@ -453,58 +512,23 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
 
   const uint32_t count_items = src.count();
   const uint32_t stride = gridDim.x * warps;
+  const unsigned lt = (1u << lane) - 1u;
 
-  uint32_t item = blockIdx.x * warps + warp;
-  int buf = 0;
-  Item nxt{};
-  if (NBUF == 2 && item < count_items) {
-    nxt = src.template decode<TH>(item);
-    stage<TH>(inbuf, nxt, lane);
-  }
-  cp_async_commit();
-  for (; item < count_items; item += stride) {
-    const Item it = NBUF == 2 ? nxt : src.template decode<TH>(item);
-    const uint8_t* in = inbuf + buf * IN_BYTES;
-    if (NBUF == 2) {
-      // prefetch the next tile into the other buffer, then wait for this one
-      if (item + stride < count_items) {
-        nxt = src.template decode<TH>(item + stride);
-        stage<TH>(inbuf + (buf ^ 1) * IN_BYTES, nxt, lane);
-      }
-    } else {
-      stage<TH>(inbuf, it, lane);
-    }
-    cp_async_commit();
-    for (int q = lane; q < SC_BYTES / 16; q += 32)
-      reinterpret_cast<uint4*>(sc)[q] = make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-    for (int q = lane; q < DET_WORDS; q += 32) detw[q] = passw[q] = 0u;
-    cp_async_wait<NBUF - 1>();
-    __syncwarp();
+  for (uint32_t item = blockIdx.x * warps + warp; item < count_items; item += stride) {
+    const Item it = src.template decode<TH>(item);
+    const uint8_t* in = inbuf;
     const int w = it.w, h = it.h, x0 = it.x0, y0 = it.y0;
     const uint32_t t = (uint32_t)it.t;
     const uint32_t t1 = t + 1u;  // score >= t  <=>  some arc beyond I_p +- t
     const uint32_t t1_low7 = (t1 & 0x7fu) * 0x01010101u;
     const bool t1_high = t1 >= 128u;
     const bool none = t1 > 255u;
-
-    // B. prefilter the score rows y0-1 .. y0+TH (input rows 3 .. TH+4), lane
-    //    -> word x0+4*lane .. +3, and the two edge columns; words holding
-    //    candidates are compacted (one ballot per row) into the word list,
-    //    each entry the prefilter bits (bit 7 of byte i: pixel i) with the
-    //    score row in bits 0-4 and the word column + 1 (0: left edge, 33:
-    //    right edge) in bits 8-13.
     const bool interior = x0 - 1 >= 3 && x0 + TW < w - 3 && y0 - 1 >= 3 && y0 + TH < h - 3;
-    const unsigned lt = (1u << lane) - 1u;
-    int nw = 0;     // words in the list (warp-uniform)
-    int npass = 0;  // passing tile pixels (warp-uniform)
-    auto add_word = [&](uint32_t entry) {
-      const unsigned bal = __ballot_sync(0xffffffffu, (entry & 0x80808080u) != 0u);
-      if (entry & 0x80808080u) wlist[nw + __popc(bal & lt)] = entry;
-      nw += __popc(bal);
-    };
+
     // rows this lane's word must score: active bins, inside the scorable band
-    uint32_t rows = active_rows<TH>(it, lane);
+    // (active_rows may set bits beyond the tile's SC_H score rows: cleared)
+    constexpr uint32_t kAllRows = (SC_H == 32) ? 0xffffffffu : ((1u << SC_H) - 1u);
+    uint32_t rows = active_rows<TH>(it, lane) & kAllRows;
     if (!interior) {
 #pragma unroll
       for (int rr = 0; rr < SC_H; ++rr) {
@@ -512,29 +536,80 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
         if (y < 3 || y >= h - 3) rows &= ~(1u << rr);
       }
     }
-    constexpr uint32_t kAllRows = (SC_H == 32) ? 0xffffffffu : ((1u << SC_H) - 1u);
+    if (none) rows = 0u;
     const uint32_t rows_any = __reduce_or_sync(0xffffffffu, rows);
-    if (!none && rows_any) {
-      const int c = 16 + 4 * lane;
-      const int x = x0 + 4 * lane;
-      uint32_t colmask = 0x80808080u;  // pixels of this word inside the scorable band
-      if (!interior) {
+    const unsigned lanes_any = __ballot_sync(0xffffffffu, rows != 0u);
+
+    // A. stage what the active words need: score rows rr read input rows
+    //    rr .. rr+6; word l reads input columns 4l+12 .. 4l+23
+    if (rows_any) {
+      const int rr_lo = __ffs(rows_any) - 1, rr_hi = 31 - __clz(rows_any);
+      const int wl_lo = __ffs(lanes_any) - 1, wl_hi = 31 - __clz(lanes_any);
+      stage<TH>(inbuf, it, lane, rr_lo, rr_hi + 6, (4 * wl_lo + 12) >> 4, (4 * wl_hi + 23) >> 4);
+    }
+    cp_async_commit();
+    for (int q = lane; q < SC_BYTES / 16; q += 32)
+      reinterpret_cast<uint4*>(sc)[q] = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (x + i < 3 || x + i >= w - 3) colmask &= ~(0x80u << (8 * i));
-      }
-      const uint32_t code = (uint32_t)(lane + 1) << 8;
-      if (__all_sync(0xffffffffu, (rows & kAllRows) == kAllRows)) {
+    for (int q = lane; q < DET_WORDS; q += 32) detw[q] = passw[q] = 0u;
+    cp_async_wait<0>();
+    __syncwarp();
+
+    // B. prefilter the score rows y0-1 .. y0+TH (input rows 3 .. TH+4), lane
+    //    -> word x0+4*lane .. +3, and the two edge columns; words holding
+    //    candidates are compacted (one ballot per 32 words) into the word
+    //    list, each entry the prefilter bits (bit 7 of byte i: pixel i) with
+    //    the score row in bits 0-4 and the word column + 1 (0: left edge, 33:
+    //    right edge) in bits 8-13.
+    int nw = 0;     // words in the list (warp-uniform)
+    int npass = 0;  // passing tile pixels (warp-uniform)
+    auto add_word = [&](uint32_t entry) {
+      const unsigned bal = __ballot_sync(0xffffffffu, (entry & 0x80808080u) != 0u);
+      if (entry & 0x80808080u) wlist[nw + __popc(bal & lt)] = entry;
+      nw += __popc(bal);
+    };
+    if (rows_any) {
+      auto colmask_of = [&](int wl) {  // pixels of word wl inside the scorable band
+        uint32_t m = 0x80808080u;
+        if (!interior) {
+          const int x = x0 + 4 * wl;
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (x + i < 3 || x + i >= w - 3) m &= ~(0x80u << (8 * i));
+        }
+        return m;
+      };
+      if (__all_sync(0xffffffffu, rows == kAllRows)) {
         // every row of every word: no per-row tests
+        const int c = 16 + 4 * lane;
+        const uint32_t colmask = colmask_of(lane), code = (uint32_t)(lane + 1) << 8;
 #pragma unroll 2
         for (int rr = 0; rr < SC_H; ++rr)
           add_word((prefilter(in, (rr + 3) * IN_W + c, t1_low7, t1_high) & colmask) | code | (uint32_t)rr);
       } else {
-#pragma unroll 2
-        for (int rr = 0; rr < SC_H; ++rr) {
-          if (!((rows_any >> rr) & 1u)) continue;  // no lane needs this row
-          const uint32_t keep = ((rows >> rr) & 1u) ? prefilter(in, (rr + 3) * IN_W + c, t1_low7, t1_high) & colmask : 0u;
-          add_word(keep | code | (uint32_t)rr);
+        // only the (row, word) units some bin needs: list them (lane order,
+        // then row order) at the head of the word list, then prefilter them
+        // 32 at a time, one unit per lane
+        const int cnt = __popc(rows);
+        int incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int o = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += o;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        int at = incl - cnt;
+        for (uint32_t r = rows; r; r &= r - 1u) wlist[at++] = ((uint32_t)(lane + 1) << 8) | (uint32_t)(__ffs(r) - 1);
+        __syncwarp();
+        for (int u0 = 0; u0 < total; u0 += 32) {
+          const uint32_t unit = u0 + lane < total ? wlist[u0 + lane] : 0u;
+          __syncwarp();  // every unit of this round is read before entries overwrite them
+          uint32_t keep = 0u;
+          if (unit) {
+            const int wl = (int)(unit >> 8) - 1, rr = (int)(unit & 31u);
+            keep = prefilter(in, (rr + 3) * IN_W + 16 + 4 * wl, t1_low7, t1_high) & colmask_of(wl);
+          }
+          add_word(keep | unit);
         }
       }
       // the score region's edge columns x0-1 and x0+TW: lane rr < SC_H owns
@@ -647,18 +722,22 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
     }
     __syncwarp();
 
-    // E. the tile's bitmap words (TH rows x TW/32 words)
+    // E. the tile's bitmap words (TH rows x TW/32 words), their detections
+    //    counted into the cells (chunk x bin) of their pixels
     uint32_t* bits = it.bits;
 #pragma unroll
     for (int j = 0; j < DET_WORDS / 32; ++j) {
       const int idx = lane + 32 * j;
       const int ly = idx / (TW / 32), wx = x0 / 32 + idx % (TW / 32);
-      if (y0 + ly < h && wx < it.wpr) bits[(long long)(y0 + ly) * it.wpr + wx] = detw[idx];
+      if (y0 + ly < h && wx < it.wpr) {
+        const uint32_t word = detw[idx];
+        bits[(long long)(y0 + ly) * it.wpr + wx] = word;
+        if (word && it.dcnt)
+          count_word(it.dcnt + it.rowcell[y0 + ly], word, wx, w, it.wbins, it.wmask, it.xstart, 1);
+      }
     }
     __syncwarp();
-    buf ^= NBUF - 1;
   }
-  cp_async_wait<0>();
 }
 
 // Does the segment test fire at threshold v (>= 1) at pixel (x, y) of the
@@ -758,7 +837,10 @@ __global__ void __launch_bounds__(kScaleWarps * 32) k_scale_nms(Src src) {
       }
       __syncwarp();
       const uint32_t d = dom[warp][lane];
-      if (valid && d) *wp = w & ~d;
+      if (valid && d) {
+        *wp = w & ~d;
+        if (si.dcnt) count_word(si.dcnt + si.rowcell[y], d, wx, si.w, si.wbins, si.wmask, si.xstart, -1);
+      }
       __syncwarp();
     }
   }

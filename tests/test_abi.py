@@ -78,22 +78,30 @@ def test_descriptor_pattern_generator():
 
 
 def test_bench_reads_profile_counters_per_launch_shape(tmp_path, monkeypatch):
-    """The bench takes the dominant kernel's traffic and ALU counts from the
-    committed profile only for the launch shape in use and unchanged sources."""
+    """The bench takes the dominant kernel's traffic and ALU counts from a
+    profile summary only for the launch shape in use and while the kernel's
+    sources match the hash the summary records."""
+    import hashlib
     import sys
     sys.path.insert(0, ROOT)
     import bench
-    got = bench.profile_counters("detect", dict(tile_h=16, warps_per_cta=8, ctas_per_sm=2))
-    assert got and got["traffic_bytes_per_launch"] > 0 and got["alu_warp_inst_per_launch"] > 0
-    assert bench.profile_counters("detect", dict(tile_h=8, warps_per_cta=4, ctas_per_sm=1)) is None
-    # a changed source no longer matches the recorded hash
     csrc = tmp_path / "paper_1503_06959_gb300" / "csrc"
     csrc.mkdir(parents=True)
     (tmp_path / "profiles").mkdir()
+    h = hashlib.sha256()
     for f in bench.KERNEL_SOURCES["detect"]:
         data = open(os.path.join(ROOT, "paper_1503_06959_gb300", "csrc", f), "rb").read()
-        (csrc / f).write_bytes(data + (b"\n" if f.endswith(".cu") else b""))
-    prof = open(os.path.join(ROOT, "profiles", "k_detect_masked_clip_640x480x300.md")).read()
-    (tmp_path / "profiles" / "k_detect_masked_clip_640x480x300.md").write_text(prof)
+        (csrc / f).write_bytes(data)
+        h.update(data)
+    summary = (f"source_sha256: {h.hexdigest()[:16]}\n"
+               "counters 16,8,2: traffic_bytes_per_launch 1000 alu_warp_inst_per_launch 2000 "
+               "alu_peak_warp_inst_per_sm_cycle 2\n")
+    (tmp_path / "profiles" / "k_detect_masked_clip_640x480x300.md").write_text(summary)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    got = bench.profile_counters("detect", dict(tile_h=16, warps_per_cta=8, ctas_per_sm=2))
+    assert got == {"traffic_bytes_per_launch": 1000.0, "alu_warp_inst_per_launch": 2000.0,
+                   "alu_peak_warp_inst_per_sm_cycle": 2.0}
+    assert bench.profile_counters("detect", dict(tile_h=8, warps_per_cta=4, ctas_per_sm=1)) is None
+    # a changed source no longer matches the recorded hash
+    (csrc / bench.KERNEL_SOURCES["detect"][0]).write_bytes(data + b"\n")
     assert bench.profile_counters("detect", dict(tile_h=16, warps_per_cta=8, ctas_per_sm=2)) is None
