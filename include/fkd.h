@@ -206,7 +206,12 @@ int fkd_get_pixel_mask(fkd_stream* s, int layer, uint8_t* out);
  *     memory; the call waits and returns FKD_E_CAPACITY itself (outputs
  *     filled up to cap).
  * With FKD_MASK_KB each frame's mask depends on the previous frame's
- * keypoints, so the batch runs frame after frame inside the call.
+ * keypoints. A bin below T_H stays inactive (its part of D_n is D_{n-1}'s,
+ * Eq. 1, so its count cannot grow), so the call detects spans of 16 frames
+ * on the bins active at each span's first frame and then resolves every
+ * frame's exact mask from the detection counts: the results are those of
+ * frame-after-frame processing. Its profile puts the spans in the detect
+ * stage (mask and worklist stages empty).
  * Errors: FKD_E_ARG, FKD_E_CAPACITY, FKD_E_CUDA.
  */
 int fkd_push_frames(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t frame_stride, int T,

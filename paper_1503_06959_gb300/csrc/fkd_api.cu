@@ -74,6 +74,9 @@ struct fkd_stream {
   uint32_t* wmask = nullptr;
   int* rowchunk = nullptr;
   int* rowcell = nullptr;
+  int* bincell_off = nullptr;  // per bin: start of its cells (NB + 1)
+  int* bincell = nullptr;      // cells of every bin
+  uint32_t* cellinfo = nullptr;  // per cell: chunk << 12 | bin
 
   Scratch s{};
   uint32_t* state_bits[2] = {nullptr, nullptr};
@@ -322,6 +325,22 @@ int build_geometry(fkd_stream* s, int W, int H) {
   g.n_tiles = s->n_tiles_shape[g.det_shape];
   g.n_chunks = (int)chunks.size();
   g.n_cells = cells;
+  // the cells of every bin, for keypoint binning in spans
+  std::vector<std::vector<int>> per_bin(g.NB);
+  for (const AsmChunk& ch : chunks)
+    for (int r = ch.rb0; r <= ch.rb1; ++r)
+      for (int c = 0; c < p.N_c; ++c) per_bin[r * p.N_c + c].push_back(ch.cell0 + (r - ch.rb0) * p.N_c + c);
+  std::vector<uint32_t> cellinfo(cells);
+  for (int ci = 0; ci < (int)chunks.size(); ++ci) {
+    const AsmChunk& ch = chunks[ci];
+    for (int i = 0; i < (ch.rb1 - ch.rb0 + 1) * p.N_c; ++i)
+      cellinfo[ch.cell0 + i] = ((uint32_t)ci << 12) | (uint32_t)((ch.rb0 + i / p.N_c) * p.N_c + i % p.N_c);
+  }
+  std::vector<int> bincell_off(1, 0), bincell;
+  for (const auto& v : per_bin) {
+    bincell.insert(bincell.end(), v.begin(), v.end());
+    bincell_off.push_back((int)bincell.size());
+  }
   g.pyr_tiles_x = (W + kPyrTile - 1) / kPyrTile;
   g.pyr_tiles_y = (H + kPyrTile - 1) / kPyrTile;
 
@@ -336,8 +355,15 @@ int build_geometry(fkd_stream* s, int W, int H) {
       (rc = s->alloc(&s->xstart, xstart.size())) || (rc = s->alloc(&s->npix, npix.size())) ||
       (rc = s->alloc(&s->tile_shape[0], all_tiles)) || (rc = s->alloc(&s->chunks, chunks.size())) ||
       (rc = s->alloc(&s->wbins, wbins.size())) || (rc = s->alloc(&s->wmask, wmask.size())) ||
-      (rc = s->alloc(&s->rowchunk, rowchunk.size())) || (rc = s->alloc(&s->rowcell, rowcell.size())))
+      (rc = s->alloc(&s->rowchunk, rowchunk.size())) || (rc = s->alloc(&s->rowcell, rowcell.size())) ||
+      (rc = s->alloc(&s->bincell_off, bincell_off.size())) || (rc = s->alloc(&s->bincell, bincell.size())) ||
+      (rc = s->alloc(&s->cellinfo, cellinfo.size())))
     return rc;
+  if (!cellinfo.empty())
+    CK(cudaMemcpy(s->cellinfo, cellinfo.data(), cellinfo.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->bincell_off, bincell_off.data(), bincell_off.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (!bincell.empty())
+    CK(cudaMemcpy(s->bincell, bincell.data(), bincell.size() * sizeof(int), cudaMemcpyHostToDevice));
   if (!rowcell.empty())
     CK(cudaMemcpy(s->rowcell, rowcell.data(), rowcell.size() * sizeof(int), cudaMemcpyHostToDevice));
   if (!rowchunk.empty())
@@ -371,7 +397,7 @@ int allocate_state(fkd_stream* s) {
       (rc = s->alloc(&sc.det_bits, (size_t)(T * std::max(g.bit_words, 1LL)))) ||
       (rc = s->alloc(&sc.det_score, (size_t)(T * g.score_bytes))) ||
       (rc = s->alloc(&sc.chunk_counts, (size_t)(T * std::max(g.n_chunks, 1)))) ||
-      (rc = s->alloc(&sc.dcnt, (size_t)(T * std::max(g.n_cells, 1)))) ||
+      (rc = s->alloc(&sc.dcnt, (size_t)(T * std::max(g.n_cells, 1)))) || (rc = s->alloc(&sc.alive, (size_t)g.NB)) ||
       (rc = s->alloc(&sc.merged, (size_t)(T * std::max(g.bit_words, 1LL)))) ||
       (rc = s->alloc(&sc.bases, (size_t)(T + 1))) || (rc = s->alloc(&sc.done, 1)) ||
       (rc = s->alloc(&sc.frame_totals, (size_t)T)) || (rc = s->alloc(&sc.out_base, 2)) ||
@@ -407,8 +433,7 @@ int allocate_state(fkd_stream* s) {
   return FKD_OK;
 }
 
-// One batch of T frames already in device memory (T == 1 for keypoint
-// binning, whose mask needs the previous frame's keypoints).
+// One batch of T frames already in device memory.
 int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride, int T,
               fkd_keypoint* out, long long cap, uint32_t* offsets, int base_slot, bool reset_base) {
   Batch b{};
@@ -422,7 +447,7 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   b.c0_vec = 0;
   Params pr{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode, s->p.nms_scale};
   Tables tb{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask, s->rowchunk,
-            s->rowcell};
+            s->rowcell, s->bincell_off, s->bincell, s->cellinfo};
   State stt{};
   stt.bits_in = s->state_bits[s->state_cur];
   stt.score_in = s->state_score[s->state_cur];
@@ -449,13 +474,31 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   mark(0);
   launch_pyramid(s->g, tb, b, s->s, pr, s->st);
   mark(1);
-  launch_mask(s->g, tb, b, s->s, pr, stt, s->st, reset_base ? base_slot : -1);
-  if (s->s.pmask) launch_pixel_mask(s->g, b, s->s, pr, s->st);
-  mark(2);
-  launch_worklist(s->g, tb, b, s->s, s->st);
-  mark(3);
-  launch_detect(s->g, tb, b, s->s, pr, s->dl, s->st);
-  if (pr.nms_scale) launch_scale_nms(s->g, tb, b, s->s, pr, s->st);
+  if (pr.mask_mode == FKD_MASK_KB) {
+    // keypoint binning: spans of frames detected on the bins still active
+    // at the span's start, then the exact masks resolved from the detection
+    // counts (the "mask" and "worklist" stages are empty; "detect" holds the
+    // spans and the source-frame scan)
+    mark(2);
+    mark(3);
+    for (int k0 = 0; k0 < T; k0 += kKbSpan) {
+      const int k1 = std::min(T, k0 + kKbSpan);
+      launch_kb_span(s->g, b, s->s, pr, stt, k0, k1, k0 == 0, s->st);
+      launch_worklist(s->g, tb, b, s->s, s->st, k0, k1);
+      launch_detect(s->g, tb, b, s->s, pr, s->dl, s->st);
+      if (pr.nms_scale) launch_scale_nms(s->g, tb, b, s->s, pr, s->st);
+      launch_kb_resolve(s->g, tb, b, s->s, pr, k0, k1, s->st);
+    }
+    launch_source_frames(s->g, tb, b, s->s, pr, stt, s->st, reset_base ? base_slot : -1);
+  } else {
+    launch_mask(s->g, tb, b, s->s, pr, stt, s->st, reset_base ? base_slot : -1);
+    if (s->s.pmask) launch_pixel_mask(s->g, b, s->s, pr, s->st);
+    mark(2);
+    launch_worklist(s->g, tb, b, s->s, s->st);
+    mark(3);
+    launch_detect(s->g, tb, b, s->s, pr, s->dl, s->st);
+    if (pr.nms_scale) launch_scale_nms(s->g, tb, b, s->s, pr, s->st);
+  }
   mark(4);
   if (s->s.pmask) launch_count_pixel(s->g, tb, b, s->s, stt, s->st);  // its last CTA fills bases
   else launch_offsets(s->g, tb, b, s->s, stt, s->st);                 // its last CTA fills s->s.bases
@@ -503,16 +546,15 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   return FKD_OK;
 }
 
-// T frames in device memory as one batch (frame by frame for keypoint
-// binning, whose mask needs the previous frame's keypoints); masks, if not
-// NULL, receive each frame's mask.
+// T frames in device memory as one batch (keypoint binning, whose mask needs
+// the previous frame's keypoints, runs in spans inside the batch); masks, if
+// not NULL, receive each frame's mask.
 // With `parts` > 1 the frames arrive in that many equal parts (the last one
 // shorter), part i ready once s->part_done[i] has fired; each part is then
 // its own batch (exactly the same results), so its kernels start while the
 // later parts are still uploading.
 int run_frames(fkd_stream* s, const uint8_t* dframes, int dpitch, long long dstride, int T, fkd_keypoint* drec,
                long long cap, uint32_t* doff, uint8_t* masks, cudaMemcpyKind mask_kind, int parts = 1) {
-  const bool serial = s->p.mask_mode == FKD_MASK_KB;
   const int per_part = (T + parts - 1) / parts;
   int slot = 0, next_part = 0;
   for (int k0 = 0; k0 < T;) {
@@ -520,7 +562,7 @@ int run_frames(fkd_stream* s, const uint8_t* dframes, int dpitch, long long dstr
       CK(cudaStreamWaitEvent(s->st, s->part_done[next_part], 0));
       ++next_part;
     }
-    const int n = serial ? 1 : (parts > 1 ? std::min(per_part, T - k0) : T);
+    const int n = parts > 1 ? std::min(per_part, T - k0) : T;
     int rc = run_batch(s, dframes + (long long)k0 * dstride, dpitch, dstride, n, drec, cap, doff + k0, slot, k0 == 0);
     if (rc) return rc;
     if (masks)
@@ -772,7 +814,7 @@ int fkd_push_frames(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t f
     s->desc_cap = (long long)cap;
   }
 
-  // 3. the batch (frame by frame for keypoint binning)
+  // 3. the batch
   int rc = run_frames(s, dframes, dpitch, dstride, T, drec, (long long)cap, doff, masks,
                       out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, parts);
   if (rc) return rc;
@@ -1143,7 +1185,7 @@ StreamDev make_dev(const fkd_stream* s, const GroupStream& gs) {
   StreamDev d{};
   d.g = s->g;
   d.tb = Tables{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask, s->rowchunk,
-                s->rowcell};
+                s->rowcell, s->bincell_off, s->bincell, s->cellinfo};
   d.s = s->s;
   d.s.bases = nullptr;  // group ticks (one frame) compute their offsets in place
   d.p = Params{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode, s->p.nms_scale};

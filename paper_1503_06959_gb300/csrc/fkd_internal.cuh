@@ -119,6 +119,9 @@ struct Tables {
   const uint32_t* wmask;   // per layer, per bitmap word column: bits of the word in its first bin
   const int* rowchunk;     // per layer, per y: the assembly chunk holding the row
   const int* rowcell;      // per layer, per y: cell of (the row's chunk, bin row, bin column 0)
+  const int* bincell_off;  // per bin: start of its cells in bincell (NB + 1 entries)
+  const int* bincell;      // the cells of every bin (all layers), bin after bin
+  const uint32_t* cellinfo;  // per cell: its chunk << 12 | its bin
 };
 
 // Arguments of one batch of T consecutive frames of one stream.
@@ -152,6 +155,7 @@ struct Scratch {
   uint32_t* chunk_counts;          // [T_max][n_chunks]: records of each chunk (per-pixel masks), or
                                    //   records of the frame before the chunk (bin masks)
   uint32_t* dcnt;                  // [T_max][n_cells]: detections of each frame in each cell
+  uint8_t* alive;                  // [NB]: keypoint binning in spans, bins active at the next frame
   uint32_t* merged;                // [T_max][bit_words]: D_n bitmap of every frame of the batch
   uint32_t* bases;                 // [T_max + 1]: records of the batch before each frame, then the total
   uint32_t* done;                  // [1]: chunks counted (last-CTA scan)
@@ -304,7 +308,18 @@ void launch_pyramid(const Geometry& g, const Tables& tb, const Batch& b, const S
 void launch_mask(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                  const Params& p, const State& state, cudaStream_t st, int reset_base_slot);
 void launch_worklist(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
-                     cudaStream_t st);
+                     cudaStream_t st, int k_lo = 0, int k_hi = -1);
+// Keypoint binning in spans of frames: the masks of frames k_lo .. k_hi-1
+// set to the bins still active (first: from the kept set's counts), then
+// resolved exactly from the detection counts; and the source frames of a
+// batch whose masks are given.
+constexpr int kKbSpan = 16;
+void launch_kb_span(const Geometry& g, const Batch& b, const Scratch& s, const Params& p, const State& state,
+                    int k_lo, int k_hi, int first, cudaStream_t st);
+void launch_kb_resolve(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s, const Params& p,
+                       int k_lo, int k_hi, cudaStream_t st);
+void launch_source_frames(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
+                          const Params& p, const State& state, cudaStream_t st, int reset_base_slot);
 void launch_detect(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                    const Params& p, const DetLaunch& dl, cudaStream_t st);
 void launch_count(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,

@@ -153,41 +153,41 @@ __device__ __forceinline__ void count_chunk(const Geometry& g, const Tables& tb,
 // batch's last frame (`last`) it also stores the counts as the new kept
 // set's and adds them up per bin for keypoint binning (Eqs. 3-4). With
 // s.bases, the CTA that finishes last of `total_ctas` turns the frame totals
-// into record offsets. Ends with a barrier.
+// into record offsets. One thread per cell (all cells' loads in flight at
+// once); chunk sums in shared memory when they fit, else in chunk_counts.
+// Ends with a barrier.
+constexpr int kOffChunks = 1024;
 __device__ __forceinline__ void offsets_frame(const Geometry& g, const Tables& tb, const Scratch& s, const State& st,
                                               int k, bool last, int T, int total_ctas) {
   __shared__ uint32_t wsum[kAsmThreads / 32];
+  __shared__ uint32_t csum[kOffChunks];
   __shared__ uint32_t carry_sh;
   __shared__ int last_cta;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int* src_k = s.src + (long long)k * g.NB;
   uint32_t* cc = s.chunk_counts + (long long)k * g.n_chunks;
-  // one warp per chunk: the sum of its cells
-  for (int c = wid; c < g.n_chunks; c += kAsmThreads / 32) {
-    const AsmChunk ch = tb.chunks[c];
-    const int ncell = (ch.rb1 - ch.rb0 + 1) * g.N_c;
-    uint32_t sum = 0;
-    for (int i = lane; i < ncell; i += 32) {
-      const int r = ch.rb0 + i / g.N_c, col = i - (i / g.N_c) * g.N_c;
-      const int bin = r * g.N_c + col, cell = ch.cell0 + i;
-      const int sf = src_k[bin];
-      const uint32_t v = sf < 0 ? st.kcnt_in[cell] : s.dcnt[(long long)sf * g.n_cells + cell];
-      if (last) {
-        st.kcnt_out[cell] = v;
-        if (v) atomicAdd(&st.cnt_out[bin], v);
-      }
-      sum += v;
+  const bool local = g.n_chunks <= kOffChunks;
+  uint32_t* sums = local ? csum : cc;
+  for (int c = threadIdx.x; c < g.n_chunks; c += kAsmThreads) sums[c] = 0;
+  __syncthreads();
+  for (int cell = threadIdx.x; cell < g.n_cells; cell += kAsmThreads) {
+    const uint32_t info = tb.cellinfo[cell];  // chunk << 12 | bin
+    const int bin = (int)(info & 0xfffu), ch = (int)(info >> 12);
+    const int sf = src_k[bin];
+    const uint32_t v = sf < 0 ? st.kcnt_in[cell] : s.dcnt[(long long)sf * g.n_cells + cell];
+    if (last) {
+      st.kcnt_out[cell] = v;
+      if (v) atomicAdd(&st.cnt_out[bin], v);
     }
-    sum = __reduce_add_sync(0xffffffffu, sum);
-    if (lane == 0) cc[c] = sum;
+    if (v) atomicAdd(&sums[ch], v);
   }
   __syncthreads();
-  // exclusive scan of the chunk counts in place, 256 at a time
+  // exclusive scan of the chunk counts into chunk_counts, 256 at a time
   if (threadIdx.x == 0) carry_sh = 0;
   __syncthreads();
   for (int c0 = 0; c0 < g.n_chunks; c0 += kAsmThreads) {
     const int c = c0 + threadIdx.x;
-    const uint32_t v = c < g.n_chunks ? cc[c] : 0u;
+    const uint32_t v = c < g.n_chunks ? sums[c] : 0u;
     uint32_t incl = v;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -244,7 +244,10 @@ __device__ __forceinline__ void offsets_frame(const Geometry& g, const Tables& t
 __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb, const Scratch& s,
                                              const State& st, const Output& out, int k, bool last,
                                              const AsmChunk& ch, const LayerGeom& lg, int j0,
-                                             const uint32_t* words, unsigned long long idx);
+                                             const uint32_t* words, unsigned long long idx, const int* srcs,
+                                             bool src_local);
+
+constexpr int kEmitSrc = 512;  // source frames of a chunk's bins kept in shared memory
 
 // Emit the records of one chunk of frame k of a batch of T frames; the last
 // frame also writes the new kept set. Ends with a barrier.
@@ -261,6 +264,18 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
   const int wpr = lg.wpr;
   const int nwords = (ch.y1 - ch.y0) * wpr;
   const long long word0 = lg.bit_off + (long long)ch.y0 * wpr;
+  // the source frames of the bins of the chunk's bin rows, in shared memory
+  // when they fit (every merged word and record looks its bins up)
+  __shared__ int srcs[kEmitSrc];
+  const int* src_k = s.src + (long long)k * g.NB;
+  const int nsrc = (ch.rb1 - ch.rb0 + 1) * g.N_c;
+  const bool src_local = !s.pmask && nsrc <= kEmitSrc;
+  if (src_local)
+    for (int i = threadIdx.x; i < nsrc; i += kAsmThreads) srcs[i] = src_k[ch.rb0 * g.N_c + i];
+  __syncthreads();
+  auto srcrow_of = [&](int r) -> const int* {
+    return src_local ? srcs + (r - ch.rb0) * g.N_c : src_k + r * g.N_c;
+  };
 
   // offsets: base of this call + earlier frames + earlier chunks of this frame
   uint32_t frame_base, chunk_base;
@@ -308,7 +323,6 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
   // shared memory, coalesced; each thread then takes 8 contiguous ones, so
   // the scan order is the canonical order
   const uint32_t* merged = s.merged + (long long)k * g.bit_words + word0;
-  const int* src_kw = s.src + (long long)k * g.NB;
   const int* xst = tb.xstart + lg.xs_off;
   const float inv_wpr_m = 1.0f / (float)wpr;
 #pragma unroll
@@ -322,7 +336,7 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
         int yy = __float2int_rz((float)j * inv_wpr_m);  // j / wpr, fixed up below
         if (yy * wpr > j) --yy;
         if ((yy + 1) * wpr <= j) ++yy;
-        const int* srcrow = src_kw + tb.rowblk[lg.row_off + ch.y0 + yy] * g.N_c;
+        const int* srcrow = srcrow_of(tb.rowblk[lg.row_off + ch.y0 + yy]);
         v = merge_word(g, tb, s, st, lg, xst, srcrow, word0, j, j - yy * wpr);
       }
     }
@@ -380,7 +394,7 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
   }
   if (total > (uint32_t)kEmitList) {
     // a dense chunk: every thread emits its own words' records
-    if (cnt) emit_records(g, tb, s, st, out, k, last, ch, lg, j0, words, base + before + incl - cnt);
+    if (cnt) emit_records(g, tb, s, st, out, k, last, ch, lg, j0, words, base + before + incl - cnt, srcs, src_local);
     __syncthreads();  // red and wsum are reused by the next chunk of this CTA
     return;
   }
@@ -399,7 +413,6 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
   __syncthreads();
   const int wpr_ = wpr;
   const float inv_wpr = 1.0f / (float)wpr_;
-  const int* src_k = s.src + (long long)k * g.NB;
   const uint16_t* colblk = tb.colblk + lg.col_off;
   for (uint32_t i = threadIdx.x; i < total; i += kAsmThreads) {
     const int p = pos[i];
@@ -421,7 +434,7 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
       const uint32_t mw = s.pmask[(long long)k * g.bit_words + word0 + j];
       flags = ((mw >> (p & 31)) & 1u) ? 0u : FKD_KP_PROPAGATED;
     } else {
-      const int sf = src_k[r * g.N_c + c];
+      const int sf = srcrow_of(r)[c];
       score = sf < 0 ? st.score_in[so] : s.det_score[(long long)sf * g.score_bytes + so];
       flags = sf != k ? FKD_KP_PROPAGATED : 0u;
     }
@@ -445,16 +458,18 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
 __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb, const Scratch& s,
                                              const State& st, const Output& out, int k, bool last,
                                              const AsmChunk& ch, const LayerGeom& lg, int j0,
-                                             const uint32_t* words, unsigned long long idx) {
+                                             const uint32_t* words, unsigned long long idx, const int* srcs,
+                                             bool src_local) {
   const int wpr = lg.wpr;
   const int* src_k = s.src + (long long)k * g.NB;
   const uint16_t* colblk = tb.colblk + lg.col_off;
   int y = ch.y0 + j0 / wpr, wx = j0 % wpr;
+#pragma unroll
   for (int jj = 0; jj < kAsmWordsPerThread; ++jj) {
     uint32_t wv = words[jj];
     if (wv) {
       const int r = tb.rowblk[lg.row_off + y];
-      const int* srcrow = src_k + r * g.N_c;
+      const int* srcrow = src_local ? srcs + (r - ch.rb0) * g.N_c : src_k + r * g.N_c;
       const long long row_off = lg.score_off + (long long)y * lg.pitch;
       while (wv) {
         const int bit = __ffs(wv) - 1;

@@ -149,12 +149,10 @@ struct Item {
 // word column wx of a row whose cells start at `cells`, to the counts of the
 // cells its pixels lie in: words inside one or two bin columns split by the
 // precomputed mask, wider ones (coarse layers, narrow bins) walk their bins.
-__device__ __forceinline__ void count_word(uint32_t* cells, uint32_t word, int wx, int w, const uint32_t* wbins,
-                                           const uint32_t* wmask, const int* xstart, int sign) {
-  const uint32_t wb = wbins[wx];
+__device__ __forceinline__ void count_word_v(uint32_t* cells, uint32_t word, int wx, int w, uint32_t wb,
+                                             uint32_t m, const int* xstart, int sign) {
   const int c_lo = wb & 0xffffu, c_hi = wb >> 16;
   if (c_hi - c_lo <= 1) {
-    const uint32_t m = wmask[wx];
     const int n0 = __popc(word & m), n1 = __popc(word & ~m);
     if (n0) atomicAdd(cells + c_lo, (uint32_t)(sign * n0));
     if (n1) atomicAdd(cells + c_hi, (uint32_t)(sign * n1));
@@ -168,6 +166,10 @@ __device__ __forceinline__ void count_word(uint32_t* cells, uint32_t word, int w
     const int n = __popc(word & m);
     if (n) atomicAdd(cells + c, (uint32_t)(sign * n));
   }
+}
+__device__ __forceinline__ void count_word(uint32_t* cells, uint32_t word, int wx, int w, const uint32_t* wbins,
+                                           const uint32_t* wmask, const int* xstart, int sign) {
+  count_word_v(cells, word, wx, w, wbins[wx], wmask[wx], xstart, sign);
 }
 
 // One layer of a frame, for the scale-space suppression. Its scale code S
@@ -207,9 +209,9 @@ struct SingleSrc {
   Tables tb;
   Params p;
   __device__ __forceinline__ uint32_t count() const { return *s.work_count; }
+  __device__ __forceinline__ uint32_t wi_at(uint32_t item) const { return s.work[item]; }
   template <int TH>
-  __device__ __forceinline__ Item decode(uint32_t item) const {
-    const uint32_t wi = s.work[item];
+  __device__ __forceinline__ Item decode(uint32_t wi) const {
     const DetTile tile = tb.tiles[wi % (uint32_t)g.n_tiles];
     const int k = (int)(wi / (uint32_t)g.n_tiles);
     const LayerGeom& lg = g.layer[tile.layer];
@@ -296,9 +298,9 @@ struct GroupSrc {
   const uint32_t* work;
   const uint32_t* work_count;
   __device__ __forceinline__ uint32_t count() const { return *work_count; }
+  __device__ __forceinline__ uint32_t wi_at(uint32_t item) const { return work[item]; }
   template <int TH>
-  __device__ __forceinline__ Item decode(uint32_t item) const {
-    const uint32_t wi = work[item];
+  __device__ __forceinline__ Item decode(uint32_t wi) const {
     const TickItem ti = items[wi >> 22];
     const StreamDev& d = devs[ti.sid];
     const DetTile tile = d.tb.tiles[wi & 0x3fffffu];
@@ -514,8 +516,13 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
   const uint32_t stride = gridDim.x * warps;
   const unsigned lt = (1u << lane) - 1u;
 
-  for (uint32_t item = blockIdx.x * warps + warp; item < count_items; item += stride) {
-    const Item it = src.template decode<TH>(item);
+  uint32_t item = blockIdx.x * warps + warp;
+  uint32_t wi_next = item < count_items ? src.wi_at(item) : 0u;
+  for (; item < count_items; item += stride) {
+    // the next item's work entry is loaded a tile ahead
+    const uint32_t wi = wi_next;
+    if (item + stride < count_items) wi_next = src.wi_at(item + stride);
+    const Item it = src.template decode<TH>(wi);
     const uint8_t* in = inbuf;
     const int w = it.w, h = it.h, x0 = it.x0, y0 = it.y0;
     const uint32_t t = (uint32_t)it.t;
@@ -539,6 +546,22 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
     if (none) rows = 0u;
     const uint32_t rows_any = __reduce_or_sync(0xffffffffu, rows);
     const unsigned lanes_any = __ballot_sync(0xffffffffu, rows != 0u);
+
+    // the cell tables of this lane's bitmap words (phase E), loaded now so
+    // that their latency hides behind the tile's work
+    constexpr int EJ = DET_WORDS / 32;
+    const int e_wx = x0 / 32 + (lane & 3);
+    uint32_t e_wb = 0u, e_wm = 0u;
+    int e_cell[EJ];
+    if (it.dcnt && e_wx < it.wpr) {
+      e_wb = it.wbins[e_wx];
+      e_wm = it.wmask[e_wx];
+    }
+#pragma unroll
+    for (int j = 0; j < EJ; ++j) {
+      const int y = y0 + (lane >> 2) + 8 * j;
+      e_cell[j] = (it.dcnt && y < h) ? it.rowcell[y] : 0;
+    }
 
     // A. stage what the active words need: score rows rr read input rows
     //    rr .. rr+6; word l reads input columns 4l+12 .. 4l+23
@@ -732,8 +755,7 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
       if (y0 + ly < h && wx < it.wpr) {
         const uint32_t word = detw[idx];
         bits[(long long)(y0 + ly) * it.wpr + wx] = word;
-        if (word && it.dcnt)
-          count_word(it.dcnt + it.rowcell[y0 + ly], word, wx, w, it.wbins, it.wmask, it.xstart, 1);
+        if (word && it.dcnt) count_word_v(it.dcnt + e_cell[j], word, wx, w, e_wb, e_wm, it.xstart, 1);
       }
     }
     __syncwarp();

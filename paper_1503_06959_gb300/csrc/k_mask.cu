@@ -1,5 +1,7 @@
 // k_mask.cu -- detection mask M'_n per bin, the source frame of each bin's
 // keypoints across a batch, and the compacted list of active detection tiles.
+#include <algorithm>
+
 #include "fkd_internal.cuh"
 
 namespace fkd {
@@ -99,8 +101,10 @@ __global__ void __launch_bounds__(kMaskThreads) k_layer_sums(Geometry g, Tables 
 //          detections of the last frame m <= k in which the bin was active;
 //          src = m, or -1 when no such frame is in the batch (the kept set):
 //          an inclusive max-scan of (active ? k : -1) over the frames.
+//   With masks_given (keypoint binning in spans) the masks are already in
+//   s.mask and only the source frames are computed.
 __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Batch b, Scratch s,
-                                                       Params p, State st, int reset_base_slot) {
+                                                       Params p, State st, int reset_base_slot, int masks_given) {
   __shared__ int wmax[kMaskThreads / 32];
   const int bin = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool layer_sums = p.mask_mode == FKD_MASK_ID && g.mask_layer > 0;
@@ -120,7 +124,9 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Ba
     int m = 0;
     if (k < b.T) {
       const long long n = b.first_frame + k;
-      if (n == 0 || p.mask_mode == FKD_MASK_FULL || p.mask_mode == FKD_MASK_IDP) {
+      if (masks_given) {
+        m = s.mask[(long long)k * g.NB + bin];
+      } else if (n == 0 || p.mask_mode == FKD_MASK_FULL || p.mask_mode == FKD_MASK_IDP) {
         m = 1;  // (per-pixel masks decide in the detection and assembly passes)
       } else if (p.mask_mode == FKD_MASK_ID) {
         unsigned long long* sum = s.bsum + (long long)bin * s.bsum_stride + k;
@@ -129,7 +135,7 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Ba
       } else {
         m = st.cnt_in[bin] >= (uint32_t)p.T_H;
       }
-      s.mask[(long long)k * g.NB + bin] = (uint8_t)m;
+      if (!masks_given) s.mask[(long long)k * g.NB + bin] = (uint8_t)m;
     }
     int v = m ? k : -1;
 #pragma unroll
@@ -161,21 +167,22 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Ba
   }
 }
 
-// One thread per (frame, tile): a tile is active when any bin its pixels map
-// to is active. Active items are compacted with a warp ballot, a popcount and
-// one atomic per warp.
-__global__ void k_worklist(Geometry g, Tables tb, Batch b, Scratch s) {
+// One thread per (frame, tile) of frames k_lo .. k_hi-1 of the batch: a tile
+// is active when any bin its pixels map to is active. Active items are
+// compacted with a warp ballot, a popcount and one atomic per warp.
+__global__ void k_worklist(Geometry g, Tables tb, Batch b, Scratch s, int k_lo, int k_hi) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = (long long)b.T * g.n_tiles;
-  for (long long q = i; q < (long long)b.T * g.n_chunks; q += (long long)gridDim.x * blockDim.x)
-    s.chunk_counts[q] = 0;  // summed by the assembly count pass (per-pixel masks)
+  const long long total = (long long)(k_hi - k_lo) * g.n_tiles;
+  for (long long q = i; q < (long long)(k_hi - k_lo) * g.n_chunks; q += (long long)gridDim.x * blockDim.x)
+    s.chunk_counts[(long long)k_lo * g.n_chunks + q] = 0;  // summed by the assembly count pass (per-pixel masks)
   if (!s.pmask)
-    for (long long q = i; q < (long long)b.T * g.n_cells; q += (long long)gridDim.x * blockDim.x)
-      s.dcnt[q] = 0;  // the detection pass counts into them
+    for (long long q = i; q < (long long)(k_hi - k_lo) * g.n_cells; q += (long long)gridDim.x * blockDim.x)
+      s.dcnt[(long long)k_lo * g.n_cells + q] = 0;  // the detection pass counts into them
   bool act = false;
   uint32_t area = 0;
+  const long long item = (long long)k_lo * g.n_tiles + i;
   if (i < total) {
-    const int k = (int)(i / g.n_tiles), tile = (int)(i % g.n_tiles);
+    const int k = (int)(item / g.n_tiles), tile = (int)(item % g.n_tiles);
     const DetTile t = tb.tiles[tile];
     if (s.pmask) {
       // per-pixel masks: a tile is active when any of its own pixels is
@@ -205,7 +212,54 @@ __global__ void k_worklist(Geometry g, Tables tb, Batch b, Scratch s) {
     atomicAdd(&s.tile_stats[1], (unsigned long long)area);
   }
   base = __shfl_sync(0xffffffffu, base, leader);
-  if (act) s.work[base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
+  if (act) s.work[base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)item;
+}
+
+// Keypoint binning (Eqs. 3-4) in spans of frames. A bin is active in frame n
+// when D_{n-1} holds at least T_H keypoints in it; while a bin is inactive its
+// part of D_n is D_{n-1}'s (Eq. 1), so its count cannot change and it stays
+// inactive. The bins active at a span's first frame are therefore a superset
+// of the active bins of every later frame of the span: the span's frames are
+// detected on that set, and the exact masks are resolved afterwards from the
+// detection counts, frame after frame (identical to running the frames one
+// by one). alive[bin]: the bin is active at the next frame to resolve.
+//
+// Span start: the masks of frames k_lo .. k_hi-1 are the alive set (from the
+// kept set's counts at the first span of a batch), and the work list is
+// emptied for the span's active tiles.
+__global__ void k_kb_span(Geometry g, Batch b, Scratch s, Params p, State st, int k_lo, int k_hi, int first) {
+  const int bin = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bin == 0) *s.work_count = 0;
+  if (bin >= g.NB) return;
+  uint8_t a;
+  if (first) {
+    a = (b.first_frame + k_lo == 0) ? 1 : (st.cnt_in[bin] >= (uint32_t)p.T_H ? 1 : 0);
+    s.alive[bin] = a;
+  } else {
+    a = s.alive[bin];
+  }
+  for (int k = k_lo; k < k_hi; ++k) s.mask[(long long)k * g.NB + bin] = a;
+}
+
+// Span end: the exact masks of frames k_lo .. k_hi-1. A bin active in frame k
+// stays active in frame k+1 when its detections in frame k (the sum over its
+// cells) reach T_H; the first frame of a stream is active everywhere.
+__global__ void k_kb_resolve(Geometry g, Tables tb, Batch b, Scratch s, Params p, int k_lo, int k_hi) {
+  const int bin = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bin >= g.NB) return;
+  uint8_t a = s.alive[bin];
+  const int c0 = tb.bincell_off[bin], c1 = tb.bincell_off[bin + 1];
+  for (int k = k_lo; k < k_hi; ++k) {
+    const uint8_t m = (b.first_frame + k == 0) ? 1 : a;
+    s.mask[(long long)k * g.NB + bin] = m;
+    if (m) {
+      const uint32_t* dc = s.dcnt + (long long)k * g.n_cells;
+      uint32_t cnt = 0;
+      for (int c = c0; c < c1; ++c) cnt += dc[tb.bincell[c]];
+      a = cnt >= (uint32_t)p.T_H ? 1 : 0;
+    }
+  }
+  s.alive[bin] = a;
 }
 
 // Group tick, one frame per stream: the mask and source frame of every bin
@@ -305,15 +359,31 @@ void launch_mask(const Geometry& g, const Tables& tb, const Batch& b, const Scra
                  const Params& p, const State& state, cudaStream_t st, int reset_base_slot) {
   if (p.mask_mode == FKD_MASK_ID && g.mask_layer > 0)
     k_layer_sums<<<b.T, kMaskThreads, 0, st>>>(g, tb, b, s);
-  k_mask<<<g.NB, kMaskThreads, 0, st>>>(g, tb, b, s, p, state, reset_base_slot);
+  k_mask<<<g.NB, kMaskThreads, 0, st>>>(g, tb, b, s, p, state, reset_base_slot, 0);
+}
+
+void launch_source_frames(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
+                          const Params& p, const State& state, cudaStream_t st, int reset_base_slot) {
+  k_mask<<<g.NB, kMaskThreads, 0, st>>>(g, tb, b, s, p, state, reset_base_slot, 1);
 }
 
 void launch_worklist(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
-                     cudaStream_t st) {
+                     cudaStream_t st, int k_lo, int k_hi) {
+  if (k_hi < 0) k_hi = b.T;
   const int threads = 256;
-  const long long total = (long long)b.T * g.n_tiles;
-  const int blocks = (int)((total + threads - 1) / threads);
-  k_worklist<<<blocks, threads, 0, st>>>(g, tb, b, s);
+  const long long total = (long long)(k_hi - k_lo) * g.n_tiles;
+  const int blocks = (int)std::max<long long>(1, (total + threads - 1) / threads);
+  k_worklist<<<blocks, threads, 0, st>>>(g, tb, b, s, k_lo, k_hi);
+}
+
+void launch_kb_span(const Geometry& g, const Batch& b, const Scratch& s, const Params& p, const State& state,
+                    int k_lo, int k_hi, int first, cudaStream_t st) {
+  k_kb_span<<<(g.NB + 255) / 256, 256, 0, st>>>(g, b, s, p, state, k_lo, k_hi, first);
+}
+
+void launch_kb_resolve(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s, const Params& p,
+                       int k_lo, int k_hi, cudaStream_t st) {
+  k_kb_resolve<<<(g.NB + 255) / 256, 256, 0, st>>>(g, tb, b, s, p, k_lo, k_hi);
 }
 
 }  // namespace fkd

@@ -367,3 +367,21 @@ def test_host_batch_layouts(clip2, mode, T):
         rec, off, _ = s.push_frames(view)
         for k, kp in enumerate(fkd.split_frames(rec, off)):
             assert_same_kp(kp, exp_kp[k], f"strided frame {k}")
+
+
+@pytest.mark.parametrize("T_H,nms_scale", [(0, 0), (1, 0), (2, 0), (4, 0), (1, 1)])
+def test_keypoint_binning_spans(clip2, T_H, nms_scale):
+    """Keypoint binning (Eqs. 3-4) in batches: spans of 16 frames are detected
+    on the bins active at each span's start and the masks resolved after;
+    every frame must equal the oracle's frame-by-frame result, across span
+    and batch boundaries, with bins going inactive inside spans."""
+    cfg, frames = clip2
+    g, o = both(params(cfg, T_H=T_H, nms_scale=nms_scale), "kb")
+    exp_kp, exp_m = run_oracle(frames, **o)
+    s = fkd.Stream(cfg.W, cfg.H, T_max=20, **g)
+    push_in_pieces(s, frames, [20, 1, 15], exp_kp, exp_m)
+    if T_H > 0:
+        # some bin turns inactive at a frame that is not the first of a span
+        starts = {0, 16, 20, 21}  # first frames of the spans of the batches above
+        drops = [n for n in range(1, len(exp_m)) if n not in starts and (exp_m[n - 1] & ~exp_m[n]).any()]
+        assert drops, "the clip must switch bins off inside a span"
