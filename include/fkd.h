@@ -526,6 +526,28 @@ int fkd_server_drain(fkd_server* s, int timeout_ms);
 int fkd_server_get_stats(fkd_server* s, fkd_server_stats* out, int reset);
 
 /*
+ * Debug build. The library also builds as libfkd_check.so (compiled with
+ * FKD_CHECK=1; the paper has no counterpart: it stands in for a memory
+ * checker). Its kernels check the index of their shared- and global-memory
+ * accesses (staging, unit and word lists, score maps and bitmaps of the
+ * detection pass; the pyramid's level tiles and bin sums; the assembly's
+ * chunk words, set-bit lists and source frames): an index out of range is
+ * recorded in a device word and the access skipped -- no fault and no trap
+ * -- and the call that launched the work waits for it and returns
+ * FKD_E_CUDA naming the access, the index and its range. Every device
+ * allocation of a stream lies between two 256-byte guard bands of a known
+ * byte. Release builds skip all of this.
+ *   fkd_check_build: 1 in the debug build, 0 in the release build.
+ *   fkd_check_guards: FKD_OK if every guard band of the stream's allocations
+ *     is intact (always in the release build), else FKD_E_CUDA naming the
+ *     allocation's size and the byte that changed. Waits for the stream.
+ *   fkd_group_check_guards: the same for every stream of a group.
+ */
+int fkd_check_build(void);
+int fkd_check_guards(const fkd_stream* s);
+int fkd_group_check_guards(fkd_group* g);
+
+/*
  * Allocation-free variant (the paper has no counterpart; it exists for
  * callers of this library that cannot let it allocate device memory: an
  * application that gives all GPU memory to its own allocator or budget at

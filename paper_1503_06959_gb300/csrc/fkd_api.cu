@@ -50,6 +50,56 @@ int fkd::set_error(int code, const char* fmt, ...) {
   return code;
 }
 
+namespace fkd {
+
+// Debug checks (FKD_CHECK): the take-functions of every translation unit.
+static std::vector<CheckTake>& check_takes() {
+  static std::vector<CheckTake> v;
+  return v;
+}
+
+int register_check(CheckTake take) {
+  check_takes().push_back(take);
+  return 1;
+}
+
+const char* check_site_name(unsigned site) {
+  static const char* names[kChkSites] = {
+      "?", "detection staging", "detection unit list", "detection word list", "detection score map",
+      "detection pass bitmap", "detection keypoint bitmap", "detection score map (global)", "detection cell counts",
+      "pyramid level tile", "pyramid bin sums", "assembly chunk words", "assembly set-bit list",
+      "assembly source frames", "assembly kept-set bin counts"};
+  return site < (unsigned)kChkSites ? names[site] : "?";
+}
+
+int collect_checks() {
+  int rc = FKD_OK;
+  for (CheckTake take : check_takes()) {
+    CheckRecord r{};
+    if (take(&r) && rc == FKD_OK)
+      rc = set_error(FKD_E_CUDA, "index check failed in %s: index %lld outside [0, %lld)", check_site_name(r.site),
+                     r.index, r.limit);
+  }
+  return rc;
+}
+
+}  // namespace fkd
+
+namespace {
+// Debug builds: every stream allocation sits between two guard bands of a
+// known byte, checked by fkd_check_guards.
+constexpr size_t kGuard = FKD_CHECK ? 256 : 0;
+constexpr unsigned char kGuardByte = 0xA5;
+
+// Debug builds: wait for the stream and report a failed index check.
+int check_after(cudaStream_t st) {
+  if (!FKD_CHECK) return FKD_OK;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(FKD_E_CUDA, "cudaStreamSynchronize failed: %s", cudaGetErrorString(e));
+  return collect_checks();
+}
+}  // namespace
+
 struct fkd_stream {
   fkd_params p{};
   Geometry g{};
@@ -76,13 +126,11 @@ struct fkd_stream {
   int* rowcell = nullptr;
   int* bincell_off = nullptr;  // per bin: start of its cells (NB + 1)
   int* bincell = nullptr;      // cells of every bin
-  uint32_t* cellinfo = nullptr;  // per cell: chunk << 12 | bin
 
   Scratch s{};
   uint32_t* state_bits[2] = {nullptr, nullptr};
   uint8_t* state_score[2] = {nullptr, nullptr};
   uint32_t* state_cnt[2] = {nullptr, nullptr};
-  uint32_t* state_kcnt[2] = {nullptr, nullptr};  // keypoints of the kept set per cell
   int state_cur = 0;
 
   uint8_t* staging[2] = {nullptr, nullptr};
@@ -144,11 +192,21 @@ struct fkd_stream {
   template <class T>
   int alloc(T** p, size_t count) {
     void* d = nullptr;
-    cudaError_t e = cudaMalloc(&d, std::max<size_t>(count, 1) * sizeof(T));
-    if (e != cudaSuccess) return fail(FKD_E_CUDA, "cudaMalloc(%zu) failed: %s", count * sizeof(T), cudaGetErrorString(e));
-    allocs.emplace_back(d, std::max<size_t>(count, 1) * sizeof(T));
-    bytes_held += allocs.back().second;
-    *p = static_cast<T*>(d);
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&d, bytes + 2 * kGuard);
+    if (e != cudaSuccess) return fail(FKD_E_CUDA, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    if (kGuard) {
+      e = cudaMemset(d, kGuardByte, kGuard);
+      if (e == cudaSuccess) e = cudaMemset(static_cast<char*>(d) + kGuard + bytes, kGuardByte, kGuard);
+      if (e != cudaSuccess) {
+        cudaFree(d);
+        return fail(FKD_E_CUDA, "guard fill failed: %s", cudaGetErrorString(e));
+      }
+    }
+    void* user = static_cast<char*>(d) + kGuard;
+    allocs.emplace_back(user, bytes);
+    bytes_held += bytes + 2 * kGuard;
+    *p = static_cast<T*>(user);
     return FKD_OK;
   }
   // free one allocation made by alloc()
@@ -157,14 +215,14 @@ struct fkd_stream {
     if (!p) return;
     auto it = std::find_if(allocs.begin(), allocs.end(), [&](const auto& a) { return a.first == (void*)p; });
     if (it != allocs.end()) {
-      bytes_held -= it->second;
+      bytes_held -= it->second + 2 * kGuard;
       allocs.erase(it);
     }
-    cudaFree(p);
+    cudaFree(reinterpret_cast<char*>(p) - kGuard);
     p = nullptr;
   }
   void release() {
-    for (auto& a : allocs) cudaFree(a.first);
+    for (auto& a : allocs) cudaFree(static_cast<char*>(a.first) - kGuard);
     allocs.clear();
     bytes_held = 0;
     for (auto& pd : pending)
@@ -330,12 +388,6 @@ int build_geometry(fkd_stream* s, int W, int H) {
   for (const AsmChunk& ch : chunks)
     for (int r = ch.rb0; r <= ch.rb1; ++r)
       for (int c = 0; c < p.N_c; ++c) per_bin[r * p.N_c + c].push_back(ch.cell0 + (r - ch.rb0) * p.N_c + c);
-  std::vector<uint32_t> cellinfo(cells);
-  for (int ci = 0; ci < (int)chunks.size(); ++ci) {
-    const AsmChunk& ch = chunks[ci];
-    for (int i = 0; i < (ch.rb1 - ch.rb0 + 1) * p.N_c; ++i)
-      cellinfo[ch.cell0 + i] = ((uint32_t)ci << 12) | (uint32_t)((ch.rb0 + i / p.N_c) * p.N_c + i % p.N_c);
-  }
   std::vector<int> bincell_off(1, 0), bincell;
   for (const auto& v : per_bin) {
     bincell.insert(bincell.end(), v.begin(), v.end());
@@ -356,11 +408,8 @@ int build_geometry(fkd_stream* s, int W, int H) {
       (rc = s->alloc(&s->tile_shape[0], all_tiles)) || (rc = s->alloc(&s->chunks, chunks.size())) ||
       (rc = s->alloc(&s->wbins, wbins.size())) || (rc = s->alloc(&s->wmask, wmask.size())) ||
       (rc = s->alloc(&s->rowchunk, rowchunk.size())) || (rc = s->alloc(&s->rowcell, rowcell.size())) ||
-      (rc = s->alloc(&s->bincell_off, bincell_off.size())) || (rc = s->alloc(&s->bincell, bincell.size())) ||
-      (rc = s->alloc(&s->cellinfo, cellinfo.size())))
+      (rc = s->alloc(&s->bincell_off, bincell_off.size())) || (rc = s->alloc(&s->bincell, bincell.size())))
     return rc;
-  if (!cellinfo.empty())
-    CK(cudaMemcpy(s->cellinfo, cellinfo.data(), cellinfo.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->bincell_off, bincell_off.data(), bincell_off.size() * sizeof(int), cudaMemcpyHostToDevice));
   if (!bincell.empty())
     CK(cudaMemcpy(s->bincell, bincell.data(), bincell.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -397,7 +446,7 @@ int allocate_state(fkd_stream* s) {
       (rc = s->alloc(&sc.det_bits, (size_t)(T * std::max(g.bit_words, 1LL)))) ||
       (rc = s->alloc(&sc.det_score, (size_t)(T * g.score_bytes))) ||
       (rc = s->alloc(&sc.chunk_counts, (size_t)(T * std::max(g.n_chunks, 1)))) ||
-      (rc = s->alloc(&sc.dcnt, (size_t)(T * std::max(g.n_cells, 1)))) || (rc = s->alloc(&sc.alive, (size_t)g.NB)) ||
+      (rc = s->alloc(&sc.alive, (size_t)g.NB)) ||
       (rc = s->alloc(&sc.merged, (size_t)(T * std::max(g.bit_words, 1LL)))) ||
       (rc = s->alloc(&sc.bases, (size_t)(T + 1))) || (rc = s->alloc(&sc.done, 1)) ||
       (rc = s->alloc(&sc.frame_totals, (size_t)T)) || (rc = s->alloc(&sc.out_base, 2)) ||
@@ -408,6 +457,8 @@ int allocate_state(fkd_stream* s) {
   CK(cudaMemset(sc.done, 0, 4));
   sc.pmask = nullptr;
   sc.pyr_last = nullptr;
+  sc.dcnt = nullptr;
+  if (s->p.mask_mode == FKD_MASK_KB && (rc = s->alloc(&sc.dcnt, (size_t)(T * std::max(g.n_cells, 1))))) return rc;
   if (s->p.mask_mode == FKD_MASK_IDP &&
       ((rc = s->alloc(&sc.pmask, (size_t)(T * std::max(g.bit_words, 1LL)))) ||
        (rc = s->alloc(&sc.pyr_last, (size_t)g.pyr_bytes))))
@@ -415,12 +466,10 @@ int allocate_state(fkd_stream* s) {
   for (int i = 0; i < 2; ++i) {
     if ((rc = s->alloc(&s->state_bits[i], (size_t)std::max(g.bit_words, 1LL))) ||
         (rc = s->alloc(&s->state_score[i], (size_t)g.score_bytes)) ||
-        (rc = s->alloc(&s->state_cnt[i], (size_t)g.NB)) ||
-        (rc = s->alloc(&s->state_kcnt[i], (size_t)std::max(g.n_cells, 1))))
+        (rc = s->alloc(&s->state_cnt[i], (size_t)g.NB)))
       return rc;
     CK(cudaMemset(s->state_bits[i], 0, (size_t)std::max(g.bit_words, 1LL) * 4));
     CK(cudaMemset(s->state_cnt[i], 0, (size_t)g.NB * 4));
-    CK(cudaMemset(s->state_kcnt[i], 0, (size_t)std::max(g.n_cells, 1) * 4));
   }
   CK(cudaMemset(sc.bsum, 0, (size_t)(T * g.NB) * 8));
   sc.bsum_stride = (int)T;
@@ -447,7 +496,7 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   b.c0_vec = 0;
   Params pr{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode, s->p.nms_scale};
   Tables tb{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask, s->rowchunk,
-            s->rowcell, s->bincell_off, s->bincell, s->cellinfo};
+            s->rowcell, s->bincell_off, s->bincell};
   State stt{};
   stt.bits_in = s->state_bits[s->state_cur];
   stt.score_in = s->state_score[s->state_cur];
@@ -455,8 +504,6 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   stt.bits_out = s->state_bits[s->state_cur ^ 1];
   stt.score_out = s->state_score[s->state_cur ^ 1];
   stt.cnt_out = s->state_cnt[s->state_cur ^ 1];
-  stt.kcnt_in = s->state_kcnt[s->state_cur];
-  stt.kcnt_out = s->state_kcnt[s->state_cur ^ 1];
   Output o{out, cap, offsets, base_slot};
   if (s->desc_D) {
     o.row_base = s->desc_rows;
@@ -501,7 +548,7 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
   }
   mark(4);
   if (s->s.pmask) launch_count_pixel(s->g, tb, b, s->s, stt, s->st);  // its last CTA fills bases
-  else launch_offsets(s->g, tb, b, s->s, stt, s->st);                 // its last CTA fills s->s.bases
+  else launch_count(s->g, tb, b, s->s, stt, s->st);                   // its last CTA fills s->s.bases
   mark(5);
   launch_emit(s->g, tb, b, s->s, stt, o, s->st);
   mark(6);
@@ -532,6 +579,7 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
     CK(cudaMemcpyAsync(s->s.pyr_last, s->s.pyr + (long long)(T - 1) * s->g.pyr_bytes, (size_t)s->g.pyr_bytes,
                        cudaMemcpyDeviceToDevice, s->st));
   CK(cudaGetLastError());
+  if (int rc = check_after(s->st)) return rc;
   if (prof) {
     pd.frames = T;
     s->pending.push_back(pd);
@@ -1104,6 +1152,27 @@ int fkd_device_keypoints(fkd_stream* s, const fkd_keypoint** records, const uint
   return FKD_OK;
 }
 
+int fkd_check_build(void) { return FKD_CHECK ? 1 : 0; }
+
+int fkd_check_guards(const fkd_stream* s) {
+  if (!s) return fail(FKD_E_ARG, "stream is NULL");
+#if FKD_CHECK
+  CK(cudaStreamSynchronize(s->st));
+  std::vector<unsigned char> band(kGuard);
+  for (const auto& a : s->allocs) {
+    for (int side = 0; side < 2; ++side) {
+      const char* at = static_cast<const char*>(a.first) + (side ? (long long)a.second : -(long long)kGuard);
+      CK(cudaMemcpy(band.data(), at, kGuard, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < kGuard; ++i)
+        if (band[i] != kGuardByte)
+          return fail(FKD_E_CUDA, "guard band %s an allocation of %zu bytes changed at byte %zu",
+                      side ? "after" : "before", a.second, i);
+    }
+  }
+#endif
+  return FKD_OK;
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------------ groups
@@ -1185,15 +1254,15 @@ StreamDev make_dev(const fkd_stream* s, const GroupStream& gs) {
   StreamDev d{};
   d.g = s->g;
   d.tb = Tables{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask, s->rowchunk,
-                s->rowcell, s->bincell_off, s->bincell, s->cellinfo};
+                s->rowcell, s->bincell_off, s->bincell};
   d.s = s->s;
   d.s.bases = nullptr;  // group ticks (one frame) compute their offsets in place
+  d.s.dcnt = nullptr;   // detection counts serve keypoint binning in spans of a batch only
   d.p = Params{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode, s->p.nms_scale};
   for (int i = 0; i < 2; ++i) {
     d.state_bits[i] = s->state_bits[i];
     d.state_score[i] = s->state_score[i];
     d.state_cnt[i] = s->state_cnt[i];
-    d.state_kcnt[i] = s->state_kcnt[i];
     d.last[i] = last[i];
   }
   d.rec[0] = s->rec;
@@ -1233,7 +1302,7 @@ int group_launch(fkd_group* G, int b, int n_items, fkd_stream::Pending* pd) {
   if (G->any_nms_scale)
     launch_group_scale_nms(G->d_devs, G->d_items, G->d_work, G->d_work_count, G->st);
   mark(4);
-  launch_group_offsets(G->d_devs, G->d_hdr, G->d_items, G->grid_small, G->st);
+  launch_group_count(G->d_devs, G->d_hdr, G->d_items, G->grid_asm, G->st);
   mark(5);
   launch_group_emit(G->d_devs, G->d_hdr, G->d_items, G->grid_asm, G->st);
   mark(6);
@@ -1478,6 +1547,7 @@ int fkd_group_tick(fkd_group* G, int n, const int* ids, const uint8_t* const* fr
     if (rc) return rc;
   }
   CK(cudaEventRecord(G->tick_done[b], G->st));
+  if (int rc = check_after(G->st)) return rc;
   G->ticks += 1;
   for (int i = 0; i < n; ++i) {
     fkd_stream* s = G->streams[ids[i]].s;
@@ -1709,6 +1779,14 @@ int fkd_group_autotune(fkd_group* G, int n, const int* ids, int m, const uint8_t
   if (rc2) return rc2;
   if (best) *best = win;
   if (best_ms) *best_ms = win_ms;
+  return FKD_OK;
+}
+
+int fkd_group_check_guards(fkd_group* G) {
+  if (!G) return fail(FKD_E_ARG, "group is NULL");
+  for (auto& gs : G->streams)
+    if (gs.s)
+      if (int rc = fkd_check_guards(gs.s)) return rc;
   return FKD_OK;
 }
 

@@ -63,6 +63,70 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// ------------------------------------------------------------ debug checks
+// Built with FKD_CHECK=1 (the debug library libfkd_check.so), the kernels
+// check the index of every shared- and global-memory access listed below
+// against its range; an index outside records (site, index, limit) in a
+// device record of its translation unit and the access is skipped -- no
+// fault, no trap. The host collects the records after each launch sequence
+// and returns the first as FKD_E_CUDA. Release builds compile the checks away.
+#ifndef FKD_CHECK
+#define FKD_CHECK 0
+#endif
+enum CheckSite : unsigned {
+  kChkDetStage = 1,  // detection: staged input (shared) / its source rows
+  kChkDetUnits,      // detection: (row, word) unit list
+  kChkDetWlist,      // detection: candidate word list
+  kChkDetScore,      // detection: score map (shared)
+  kChkDetPass,       // detection: pass / keypoint bitmap words (shared)
+  kChkDetBits,       // detection: the frame's keypoint bitmap (global)
+  kChkDetDscore,     // detection: the frame's score map (global)
+  kChkDetCells,      // detection: per-cell detection counts (global)
+  kChkPyrSmem,       // pyramid: a level's tile (shared)
+  kChkPyrBins,       // pyramid: per-bin change sums (shared / global)
+  kChkAsmWords,      // assembly: a chunk's words (shared / global)
+  kChkAsmPos,        // assembly: the chunk's list of set bits (shared)
+  kChkAsmSrc,        // assembly: source frames of the chunk's bins (shared)
+  kChkAsmBins,       // assembly: the kept set's per-bin counts (global)
+  kChkSites
+};
+struct CheckRecord {
+  unsigned hit, site;
+  long long index, limit;
+};
+// every translation unit of a debug build registers a function that takes
+// (and clears) its record
+using CheckTake = int (*)(CheckRecord*);
+int register_check(CheckTake take);
+#if FKD_CHECK
+static __device__ CheckRecord g_check_rec;  // one per translation unit
+__device__ __forceinline__ bool check_index(unsigned site, long long idx, long long limit) {
+  if (idx >= 0 && idx < limit) return true;
+  if (atomicCAS(&g_check_rec.hit, 0u, 1u) == 0u) {
+    g_check_rec.site = site;
+    g_check_rec.index = idx;
+    g_check_rec.limit = limit;
+  }
+  return false;
+}
+static int take_check_record(CheckRecord* out) {
+  CheckRecord r{};
+  if (cudaMemcpyFromSymbol(&r, g_check_rec, sizeof r) != cudaSuccess || !r.hit) return 0;
+  const CheckRecord zero{};
+  cudaMemcpyToSymbol(g_check_rec, &zero, sizeof zero);
+  *out = r;
+  return 1;
+}
+static const int g_check_registered = register_check(take_check_record);
+#define FKD_IDX(site, idx, limit) ::fkd::check_index((site), (long long)(idx), (long long)(limit))
+#else
+#define FKD_IDX(site, idx, limit) true
+#endif
+// Host: after the stream's work has finished, FKD_OK or FKD_E_CUDA with the
+// first recorded failure (debug builds; release builds return FKD_OK).
+int collect_checks();
+const char* check_site_name(unsigned site);
+
 struct LayerGeom {
   int w, h, S;         // size and scale code 2*sigma
   int pitch;           // row pitch in the pyramid and score buffers (multiple of 16)
@@ -121,7 +185,6 @@ struct Tables {
   const int* rowcell;      // per layer, per y: cell of (the row's chunk, bin row, bin column 0)
   const int* bincell_off;  // per bin: start of its cells in bincell (NB + 1 entries)
   const int* bincell;      // the cells of every bin (all layers), bin after bin
-  const uint32_t* cellinfo;  // per cell: its chunk << 12 | its bin
 };
 
 // Arguments of one batch of T consecutive frames of one stream.
@@ -152,9 +215,9 @@ struct Scratch {
   uint32_t* work_count;            // [1]
   uint32_t* det_bits;              // [T_max][bit_words]
   uint8_t* det_score;              // [T_max][score_bytes]
-  uint32_t* chunk_counts;          // [T_max][n_chunks]: records of each chunk (per-pixel masks), or
-                                   //   records of the frame before the chunk (bin masks)
-  uint32_t* dcnt;                  // [T_max][n_cells]: detections of each frame in each cell
+  uint32_t* chunk_counts;          // [T_max][n_chunks]
+  uint32_t* dcnt;                  // keypoint binning: [T_max][n_cells] detections of each frame in
+                                   //   each cell (null for the other mask modes)
   uint8_t* alive;                  // [NB]: keypoint binning in spans, bins active at the next frame
   uint32_t* merged;                // [T_max][bit_words]: D_n bitmap of every frame of the batch
   uint32_t* bases;                 // [T_max + 1]: records of the batch before each frame, then the total
@@ -173,11 +236,9 @@ struct State {
   const uint32_t* bits_in;
   const uint8_t* score_in;
   const uint32_t* cnt_in;          // keypoints per bin (for keypoint binning)
-  const uint32_t* kcnt_in;         // keypoints per cell
   uint32_t* bits_out;
   uint8_t* score_out;
   uint32_t* cnt_out;
-  uint32_t* kcnt_out;
 };
 
 struct Output {
@@ -229,7 +290,6 @@ struct StreamDev {
   uint32_t* state_bits[2];
   uint8_t* state_score[2];
   uint32_t* state_cnt[2];
-  uint32_t* state_kcnt[2];
   uint8_t* last[2];          // copies of the stream's last two frames (c_0, pitch layer[0].pitch)
   fkd_keypoint* rec[2];      // D_n of frame n in rec[n & 1] (K_max records each)
   uint32_t* rec_offsets[2];  // [2] each: 0 and |D_n|
@@ -270,8 +330,8 @@ void launch_group_worklist(const StreamDev* devs, const TickHeader* hdr, const T
                            uint32_t* work, uint32_t* work_count, int grid, cudaStream_t st);
 void launch_group_detect(const StreamDev* devs, const TickItem* items, const uint32_t* work,
                          const uint32_t* work_count, const DetLaunch& dl, cudaStream_t st);
-void launch_group_offsets(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
-                          int grid, cudaStream_t st);
+void launch_group_count(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
+                        int grid, cudaStream_t st);
 void launch_group_emit(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
                        int grid, cudaStream_t st);
 
@@ -324,11 +384,7 @@ void launch_detect(const Geometry& g, const Tables& tb, const Batch& b, const Sc
                    const Params& p, const DetLaunch& dl, cudaStream_t st);
 void launch_count(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                   const State& state, cudaStream_t st);
-// Bin masks: the records of every (frame, chunk) from the detection counts
-// per cell, the source frames and the kept set's counts (no pass over the
-// bitmaps); also the kept counts of the batch's last frame.
-void launch_offsets(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
-                    const State& state, cudaStream_t st);
+
 void launch_emit(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                  const State& state, const Output& out, cudaStream_t st);
 // FKD_MASK_IDP: per-pixel masks of every layer of the batch (Eq. 2 per

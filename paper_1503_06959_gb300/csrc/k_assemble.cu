@@ -7,25 +7,20 @@
 // the frame src(k, bin) -- the last frame up to k in which the bin was active
 // -- or from the kept set D_{n0-1} when the bin was inactive since the batch
 // began. Work is cut into chunks of whole rows of one layer, so a CTA knows
-// its layer and each row's bin row up front. A chunk's parts inside one bin
-// each are its cells.
-//   k_offsets (bin masks): the records of cell c of frame k are the detections
-//            the detection pass counted in cell c of frame src(k, bin(c)), or
-//            the kept set's count of cell c; their sums give every chunk's
-//            first record and every frame's total without reading a bitmap;
-//            the last frame's counts become the kept set's;
-//   k_count  (per-pixel masks): merge each word from its sources, store it,
-//            and sum the popcounts per chunk and per frame;
-//   k_emit:  merge (or load) the chunk's words, scan their popcounts, and
-//            write one record per set bit, in order.
+// its layer and each row's bin row up front.
+//   k_count: merge each word from its sources, store it, and sum the
+//            popcounts per chunk and per frame;
+//   k_emit:  turn chunk counts and frame totals into output offsets, scan the
+//            chunk's stored words, and write one record per set bit, in order.
 // The last frame of the batch also becomes the new kept set (bitmap, scores,
-// keypoints per bin and per cell).
+// keypoints per bin).
 #include "fkd_internal.cuh"
 
 namespace fkd {
 namespace {
 
-constexpr int kEmitList = 4096;  // set bits of a chunk emitted from a shared list (denser chunks: per thread)
+constexpr int kEmitList = 4096;
+constexpr int kSrcCache = 512;  // source frames of a chunk's bins kept in shared memory  // set bits of a chunk emitted from a shared list (denser chunks: per thread)
 static_assert(kAsmChunkWords * 32 <= 65536, "word * 32 + bit fits 16 bits");
 
 
@@ -84,6 +79,13 @@ __device__ __forceinline__ void count_chunk(const Geometry& g, const Tables& tb,
   const long long word0 = lg.bit_off + (long long)ch.y0 * wpr;
   const int* xst = tb.xstart + lg.xs_off;
   const int* src_k = s.src + (long long)k * g.NB;
+  // the source frames of the chunk's bin rows, in shared memory when they fit
+  __shared__ int srcs[kSrcCache];
+  const int nsrc = (ch.rb1 - ch.rb0 + 1) * g.N_c;
+  const bool src_local = !s.pmask && nsrc <= kSrcCache;
+  if (src_local)
+    for (int i = threadIdx.x; i < nsrc; i += kAsmThreads) srcs[i] = src_k[ch.rb0 * g.N_c + i];
+  __syncthreads();
   uint32_t* out = s.merged + (long long)k * g.bit_words + word0;
   // words tid, tid + 256, ...: coalesced; the count does not care about order
   const float inv_wpr = 1.0f / (float)wpr;
@@ -96,7 +98,8 @@ __device__ __forceinline__ void count_chunk(const Geometry& g, const Tables& tb,
       if (yy * wpr > j) --yy;
       if ((yy + 1) * wpr <= j) ++yy;
       const int wx = j - yy * wpr;
-      const int* srcrow = src_k + tb.rowblk[lg.row_off + ch.y0 + yy] * g.N_c;
+      const int r = tb.rowblk[lg.row_off + ch.y0 + yy];
+      const int* srcrow = src_local ? srcs + (r - ch.rb0) * g.N_c : src_k + r * g.N_c;
       uint32_t word;
       if (s.pmask) {
         word = out[j];  // per-pixel masks: merged by the per-pixel recurrence
@@ -146,108 +149,11 @@ __device__ __forceinline__ void count_chunk(const Geometry& g, const Tables& tb,
   __syncthreads();  // red and last_cta are reused by the next chunk of this CTA
 }
 
-// Records of every chunk of frame k (bin masks) from the per-cell counts:
-// cell c of bin b holds the detections of frame src(k, b) there, or the kept
-// set's when src < 0. The CTA writes, in chunk_counts, the frame's records
-// before each chunk (exclusive scan) and its total in frame_totals[k]; for the
-// batch's last frame (`last`) it also stores the counts as the new kept
-// set's and adds them up per bin for keypoint binning (Eqs. 3-4). With
-// s.bases, the CTA that finishes last of `total_ctas` turns the frame totals
-// into record offsets. One thread per cell (all cells' loads in flight at
-// once); chunk sums in shared memory when they fit, else in chunk_counts.
-// Ends with a barrier.
-constexpr int kOffChunks = 1024;
-__device__ __forceinline__ void offsets_frame(const Geometry& g, const Tables& tb, const Scratch& s, const State& st,
-                                              int k, bool last, int T, int total_ctas) {
-  __shared__ uint32_t wsum[kAsmThreads / 32];
-  __shared__ uint32_t csum[kOffChunks];
-  __shared__ uint32_t carry_sh;
-  __shared__ int last_cta;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int* src_k = s.src + (long long)k * g.NB;
-  uint32_t* cc = s.chunk_counts + (long long)k * g.n_chunks;
-  const bool local = g.n_chunks <= kOffChunks;
-  uint32_t* sums = local ? csum : cc;
-  for (int c = threadIdx.x; c < g.n_chunks; c += kAsmThreads) sums[c] = 0;
-  __syncthreads();
-  for (int cell = threadIdx.x; cell < g.n_cells; cell += kAsmThreads) {
-    const uint32_t info = tb.cellinfo[cell];  // chunk << 12 | bin
-    const int bin = (int)(info & 0xfffu), ch = (int)(info >> 12);
-    const int sf = src_k[bin];
-    const uint32_t v = sf < 0 ? st.kcnt_in[cell] : s.dcnt[(long long)sf * g.n_cells + cell];
-    if (last) {
-      st.kcnt_out[cell] = v;
-      if (v) atomicAdd(&st.cnt_out[bin], v);
-    }
-    if (v) atomicAdd(&sums[ch], v);
-  }
-  __syncthreads();
-  // exclusive scan of the chunk counts into chunk_counts, 256 at a time
-  if (threadIdx.x == 0) carry_sh = 0;
-  __syncthreads();
-  for (int c0 = 0; c0 < g.n_chunks; c0 += kAsmThreads) {
-    const int c = c0 + threadIdx.x;
-    const uint32_t v = c < g.n_chunks ? sums[c] : 0u;
-    uint32_t incl = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += o;
-    }
-    if (lane == 31) wsum[wid] = incl;
-    __syncthreads();
-    uint32_t before = carry_sh, total = 0;
-#pragma unroll
-    for (int q = 0; q < kAsmThreads / 32; ++q) {
-      before += q < wid ? wsum[q] : 0u;
-      total += wsum[q];
-    }
-    if (c < g.n_chunks) cc[c] = before + incl - v;
-    __syncthreads();
-    if (threadIdx.x == 0) carry_sh += total;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    s.frame_totals[k] = carry_sh;
-    bool lastc = false;
-    if (s.bases) {
-      __threadfence();
-      lastc = atomicAdd(s.done, 1u) == (unsigned)(total_ctas - 1);
-    }
-    last_cta = lastc;
-  }
-  __syncthreads();
-  if (last_cta && threadIdx.x < 32) {
-    // exclusive scan of the frame totals, 32 at a time
-    __threadfence();
-    uint32_t carry = 0;
-    for (int e0 = 0; e0 < T; e0 += 32) {
-      const int e = e0 + lane;
-      const uint32_t c = e < T ? __ldcg(&s.frame_totals[e]) : 0u;
-      uint32_t incl = c;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += v;
-      }
-      if (e < T) s.bases[e] = carry + incl - c;
-      carry += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (lane == 0) {
-      s.bases[T] = carry;
-      *s.done = 0u;
-    }
-  }
-  __syncthreads();
-}
-
 __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb, const Scratch& s,
                                              const State& st, const Output& out, int k, bool last,
                                              const AsmChunk& ch, const LayerGeom& lg, int j0,
                                              const uint32_t* words, unsigned long long idx, const int* srcs,
                                              bool src_local);
-
-constexpr int kEmitSrc = 512;  // source frames of a chunk's bins kept in shared memory
 
 // Emit the records of one chunk of frame k of a batch of T frames; the last
 // frame also writes the new kept set. Ends with a barrier.
@@ -264,32 +170,18 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
   const int wpr = lg.wpr;
   const int nwords = (ch.y1 - ch.y0) * wpr;
   const long long word0 = lg.bit_off + (long long)ch.y0 * wpr;
-  // the source frames of the bins of the chunk's bin rows, in shared memory
-  // when they fit (every merged word and record looks its bins up)
-  __shared__ int srcs[kEmitSrc];
+  // the source frames of the chunk's bin rows, in shared memory when they fit
+  __shared__ int srcs[kSrcCache];
   const int* src_k = s.src + (long long)k * g.NB;
   const int nsrc = (ch.rb1 - ch.rb0 + 1) * g.N_c;
-  const bool src_local = !s.pmask && nsrc <= kEmitSrc;
+  const bool src_local = !s.pmask && nsrc <= kSrcCache;
   if (src_local)
     for (int i = threadIdx.x; i < nsrc; i += kAsmThreads) srcs[i] = src_k[ch.rb0 * g.N_c + i];
   __syncthreads();
-  auto srcrow_of = [&](int r) -> const int* {
-    return src_local ? srcs + (r - ch.rb0) * g.N_c : src_k + r * g.N_c;
-  };
 
   // offsets: base of this call + earlier frames + earlier chunks of this frame
   uint32_t frame_base, chunk_base;
-  if (!s.pmask) {
-    // bin masks: the offsets pass stored the records before the chunk
-    chunk_base = s.chunk_counts[(long long)k * g.n_chunks + chunk];
-    if (s.bases) {
-      frame_base = s.bases[k];
-    } else {
-      uint32_t part = 0;
-      for (int q = threadIdx.x; q < k; q += kAsmThreads) part += s.frame_totals[q];
-      frame_base = block_sum(part, red);
-    }
-  } else if (s.bases) {
+  if (s.bases) {
     // warp 0 sums the earlier chunks of this frame (few) and shares it
     if (threadIdx.x < 32) {
       uint32_t part = 0;
@@ -318,29 +210,14 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
     }
   }
 
-  // the chunk's words -- merged here from their source frames (bin masks)
-  // or loaded (per-pixel masks: merged by the per-pixel recurrence) -- into
-  // shared memory, coalesced; each thread then takes 8 contiguous ones, so
-  // the scan order is the canonical order
+  // the chunk's words, loaded coalesced into shared memory; each thread then
+  // takes 8 contiguous ones, so the scan order is the canonical order
   const uint32_t* merged = s.merged + (long long)k * g.bit_words + word0;
-  const int* xst = tb.xstart + lg.xs_off;
-  const float inv_wpr_m = 1.0f / (float)wpr;
 #pragma unroll
   for (int jj = 0; jj < kAsmWordsPerThread; ++jj) {
     const int j = threadIdx.x + jj * kAsmThreads;
-    uint32_t v = 0u;
-    if (j < nwords) {
-      if (s.pmask) {
-        v = merged[j];
-      } else {
-        int yy = __float2int_rz((float)j * inv_wpr_m);  // j / wpr, fixed up below
-        if (yy * wpr > j) --yy;
-        if ((yy + 1) * wpr <= j) ++yy;
-        const int* srcrow = srcrow_of(tb.rowblk[lg.row_off + ch.y0 + yy]);
-        v = merge_word(g, tb, s, st, lg, xst, srcrow, word0, j, j - yy * wpr);
-      }
-    }
-    stage_words[j] = v;
+    const uint32_t v = j < nwords ? merged[j] : 0u;
+    if (FKD_IDX(kChkAsmWords, j, kAsmChunkWords)) stage_words[j] = v;
     if (last && j < nwords) st.bits_out[word0 + j] = v;
   }
   __syncthreads();
@@ -407,7 +284,8 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
     while (wv) {
       const int bit = __ffs(wv) - 1;
       wv &= wv - 1;
-      pos[at++] = (uint16_t)((j0 + jj) * 32 + bit);
+      if (FKD_IDX(kChkAsmPos, at, kEmitList)) pos[at] = (uint16_t)((j0 + jj) * 32 + bit);
+      ++at;
     }
   }
   __syncthreads();
@@ -434,7 +312,8 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
       const uint32_t mw = s.pmask[(long long)k * g.bit_words + word0 + j];
       flags = ((mw >> (p & 31)) & 1u) ? 0u : FKD_KP_PROPAGATED;
     } else {
-      const int sf = srcrow_of(r)[c];
+      const int sf = src_local && FKD_IDX(kChkAsmSrc, (r - ch.rb0) * g.N_c + c, kSrcCache)
+                         ? srcs[(r - ch.rb0) * g.N_c + c] : src_k[r * g.N_c + c];
       score = sf < 0 ? st.score_in[so] : s.det_score[(long long)sf * g.score_bytes + so];
       flags = sf != k ? FKD_KP_PROPAGATED : 0u;
     }
@@ -449,7 +328,7 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
     }
     if (last) {
       st.score_out[so] = score;
-      if (s.pmask) atomicAdd(&st.cnt_out[r * g.N_c + c], 1u);  // bin masks: counted by the offsets pass
+      if (FKD_IDX(kChkAsmBins, r * g.N_c + c, g.NB)) atomicAdd(&st.cnt_out[r * g.N_c + c], 1u);
     }
   }
   __syncthreads();  // red, wsum and pos are reused by the next chunk of this CTA
@@ -498,7 +377,7 @@ __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb
         ++idx;
         if (last) {
           st.score_out[row_off + x] = score;
-          if (s.pmask) atomicAdd(&st.cnt_out[r * g.N_c + c], 1u);  // bin masks: counted by the offsets pass
+          if (FKD_IDX(kChkAsmBins, r * g.N_c + c, g.NB)) atomicAdd(&st.cnt_out[r * g.N_c + c], 1u);
         }
       }
     }
@@ -511,10 +390,6 @@ __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb
 
 __global__ void __launch_bounds__(kAsmThreads) k_count(Geometry g, Tables tb, Scratch s, State st, int T) {
   count_chunk(g, tb, s, st, blockIdx.y, blockIdx.x, T, gridDim.x * gridDim.y);
-}
-
-__global__ void __launch_bounds__(kAsmThreads) k_offsets(Geometry g, Tables tb, Scratch s, State st, int T) {
-  offsets_frame(g, tb, s, st, blockIdx.x, blockIdx.x == T - 1, T, gridDim.x);
 }
 
 __global__ void __launch_bounds__(kAsmThreads) k_emit(Geometry g, Tables tb, Batch b, Scratch s,
@@ -530,20 +405,18 @@ __device__ __forceinline__ State state_of(const StreamDev& d, int cur) {
   st.bits_out = d.state_bits[cur ^ 1];
   st.score_out = d.state_score[cur ^ 1];
   st.cnt_out = d.state_cnt[cur ^ 1];
-  st.kcnt_in = d.state_kcnt[cur];
-  st.kcnt_out = d.state_kcnt[cur ^ 1];
   return st;
 }
 
-// Group tick: persistent CTAs over the participating frames (one frame of
-// each stream): the records of each chunk from the per-cell counts.
-__global__ void __launch_bounds__(kAsmThreads) k_group_offsets(const StreamDev* devs, const TickHeader* hdr,
-                                                               const TickItem* items) {
-  const int n = hdr->n_items;
-  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+// Group tick: persistent CTAs over the chunks of every participating frame.
+__global__ void __launch_bounds__(kAsmThreads) k_group_count(const StreamDev* devs, const TickHeader* hdr,
+                                                             const TickItem* items) {
+  const int n = hdr->n_items, total = hdr->total_chunks;
+  for (int j = blockIdx.x; j < total; j += gridDim.x) {
+    const int i = find_item(n, j, [&](int q) { return items[q].chunk_base; });
     const TickItem it = items[i];
     const StreamDev& d = devs[it.sid];
-    offsets_frame(d.g, d.tb, d.s, state_of(d, it.state_cur), 0, true, 1, 0);
+    count_chunk(d.g, d.tb, d.s, state_of(d, it.state_cur), 0, j - it.chunk_base, 1, 0);
   }
 }
 
@@ -566,9 +439,9 @@ __global__ void __launch_bounds__(kAsmThreads) k_group_emit(const StreamDev* dev
 
 }  // namespace
 
-void launch_group_offsets(const StreamDev* devs, const TickHeader* hdr, const TickItem* items, int grid,
-                          cudaStream_t st) {
-  k_group_offsets<<<grid, kAsmThreads, 0, st>>>(devs, hdr, items);
+void launch_group_count(const StreamDev* devs, const TickHeader* hdr, const TickItem* items, int grid,
+                        cudaStream_t st) {
+  k_group_count<<<grid, kAsmThreads, 0, st>>>(devs, hdr, items);
 }
 
 void launch_group_emit(const StreamDev* devs, const TickHeader* hdr, const TickItem* items, int grid,
@@ -579,11 +452,6 @@ void launch_group_emit(const StreamDev* devs, const TickHeader* hdr, const TickI
 void launch_count(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                   const State& state, cudaStream_t st) {
   k_count<<<dim3(g.n_chunks, b.T), kAsmThreads, 0, st>>>(g, tb, s, state, b.T);
-}
-
-void launch_offsets(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
-                    const State& state, cudaStream_t st) {
-  k_offsets<<<b.T, kAsmThreads, 0, st>>>(g, tb, s, state, b.T);
 }
 
 void launch_emit(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,

@@ -138,7 +138,8 @@ struct Item {
   const uint16_t* rowblk;    // bin row of each layer row
   int N_c;
   const uint32_t* pmask;     // per-pixel mask of the layer (row 0; FKD_MASK_IDP), else null
-  uint32_t* dcnt;            // the frame's detections per cell (bin masks), else null
+  uint32_t* dcnt;            // the frame's detections per cell (keypoint binning), else null
+  int n_cells;               // cells per frame
   const int* rowcell;        // the layer's first cell of each row
   const uint32_t* wbins;     // the layer's bin columns of each bitmap word column
   const uint32_t* wmask;     // the layer's bits of each word column in its first bin
@@ -237,7 +238,8 @@ struct SingleSrc {
     it.rowblk = tb.rowblk + lg.row_off;
     it.N_c = g.N_c;
     it.pmask = s.pmask ? s.pmask + (long long)k * g.bit_words + lg.bit_off : nullptr;
-    it.dcnt = s.pmask ? nullptr : s.dcnt + (long long)k * g.n_cells;
+    it.dcnt = s.dcnt ? s.dcnt + (long long)k * g.n_cells : nullptr;
+    it.n_cells = g.n_cells;
     it.rowcell = tb.rowcell + lg.row_off;
     it.wbins = tb.wbins + lg.wb_off;
     it.wmask = tb.wmask + lg.wb_off;
@@ -263,7 +265,7 @@ struct SingleSrc {
     si.dscore = s.det_score + (long long)k * g.score_bytes + lg.score_off;
     si.dpitch = lg.pitch;
     si.w = lg.w;
-    si.dcnt = s.pmask ? nullptr : s.dcnt + (long long)k * g.n_cells;
+    si.dcnt = s.dcnt ? s.dcnt + (long long)k * g.n_cells : nullptr;
     si.rowcell = tb.rowcell + lg.row_off;
     si.wbins = tb.wbins + lg.wb_off;
     si.wmask = tb.wmask + lg.wb_off;
@@ -328,6 +330,7 @@ struct GroupSrc {
     it.N_c = d.g.N_c;
     it.pmask = nullptr;  // groups use bin masks
     it.dcnt = d.s.dcnt;
+    it.n_cells = d.g.n_cells;
     it.rowcell = d.tb.rowcell + lg.row_off;
     it.wbins = d.tb.wbins + lg.wb_off;
     it.wmask = d.tb.wmask + lg.wb_off;
@@ -469,7 +472,9 @@ __device__ __forceinline__ void stage(uint8_t* in, const Item& it, int lane, int
     uint8_t* dst = in + r_lo * IN_W + 16 * c_lo;
     for (int q = lane; q < n; q += 32) {
       const int r = __float2int_rz(((float)q + 0.5f) * inv), c = q - r * nch;
-      cp_async16(dst + r * IN_W + 16 * c, base + (long long)r * it.pitch + 16 * c, 16);
+      if (FKD_IDX(kChkDetStage, (r_lo + r) * IN_W + 16 * (c_lo + c), Shape<TH>::IN_BYTES - 15) &&
+          FKD_IDX(kChkDetStage, gy0 + r, it.h))
+        cp_async16(dst + r * IN_W + 16 * c, base + (long long)r * it.pitch + 16 * c, 16);
     }
     return;
   }
@@ -479,6 +484,7 @@ __device__ __forceinline__ void stage(uint8_t* in, const Item& it, int lane, int
     const int gy = it.y0 - 4 + r, gx = it.x0 - 16 + c;
     uint8_t* d = in + r * IN_W + c;
     const bool row_ok = gy >= 0 && gy < it.h;
+    if (!FKD_IDX(kChkDetStage, r * IN_W + c, Shape<TH>::IN_BYTES - 15)) continue;
     if (vec) {
       const int bytes = (row_ok && gx >= 0) ? max(0, min(16, it.w - gx)) : 0;
       cp_async16(d, bytes ? it.src + (long long)gy * it.pitch + gx : it.src, bytes);
@@ -588,7 +594,8 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
     int npass = 0;  // passing tile pixels (warp-uniform)
     auto add_word = [&](uint32_t entry) {
       const unsigned bal = __ballot_sync(0xffffffffu, (entry & 0x80808080u) != 0u);
-      if (entry & 0x80808080u) wlist[nw + __popc(bal & lt)] = entry;
+      if ((entry & 0x80808080u) && FKD_IDX(kChkDetWlist, nw + __popc(bal & lt), Sh::WLIST))
+        wlist[nw + __popc(bal & lt)] = entry;
       nw += __popc(bal);
     };
     if (rows_any) {
@@ -622,7 +629,8 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
         int at = incl - cnt;
-        for (uint32_t r = rows; r; r &= r - 1u) wlist[at++] = ((uint32_t)(lane + 1) << 8) | (uint32_t)(__ffs(r) - 1);
+        for (uint32_t r = rows; r; r &= r - 1u, ++at)
+          if (FKD_IDX(kChkDetUnits, at, Sh::WLIST)) wlist[at] = ((uint32_t)(lane + 1) << 8) | (uint32_t)(__ffs(r) - 1);
         __syncwarp();
         for (int u0 = 0; u0 < total; u0 += 32) {
           const uint32_t unit = u0 + lane < total ? wlist[u0 + lane] : 0u;
@@ -671,11 +679,12 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
             const int o = j ? o2 : o1;
             const uint32_t v = (sp >> (16 * j)) & 0xffffu;
             const bool ok = v >= t;
-            sc[sc_of(o)] = ok ? (uint8_t)v : 0;
+            if (FKD_IDX(kChkDetScore, sc_of(o), SC_BYTES)) sc[sc_of(o)] = ok ? (uint8_t)v : 0;
             const int r = o / IN_W, cc = o % IN_W;  // tile pixel: rows 4..TH+3, cols 16..TW+15
             if (ok && r >= 4 && r < TH + 4 && cc >= 16 && cc < TW + 16) {
               const int ly = r - 4, lx = cc - 16;
-              atomicOr(&passw[ly * (TW / 32) + (lx >> 5)], 1u << (lx & 31));
+              if (FKD_IDX(kChkDetPass, ly * (TW / 32) + (lx >> 5), DET_WORDS))
+                atomicOr(&passw[ly * (TW / 32) + (lx >> 5)], 1u << (lx & 31));
               pass[j] = true;
               po[j] = o;
             }
@@ -720,8 +729,10 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
         const int v = q[0];
         if (v > q[-SC_P - 1] && v > q[-SC_P] && v > q[-SC_P + 1] && v > q[-1] && v > q[1] &&
             v > q[SC_P - 1] && v > q[SC_P] && v > q[SC_P + 1]) {
-          atomicOr(&detw[ly * (TW / 32) + (lx >> 5)], 1u << (lx & 31));
-          dscore[(long long)(y0 + ly) * it.dpitch + x0 + lx] = (uint8_t)v;
+          if (FKD_IDX(kChkDetPass, ly * (TW / 32) + (lx >> 5), DET_WORDS))
+            atomicOr(&detw[ly * (TW / 32) + (lx >> 5)], 1u << (lx & 31));
+          if (FKD_IDX(kChkDetDscore, y0 + ly, h) && FKD_IDX(kChkDetDscore, x0 + lx, w))
+            dscore[(long long)(y0 + ly) * it.dpitch + x0 + lx] = (uint8_t)v;
         }
       }
     } else
@@ -739,7 +750,8 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
         if (v > q[-SC_P - 1] && v > q[-SC_P] && v > q[-SC_P + 1] && v > q[-1] && v > q[1] &&
             v > q[SC_P - 1] && v > q[SC_P] && v > q[SC_P + 1]) {
           atomicOr(&detw[idx], 1u << bb);
-          dscore[(long long)(y0 + ly) * it.dpitch + x0 + lx] = (uint8_t)v;
+          if (FKD_IDX(kChkDetDscore, y0 + ly, h) && FKD_IDX(kChkDetDscore, x0 + lx, w))
+            dscore[(long long)(y0 + ly) * it.dpitch + x0 + lx] = (uint8_t)v;
         }
       }
     }
@@ -754,8 +766,10 @@ __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) 
       const int ly = idx / (TW / 32), wx = x0 / 32 + idx % (TW / 32);
       if (y0 + ly < h && wx < it.wpr) {
         const uint32_t word = detw[idx];
-        bits[(long long)(y0 + ly) * it.wpr + wx] = word;
-        if (word && it.dcnt) count_word_v(it.dcnt + e_cell[j], word, wx, w, e_wb, e_wm, it.xstart, 1);
+        if (FKD_IDX(kChkDetBits, (long long)(y0 + ly) * it.wpr + wx, (long long)h * it.wpr))
+          bits[(long long)(y0 + ly) * it.wpr + wx] = word;
+        if (word && it.dcnt && FKD_IDX(kChkDetCells, e_cell[j] + (int)(e_wb >> 16), it.n_cells))
+          count_word_v(it.dcnt + e_cell[j], word, wx, w, e_wb, e_wm, it.xstart, 1);
       }
     }
     __syncwarp();

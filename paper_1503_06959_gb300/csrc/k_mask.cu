@@ -174,8 +174,8 @@ __global__ void k_worklist(Geometry g, Tables tb, Batch b, Scratch s, int k_lo, 
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = (long long)(k_hi - k_lo) * g.n_tiles;
   for (long long q = i; q < (long long)(k_hi - k_lo) * g.n_chunks; q += (long long)gridDim.x * blockDim.x)
-    s.chunk_counts[(long long)k_lo * g.n_chunks + q] = 0;  // summed by the assembly count pass (per-pixel masks)
-  if (!s.pmask)
+    s.chunk_counts[(long long)k_lo * g.n_chunks + q] = 0;  // summed by the assembly count pass
+  if (s.dcnt)
     for (long long q = i; q < (long long)(k_hi - k_lo) * g.n_cells; q += (long long)gridDim.x * blockDim.x)
       s.dcnt[(long long)k_lo * g.n_cells + q] = 0;  // the detection pass counts into them
   bool act = false;
@@ -304,7 +304,7 @@ __global__ void k_group_mask(const StreamDev* devs, const TickHeader* hdr, const
         d.s.out_base[0] = 0;
       }
     }
-    for (int q = bin + lane * d.g.NB; q < d.g.n_cells; q += 32 * d.g.NB) d.s.dcnt[q] = 0;
+    for (int q = bin + lane * d.g.NB; q < d.g.n_chunks; q += 32 * d.g.NB) d.s.chunk_counts[q] = 0;
   }
 }
 

@@ -99,7 +99,7 @@ __device__ __forceinline__ void half_level(const uint8_t* src, uint8_t* dst, con
                             __byte_perm(b1, 0, 0x4240) + __byte_perm(b1, 0, 0x4341) + 0x00020002u;
         // lanes hold sums <= 1022; >> 2 leaves each result in its lane's low byte
         const uint32_t v = __byte_perm((lo >> 2) & 0x00ff00ffu, (hi >> 2) & 0x00ff00ffu, 0x6420);
-        *reinterpret_cast<uint32_t*>(dst + y * M + 4 * xw) = v;
+        if (FKD_IDX(kChkPyrSmem, y * M + 4 * xw, M * M - 3)) *reinterpret_cast<uint32_t*>(dst + y * M + 4 * xw) = v;
         if (WRITE && y < o.ny) {
           const int x = 4 * xw;
           uint8_t* gp = o.p + (long long)y * o.pitch + x;
@@ -121,7 +121,7 @@ __device__ __forceinline__ void half_level(const uint8_t* src, uint8_t* dst, con
         const int y = q / M, x = q % M;
         const uint8_t* sp = src + (2 * y) * N + 2 * x;
         const uint8_t v = (uint8_t)((sp[0] + sp[1] + sp[N] + sp[N + 1] + 2u) >> 2);
-        dst[q] = v;
+        if (FKD_IDX(kChkPyrSmem, q, M * M)) dst[q] = v;
         if (WRITE && y < o.ny && x < o.nx) o.p[(long long)y * o.pitch + x] = v;
       }
     }
@@ -147,6 +147,7 @@ __device__ __forceinline__ void two_thirds(const uint8_t* src, uint8_t* dst, con
     const unsigned top = ((4u * p00 + e01 + 2u * p10 + 4u) / 9u) | (((4u * p02 + e01 + 2u * p12 + 4u) / 9u) << 8);
     const unsigned bot = ((4u * p20 + e21 + 2u * p10 + 4u) / 9u) | (((4u * p22 + e21 + 2u * p12 + 4u) / 9u) << 8);
     uint8_t* d = dst + (2 * by) * M + 2 * bx;
+    if (!FKD_IDX(kChkPyrSmem, (2 * by + 1) * M + 2 * bx, M * M - 1)) continue;
     *reinterpret_cast<uint16_t*>(d) = (uint16_t)top;
     *reinterpret_cast<uint16_t*>(d + M) = (uint16_t)bot;
     if (WRITE) {
@@ -284,8 +285,12 @@ __device__ __forceinline__ void pyramid_tile(uint8_t* smem, const Geometry& g, c
     const uint8_t* B = prv;
     auto flush = [&](int rb, int cb, uint32_t v) {
       if (!v) return;
-      if (local) atomicAdd(&bins[(rb - rb_lo) * ncols + (cb - cb_lo)], v);
-      else atomicAdd(&gsum[(long long)(rb * g.N_c + cb) * gstride], (unsigned long long)v);
+      if (local) {
+        if (FKD_IDX(kChkPyrBins, (rb - rb_lo) * ncols + (cb - cb_lo), kLocalBins))
+          atomicAdd(&bins[(rb - rb_lo) * ncols + (cb - cb_lo)], v);
+      } else if (FKD_IDX(kChkPyrBins, rb * g.N_c + cb, g.NB)) {
+        atomicAdd(&gsum[(long long)(rb * g.N_c + cb) * gstride], (unsigned long long)v);
+      }
     };
     // warp w takes a band of rows, lane l the 4-pixel word column l
     static_assert(P / 4 <= 32 && NT == 256, "one lane per word column, 8 row bands");

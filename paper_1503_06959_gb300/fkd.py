@@ -37,6 +37,7 @@ EXPORTS = [
     "fkd_group_get_launch_config", "fkd_group_set_launch_config", "fkd_group_autotune",
     "fkd_get_pixel_mask", "fkd_set_descriptor", "fkd_get_descriptors", "fkd_group_set_descriptor",
     "fkd_group_get_descriptors", "fkd_server_set_descriptor", "fkd_server_get_descriptors",
+    "fkd_check_build", "fkd_check_guards", "fkd_group_check_guards",
 ]
 STAGES = ["pyramid", "mask", "worklist", "detect", "count", "emit", "describe"]
 
@@ -86,12 +87,20 @@ class FkdError(RuntimeError):
 _lib = None
 
 
+def check_build_requested() -> bool:
+    """FKD_CHECK=1 in the environment selects the debug library
+    libfkd_check.so (index checks in the kernels, guard-banded allocations)."""
+    return os.environ.get("FKD_CHECK", "0") not in ("", "0")
+
+
 def load(build: bool = True) -> ctypes.CDLL:
-    """Load libfkd.so (building it first if asked). Raises if unavailable."""
+    """Load libfkd.so, or libfkd_check.so when FKD_CHECK=1 (building it first
+    if asked). Raises if unavailable."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build() if build else _build.LIB
+    check = check_build_requested()
+    path = _build.build(check=check) if build else (_build.LIB_CHECK if check else _build.LIB)
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library {path} is missing; run build() first")
     lib = ctypes.CDLL(path)
@@ -143,6 +152,9 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.fkd_server_get_descriptors.argtypes = [vp, c_int, vp, c_size, P(c_size)]
     lib.fkd_get_launch_config.argtypes = [vp, P(fkd_launch_config)]
     lib.fkd_set_launch_config.argtypes = [vp, P(fkd_launch_config)]
+    lib.fkd_check_build.argtypes = []
+    lib.fkd_check_guards.argtypes = [vp]
+    lib.fkd_group_check_guards.argtypes = [vp]
     lib.fkd_autotune.argtypes = [vp, vp, c_size, c_size, c_int, c_int, P(fkd_launch_config),
                                  P(ctypes.c_float)]
     lib.fkd_group_get_launch_config.argtypes = [vp, P(fkd_launch_config)]
@@ -319,6 +331,11 @@ class Stream:
             _check(_lib.fkd_get_descriptors(self._h, _ptr(res), n.value, ctypes.byref(n), 0))
         return res
 
+    def check_guards(self):
+        """fkd_check_guards: raises if a guard band of the stream's device
+        allocations changed (debug library; a no-op in the release one)."""
+        _check(_lib.fkd_check_guards(self._h))
+
     def frame_count(self) -> int:
         n = ctypes.c_int64()
         _check(_lib.fkd_frame_count(self._h, ctypes.byref(n)))
@@ -404,6 +421,10 @@ class Group:
         fa = (ctypes.c_void_p * n)(*[f.data_ptr() for f in frames])
         pa = (ctypes.c_size_t * n)(*[f.stride(0) for f in frames])
         _check(_lib.fkd_group_tick(self._h, n, ia, fa, pa))
+
+    def check_guards(self):
+        """fkd_group_check_guards over every stream of the group."""
+        _check(_lib.fkd_group_check_guards(self._h))
 
     def use_graph(self, on: bool):
         _check(_lib.fkd_group_use_graph(self._h, int(on)))
@@ -575,6 +596,11 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def check_build() -> bool:
+    """True when the loaded library is the debug build (fkd_check_build)."""
+    return bool(load().fkd_check_build())
 
 
 def id_mask_noalloc(cur, prev, N_r: int, N_c: int, T_I: int, mask_out, cuda_stream: int | None = None):

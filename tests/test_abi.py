@@ -27,6 +27,18 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
 
 
+def test_debug_library_loads_and_exports_every_declared_symbol():
+    """libfkd_check.so (FKD_CHECK=1: index checks, guard bands) builds, loads
+    without a GPU, exports the same entry points and says it is the debug
+    build; the release library says it is not."""
+    from paper_1503_06959_gb300 import build
+    dbg = ctypes.CDLL(build.build(check=True))
+    for name in declared_functions():
+        assert hasattr(dbg, name), name
+    assert dbg.fkd_check_build() == 1
+    assert fkd.load().fkd_check_build() == 0
+
+
 def test_params_default_and_validation_without_gpu():
     lib = fkd.load()
     p = fkd.params_default()
