@@ -499,6 +499,32 @@ int fkd_server_close_stream(fkd_server* s, int id);
  * FKD_E_CUDA (an earlier round failed). */
 int fkd_server_submit(fkd_server* s, int id, const uint8_t* frame, size_t pitch, int64_t arrival_ns);
 
+/* As fkd_server_submit, but the frame is queued by reference and uploaded
+ * from where it is (no copy on the host; pinned memory makes the upload
+ * asynchronous): it must stay valid and unmodified until its result has
+ * been collected (fkd_server_poll returns it, or fkd_server_drain returns).
+ * For callers whose frames already sit in pinned buffers (a capture or
+ * decode pipeline), and for load tests at rates a host copy cannot feed. */
+int fkd_server_submit_ref(fkd_server* s, int id, const uint8_t* frame, size_t pitch, int64_t arrival_ns);
+
+/* keep = 0: finished frames are counted and timed (fkd_server_get_stats)
+ * but their keypoints are not kept for fkd_server_poll (load tests that
+ * never poll); keep = 1 (the default): kept until polled. */
+int fkd_server_keep_results(fkd_server* s, int keep);
+
+/* Load generator: submits frame i of the n given (host memory, row pitch
+ * pitches[i]) to stream ids[i] by reference (fkd_server_submit_ref) at its
+ * arrival time arrival_ns[i] on the steady clock (CLOCK_MONOTONIC;
+ * non-decreasing), waiting in this thread (sleeping through long gaps,
+ * spinning through short ones) so that no interpreter sits in the loop.
+ * A frame whose stream already has 4 frames waiting is dropped and counted
+ * in *refused (may be NULL): offered load beyond what the loop serves shows
+ * as dropped frames and queueing latency. The frames must stay valid until
+ * fkd_server_drain returns. Errors: FKD_E_ARG (NULL argument, decreasing
+ * arrival times), and those of fkd_server_submit_ref. */
+int fkd_server_replay(fkd_server* s, int n, const int* ids, const uint8_t* const* frames, const size_t* pitches,
+                      const int64_t* arrival_ns, uint64_t* refused);
+
 /* Take the oldest finished frame of stream `id`: its index n and D_n
  * (sorted by (layer, y, x)) into host memory. Errors: FKD_E_STATE (nothing
  * finished yet), FKD_E_CAPACITY (more than cap records: the result stays

@@ -343,6 +343,16 @@ struct ResultRef {
   long long cap;  // records rec can hold (K_max)
 };
 
+// Serving: frames copied from device-accessible host memory (pinned) into
+// device staging by one kernel for all the frames of a round.
+struct UploadItem {
+  const uint8_t* src;  // device-accessible address of the host frame
+  long long src_pitch;
+  uint8_t* dst;
+  int dst_pitch, W, H;
+};
+void launch_upload(const UploadItem* items, int n, cudaStream_t st);
+
 // counts[i] = |D_n| of refs[i] (may exceed its cap); offsets[i] = records
 // gathered before item i, each item contributing min(count, cap), offsets[n]
 // = their total; records copied to out (up to out_cap) in that order.

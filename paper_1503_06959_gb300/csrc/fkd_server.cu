@@ -54,6 +54,10 @@ struct SStream {
   int W = 0, H = 0, pitch = 0, K_max = 0;
   size_t bytes = 0;            // device bytes charged to the budget
   uint8_t* ring = nullptr;     // pinned host frames, kRingSlots x W*H
+  const uint8_t* ref[kRingSlots] = {};  // a caller's frame queued by reference (else null: the ring's copy)
+  size_t ref_pitch[kRingSlots] = {};
+  const uint8_t* src_dev[kRingSlots] = {};  // device-accessible address of the slot's frame (null: copy by DMA)
+  uint8_t* ring_dev = nullptr;              // device-accessible address of the ring
   int64_t arrival[kRingSlots] = {};
   int head = 0, count = 0;     // queued frames (oldest at head), including in flight
   int in_flight = 0;           // of those, frames already in a launched tick
@@ -85,11 +89,14 @@ struct fkd_server {
   int error = FKD_OK;
   std::vector<SStream> streams;  // by group stream id
   long long cap = 0;             // records one tick can bring back
+  UploadItem* h_up[2] = {nullptr, nullptr};  // a round's frames read by the upload kernel
+  UploadItem* d_up[2] = {nullptr, nullptr};
   ResultRef* h_refs[2] = {nullptr, nullptr};
   ResultRef* d_refs[2] = {nullptr, nullptr};
   uint32_t* h_off[2] = {nullptr, nullptr};  // n + 1 offsets, then n counts
   uint32_t* d_off[2] = {nullptr, nullptr};
   std::string err_msg;                        // message of a worker failure
+  bool keep_results = true;                   // false: results are counted and timed, then dropped
   fkd_keypoint* h_out[2] = {nullptr, nullptr};
   fkd_keypoint* d_out[2] = {nullptr, nullptr};
   // statistics
@@ -120,15 +127,22 @@ bool any_ready(const fkd_server* S) {
 int fkd_server::launch_tick(TickRec& t, int b) {
   std::vector<const uint8_t*> frames;
   std::vector<size_t> pitches;
+  int nup = 0;
   for (int id = 0; id < (int)streams.size(); ++id) {
     SStream& s = streams[id];
     if (!s.open || s.count <= s.in_flight) continue;
     const int slot = (s.head + s.in_flight) % kRingSlots;
     const int64_t idx = s.taken;
     uint8_t* dst = s.dstage[idx & 1];
-    cudaError_t e = cudaMemcpy2DAsync(dst, s.pitch, s.ring + (size_t)slot * s.W * s.H, s.W, s.W, s.H,
-                                      cudaMemcpyHostToDevice, copy);
-    if (e != cudaSuccess) return set_error(FKD_E_CUDA, "frame upload failed: %s", cudaGetErrorString(e));
+    const uint8_t* from = s.ref[slot] ? s.ref[slot] : s.ring + (size_t)slot * s.W * s.H;
+    const size_t from_pitch = s.ref[slot] ? s.ref_pitch[slot] : (size_t)s.W;
+    if (s.src_dev[slot]) {
+      // pinned host memory the GPU can read: copied by the round's upload kernel
+      h_up[b][nup++] = UploadItem{s.src_dev[slot], (long long)from_pitch, dst, s.pitch, s.W, s.H};
+    } else {
+      cudaError_t e = cudaMemcpy2DAsync(dst, s.pitch, from, from_pitch, s.W, s.H, cudaMemcpyHostToDevice, copy);
+      if (e != cudaSuccess) return set_error(FKD_E_CUDA, "frame upload failed: %s", cudaGetErrorString(e));
+    }
     t.ids.push_back(id);
     t.index.push_back(idx);
     t.arrival.push_back(s.arrival[slot]);
@@ -139,6 +153,11 @@ int fkd_server::launch_tick(TickRec& t, int b) {
   }
   const int n = (int)t.ids.size();
   t.buf = b;
+  if (nup) {
+    cudaError_t e = cudaMemcpyAsync(d_up[b], h_up[b], (size_t)nup * sizeof(UploadItem), cudaMemcpyHostToDevice, copy);
+    if (e != cudaSuccess) return set_error(FKD_E_CUDA, "upload list copy failed: %s", cudaGetErrorString(e));
+    launch_upload(d_up[b], nup, copy);
+  }
   cudaEventRecord(copied[b], copy);
   cudaStreamWaitEvent(comp, copied[b], 0);
   int rc = fkd_group_tick(G, n, t.ids.data(), frames.data(), pitches.data());
@@ -164,7 +183,7 @@ void fkd_server::collect(const TickRec& t) {
   long long total = 0;
   if (e == cudaSuccess) {
     total = h_off[b][n];
-    const long long ncopy = std::min(total, cap);
+    const long long ncopy = keep_results ? std::min(total, cap) : 0;
     if (ncopy > 0) e = cudaMemcpyAsync(h_out[b], d_out[b], (size_t)ncopy * sizeof(fkd_keypoint),
                                        cudaMemcpyDeviceToHost, copy);
     if (e == cudaSuccess) e = cudaStreamSynchronize(copy);
@@ -181,6 +200,12 @@ void fkd_server::collect(const TickRec& t) {
     SStream& s = streams[t.ids[i]];
     const long long o = h_off[b][i], c = (long long)h_off[b][i + 1] - o;
     const long long raw = h_off[b][n + 1 + i];
+    s.head = (s.head + 1) % kRingSlots;
+    s.count -= 1;
+    s.in_flight -= 1;
+    lat_ms.push_back((t_done - t.arrival[i]) * 1e-6);
+    frames_done += 1;
+    if (!keep_results) continue;
     Result r;
     r.index = t.index[i];
     const long long keep = std::max(0LL, std::min(c, cap - o));
@@ -202,11 +227,6 @@ void fkd_server::collect(const TickRec& t) {
       }
     }
     s.results.push_back(std::move(r));
-    s.head = (s.head + 1) % kRingSlots;
-    s.count -= 1;
-    s.in_flight -= 1;
-    lat_ms.push_back((t_done - t.arrival[i]) * 1e-6);
-    frames_done += 1;
   }
   t_last = t_done;
   cv_done.notify_all();
@@ -253,7 +273,7 @@ int fkd_server_create(int O, int intra, size_t budget_bytes, size_t max_tick_key
   if (max_tick_keypoints < 1 || max_tick_keypoints > ((size_t)1 << 31))
     return set_error(FKD_E_ARG, "max_tick_keypoints outside 1..2^31");
   const size_t fixed = 2 * (max_tick_keypoints * sizeof(fkd_keypoint) + (2 * kMaxTickItems + 1) * 4 +
-                            kMaxTickItems * sizeof(ResultRef));
+                            kMaxTickItems * (sizeof(ResultRef) + sizeof(UploadItem)));
   if (fixed > budget_bytes)
     return set_error(FKD_E_BUDGET, "budget %zu below the server's own %zu bytes", budget_bytes, fixed);
   fkd_server* S = new (std::nothrow) fkd_server();
@@ -271,6 +291,8 @@ int fkd_server_create(int O, int intra, size_t budget_bytes, size_t max_tick_key
   for (int b = 0; b < 2; ++b) {
     if ((e = cudaEventCreateWithFlags(&S->copied[b], cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&S->done[b], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaHostAlloc(&S->h_up[b], kMaxTickItems * sizeof(UploadItem), cudaHostAllocDefault)) != cudaSuccess ||
+        (e = cudaMalloc(&S->d_up[b], kMaxTickItems * sizeof(UploadItem))) != cudaSuccess ||
         (e = cudaHostAlloc(&S->h_refs[b], kMaxTickItems * sizeof(ResultRef), cudaHostAllocDefault)) != cudaSuccess ||
         (e = cudaMalloc(&S->d_refs[b], kMaxTickItems * sizeof(ResultRef))) != cudaSuccess ||
         (e = cudaHostAlloc(&S->h_off[b], (2 * kMaxTickItems + 1) * 4, cudaHostAllocDefault)) != cudaSuccess ||
@@ -307,6 +329,8 @@ int fkd_server_destroy(fkd_server* S) {
     if (S->copied[b]) cudaEventDestroy(S->copied[b]);
     if (S->done[b]) cudaEventDestroy(S->done[b]);
     if (S->h_refs[b]) cudaFreeHost(S->h_refs[b]);
+    if (S->h_up[b]) cudaFreeHost(S->h_up[b]);
+    cudaFree(S->d_up[b]);
     if (S->h_off[b]) cudaFreeHost(S->h_off[b]);
     if (S->h_out[b]) cudaFreeHost(S->h_out[b]);
     cudaFree(S->d_refs[b]);
@@ -358,6 +382,13 @@ int fkd_server_open_stream(fkd_server* S, const fkd_params* p, int W, int H, int
     fkd_group_remove_stream(S->G, gid);
     return set_error(FKD_E_CUDA, "stream buffers: %s", cudaGetErrorString(e));
   }
+  {
+    // the ring as the device addresses it (pinned memory is mapped under
+    // unified addressing); without it frames are copied by DMA
+    void* dp = nullptr;
+    s.ring_dev = cudaHostGetDevicePointer(&dp, s.ring, 0) == cudaSuccess ? static_cast<uint8_t*>(dp) : nullptr;
+    if (!s.ring_dev) cudaGetLastError();
+  }
   s.open = true;
   S->used += bytes;
   *id = gid;
@@ -386,9 +417,25 @@ int fkd_server_close_stream(fkd_server* S, int id) {
   return FKD_OK;
 }
 
-int fkd_server_submit(fkd_server* S, int id, const uint8_t* frame, size_t pitch, int64_t arrival_ns) {
+}  // extern "C"
+
+namespace {
+
+// Queue the next frame of stream `id`: a copy into the stream's pinned ring,
+// or (by_ref) the caller's pointer, uploaded from where it is.
+int submit_frame(fkd_server* S, int id, const uint8_t* frame, size_t pitch, int64_t arrival_ns, bool by_ref) {
   if (!S || !frame) return set_error(FKD_E_ARG, "NULL argument");
   const int64_t t = arrival_ns > 0 ? arrival_ns : now_ns();
+  // a frame queued by reference is read by the upload kernel when it lies in
+  // pinned host memory the device can address, else copied by DMA
+  const uint8_t* src_dev = nullptr;
+  if (by_ref) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, frame) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer)
+      src_dev = static_cast<const uint8_t*>(a.devicePointer);
+    else
+      cudaGetLastError();  // an unregistered pointer is not an error of this call
+  }
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->error) return worker_error(S);
@@ -401,13 +448,64 @@ int fkd_server_submit(fkd_server* S, int id, const uint8_t* frame, size_t pitch,
       return set_error(FKD_E_CAPACITY, "stream %d already has %d frames waiting", id, kRingSlots);
     }
     const int slot = (s.head + s.count) % kRingSlots;
-    uint8_t* dst = s.ring + (size_t)slot * s.W * s.H;
-    for (int y = 0; y < s.H; ++y) std::memcpy(dst + (size_t)y * s.W, frame + (size_t)y * pitch, (size_t)s.W);
+    if (by_ref) {
+      s.ref[slot] = frame;
+      s.ref_pitch[slot] = pitch;
+      s.src_dev[slot] = src_dev;
+    } else {
+      s.ref[slot] = nullptr;
+      uint8_t* dst = s.ring + (size_t)slot * s.W * s.H;
+      for (int y = 0; y < s.H; ++y) std::memcpy(dst + (size_t)y * s.W, frame + (size_t)y * pitch, (size_t)s.W);
+      s.src_dev[slot] = s.ring_dev ? s.ring_dev + (size_t)slot * s.W * s.H : nullptr;
+    }
     s.arrival[slot] = t;
     s.count += 1;
     if (!S->t_first) S->t_first = t;
   }
   S->cv_work.notify_one();
+  return FKD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fkd_server_submit(fkd_server* S, int id, const uint8_t* frame, size_t pitch, int64_t arrival_ns) {
+  return submit_frame(S, id, frame, pitch, arrival_ns, false);
+}
+
+int fkd_server_submit_ref(fkd_server* S, int id, const uint8_t* frame, size_t pitch, int64_t arrival_ns) {
+  return submit_frame(S, id, frame, pitch, arrival_ns, true);
+}
+
+int fkd_server_keep_results(fkd_server* S, int keep) {
+  if (!S) return set_error(FKD_E_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->keep_results = keep != 0;
+  return FKD_OK;
+}
+
+int fkd_server_replay(fkd_server* S, int n, const int* ids, const uint8_t* const* frames, const size_t* pitches,
+                      const int64_t* arrival_ns, uint64_t* refused) {
+  if (!S || n < 0 || (n > 0 && (!ids || !frames || !pitches || !arrival_ns))) return set_error(FKD_E_ARG, "NULL argument");
+  uint64_t dropped = 0;
+  for (int i = 0; i < n; ++i) {
+    if (i > 0 && arrival_ns[i] < arrival_ns[i - 1]) return set_error(FKD_E_ARG, "arrival times must not decrease");
+    // wait for the arrival: sleep through long gaps, spin through short ones
+    for (;;) {
+      const int64_t left = arrival_ns[i] - now_ns();
+      if (left <= 0) break;
+      if (left > 200000) std::this_thread::sleep_for(std::chrono::nanoseconds(left - 100000));
+    }
+    const int rc = submit_frame(S, ids[i], frames[i], pitches[i], arrival_ns[i], true);
+    if (rc == FKD_E_CAPACITY) {
+      dropped += 1;
+    } else if (rc) {
+      if (refused) *refused = dropped;
+      return rc;
+    }
+  }
+  if (refused) *refused = dropped;
   return FKD_OK;
 }
 

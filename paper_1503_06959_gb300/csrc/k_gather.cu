@@ -1,4 +1,5 @@
-// k_gather.cu -- gather the keypoint sets of many streams into one buffer.
+// k_gather.cu -- gather the keypoint sets of many streams into one buffer,
+// and upload the frames of a serving round.
 //
 // After a group tick each stream's D_n sits in its own device buffer. The
 // serving loop copies all of them back to the host at once: one kernel turns
@@ -62,6 +63,41 @@ void launch_gather(const ResultRef* refs, int n, uint32_t* offsets, fkd_keypoint
                    cudaStream_t st) {
   k_gather_offsets<<<1, kGatherThreads, 0, st>>>(refs, n, offsets);
   k_gather_copy<<<max(1, min(n, 1024)), 256, 0, st>>>(refs, n, offsets, out, out_cap);
+}
+
+namespace {
+
+// Frame upload of a round: CTA (part, item) copies rows part*H/8 ..
+// (part+1)*H/8 - 1 of frame `item`, 16 bytes per thread per step when the
+// addresses, pitches and width allow it.
+constexpr int kUploadParts = 8;
+__global__ void __launch_bounds__(256) k_upload(const UploadItem* items) {
+  const UploadItem it = items[blockIdx.y];
+  const int y0 = (int)((long long)blockIdx.x * it.H / kUploadParts);
+  const int y1 = (int)((long long)(blockIdx.x + 1) * it.H / kUploadParts);
+  const bool vec = ((reinterpret_cast<uintptr_t>(it.src) | (uintptr_t)it.src_pitch |
+                     reinterpret_cast<uintptr_t>(it.dst) | (uintptr_t)it.dst_pitch | (uintptr_t)it.W) & 15) == 0;
+  if (vec) {
+    const int wv = it.W / 16;
+    const long long total = (long long)(y1 - y0) * wv;
+    for (long long q = threadIdx.x; q < total; q += blockDim.x) {
+      const int y = y0 + (int)(q / wv), x = (int)(q % wv);
+      reinterpret_cast<uint4*>(it.dst + (long long)y * it.dst_pitch)[x] =
+          reinterpret_cast<const uint4*>(it.src + (long long)y * it.src_pitch)[x];
+    }
+  } else {
+    const long long total = (long long)(y1 - y0) * it.W;
+    for (long long q = threadIdx.x; q < total; q += blockDim.x) {
+      const int y = y0 + (int)(q / it.W), x = (int)(q % it.W);
+      it.dst[(long long)y * it.dst_pitch + x] = it.src[(long long)y * it.src_pitch + x];
+    }
+  }
+}
+
+}  // namespace
+
+void launch_upload(const UploadItem* items, int n, cudaStream_t st) {
+  if (n > 0) k_upload<<<dim3(kUploadParts, n), 256, 0, st>>>(items);
 }
 
 }  // namespace fkd

@@ -38,6 +38,7 @@ EXPORTS = [
     "fkd_get_pixel_mask", "fkd_set_descriptor", "fkd_get_descriptors", "fkd_group_set_descriptor",
     "fkd_group_get_descriptors", "fkd_server_set_descriptor", "fkd_server_get_descriptors",
     "fkd_check_build", "fkd_check_guards", "fkd_group_check_guards",
+    "fkd_server_submit_ref", "fkd_server_keep_results", "fkd_server_replay",
 ]
 STAGES = ["pyramid", "mask", "worklist", "detect", "count", "emit", "describe"]
 
@@ -152,6 +153,10 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.fkd_server_get_descriptors.argtypes = [vp, c_int, vp, c_size, P(c_size)]
     lib.fkd_get_launch_config.argtypes = [vp, P(fkd_launch_config)]
     lib.fkd_set_launch_config.argtypes = [vp, P(fkd_launch_config)]
+    lib.fkd_server_submit_ref.argtypes = [vp, c_int, vp, c_size, ctypes.c_int64]
+    lib.fkd_server_keep_results.argtypes = [vp, c_int]
+    lib.fkd_server_replay.argtypes = [vp, c_int, P(c_int), P(vp), P(c_size), P(ctypes.c_int64),
+                                      P(ctypes.c_uint64)]
     lib.fkd_check_build.argtypes = []
     lib.fkd_check_guards.argtypes = [vp]
     lib.fkd_group_check_guards.argtypes = [vp]
@@ -545,6 +550,32 @@ class Server:
     def submit(self, sid: int, frame: np.ndarray, arrival_ns: int = 0):
         frame = np.ascontiguousarray(frame, dtype=np.uint8)
         _check(_lib.fkd_server_submit(self._h, sid, _ptr(frame), frame.strides[0], arrival_ns))
+
+    def submit_ref(self, sid: int, frame, arrival_ns: int = 0):
+        """fkd_server_submit_ref: queue a host frame (numpy or pinned torch
+        CPU tensor) by reference; it must stay alive until drained."""
+        ptr = frame.data_ptr() if hasattr(frame, "data_ptr") else frame.ctypes.data
+        pitch = frame.stride(0) if hasattr(frame, "data_ptr") else frame.strides[0]
+        _check(_lib.fkd_server_submit_ref(self._h, sid, ctypes.c_void_p(ptr), pitch, arrival_ns))
+
+    def keep_results(self, keep: bool):
+        _check(_lib.fkd_server_keep_results(self._h, int(keep)))
+
+    def replay(self, ids, frame_ptrs, pitches, arrival_ns) -> int:
+        """fkd_server_replay: submit frame_ptrs[i] (host addresses, kept alive
+        by the caller until drain) to ids[i] at arrival_ns[i] (steady clock),
+        in C; returns the number of frames dropped for a full queue."""
+        n = len(ids)
+        ia = np.ascontiguousarray(ids, dtype=np.int32)
+        fa = np.ascontiguousarray(frame_ptrs, dtype=np.uint64)
+        pa = np.ascontiguousarray(pitches, dtype=np.uint64)
+        ta = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        refused = ctypes.c_uint64()
+        _check(_lib.fkd_server_replay(self._h, n, ia.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                      fa.ctypes.data_as(ctypes.POINTER(ctypes.c_void_p)),
+                                      pa.ctypes.data_as(ctypes.POINTER(ctypes.c_size_t)),
+                                      ta.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(refused)))
+        return refused.value
 
     def poll(self, sid: int):
         """(frame index, keypoints) of the oldest finished frame, or None."""

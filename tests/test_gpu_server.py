@@ -118,3 +118,41 @@ def test_admission_by_memory_budget():
     idx, kp = srv.poll(b)
     assert idx == 0 and len(kp) > 0
     srv.close()
+
+
+def test_replay_by_reference_equals_oracle_and_drops_when_overloaded():
+    """fkd_server_replay submits pinned frames by reference at their arrival
+    times from C: the served results equal the oracle's; then an offered load
+    far beyond four queued frames per stream drops the surplus (counted) and
+    every frame it kept is still served, with results dropped on request."""
+    torch = pytest.importorskip("torch")
+    clips = {i: clip(i) for i in range(len(SPECS))}
+    expect = {i: oracle_run(i, clips[i]) for i in range(len(SPECS))}
+    pinned = {i: torch.from_numpy(clips[i]).pin_memory() for i in clips}
+    srv = fkd.Server(O, INTRA, budget_bytes=2 << 30, max_tick_keypoints=1 << 20)
+    ids = {i: srv.open_stream(SPECS[i][0], SPECS[i][1], **SPECS[i][2]) for i in clips}
+    t0 = time.monotonic_ns() + 50_000_000
+    ev = sorted((t0 + n * 3_000_000 + i * 500_000, i, n) for i in clips for n in range(FRAMES))
+    refused = srv.replay([ids[i] for _, i, _ in ev], [pinned[i][n].data_ptr() for _, i, n in ev],
+                         [pinned[i].stride(1) for _, i, _ in ev], [t for t, _, _ in ev])
+    srv.drain(60000)
+    assert refused == 0
+    for i in clips:
+        got = []
+        while (r := srv.poll(ids[i])) is not None:
+            got.append(r)
+        assert [r[0] for r in got] == list(range(FRAMES))
+        for n in range(FRAMES):
+            same(got[n][1], expect[i][n], f"replayed stream {i} frame {n}")
+    # overload: every frame of stream 2 offered at the same instant, 4 times over
+    srv.stats(reset=True)
+    srv.keep_results(False)
+    t1 = time.monotonic_ns() + 10_000_000
+    refused = srv.replay([ids[2]] * (4 * FRAMES), [pinned[2][n % FRAMES].data_ptr() for n in range(4 * FRAMES)],
+                         [pinned[2].stride(1)] * (4 * FRAMES), [t1] * (4 * FRAMES))
+    srv.drain(60000)
+    st = srv.stats()
+    assert refused > 0 and st["frames_done"] == 4 * FRAMES - refused
+    assert st["rejected_frames"] == refused
+    assert srv.poll(ids[2]) is None  # results were not kept
+    srv.close()
