@@ -799,8 +799,11 @@ def run_config4(args):
 
     def knee(points):
         """The highest offered load the loop kept up with (served >= 98 % of
-        it, nothing dropped), and the largest served rate seen."""
-        kept = [p for p in points if p["frames_dropped"] == 0 and p["fps"] >= 0.98 * p["offered_fps"]]
+        it, at most 0.1 % of its frames dropped: with four queued frames per
+        stream a Poisson burst can drop a frame well below capacity), and the
+        largest served rate seen."""
+        kept = [p for p in points
+                if p["frames_dropped"] <= 0.001 * p["frames_offered"] and p["fps"] >= 0.98 * p["offered_fps"]]
         return {"kept_up_to_offered_fps": max((p["offered_fps"] for p in kept), default=None),
                 "p99_ms_there": max(kept, key=lambda p: p["offered_fps"])["p99_ms"] if kept else None,
                 "max_served_fps": max(p["fps"] for p in points)}
