@@ -878,6 +878,7 @@ int fkd_push_frames(fkd_stream* s, const uint8_t* frames, size_t pitch, size_t f
   CK(cudaMemcpyAsync(&ov, s->s.overflow, 4, cudaMemcpyDeviceToHost, s->st));
   CK(cudaMemsetAsync(s->s.overflow, 0, 4, s->st));
   CK(cudaStreamSynchronize(s->st));
+  if (ov & 2) return fail(FKD_E_CUDA, "a pyramid tile copy did not complete");
   if (total > (long long)cap || ov)
     return fail(FKD_E_CAPACITY, "batch produced %lld keypoints, cap %zu", total, cap);
   return FKD_OK;
@@ -956,6 +957,7 @@ int fkd_synchronize(fkd_stream* s) {
   CK(cudaMemcpyAsync(&ov, s->s.overflow, 4, cudaMemcpyDeviceToHost, s->st));
   CK(cudaMemsetAsync(s->s.overflow, 0, 4, s->st));
   CK(cudaStreamSynchronize(s->st));
+  if (ov & 2) return fail(FKD_E_CUDA, "a pyramid tile copy did not complete");
   if (ov) return fail(FKD_E_CAPACITY, "an asynchronous batch dropped records past its capacity");
   return FKD_OK;
 }

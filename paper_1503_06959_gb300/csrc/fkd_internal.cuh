@@ -224,7 +224,7 @@ struct Scratch {
   uint32_t* done;                  // [1]: chunks counted (last-CTA scan)
   uint32_t* frame_totals;          // [T_max]
   unsigned long long* out_base;    // [2]: running output offset (ping-pong)
-  int* overflow;                   // [1]
+  int* overflow;                   // [1]: bit 0 records dropped past a capacity, bit 1 a tile copy that did not land
   unsigned long long* tile_stats;  // [2]: detection tiles and their layer pixels (running totals)
   uint8_t* ml_prev;                // the mask layer of the stream's last frame (mask layers above c_0)
   uint32_t* pmask;                 // [T_max][bit_words]: per-pixel masks, FKD_MASK_IDP only (else null)

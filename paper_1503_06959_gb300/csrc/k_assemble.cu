@@ -170,6 +170,15 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
   const int wpr = lg.wpr;
   const int nwords = (ch.y1 - ch.y0) * wpr;
   const long long word0 = lg.bit_off + (long long)ch.y0 * wpr;
+  // the chunk's merged words, loaded first so that the loads overlap the
+  // offset sums below
+  const uint32_t* merged = s.merged + (long long)k * g.bit_words + word0;
+  uint32_t v[kAsmWordsPerThread];
+#pragma unroll
+  for (int jj = 0; jj < kAsmWordsPerThread; ++jj) {
+    const int j = threadIdx.x + jj * kAsmThreads;
+    v[jj] = j < nwords ? merged[j] : 0u;
+  }
   // the source frames of the chunk's bin rows, in shared memory when they fit
   __shared__ int srcs[kSrcCache];
   const int* src_k = s.src + (long long)k * g.NB;
@@ -210,15 +219,13 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
     }
   }
 
-  // the chunk's words, loaded coalesced into shared memory; each thread then
-  // takes 8 contiguous ones, so the scan order is the canonical order
-  const uint32_t* merged = s.merged + (long long)k * g.bit_words + word0;
+  // the chunk's words, coalesced, into shared memory; each thread then takes
+  // 8 contiguous ones, so the scan order is the canonical order
 #pragma unroll
   for (int jj = 0; jj < kAsmWordsPerThread; ++jj) {
     const int j = threadIdx.x + jj * kAsmThreads;
-    const uint32_t v = j < nwords ? merged[j] : 0u;
-    if (FKD_IDX(kChkAsmWords, j, kAsmChunkWords)) stage_words[j] = v;
-    if (last && j < nwords) st.bits_out[word0 + j] = v;
+    if (FKD_IDX(kChkAsmWords, j, kAsmChunkWords)) stage_words[j] = v[jj];
+    if (last && j < nwords) st.bits_out[word0 + j] = v[jj];
   }
   __syncthreads();
   const int j0 = threadIdx.x * kAsmWordsPerThread;
@@ -324,7 +331,7 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
       rec.y = (uint32_t)ch.layer | ((uint32_t)score << 8) | (flags << 16);
       reinterpret_cast<uint2*>(out.rec)[idx] = rec;
     } else {
-      *s.overflow = 1;
+      atomicOr(s.overflow, 1);
     }
     if (last) {
       st.score_out[so] = score;
@@ -372,7 +379,7 @@ __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb
           rec.y = (uint32_t)ch.layer | ((uint32_t)score << 8) | (flags << 16);
           reinterpret_cast<uint2*>(out.rec)[idx] = rec;
         } else {
-          *s.overflow = 1;
+          atomicOr(s.overflow, 1);
         }
         ++idx;
         if (last) {

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kNewWarps * 32, kNewMinBlocks)
     const long long n_last = (long long)off[T] - last_first;
     const long long kept = max(0LL, end - last_first);
     *d.keep_n_out = (uint32_t)min(kept, d.keep_cap);
-    if (kept < n_last || kept > d.keep_cap) *s.overflow = 1;
+    if (kept < n_last || kept > d.keep_cap) atomicOr(s.overflow, 1);
   }
   const long long groups = end > first ? (end - first + 31) / 32 : 0;
   const uint2* recs = reinterpret_cast<const uint2*>(out.rec);
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kCarriedThreads) k_describe_carried(Geometry g
       if (j >= 0) from = d.keep_desc_in + j * DW;
     }
     if (!from) {
-      *d.missing = 1;  // only after an overflow dropped the origin record
+      atomicOr(d.missing, 1);  // only after an overflow dropped the origin record
       continue;
     }
     uint32_t* to = d.desc + idx * DW;
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(kCarriedThreads)
     const long long hi = gr + 1 < d.rows ? (long long)d.row_base[pp][gr + 1] : prev_end;
     const long long o = find_record(prev, lo, min(hi, prev_end), rec_key(r));
     if (o < 0) {
-      *d.s.overflow = 1;  // only after an overflow dropped the origin record
+      atomicOr(d.s.overflow, 1);  // only after an overflow dropped the origin record
       continue;
     }
     const uint32_t* from = d.desc[pp] + o * DW;

@@ -14,6 +14,16 @@
 //
 // 96 is a multiple of 3 * 2^5: for O <= 6 every layer's tile is whole, so the
 // 2x2 box and the 3x3 -> 2x2 resampling never cross a tile edge.
+//
+// In a batch whose frames allow it (16-byte aligned base, pitch and frame
+// stride) the c_0 tile -- and, for change sums on c_0, the previous frame's
+// tile -- arrives by one tensor-memory-access copy each (a 96 x 96 box of a
+// 3-D tensor map over the batch's frames, zero-filled outside the frame),
+// completed on an mbarrier; otherwise, and in group ticks, by cp.async.
+#include <mutex>
+
+#include <cuda.h>
+
 #include "fkd_internal.cuh"
 
 namespace fkd {
@@ -29,12 +39,56 @@ __host__ __device__ constexpr int d_off(int i) { return i == 0 ? r16(c_off(6)) :
 constexpr int kPyrSmem = d_off(6);
 
 constexpr int kLocalBins = 256;  // bins a tile may span and still sum in shared memory
+constexpr int kPrvOff = (kPyrSmem + 127) / 128 * 128;  // the previous frame's c_0 tile
 
 // Dynamic shared memory of a CTA: the tile's levels (c_0 first), then -- when
 // the change sums of c_0 may be needed -- the previous frame's c_0 tile and
-// the tile's bin sums.
-__host__ __device__ constexpr int pyr_smem(bool diff) { return kPyrSmem + (diff ? P * P + kLocalBins * 4 : 0); }
-static_assert(kPyrSmem % 16 == 0 && (P * P) % 16 == 0, "16-byte aligned regions");
+// the tile's bin sums. Both c_0 tiles start on 128-byte boundaries (tensor
+// copies land there).
+__host__ __device__ constexpr int pyr_smem(bool diff) { return diff ? kPrvOff + P * P + kLocalBins * 4 : kPyrSmem; }
+static_assert(kPyrSmem % 16 == 0 && (P * P) % 128 == 0, "aligned regions");
+
+// ---- tensor-memory-access copy of a c_0 tile, completed on an mbarrier
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  // make the initialised barrier visible to the copy engine
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Box (x, y) .. (x + 95, y + 95) of frame z into `dst` (128-byte aligned).
+// x is a multiple of 96, hence of 16 bytes.
+__device__ __forceinline__ void tma_tile(uint8_t* dst, const CUtensorMap* map, int x, int y, int z,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Wait for phase 0 of the barrier, for at most ~2^30 SM cycles (about half a
+// second): false when the copies have not landed by then.
+__device__ __forceinline__ bool mbar_wait0(uint64_t* bar) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_addr(bar))
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1LL << 30)) return false;
+  }
+}
 
 __device__ __forceinline__ uint32_t ld32(const uint8_t* p) {
   return *reinterpret_cast<const uint32_t*>(p);
@@ -221,24 +275,43 @@ __device__ __forceinline__ void build(const Geometry& g, uint8_t* pyr, uint8_t* 
 // of |I_n - I_{n-1}| on c_0 (if `diff`; the mask layer is c_0), and a copy of
 // the c_0 tile to `keep` (if not null, pitch `keep_pitch`). Ends with a
 // barrier, so a CTA can run it again at once.
+//
+// c0map (nullptr: cp.async): the batch's tensor map, this frame at z, the
+// previous one (when prev_in_map) at z - 1. A copy that has not landed after
+// the wait limit sets bit 1 of *err and the CTA leaves the tile.
 template <int O, int INTRA>
 __device__ __forceinline__ void pyramid_tile(uint8_t* smem, const Geometry& g, const Tables& tb,
                                              const uint8_t* frame, int pitch, const uint8_t* prevf,
                                              int prev_pitch, bool diff, uint8_t* pyr,
                                              unsigned long long* gsum, int gstride, uint8_t* keep,
-                                             int keep_pitch, int tx, int ty) {
+                                             int keep_pitch, int tx, int ty,
+                                             const CUtensorMap* c0map = nullptr, int z = 0,
+                                             bool prev_in_map = false, int* err = nullptr) {
   __shared__ uint16_t tcol[P], trow[P], trun[P];
+  __shared__ __align__(8) uint64_t tma_bar;
   uint8_t* cur = smem;
-  uint8_t* prv = smem + kPyrSmem;
+  uint8_t* prv = smem + kPrvOff;
   uint32_t* bins = reinterpret_cast<uint32_t*>(prv + P * P);
 
-  load_c0(cur, frame, pitch, tx * P, ty * P, g.W, g.H);
+  const bool via_tma = c0map && (smem_addr(smem) & 127u) == 0;
+  const bool prev_tma = via_tma && diff && prev_in_map;
+  if (via_tma) {
+    if (threadIdx.x == 0) mbar_init(&tma_bar);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(&tma_bar, (prev_tma ? 2u : 1u) * P * P);
+      tma_tile(cur, c0map, tx * P, ty * P, z, &tma_bar);
+      if (prev_tma) tma_tile(prv, c0map, tx * P, ty * P, z - 1, &tma_bar);
+    }
+  } else {
+    load_c0(cur, frame, pitch, tx * P, ty * P, g.W, g.H);
+  }
   const LayerGeom& mlg = g.layer[0];
   constexpr int mn = P;
   const int mgx0 = tx * mn, mgy0 = ty * mn;
   const int mnx = min(mn, mlg.w - mgx0), mny = min(mn, mlg.h - mgy0);
   if (diff) {
-    load_c0(prv, prevf, prev_pitch, tx * P, ty * P, g.W, g.H);
+    if (!prev_tma) load_c0(prv, prevf, prev_pitch, tx * P, ty * P, g.W, g.H);
     for (int q = threadIdx.x; q < kLocalBins; q += NT) bins[q] = 0;
     for (int q = threadIdx.x; q < mn; q += NT) {
       tcol[q] = q < mnx ? tb.colblk[mlg.col_off + mgx0 + q] : 0;
@@ -254,6 +327,19 @@ __device__ __forceinline__ void pyramid_tile(uint8_t* smem, const Geometry& g, c
   }
   cp_async_commit();
   cp_async_wait<0>();
+  if (via_tma) {
+    const bool landed = mbar_wait0(&tma_bar);
+    if (__syncthreads_or(!landed)) {
+      // not landed: flag it, wait once more for the copies still in flight
+      // (again bounded), and leave the tile
+      if (threadIdx.x == 0) {
+        if (err) atomicOr(err, 2);
+        mbar_wait0(&tma_bar);
+      }
+      __syncthreads();
+      return;
+    }
+  }
   __syncthreads();
 
   if (keep) {  // the frame's own copy of c_0, kept for the next frame's change test
@@ -360,8 +446,11 @@ __device__ __forceinline__ void pyramid_tile(uint8_t* smem, const Geometry& g, c
 
 template <int O, int INTRA>
 __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Geometry g, Tables tb, Batch b, Scratch s,
-                                                         Params p) {
-  extern __shared__ __align__(16) uint8_t smem[];
+                                                         Params p, const __grid_constant__ CUtensorMap c0map,
+                                                         int use_map) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  // the launch adds 128 bytes, so the tiles can start on a 128-byte boundary
+  uint8_t* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
   const int k = blockIdx.z;
   const uint8_t* frame = b.frames + (long long)k * b.frame_stride;
   // change sums of c_0 here; those of a coarser mask layer in the mask kernel
@@ -369,7 +458,8 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Geometry g, Tables tb, 
   const uint8_t* pf = k == 0 ? b.prev : frame - b.frame_stride;
   const int pp = k == 0 ? b.prev_pitch : b.pitch;
   pyramid_tile<O, INTRA>(smem, g, tb, frame, b.pitch, pf, pp, diff, s.pyr + (long long)k * g.pyr_bytes,
-                         s.bsum + k, s.bsum_stride, nullptr, 0, blockIdx.x, blockIdx.y);
+                         s.bsum + k, s.bsum_stride, nullptr, 0, blockIdx.x, blockIdx.y,
+                         use_map ? &c0map : nullptr, k, k > 0, s.overflow);
 }
 
 // Group tick: persistent CTAs over the c_0 tiles of every participating frame.
@@ -377,7 +467,7 @@ template <int O, int INTRA>
 __global__ void __launch_bounds__(kPyrThreads, 4) k_group_pyramid(const StreamDev* devs,
                                                                const TickHeader* hdr,
                                                                const TickItem* items) {
-  extern __shared__ __align__(16) uint8_t smem[];
+  extern __shared__ __align__(128) uint8_t smem[];
   const int n = hdr->n_items, total = hdr->total_pyr;
   for (int j = blockIdx.x; j < total; j += gridDim.x) {
     const int i = find_item(n, j, [&](int q) { return items[q].pyr_base; });
@@ -395,12 +485,47 @@ __global__ void __launch_bounds__(kPyrThreads, 4) k_group_pyramid(const StreamDe
   }
 }
 
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                   CUtensorMapFloatOOBfill);
+
+// The batch's frames as a 3-D byte tensor (x, y, frame) with 96 x 96 x 1
+// boxes, zero fill outside; false when the layout does not allow one (base,
+// pitch or frame stride not a multiple of 16, overlapping frames) or the
+// driver has no encoder.
+bool encode_c0_map(CUtensorMap* map, const Geometry& g, const Batch& b) {
+  static EncodeTiledFn encode = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<EncodeTiledFn>(f);
+  });
+  if (!encode || b.T < 1) return false;
+  const long long plane = (long long)b.pitch * g.H;
+  const long long fstride = b.T > 1 ? b.frame_stride : (plane + 15) / 16 * 16;
+  if ((reinterpret_cast<uintptr_t>(b.frames) & 15) || (b.pitch & 15) || (fstride & 15) || fstride < plane)
+    return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.W, (cuuint64_t)g.H, (cuuint64_t)b.T};
+  const cuuint64_t strides[2] = {(cuuint64_t)b.pitch, (cuuint64_t)fstride};
+  const cuuint32_t box[3] = {P, P, 1}, step[3] = {1, 1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(b.frames), dims, strides, box,
+                step, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int O, int INTRA>
 void launch_t(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s, const Params& p,
               cudaStream_t st) {
   dim3 grid(g.pyr_tiles_x, g.pyr_tiles_y, b.T);
   const int smem = pyr_smem(p.mask_mode == FKD_MASK_ID && g.mask_layer == 0);
-  k_pyramid<O, INTRA><<<grid, kPyrThreads, smem, st>>>(g, tb, b, s, p);
+  CUtensorMap map{};
+  const int use_map = encode_c0_map(&map, g, b) ? 1 : 0;
+  k_pyramid<O, INTRA><<<grid, kPyrThreads, smem + 128, st>>>(g, tb, b, s, p, map, use_map);
 }
 
 template <int O, int INTRA>
