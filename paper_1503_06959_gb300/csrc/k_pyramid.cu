@@ -186,33 +186,67 @@ __device__ __forceinline__ void half_level(const uint8_t* src, uint8_t* dst, con
 // block gives a 2x2 block; an output is the mean of its 1.5 x 1.5 footprint
 // (weights 4 for the corner it sits on, 2 and 2 for the half-covered edge
 // pixels, 1 for the quarter-covered centre, over 9), rounded to nearest.
+//
+// A thread takes four neighbouring blocks of one block row (a 3 x 12 input
+// patch: nine aligned words), blocks 0 and 1 in the two 16-bit lanes of one
+// set of registers and blocks 2 and 3 in another, so that every weighted sum
+// (at most 9 * 255 + 4) is one lane-wise add for two outputs; the divisions
+// by 9 run per lane, and each output row of the four blocks is 8 bytes.
 template <bool WRITE>
 __device__ __forceinline__ void two_thirds(const uint8_t* src, uint8_t* dst, const Out& o) {
   constexpr int NB = P / 3, N = P, M = 2 * P / 3;
+  static_assert(NB * (NB / 4) == NT, "one thread per four blocks of a block row");
+  const int by = threadIdx.x / (NB / 4), bq = threadIdx.x % (NB / 4);
+  const uint8_t* sp = src + (3 * by) * N + 12 * bq;
+  // lanes: L = left, C = middle, R = right column of each block; A = blocks
+  // (0, 1) of the four, B = blocks (2, 3); index = row of the block
+  uint32_t LA[3], CA[3], RA[3], LB[3], CB[3], RB[3];
 #pragma unroll
-  for (int q0 = 0; q0 < NB * NB; q0 += NT) {
-    const int q = q0 + threadIdx.x;
-    const int by = q / NB, bx = q % NB;
-    const uint8_t* sp = src + (3 * by) * N + 3 * bx;
-    const unsigned p00 = sp[0], p01 = sp[1], p02 = sp[2];
-    const unsigned p10 = sp[N], p11 = sp[N + 1], p12 = sp[N + 2];
-    const unsigned p20 = sp[2 * N], p21 = sp[2 * N + 1], p22 = sp[2 * N + 2];
-    const unsigned e01 = 2u * p01 + p11, e21 = 2u * p21 + p11;
-    const unsigned top = ((4u * p00 + e01 + 2u * p10 + 4u) / 9u) | (((4u * p02 + e01 + 2u * p12 + 4u) / 9u) << 8);
-    const unsigned bot = ((4u * p20 + e21 + 2u * p10 + 4u) / 9u) | (((4u * p22 + e21 + 2u * p12 + 4u) / 9u) << 8);
-    uint8_t* d = dst + (2 * by) * M + 2 * bx;
-    if (!FKD_IDX(kChkPyrSmem, (2 * by + 1) * M + 2 * bx, M * M - 1)) continue;
-    *reinterpret_cast<uint16_t*>(d) = (uint16_t)top;
-    *reinterpret_cast<uint16_t*>(d + M) = (uint16_t)bot;
-    if (WRITE) {
-      const int x = 2 * bx, y = 2 * by;
-      uint8_t* gp = o.p + (long long)y * o.pitch + x;
-      if (x + 2 <= o.nx) {
-        if (y < o.ny) *reinterpret_cast<uint16_t*>(gp) = (uint16_t)top;
-        if (y + 1 < o.ny) *reinterpret_cast<uint16_t*>(gp + o.pitch) = (uint16_t)bot;
-      } else if (x < o.nx) {
-        if (y < o.ny) gp[0] = (uint8_t)top;
-        if (y + 1 < o.ny) gp[o.pitch] = (uint8_t)bot;
+  for (int r = 0; r < 3; ++r) {
+    const uint32_t w0 = ld32(sp + r * N), w1 = ld32(sp + r * N + 4), w2 = ld32(sp + r * N + 8);
+    LA[r] = __byte_perm(w0, 0u, 0x4340);                // bytes 0, 3
+    CA[r] = __byte_perm(w0, w1, 0x0401) & 0x00ff00ffu;  // bytes 1, 4
+    RA[r] = __byte_perm(w0, w1, 0x0502) & 0x00ff00ffu;  // bytes 2, 5
+    LB[r] = __byte_perm(w1, w2, 0x0502) & 0x00ff00ffu;  // bytes 6, 9
+    CB[r] = __byte_perm(w1, w2, 0x0603) & 0x00ff00ffu;  // bytes 7, 10
+    RB[r] = __byte_perm(w2, 0u, 0x4340);                // bytes 8, 11
+  }
+  // per lane: top-left 4 p00 + 2 p01 + 2 p10 + p11 (+ 4 to round), etc.
+  auto sums = [](const uint32_t* L, const uint32_t* C, const uint32_t* R, uint32_t* q) {
+    const uint32_t e01 = 2u * C[0] + C[1] + 0x00040004u, e21 = 2u * C[2] + C[1] + 0x00040004u;
+    q[0] = 4u * L[0] + 2u * L[1] + e01;  // top-left
+    q[1] = 4u * R[0] + 2u * R[1] + e01;  // top-right
+    q[2] = 4u * L[2] + 2u * L[1] + e21;  // bottom-left
+    q[3] = 4u * R[2] + 2u * R[1] + e21;  // bottom-right
+  };
+  auto div9 = [](uint32_t v) { return ((v & 0xffffu) / 9u) | (((v >> 16) / 9u) << 16); };
+  uint32_t qa[4], qb[4];
+  sums(LA, CA, RA, qa);
+  sums(LB, CB, RB, qb);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    qa[i] = div9(qa[i]);
+    qb[i] = div9(qb[i]);
+  }
+  // output rows 2by (top) and 2by+1 (bottom), columns 8bq .. 8bq+7:
+  // left, right of block 0, of block 1, ... -> bytes of (left | right << 8)
+  const uint2 top = make_uint2(qa[0] | (qa[1] << 8), qb[0] | (qb[1] << 8));
+  const uint2 bot = make_uint2(qa[2] | (qa[3] << 8), qb[2] | (qb[3] << 8));
+  const int y = 2 * by, x = 8 * bq;
+  if (FKD_IDX(kChkPyrSmem, (y + 1) * M + x, M * M - 7)) {
+    *reinterpret_cast<uint2*>(dst + y * M + x) = top;
+    *reinterpret_cast<uint2*>(dst + (y + 1) * M + x) = bot;
+  }
+  if (WRITE) {
+    uint8_t* gp = o.p + (long long)y * o.pitch + x;
+    if (x + 8 <= o.nx) {
+      if (y < o.ny) *reinterpret_cast<uint2*>(gp) = top;
+      if (y + 1 < o.ny) *reinterpret_cast<uint2*>(gp + o.pitch) = bot;
+    } else if (x < o.nx) {
+      for (int j = 0; j < o.nx - x; ++j) {
+        const uint32_t tw = j < 4 ? top.x : top.y, bw = j < 4 ? bot.x : bot.y;
+        if (y < o.ny) gp[j] = (uint8_t)(tw >> (8 * (j & 3)));
+        if (y + 1 < o.ny) gp[o.pitch + j] = (uint8_t)(bw >> (8 * (j & 3)));
       }
     }
   }
@@ -445,7 +479,7 @@ __device__ __forceinline__ void pyramid_tile(uint8_t* smem, const Geometry& g, c
 }
 
 template <int O, int INTRA>
-__global__ void __launch_bounds__(kPyrThreads) k_pyramid(Geometry g, Tables tb, Batch b, Scratch s,
+__global__ void __launch_bounds__(kPyrThreads, 8) k_pyramid(Geometry g, Tables tb, Batch b, Scratch s,
                                                          Params p, const __grid_constant__ CUtensorMap c0map,
                                                          int use_map) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
