@@ -299,43 +299,53 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
   const int wpr_ = wpr;
   const float inv_wpr = 1.0f / (float)wpr_;
   const uint16_t* colblk = tb.colblk + lg.col_off;
-  for (uint32_t i = threadIdx.x; i < total; i += kAsmThreads) {
-    const int p = pos[i];
-    const int j = p >> 5;
-    int yy = __float2int_rz((float)j * inv_wpr);  // j / wpr, fixed up below
-    if (yy * wpr_ > j) --yy;
-    if ((yy + 1) * wpr_ <= j) ++yy;
-    const int y = ch.y0 + yy;
-    const int x = (j - yy * wpr_) * 32 + (p & 31);
-    const int r = tb.rowblk[lg.row_off + y];
-    const int c = colblk[x];
-    const long long so = lg.score_off + (long long)y * lg.pitch + x;
-    uint8_t score;
-    uint32_t flags;
-    if (s.pmask) {
-      // per-pixel masks: every frame's map holds its keypoints' scores; a
-      // keypoint is carried where its pixel was inactive
-      score = s.det_score[(long long)k * g.score_bytes + so];
-      const uint32_t mw = s.pmask[(long long)k * g.bit_words + word0 + j];
-      flags = ((mw >> (p & 31)) & 1u) ? 0u : FKD_KP_PROPAGATED;
-    } else {
-      const int sf = src_local && FKD_IDX(kChkAsmSrc, (r - ch.rb0) * g.N_c + c, kSrcCache)
-                         ? srcs[(r - ch.rb0) * g.N_c + c] : src_k[r * g.N_c + c];
-      score = sf < 0 ? st.score_in[so] : s.det_score[(long long)sf * g.score_bytes + so];
-      flags = sf != k ? FKD_KP_PROPAGATED : 0u;
-    }
-    const unsigned long long idx = base + i;
-    if (idx < (unsigned long long)out.cap) {
-      uint2 rec;
-      rec.x = (uint32_t)x | ((uint32_t)y << 16);
-      rec.y = (uint32_t)ch.layer | ((uint32_t)score << 8) | (flags << 16);
-      reinterpret_cast<uint2*>(out.rec)[idx] = rec;
-    } else {
-      atomicOr(s.overflow, 1);
+  // (the loop runs whole warps, so that the kept set's per-bin counts can be
+  // added once per bin and warp)
+  for (uint32_t i0 = 0; i0 < total; i0 += kAsmThreads) {
+    const uint32_t i = i0 + threadIdx.x;
+    int bin = -1;
+    if (i < total) {
+      const int p = pos[i];
+      const int j = p >> 5;
+      int yy = __float2int_rz((float)j * inv_wpr);  // j / wpr, fixed up below
+      if (yy * wpr_ > j) --yy;
+      if ((yy + 1) * wpr_ <= j) ++yy;
+      const int y = ch.y0 + yy;
+      const int x = (j - yy * wpr_) * 32 + (p & 31);
+      const int r = tb.rowblk[lg.row_off + y];
+      const int c = colblk[x];
+      const long long so = lg.score_off + (long long)y * lg.pitch + x;
+      uint8_t score;
+      uint32_t flags;
+      if (s.pmask) {
+        // per-pixel masks: every frame's map holds its keypoints' scores; a
+        // keypoint is carried where its pixel was inactive
+        score = s.det_score[(long long)k * g.score_bytes + so];
+        const uint32_t mw = s.pmask[(long long)k * g.bit_words + word0 + j];
+        flags = ((mw >> (p & 31)) & 1u) ? 0u : FKD_KP_PROPAGATED;
+      } else {
+        const int sf = src_local && FKD_IDX(kChkAsmSrc, (r - ch.rb0) * g.N_c + c, kSrcCache)
+                           ? srcs[(r - ch.rb0) * g.N_c + c] : src_k[r * g.N_c + c];
+        score = sf < 0 ? st.score_in[so] : s.det_score[(long long)sf * g.score_bytes + so];
+        flags = sf != k ? FKD_KP_PROPAGATED : 0u;
+      }
+      const unsigned long long idx = base + i;
+      if (idx < (unsigned long long)out.cap) {
+        uint2 rec;
+        rec.x = (uint32_t)x | ((uint32_t)y << 16);
+        rec.y = (uint32_t)ch.layer | ((uint32_t)score << 8) | (flags << 16);
+        reinterpret_cast<uint2*>(out.rec)[idx] = rec;
+      } else {
+        atomicOr(s.overflow, 1);
+      }
+      if (last) st.score_out[so] = score;
+      bin = r * g.N_c + c;
     }
     if (last) {
-      st.score_out[so] = score;
-      if (FKD_IDX(kChkAsmBins, r * g.N_c + c, g.NB)) atomicAdd(&st.cnt_out[r * g.N_c + c], 1u);
+      // consecutive records mostly share a bin: one atomic per bin and warp
+      const unsigned peers = __match_any_sync(0xffffffffu, bin);
+      if (bin >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1 && FKD_IDX(kChkAsmBins, bin, g.NB))
+        atomicAdd(&st.cnt_out[bin], (uint32_t)__popc(peers));
     }
   }
   __syncthreads();  // red, wsum and pos are reused by the next chunk of this CTA
@@ -350,6 +360,8 @@ __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb
   const int* src_k = s.src + (long long)k * g.NB;
   const uint16_t* colblk = tb.colblk + lg.col_off;
   int y = ch.y0 + j0 / wpr, wx = j0 % wpr;
+  int run_bin = -1;
+  uint32_t run_n = 0;
 #pragma unroll
   for (int jj = 0; jj < kAsmWordsPerThread; ++jj) {
     uint32_t wv = words[jj];
@@ -384,7 +396,14 @@ __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb
         ++idx;
         if (last) {
           st.score_out[row_off + x] = score;
-          if (FKD_IDX(kChkAsmBins, r * g.N_c + c, g.NB)) atomicAdd(&st.cnt_out[r * g.N_c + c], 1u);
+          // a thread's records run along its words: one atomic per run of a bin
+          const int bin = r * g.N_c + c;
+          if (bin != run_bin) {
+            if (run_n && FKD_IDX(kChkAsmBins, run_bin, g.NB)) atomicAdd(&st.cnt_out[run_bin], run_n);
+            run_bin = bin;
+            run_n = 0;
+          }
+          ++run_n;
         }
       }
     }
@@ -393,6 +412,7 @@ __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb
       ++y;
     }
   }
+  if (run_n && FKD_IDX(kChkAsmBins, run_bin, g.NB)) atomicAdd(&st.cnt_out[run_bin], run_n);
 }
 
 __global__ void __launch_bounds__(kAsmThreads) k_count(Geometry g, Tables tb, Scratch s, State st, int T) {
