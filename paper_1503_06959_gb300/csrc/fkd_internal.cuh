@@ -49,6 +49,31 @@ constexpr int kAsmChunkWords = kAsmThreads * kAsmWordsPerThread;
 // Mask kernel: one CTA per bin walks the batch's frames 256 at a time.
 constexpr int kMaskThreads = 256;
 
+// Programmatic dependent launch. A kernel launched with pdl_launch may be
+// scheduled while the kernel before it on the stream is still running; it
+// waits in pdl_wait() -- its first statement -- until that kernel has
+// completed and its memory is visible, so only launch latency overlaps.
+// pdl_trigger() lets the next kernel be scheduled once every CTA of this one
+// has started. Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Asynchronous 16-byte global -> shared copy (cp.async, LDGSTS): `bytes` of
 // the 16 are read (0..16) and the rest of the destination is zero-filled.
 // The source must be 16-byte aligned whenever bytes > 0.

@@ -416,11 +416,15 @@ __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb
 }
 
 __global__ void __launch_bounds__(kAsmThreads) k_count(Geometry g, Tables tb, Scratch s, State st, int T) {
+  pdl_wait();
+  pdl_trigger();
   count_chunk(g, tb, s, st, blockIdx.y, blockIdx.x, T, gridDim.x * gridDim.y);
 }
 
 __global__ void __launch_bounds__(kAsmThreads) k_emit(Geometry g, Tables tb, Batch b, Scratch s,
                                                       State st, Output out) {
+  pdl_wait();
+  pdl_trigger();
   emit_chunk(g, tb, s, st, out, blockIdx.y, b.T, blockIdx.x);
 }
 
@@ -478,12 +482,12 @@ void launch_group_emit(const StreamDev* devs, const TickHeader* hdr, const TickI
 
 void launch_count(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                   const State& state, cudaStream_t st) {
-  k_count<<<dim3(g.n_chunks, b.T), kAsmThreads, 0, st>>>(g, tb, s, state, b.T);
+  pdl_launch(k_count, dim3(g.n_chunks, b.T), dim3(kAsmThreads), 0, st, g, tb, s, state, b.T);
 }
 
 void launch_emit(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                  const State& state, const Output& out, cudaStream_t st) {
-  k_emit<<<dim3(g.n_chunks, b.T), kAsmThreads, 0, st>>>(g, tb, b, s, state, out);
+  pdl_launch(k_emit, dim3(g.n_chunks, b.T), dim3(kAsmThreads), 0, st, g, tb, b, s, state, out);
 }
 
 }  // namespace fkd

@@ -129,6 +129,8 @@ __device__ __forceinline__ uint32_t describe_record(const uint8_t* img, int pitc
 
 __global__ void __launch_bounds__(kNewWarps * 32, kNewMinBlocks)
     k_describe_new(Geometry g, Batch b, Scratch s, Output out, Describe d) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t pat[kDescMaxBits];                  // pair i: 16-bit indices of its two box sums
   __shared__ uint32_t boxes[kNewWarps][kHalfRows * kBoxPitch];  // 5 x 5 sums, two rows per word
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -196,6 +198,8 @@ __global__ void __launch_bounds__(kNewWarps * 32, kNewMinBlocks)
 
 __global__ void __launch_bounds__(kCarriedThreads) k_describe_carried(Geometry g, Tables tb, Batch b, Scratch s,
                                                                       Output out, Describe d) {
+  pdl_wait();
+  pdl_trigger();
   const int T = b.T;
   const uint32_t* off = out.offsets;
   const long long first = off[0];
@@ -421,8 +425,8 @@ __global__ void __launch_bounds__(kCarriedThreads)
 void launch_describe(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s, const Output& out,
                      const Describe& d, cudaStream_t st) {
   const int sms = sm_count();
-  k_describe_new<<<sms * kNewMinBlocks, kNewWarps * 32, 0, st>>>(g, b, s, out, d);
-  k_describe_carried<<<sms * 8, kCarriedThreads, 0, st>>>(g, tb, b, s, out, d);
+  pdl_launch(k_describe_new, dim3(sms * kNewMinBlocks), dim3(kNewWarps * 32), 0, st, g, b, s, out, d);
+  pdl_launch(k_describe_carried, dim3(sms * 8), dim3(kCarriedThreads), 0, st, g, tb, b, s, out, d);
 }
 
 void launch_group_describe(const StreamDev* devs, const TickHeader* hdr, const TickItem* items, cudaStream_t st) {

@@ -30,6 +30,7 @@
 // Bins are not consulted beyond B: assembly takes each pixel from the frame
 // its bin points to, so the kernel only has to be right on the tiles it runs.
 #include <algorithm>
+#include <type_traits>
 
 #include "fkd_internal.cuh"
 
@@ -506,6 +507,8 @@ __device__ __forceinline__ int sc_of(int o) { return (o / IN_W - 3) * SC_P + (o 
 
 template <class Src, int TH>
 __global__ void __launch_bounds__(kDetMaxThreads, MIN_BLOCKS) k_detect(Src src) {
+  pdl_wait();
+  pdl_trigger();
   using Sh = Shape<TH>;
   constexpr int SC_H = Sh::SC_H, IN_BYTES = Sh::IN_BYTES, SC_BYTES = Sh::SC_BYTES, DET_WORDS = Sh::DET_WORDS;
   extern __shared__ __align__(16) uint8_t smem[];
@@ -816,6 +819,8 @@ __device__ __forceinline__ bool fires(const LayerView& L, int x, int y, int v) {
 constexpr int kScaleWarps = 8;
 template <class Src>
 __global__ void __launch_bounds__(kScaleWarps * 32) k_scale_nms(Src src) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t wsm[kScaleWarps][32], pre[kScaleWarps][32], dom[kScaleWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t n_items = src.count();
@@ -886,7 +891,7 @@ __global__ void __launch_bounds__(kScaleWarps * 32) k_scale_nms(Src src) {
 
 void launch_scale_nms(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                       const Params& p, cudaStream_t st) {
-  k_scale_nms<SingleSrc><<<sm_count() * 8, kScaleWarps * 32, 0, st>>>(SingleSrc{g, b, s, tb, p});
+  pdl_launch(k_scale_nms<SingleSrc>, dim3(sm_count() * 8), dim3(kScaleWarps * 32), 0, st, SingleSrc{g, b, s, tb, p});
 }
 
 void launch_group_scale_nms(const StreamDev* devs, const TickItem* items, const uint32_t* work,
@@ -927,12 +932,21 @@ int sm_count() {
   return sms > 0 ? sms : 1;
 }
 
+// Batches launch with programmatic dependence (the kernel before is on the
+// same stream); group ticks, replayed from captured graphs, plainly.
+template <class Src>
+constexpr bool kPdl = std::is_same<Src, SingleSrc>::value;
+
 template <class Src>
 void launch_shape(const Src& src, const DetLaunch& dl, cudaStream_t st) {
   switch (dl.shape) {
 #define FKD_DET_CASE(i)                                                                         \
   case i:                                                                                       \
-    k_detect<Src, kDetTH[i]><<<dl.grid, dl.warps * 32, dl.warps * Shape<kDetTH[i]>::WARP_SMEM, st>>>(src); \
+    if constexpr (kPdl<Src>)                                                                    \
+      pdl_launch(k_detect<Src, kDetTH[i]>, dim3(dl.grid), dim3(dl.warps * 32),                  \
+                 (size_t)dl.warps * Shape<kDetTH[i]>::WARP_SMEM, st, src);                      \
+    else                                                                                        \
+      k_detect<Src, kDetTH[i]><<<dl.grid, dl.warps * 32, dl.warps * Shape<kDetTH[i]>::WARP_SMEM, st>>>(src); \
     break;
     FKD_DET_CASE(0)
     FKD_DET_CASE(1)

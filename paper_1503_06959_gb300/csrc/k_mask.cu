@@ -57,6 +57,8 @@ __device__ __forceinline__ unsigned long long layer_change_warp(const BinRect& b
 // a shared bin whenever the bin changes.
 constexpr int kLayerSumBins = kMaxBins;
 __global__ void __launch_bounds__(kMaskThreads) k_layer_sums(Geometry g, Tables tb, Batch b, Scratch s) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ unsigned long long bins[kLayerSumBins];
   const int k = blockIdx.x;
   const LayerGeom& lg = g.layer[g.mask_layer];
@@ -105,6 +107,8 @@ __global__ void __launch_bounds__(kMaskThreads) k_layer_sums(Geometry g, Tables 
 //   s.mask and only the source frames are computed.
 __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Batch b, Scratch s,
                                                        Params p, State st, int reset_base_slot, int masks_given) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ int wmax[kMaskThreads / 32];
   const int bin = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool layer_sums = p.mask_mode == FKD_MASK_ID && g.mask_layer > 0;
@@ -171,6 +175,8 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask(Geometry g, Tables tb, Ba
 // is active when any bin its pixels map to is active. Active items are
 // compacted with a warp ballot, a popcount and one atomic per warp.
 __global__ void k_worklist(Geometry g, Tables tb, Batch b, Scratch s, int k_lo, int k_hi) {
+  pdl_wait();
+  pdl_trigger();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = (long long)(k_hi - k_lo) * g.n_tiles;
   for (long long q = i; q < (long long)(k_hi - k_lo) * g.n_chunks; q += (long long)gridDim.x * blockDim.x)
@@ -228,6 +234,8 @@ __global__ void k_worklist(Geometry g, Tables tb, Batch b, Scratch s, int k_lo, 
 // kept set's counts at the first span of a batch), and the work list is
 // emptied for the span's active tiles.
 __global__ void k_kb_span(Geometry g, Batch b, Scratch s, Params p, State st, int k_lo, int k_hi, int first) {
+  pdl_wait();
+  pdl_trigger();
   const int bin = blockIdx.x * blockDim.x + threadIdx.x;
   if (bin == 0) *s.work_count = 0;
   if (bin >= g.NB) return;
@@ -245,6 +253,8 @@ __global__ void k_kb_span(Geometry g, Batch b, Scratch s, Params p, State st, in
 // stays active in frame k+1 when its detections in frame k (the sum over its
 // cells) reach T_H; the first frame of a stream is active everywhere.
 __global__ void k_kb_resolve(Geometry g, Tables tb, Batch b, Scratch s, Params p, int k_lo, int k_hi) {
+  pdl_wait();
+  pdl_trigger();
   const int bin = blockIdx.x * blockDim.x + threadIdx.x;
   if (bin >= g.NB) return;
   uint8_t a = s.alive[bin];
@@ -358,13 +368,13 @@ void launch_group_worklist(const StreamDev* devs, const TickHeader* hdr, const T
 void launch_mask(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                  const Params& p, const State& state, cudaStream_t st, int reset_base_slot) {
   if (p.mask_mode == FKD_MASK_ID && g.mask_layer > 0)
-    k_layer_sums<<<b.T, kMaskThreads, 0, st>>>(g, tb, b, s);
-  k_mask<<<g.NB, kMaskThreads, 0, st>>>(g, tb, b, s, p, state, reset_base_slot, 0);
+    pdl_launch(k_layer_sums, dim3(b.T), dim3(kMaskThreads), 0, st, g, tb, b, s);
+  pdl_launch(k_mask, dim3(g.NB), dim3(kMaskThreads), 0, st, g, tb, b, s, p, state, reset_base_slot, 0);
 }
 
 void launch_source_frames(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                           const Params& p, const State& state, cudaStream_t st, int reset_base_slot) {
-  k_mask<<<g.NB, kMaskThreads, 0, st>>>(g, tb, b, s, p, state, reset_base_slot, 1);
+  pdl_launch(k_mask, dim3(g.NB), dim3(kMaskThreads), 0, st, g, tb, b, s, p, state, reset_base_slot, 1);
 }
 
 void launch_worklist(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
@@ -373,17 +383,17 @@ void launch_worklist(const Geometry& g, const Tables& tb, const Batch& b, const 
   const int threads = 256;
   const long long total = (long long)(k_hi - k_lo) * g.n_tiles;
   const int blocks = (int)std::max<long long>(1, (total + threads - 1) / threads);
-  k_worklist<<<blocks, threads, 0, st>>>(g, tb, b, s, k_lo, k_hi);
+  pdl_launch(k_worklist, dim3(blocks), dim3(threads), 0, st, g, tb, b, s, k_lo, k_hi);
 }
 
 void launch_kb_span(const Geometry& g, const Batch& b, const Scratch& s, const Params& p, const State& state,
                     int k_lo, int k_hi, int first, cudaStream_t st) {
-  k_kb_span<<<(g.NB + 255) / 256, 256, 0, st>>>(g, b, s, p, state, k_lo, k_hi, first);
+  pdl_launch(k_kb_span, dim3((g.NB + 255) / 256), dim3(256), 0, st, g, b, s, p, state, k_lo, k_hi, first);
 }
 
 void launch_kb_resolve(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s, const Params& p,
                        int k_lo, int k_hi, cudaStream_t st) {
-  k_kb_resolve<<<(g.NB + 255) / 256, 256, 0, st>>>(g, tb, b, s, p, k_lo, k_hi);
+  pdl_launch(k_kb_resolve, dim3((g.NB + 255) / 256), dim3(256), 0, st, g, tb, b, s, p, k_lo, k_hi);
 }
 
 }  // namespace fkd

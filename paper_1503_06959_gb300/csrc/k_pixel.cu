@@ -38,6 +38,8 @@ __device__ __forceinline__ uint32_t gather_bits(uint32_t g) {
 }
 
 __global__ void __launch_bounds__(256) k_pixel_mask(Geometry g, Batch b, Scratch s, Params p) {
+  pdl_wait();
+  pdl_trigger();
   const long long total = (long long)b.T * g.bit_words;
   const uint32_t T1 = (uint32_t)p.T_I + 1u;
   const bool none = T1 > 255u;  // |d| <= 255 never exceeds T_I >= 255
@@ -105,6 +107,8 @@ __global__ void __launch_bounds__(256) k_pixel_mask(Geometry g, Batch b, Scratch
 constexpr int kMergeWarps = 8;
 
 __global__ void __launch_bounds__(kMergeWarps * 32) k_merge_pixel(Geometry g, Batch b, Scratch s, State st) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long j = blockIdx.x * (long long)kMergeWarps + warp;
   if (j >= g.bit_words) return;  // whole warps leave together
@@ -153,13 +157,13 @@ void launch_pixel_mask(const Geometry& g, const Batch& b, const Scratch& s, cons
                        cudaStream_t st) {
   const long long total = (long long)b.T * g.bit_words;
   const int blocks = (int)std::min<long long>((total + 255) / 256, (long long)sm_count() * 16);
-  k_pixel_mask<<<std::max(blocks, 1), 256, 0, st>>>(g, b, s, p);
+  pdl_launch(k_pixel_mask, dim3(std::max(blocks, 1)), dim3(256), 0, st, g, b, s, p);
 }
 
 void launch_count_pixel(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                         const State& state, cudaStream_t st) {
   const int blocks = (int)((g.bit_words + kMergeWarps - 1) / kMergeWarps);
-  k_merge_pixel<<<std::max(blocks, 1), kMergeWarps * 32, 0, st>>>(g, b, s, state);
+  pdl_launch(k_merge_pixel, dim3(std::max(blocks, 1)), dim3(kMergeWarps * 32), 0, st, g, b, s, state);
   launch_count(g, tb, b, s, state, st);  // counts the merged words (and fills the offsets)
 }
 

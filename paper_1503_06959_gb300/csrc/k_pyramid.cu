@@ -482,6 +482,8 @@ template <int O, int INTRA>
 __global__ void __launch_bounds__(kPyrThreads, 8) k_pyramid(Geometry g, Tables tb, Batch b, Scratch s,
                                                          Params p, const __grid_constant__ CUtensorMap c0map,
                                                          int use_map) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(128) uint8_t smem_raw[];
   // the launch adds 128 bytes, so the tiles can start on a 128-byte boundary
   uint8_t* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
@@ -559,7 +561,7 @@ void launch_t(const Geometry& g, const Tables& tb, const Batch& b, const Scratch
   const int smem = pyr_smem(p.mask_mode == FKD_MASK_ID && g.mask_layer == 0);
   CUtensorMap map{};
   const int use_map = encode_c0_map(&map, g, b) ? 1 : 0;
-  k_pyramid<O, INTRA><<<grid, kPyrThreads, smem + 128, st>>>(g, tb, b, s, p, map, use_map);
+  pdl_launch(k_pyramid<O, INTRA>, grid, dim3(kPyrThreads), smem + 128, st, g, tb, b, s, p, map, use_map);
 }
 
 template <int O, int INTRA>
