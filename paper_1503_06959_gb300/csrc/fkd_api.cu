@@ -448,13 +448,11 @@ int allocate_state(fkd_stream* s) {
       (rc = s->alloc(&sc.chunk_counts, (size_t)(T * std::max(g.n_chunks, 1)))) ||
       (rc = s->alloc(&sc.alive, (size_t)g.NB)) ||
       (rc = s->alloc(&sc.merged, (size_t)(T * std::max(g.bit_words, 1LL)))) ||
-      (rc = s->alloc(&sc.bases, (size_t)(T + 1))) || (rc = s->alloc(&sc.done, 1)) ||
       (rc = s->alloc(&sc.frame_totals, (size_t)T)) || (rc = s->alloc(&sc.out_base, 2)) ||
       (rc = s->alloc(&sc.overflow, 1)) || (rc = s->alloc(&sc.tile_stats, 2)) ||
       (rc = s->alloc(&sc.ml_prev, (size_t)g.layer[g.mask_layer].pitch * std::max(g.layer[g.mask_layer].h, 1))))
     return rc;
   CK(cudaMemset(sc.tile_stats, 0, 16));
-  CK(cudaMemset(sc.done, 0, 4));
   sc.pmask = nullptr;
   sc.pyr_last = nullptr;
   sc.dcnt = nullptr;
@@ -547,8 +545,8 @@ int run_batch(fkd_stream* s, const uint8_t* frames, int pitch, long long stride,
     if (pr.nms_scale) launch_scale_nms(s->g, tb, b, s->s, pr, s->st);
   }
   mark(4);
-  if (s->s.pmask) launch_count_pixel(s->g, tb, b, s->s, stt, s->st);  // its last CTA fills bases
-  else launch_count(s->g, tb, b, s->s, stt, s->st);                   // its last CTA fills s->s.bases
+  if (s->s.pmask) launch_count_pixel(s->g, tb, b, s->s, stt, s->st);
+  else launch_count(s->g, tb, b, s->s, stt, s->st);
   mark(5);
   launch_emit(s->g, tb, b, s->s, stt, o, s->st);
   mark(6);
@@ -1258,7 +1256,6 @@ StreamDev make_dev(const fkd_stream* s, const GroupStream& gs) {
   d.tb = Tables{s->colblk, s->rowblk, s->xstart, s->npix, s->tiles, s->chunks, s->wbins, s->wmask, s->rowchunk,
                 s->rowcell, s->bincell_off, s->bincell};
   d.s = s->s;
-  d.s.bases = nullptr;  // group ticks (one frame) compute their offsets in place
   d.s.dcnt = nullptr;   // detection counts serve keypoint binning in spans of a batch only
   d.p = Params{s->p.T_I, s->p.T_H, s->p.t, s->p.mask_mode, s->p.nms_scale};
   for (int i = 0; i < 2; ++i) {

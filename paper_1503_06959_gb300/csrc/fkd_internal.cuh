@@ -245,8 +245,6 @@ struct Scratch {
                                    //   each cell (null for the other mask modes)
   uint8_t* alive;                  // [NB]: keypoint binning in spans, bins active at the next frame
   uint32_t* merged;                // [T_max][bit_words]: D_n bitmap of every frame of the batch
-  uint32_t* bases;                 // [T_max + 1]: records of the batch before each frame, then the total
-  uint32_t* done;                  // [1]: chunks counted (last-CTA scan)
   uint32_t* frame_totals;          // [T_max]
   unsigned long long* out_base;    // [2]: running output offset (ping-pong)
   int* overflow;                   // [1]: bit 0 records dropped past a capacity, bit 1 a tile copy that did not land

@@ -10,8 +10,9 @@
 // its layer and each row's bin row up front.
 //   k_count: merge each word from its sources, store it, and sum the
 //            popcounts per chunk and per frame;
-//   k_emit:  turn chunk counts and frame totals into output offsets, scan the
-//            chunk's stored words, and write one record per set bit, in order.
+//   k_emit:  sum the totals of the frames before and the counts of the
+//            chunks before into the chunk's output offset, scan the chunk's
+//            stored words, and write one record per set bit, in order.
 // The last frame of the batch also becomes the new kept set (bitmap, scores,
 // keypoints per bin).
 #include "fkd_internal.cuh"
@@ -65,13 +66,11 @@ __device__ __forceinline__ uint32_t merge_word(const Geometry& g, const Tables& 
 }
 
 // Merge and count one chunk of frame k: the CTA adds its popcount to the
-// chunk's and the frame's counters (zeroed by the active-tile kernel). With
-// s.bases, the CTA that finishes last of `total_ctas` also turns the T frame
-// totals into record offsets. Ends with a barrier.
+// chunk's and the frame's counters (zeroed by the active-tile kernel). Ends
+// with a barrier.
 __device__ __forceinline__ void count_chunk(const Geometry& g, const Tables& tb, const Scratch& s,
-                                            const State& st, int k, int chunk, int T, int total_ctas) {
+                                            const State& st, int k, int chunk) {
   __shared__ uint32_t red[kAsmThreads / 32];
-  __shared__ int last_cta;
   const AsmChunk ch = tb.chunks[chunk];
   const LayerGeom& lg = g.layer[ch.layer];
   const int wpr = lg.wpr;
@@ -110,43 +109,12 @@ __device__ __forceinline__ void count_chunk(const Geometry& g, const Tables& tb,
       cnt += __popc(word);
     }
   }
-  const int lane = threadIdx.x & 31;
   cnt = block_sum(cnt, red);
-  if (threadIdx.x == 0) {
-    if (cnt) {
-      atomicAdd(&s.chunk_counts[(long long)k * g.n_chunks + chunk], cnt);
-      atomicAdd(&s.frame_totals[k], cnt);
-    }
-    bool last = false;
-    if (s.bases) {
-      __threadfence();
-      last = atomicAdd(s.done, 1u) == (unsigned)(total_ctas - 1);
-    }
-    last_cta = last;
+  if (threadIdx.x == 0 && cnt) {
+    atomicAdd(&s.chunk_counts[(long long)k * g.n_chunks + chunk], cnt);
+    atomicAdd(&s.frame_totals[k], cnt);
   }
-  __syncthreads();
-  if (last_cta && threadIdx.x < 32) {
-    // exclusive scan of the frame totals, 32 at a time
-    __threadfence();
-    uint32_t carry = 0;
-    for (int e0 = 0; e0 < T; e0 += 32) {
-      const int e = e0 + lane;
-      const uint32_t c = e < T ? __ldcg(&s.frame_totals[e]) : 0u;
-      uint32_t incl = c;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += v;
-      }
-      if (e < T) s.bases[e] = carry + incl - c;
-      carry += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (lane == 0) {
-      s.bases[T] = carry;
-      *s.done = 0u;
-    }
-  }
-  __syncthreads();  // red and last_cta are reused by the next chunk of this CTA
+  __syncthreads();  // red is reused by the next chunk of this CTA
 }
 
 __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb, const Scratch& s,
@@ -188,26 +156,28 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
     for (int i = threadIdx.x; i < nsrc; i += kAsmThreads) srcs[i] = src_k[ch.rb0 * g.N_c + i];
   __syncthreads();
 
-  // offsets: base of this call + earlier frames + earlier chunks of this frame
+  // offsets: base of this call + earlier frames + earlier chunks of this
+  // frame, both sums in one block reduction
   uint32_t frame_base, chunk_base;
-  if (s.bases) {
-    // warp 0 sums the earlier chunks of this frame (few) and shares it
-    if (threadIdx.x < 32) {
-      uint32_t part = 0;
-      for (int q = threadIdx.x; q < chunk; q += 32) part += s.chunk_counts[(long long)k * g.n_chunks + q];
-      part = __reduce_add_sync(0xffffffffu, part);
-      if (threadIdx.x == 0) red[0] = part;
+  {
+    uint32_t pf = 0, pc = 0;
+    for (int q = threadIdx.x; q < k; q += kAsmThreads) pf += s.frame_totals[q];
+    for (int q = threadIdx.x; q < chunk; q += kAsmThreads) pc += s.chunk_counts[(long long)k * g.n_chunks + q];
+    pf = __reduce_add_sync(0xffffffffu, pf);
+    pc = __reduce_add_sync(0xffffffffu, pc);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+      red[wid] = pf;
+      wsum[wid] = pc;
     }
     __syncthreads();
-    frame_base = s.bases[k];
-    chunk_base = red[0];
-  } else {
-    uint32_t part = 0;
-    for (int q = threadIdx.x; q < k; q += kAsmThreads) part += s.frame_totals[q];
-    frame_base = block_sum(part, red);
-    part = 0;
-    for (int q = threadIdx.x; q < chunk; q += kAsmThreads) part += s.chunk_counts[(long long)k * g.n_chunks + q];
-    chunk_base = block_sum(part, red);
+    frame_base = chunk_base = 0;
+#pragma unroll
+    for (int q = 0; q < kAsmThreads / 32; ++q) {
+      frame_base += red[q];
+      chunk_base += wsum[q];
+    }
+    __syncthreads();  // wsum is reused by the scan below
   }
   const unsigned long long call_base = s.out_base[out.base_slot];
   if (chunk == 0 && threadIdx.x == 0) {
@@ -415,10 +385,10 @@ __device__ __forceinline__ void emit_records(const Geometry& g, const Tables& tb
   if (run_n && FKD_IDX(kChkAsmBins, run_bin, g.NB)) atomicAdd(&st.cnt_out[run_bin], run_n);
 }
 
-__global__ void __launch_bounds__(kAsmThreads) k_count(Geometry g, Tables tb, Scratch s, State st, int T) {
+__global__ void __launch_bounds__(kAsmThreads) k_count(Geometry g, Tables tb, Scratch s, State st) {
   pdl_wait();
   pdl_trigger();
-  count_chunk(g, tb, s, st, blockIdx.y, blockIdx.x, T, gridDim.x * gridDim.y);
+  count_chunk(g, tb, s, st, blockIdx.y, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kAsmThreads) k_emit(Geometry g, Tables tb, Batch b, Scratch s,
@@ -447,7 +417,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_group_count(const StreamDev* de
     const int i = find_item(n, j, [&](int q) { return items[q].chunk_base; });
     const TickItem it = items[i];
     const StreamDev& d = devs[it.sid];
-    count_chunk(d.g, d.tb, d.s, state_of(d, it.state_cur), 0, j - it.chunk_base, 1, 0);
+    count_chunk(d.g, d.tb, d.s, state_of(d, it.state_cur), 0, j - it.chunk_base);
   }
 }
 
@@ -482,7 +452,7 @@ void launch_group_emit(const StreamDev* devs, const TickHeader* hdr, const TickI
 
 void launch_count(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,
                   const State& state, cudaStream_t st) {
-  pdl_launch(k_count, dim3(g.n_chunks, b.T), dim3(kAsmThreads), 0, st, g, tb, s, state, b.T);
+  pdl_launch(k_count, dim3(g.n_chunks, b.T), dim3(kAsmThreads), 0, st, g, tb, s, state);
 }
 
 void launch_emit(const Geometry& g, const Tables& tb, const Batch& b, const Scratch& s,

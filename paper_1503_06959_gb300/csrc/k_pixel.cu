@@ -164,7 +164,7 @@ void launch_count_pixel(const Geometry& g, const Tables& tb, const Batch& b, con
                         const State& state, cudaStream_t st) {
   const int blocks = (int)((g.bit_words + kMergeWarps - 1) / kMergeWarps);
   pdl_launch(k_merge_pixel, dim3(std::max(blocks, 1)), dim3(kMergeWarps * 32), 0, st, g, b, s, state);
-  launch_count(g, tb, b, s, state, st);  // counts the merged words (and fills the offsets)
+  launch_count(g, tb, b, s, state, st);  // counts the merged words
 }
 
 }  // namespace fkd
