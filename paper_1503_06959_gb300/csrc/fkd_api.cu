@@ -439,7 +439,7 @@ int allocate_state(fkd_stream* s) {
   Scratch& sc = s->s;
   int rc;
   if ((rc = s->alloc(&sc.pyr, (size_t)(T * g.pyr_bytes))) ||
-      (rc = s->alloc(&sc.bsum, (size_t)(T * g.NB))) || (rc = s->alloc(&sc.mask, (size_t)(T * g.NB))) ||
+      (rc = s->alloc(&sc.bsum, (size_t)(T * g.NB))) || (rc = s->alloc(&sc.mask, (size_t)(T * g.NB + 4))) ||
       (rc = s->alloc(&sc.src, (size_t)(T * g.NB))) ||
       (rc = s->alloc(&sc.work, (size_t)(T * std::max(s->n_tiles_max, 1)))) ||
       (rc = s->alloc(&sc.work_count, 1)) ||

@@ -234,7 +234,7 @@ struct Scratch {
   uint8_t* pyr;                    // [T_max][pyr_bytes]
   unsigned long long* bsum;        // [NB][bsum_stride]: bin-major, frame k at bin*bsum_stride + k; kept zero
   int bsum_stride;                 // T_max (1 in groups)
-  uint8_t* mask;                   // [T_max][NB]
+  uint8_t* mask;                   // [T_max][NB], then 4 bytes of padding
   int* src;                        // [T_max][NB]: batch frame whose detections the bin shows, -1 = kept set
   uint32_t* work;                  // [T_max * n_tiles] active (frame, tile) items
   uint32_t* work_count;            // [1]

@@ -147,6 +147,19 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
     const int j = threadIdx.x + jj * kAsmThreads;
     v[jj] = j < nwords ? merged[j] : 0u;
   }
+  // offsets: base of this call + earlier frames + earlier chunks of this
+  // frame (partial sums per warp here, summed after the barrier below)
+  {
+    uint32_t pf = 0, pc = 0;
+    for (int q = threadIdx.x; q < k; q += kAsmThreads) pf += s.frame_totals[q];
+    for (int q = threadIdx.x; q < chunk; q += kAsmThreads) pc += s.chunk_counts[(long long)k * g.n_chunks + q];
+    pf = __reduce_add_sync(0xffffffffu, pf);
+    pc = __reduce_add_sync(0xffffffffu, pc);
+    if ((threadIdx.x & 31) == 0) {
+      red[threadIdx.x >> 5] = pf;
+      wsum[threadIdx.x >> 5] = pc;
+    }
+  }
   // the source frames of the chunk's bin rows, in shared memory when they fit
   __shared__ int srcs[kSrcCache];
   const int* src_k = s.src + (long long)k * g.NB;
@@ -155,29 +168,11 @@ __device__ __forceinline__ void emit_chunk(const Geometry& g, const Tables& tb, 
   if (src_local)
     for (int i = threadIdx.x; i < nsrc; i += kAsmThreads) srcs[i] = src_k[ch.rb0 * g.N_c + i];
   __syncthreads();
-
-  // offsets: base of this call + earlier frames + earlier chunks of this
-  // frame, both sums in one block reduction
-  uint32_t frame_base, chunk_base;
-  {
-    uint32_t pf = 0, pc = 0;
-    for (int q = threadIdx.x; q < k; q += kAsmThreads) pf += s.frame_totals[q];
-    for (int q = threadIdx.x; q < chunk; q += kAsmThreads) pc += s.chunk_counts[(long long)k * g.n_chunks + q];
-    pf = __reduce_add_sync(0xffffffffu, pf);
-    pc = __reduce_add_sync(0xffffffffu, pc);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-      red[wid] = pf;
-      wsum[wid] = pc;
-    }
-    __syncthreads();
-    frame_base = chunk_base = 0;
+  uint32_t frame_base = 0, chunk_base = 0;
 #pragma unroll
-    for (int q = 0; q < kAsmThreads / 32; ++q) {
-      frame_base += red[q];
-      chunk_base += wsum[q];
-    }
-    __syncthreads();  // wsum is reused by the scan below
+  for (int q = 0; q < kAsmThreads / 32; ++q) {
+    frame_base += red[q];
+    chunk_base += wsum[q];  // (wsum is next written after the barrier below)
   }
   const unsigned long long call_base = s.out_base[out.base_slot];
   if (chunk == 0 && threadIdx.x == 0) {

@@ -200,10 +200,21 @@ __global__ void k_worklist(Geometry g, Tables tb, Batch b, Scratch s, int k_lo, 
         for (int wx = t.tx * wpt; wx < w1; ++wx)
           if (pm[(long long)y * lg.wpr + wx]) { act = true; break; }
     } else {
-      const uint8_t* m = s.mask + (long long)k * g.NB;
-      for (int r = t.rb0; r <= t.rb1 && !act; ++r)
-        for (int c = t.cb0; c <= t.cb1; ++c)
-          if (m[r * g.N_c + c]) { act = true; break; }
+      // the tile's bins of each bin row, four mask bytes per load (the mask
+      // buffer is padded so that the last word stays inside it)
+      const long long m0 = (long long)k * g.NB;
+      for (int r = t.rb0; r <= t.rb1 && !act; ++r) {
+        const long long lo = m0 + r * g.N_c + t.cb0, hi = m0 + r * g.N_c + t.cb1;  // bytes lo..hi
+        for (long long w = lo >> 2; w <= (hi >> 2); ++w) {
+          uint32_t v = reinterpret_cast<const uint32_t*>(s.mask)[w];
+          if (w == (lo >> 2)) v &= 0xffffffffu << (8 * (lo & 3));
+          if (w == (hi >> 2)) v &= 0xffffffffu >> (8 * (3 - (hi & 3)));
+          if (v) {
+            act = true;
+            break;
+          }
+        }
+      }
     }
     if (act) area = t.area;
   }
