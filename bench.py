@@ -13,7 +13,9 @@ end-to-end figure through the C ABI with pinned host buffers (host->device
 copies of the frames and device->host copies of the keypoints inside the
 timed region), the roofline of the dominant kernel from CUDA events recorded
 around each kernel on the launching stream (in further steps after the timed
-ones, so that the timed steps run plain launches), the SM clocks sampled
+ones, so that the timed steps run plain launches) -- for the detection
+kernel its integer-ALU pipe from the committed ncu counters, with the HBM
+view on active bytes nested as "hbm" -- the SM clocks sampled
 during the timed region, variants (mask on c_0, per-pixel masks, scale-space
 suppression, detection + masked description), and the CPU oracle timed on a
 bounded sample on this host.
@@ -26,7 +28,7 @@ detection kernel's roofline on active bytes and their own clock records
 (--no-groups leaves them out).
 
 --config 3|4|5: one of those alone, or the serving loop (256 streams at 30
-fps for 20 s, 600 frames each) with its clocks. --sweep: the T_I / T_H
+fps, 600 frames each, then a sweep of the rate) with its clocks. --sweep: the T_I / T_H
 trade-off against full-frame detection. --describe masked|full|both:
 detection + description alone on the 640x480 clip.
 --impl reference times the CPU oracle (single-threaded C, the correctness
@@ -1139,26 +1141,30 @@ def main():
         bytes_desc = "per frame: keypoint bitmap words read and written"
     achieved = bytes_per_launch / dur_s / 1e9
     counters = profile_counters(dom, shape_masked) if T == cfg.frames else None
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "peak_source": f"{pk_kind} hbm_gbs",
-            "traffic": counters.get("traffic_bytes_per_launch") if counters else None,
-            "bytes_per_launch": bytes_per_launch, "bytes": bytes_desc, "launch_ms": dur_s * 1e3,
-            "processed_tile_pixels_per_launch": prof["tile_pixels"] / launches if dom == "detect" else None}
+    # the HBM view: algorithmic bytes per launch over the launch time
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+           "frac": achieved / pk["hbm_gbs"], "peak_source": f"{pk_kind} hbm_gbs",
+           "bytes_per_launch": bytes_per_launch, "bytes": bytes_desc}
+    roof = dict(kernel=dom, **hbm)
     alu_inst = counters.get("alu_warp_inst_per_launch") if counters else None
     alu_rate = counters.get("alu_peak_warp_inst_per_sm_cycle") if counters else None
     if alu_inst and alu_rate and clk and clk.get("sm_mhz"):
-        # the integer ALU pipe: warp instructions the kernel issued to it
-        # (ncu smsp__inst_executed_pipe_alu.sum) per launch duration, against
-        # the pipe's issue rate per SM and cycle (ncu
+        # the integer ALU pipe, the detection kernel's bound: warp instructions
+        # the kernel issued to it (ncu smsp__inst_executed_pipe_alu.sum) per
+        # launch duration, against the pipe's issue rate per SM and cycle (ncu
         # sm__inst_executed_pipe_alu.avg.peak_sustained) x SMs x the median SM
-        # clock sampled during the timed steps
+        # clock sampled during the timed steps; the HBM view beside it
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         peak_alu = n_sm * alu_rate * clk["sm_mhz"] * 1e6 / 1e9
         ach_alu = alu_inst / dur_s / 1e9
-        roof["alu"] = {"achieved": ach_alu, "peak": peak_alu, "unit": "G warp-instructions/s (integer ALU pipe)",
-                       "frac": ach_alu / peak_alu, "alu_warp_inst_per_launch": alu_inst,
-                       "peak_source": f"{n_sm} SMs x {alu_rate} ALU warp-instructions/cycle/SM (ncu peak_sustained) "
-                                      f"x {clk['sm_mhz']:.0f} MHz (median sampled)"}
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach_alu, "peak": peak_alu,
+                "unit": "G warp-instructions/s (integer ALU pipe)", "frac": ach_alu / peak_alu,
+                "peak_source": f"{n_sm} SMs x {alu_rate} ALU warp-instructions/cycle/SM (ncu peak_sustained) "
+                               f"x {clk['sm_mhz']:.0f} MHz (median sampled)",
+                "alu_warp_inst_per_launch": alu_inst, "hbm": hbm}
+    roof.update({"traffic": counters.get("traffic_bytes_per_launch") if counters else None,
+                 "launch_ms": dur_s * 1e3,
+                 "processed_tile_pixels_per_launch": prof["tile_pixels"] / launches if dom == "detect" else None})
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:

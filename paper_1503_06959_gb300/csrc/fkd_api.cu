@@ -105,7 +105,7 @@ struct fkd_stream {
   Geometry g{};
   cudaStream_t st = nullptr;
   cudaStream_t copy_st = nullptr;  // host-frame uploads, overlapped with the previous part's kernels
-  static constexpr int kParts = 2;
+  static constexpr int kParts = 3;
   cudaEvent_t part_done[kParts] = {};  // upload of part i finished
   cudaEvent_t staging_free = nullptr;  // earlier work on the stream no longer needs the staging buffer
   std::vector<std::pair<void*, size_t>> allocs;  // device allocations and their sizes

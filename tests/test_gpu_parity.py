@@ -369,6 +369,43 @@ def test_host_batch_layouts(clip2, mode, T):
             assert_same_kp(kp, exp_kp[k], f"strided frame {k}")
 
 
+@pytest.mark.parametrize("mode", ["id", "kb"])
+def test_host_batch_into_pinned_output(clip2, mode):
+    """Host frames with caller-owned pinned outputs: a batch of 32 or more
+    back-to-back frames is uploaded in parts, each part its own batch whose
+    kernels start while the later parts are still arriving. Records, offsets
+    and masks must equal the oracle's; a cap below the total keeps the
+    records up to it and reports the overflow."""
+    torch = pytest.importorskip("torch")
+    cfg, frames = clip2
+    T = len(frames)
+    g, o = both(params(cfg, mask_layer=-1), mode)
+    exp_kp, exp_m = run_oracle(frames, **o)
+    s = fkd.Stream(cfg.W, cfg.H, T_max=T, **g)
+    total = sum(len(k) for k in exp_kp)
+    out = torch.zeros(total + 1000, dtype=torch.int64).pin_memory().numpy().view(fkd.KEYPOINT_DTYPE)
+    off = torch.zeros(T + 1, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+    msk = torch.zeros((T, cfg.N_r, cfg.N_c), dtype=torch.uint8).pin_memory().numpy()
+    for rep in range(2):  # the second call reuses the staging and the parts
+        s.reset()
+        s.push_frames(frames, out=out, offsets=off, masks=msk)
+        assert off[T] == total
+        for k, kp in enumerate(fkd.split_frames(out[:off[T]], off)):
+            assert_same_kp(kp, exp_kp[k], f"call {rep} frame {k}")
+            np.testing.assert_array_equal(msk[k], exp_m[k], err_msg=f"mask of frame {k}")
+    # a capacity below the total: the records up to it, then FKD_E_CAPACITY
+    cap = total // 2
+    out[:] = 0
+    s.reset()
+    with pytest.raises(fkd.FkdError):
+        s.push_frames(frames, out=out, offsets=off, masks=msk, cap=cap)
+    flat = np.concatenate(exp_kp)
+    got = out[:cap]
+    for field in ("layer", "y", "x", "score", "flags"):
+        np.testing.assert_array_equal(got[field], flat[:cap][field], err_msg=f"capped records: {field}")
+    assert not out[cap:].view(np.int64).any(), "nothing past the capacity"
+
+
 @pytest.mark.parametrize("T_H,nms_scale", [(0, 0), (1, 0), (2, 0), (4, 0), (1, 1)])
 def test_keypoint_binning_spans(clip2, T_H, nms_scale):
     """Keypoint binning (Eqs. 3-4) in batches: spans of 16 frames are detected
