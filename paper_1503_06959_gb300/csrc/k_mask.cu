@@ -31,21 +31,30 @@ __device__ __forceinline__ BinRect bin_rect(const Geometry& g, const Tables& tb,
 __device__ __forceinline__ unsigned long long layer_change_warp(const BinRect& br, const uint8_t* cur,
                                                                 const uint8_t* prv, int pitch, uint8_t* copy) {
   const int lane = threadIdx.x & 31;
-  const int bw = br.x1 - br.x0, npx = bw * max(0, br.y1 - br.y0);
+  const int bw = br.x1 - br.x0;
+  // lanes over the bin: 32 columns of a row at a time when the bin is at
+  // least 32 wide, else 32 / bw rows of bw lanes (one division per lane)
+  const bool wide = bw >= 32;
+  const int rows_per = wide ? 1 : 32 / max(bw, 1), step_x = wide ? 32 : max(bw, 1);
+  const int lr = wide ? 0 : lane / max(bw, 1), lc = wide ? lane : lane - lr * bw;
   unsigned long long sum = 0;
-  for (int i = lane; i < npx; i += 32) {
-    const long long o = (long long)(br.y0 + i / bw) * pitch + br.x0 + i % bw;
-    const int d = (int)cur[o] - (int)prv[o];
-    sum += (unsigned long long)(d < 0 ? -d : d);
-  }
+  if (lr < rows_per && bw > 0)
+    for (int y = br.y0 + lr; y < br.y1; y += rows_per) {
+      const long long ro = (long long)y * pitch;
+      for (int x = br.x0 + lc; x < br.x1; x += step_x) {
+        const int d = (int)cur[ro + x] - (int)prv[ro + x];
+        sum += (unsigned long long)(d < 0 ? -d : d);
+      }
+    }
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
   if (copy) {
     __syncwarp();
-    for (int i = lane; i < npx; i += 32) {
-      const long long o = (long long)(br.y0 + i / bw) * pitch + br.x0 + i % bw;
-      copy[o] = cur[o];
-    }
+    if (lr < rows_per && bw > 0)
+      for (int y = br.y0 + lr; y < br.y1; y += rows_per) {
+        const long long ro = (long long)y * pitch;
+        for (int x = br.x0 + lc; x < br.x1; x += step_x) copy[ro + x] = cur[ro + x];
+      }
   }
   return sum;
 }
@@ -338,20 +347,41 @@ __global__ void k_group_worklist(const StreamDev* devs, const TickHeader* hdr, c
   for (int j0 = blockIdx.x * blockDim.x; j0 < total; j0 += gridDim.x * blockDim.x) {
     const int j = j0 + threadIdx.x;
     bool act = false;
-    uint32_t entry = 0;
+    uint32_t entry = 0, area = 0;
+    int sid_act = -1;  // item of an active tile, else -1
     if (j < total) {
       const int i = find_item(n, j, [&](int q) { return items[q].tile_base; });
       const TickItem it = items[i];
       const StreamDev& d = devs[it.sid];
       const int tile = j - it.tile_base;
       const DetTile t = d.tb.tiles[tile];
-      for (int r = t.rb0; r <= t.rb1 && !act; ++r)
-        for (int c = t.cb0; c <= t.cb1; ++c)
-          if (d.s.mask[r * d.g.N_c + c]) { act = true; break; }
+      // four mask bytes per load (the mask buffer is padded)
+      for (int r = t.rb0; r <= t.rb1 && !act; ++r) {
+        const int lo = r * d.g.N_c + t.cb0, hi = r * d.g.N_c + t.cb1;
+        for (int w = lo >> 2; w <= (hi >> 2); ++w) {
+          uint32_t v = reinterpret_cast<const uint32_t*>(d.s.mask)[w];
+          if (w == (lo >> 2)) v &= 0xffffffffu << (8 * (lo & 3));
+          if (w == (hi >> 2)) v &= 0xffffffffu >> (8 * (3 - (hi & 3)));
+          if (v) {
+            act = true;
+            break;
+          }
+        }
+      }
       if (act) {
         entry = ((uint32_t)i << 22) | (uint32_t)tile;
-        atomicAdd(&d.s.tile_stats[0], 1ull);
-        atomicAdd(&d.s.tile_stats[1], (unsigned long long)t.area);
+        area = t.area;
+      }
+      sid_act = act ? i : -1;
+    }
+    // tile statistics: one atomic pair per stream and warp
+    const unsigned peers = __match_any_sync(0xffffffffu, sid_act);
+    if (sid_act >= 0) {
+      const unsigned long long sum_area = __reduce_add_sync(peers, area);
+      if ((int)lane == __ffs(peers) - 1) {
+        const StreamDev& d = devs[items[sid_act].sid];
+        atomicAdd(&d.s.tile_stats[0], (unsigned long long)__popc(peers));
+        atomicAdd(&d.s.tile_stats[1], sum_area);
       }
     }
     const unsigned bal = __ballot_sync(0xffffffffu, act);
