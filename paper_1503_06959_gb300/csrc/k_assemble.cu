@@ -405,8 +405,11 @@ __device__ __forceinline__ State state_of(const StreamDev& d, int cur) {
 }
 
 // Group tick: persistent CTAs over the chunks of every participating frame.
-__global__ void __launch_bounds__(kAsmThreads) k_group_count(const StreamDev* devs, const TickHeader* hdr,
-                                                             const TickItem* items) {
+// (6 and 5 resident CTAs per SM, on a grid of 8 CTAs per SM: the CTAs beyond
+// the resident ones start as others finish, which evens out the unequal
+// chunks better than a grid of exactly the resident CTAs)
+__global__ void __launch_bounds__(kAsmThreads, 6) k_group_count(const StreamDev* devs, const TickHeader* hdr,
+                                                                const TickItem* items) {
   const int n = hdr->n_items, total = hdr->total_chunks;
   for (int j = blockIdx.x; j < total; j += gridDim.x) {
     const int i = find_item(n, j, [&](int q) { return items[q].chunk_base; });
@@ -416,8 +419,8 @@ __global__ void __launch_bounds__(kAsmThreads) k_group_count(const StreamDev* de
   }
 }
 
-__global__ void __launch_bounds__(kAsmThreads) k_group_emit(const StreamDev* devs, const TickHeader* hdr,
-                                                            const TickItem* items) {
+__global__ void __launch_bounds__(kAsmThreads, 5) k_group_emit(const StreamDev* devs, const TickHeader* hdr,
+                                                               const TickItem* items) {
   const int n = hdr->n_items, total = hdr->total_chunks;
   for (int j = blockIdx.x; j < total; j += gridDim.x) {
     const int i = find_item(n, j, [&](int q) { return items[q].chunk_base; });
