@@ -294,8 +294,9 @@ __global__ void k_kb_resolve(Geometry g, Tables tb, Batch b, Scratch s, Params p
 
 // Group tick, one frame per stream: the mask and source frame of every bin
 // of every participating stream (src = 0 for active bins, -1 = kept set).
-__global__ void k_group_mask(const StreamDev* devs, const TickHeader* hdr, const TickItem* items,
-                             uint32_t* work_count) {
+// (6 resident CTAs per SM: the per-(stream, bin) load chains are latency-bound)
+__global__ void __launch_bounds__(256, 6) k_group_mask(const StreamDev* devs, const TickHeader* hdr,
+                                                       const TickItem* items, uint32_t* work_count) {
   // one warp per (stream, bin) of the tick
   const int n = hdr->n_items, total = hdr->total_bins;
   const int lane = threadIdx.x & 31;
